@@ -1,0 +1,519 @@
+"""Numeric factorization (oracle; test infrastructure).
+
+Algorithm by algorithm, in the paper's order and notation:
+
+* ``factor_supernode``          Alg. 1 (Section 2.1, Eqs. "schurDiag", "schurOffDiag").
+* ``offdiag_multiply``          Alg. 2 (Section 3.4), with Eq. "lowRankMult" for
+                                descendants stored as V_k U_k^T.
+* ``offdiag_multiply_T``        (L^O_j)^T G.  The paper only says it has "similar
+                                structure" (Section 3.4).  Reading: (L^O_j)^T =
+                                (L^D_j)^{-1} (U^O_j)^T with U^O_j from Eq. "schurOffDiag":
+                                W = A(R_j,C_j)^T G; for each k in D_j:
+                                T = L^O_k(R^O,:)^T gatherRows(G, R_j, R^O_glob);
+                                T = L^O_k(R^D,:) T; W -= scatterRows(T, R^D_glob, C_j);
+                                then W <- diagonalSolve(j, W, transpose=false).
+* ``approximate_offdiag``       Alg. 3 in adaptive form.  The paper fixes ranks by a
+                                heuristic (Section 5.2) but notes adaptive tolerance
+                                as an option; here the blocked adaptive range finder:
+                                16-column passes, each projected twice against the
+                                current basis U (CGS2); stop before appending when
+                                ||Yhat||_F <= tol ||Y_1||_F (Y_1 = first pass), or when
+                                rank reaches min(|C_j|, |R_j|).  makeOrthonormal is a
+                                Householder QR, re-projected and re-orthonormalised
+                                once so the new columns stay orthogonal to U; a pass
+                                that would exceed min(|C_j|, |R_j|) keeps only its
+                                first min(16, remaining) projected columns.
+* ``diagonal_solve``            Alg. 4.  Reading: the printed branches are swapped;
+                                L^{-1} solves G1 first, then G2 -= V_s (U_s^T G1), then
+                                G2; L^{-T} solves G2 first, then G1 -= U_s (V_s^T G2),
+                                then G1.
+* ``diagonal_multiply(_T)``     Alg. 5 and its transpose (Section 4.2).
+* ``factor_diagonal``           Alg. 6.  Readings: the descendant update uses L^O_k
+                                (the printed L^D_k cannot be indexed by R_k), and the
+                                loop over ancestors advances p <- parent(p).
+* ``approximate_diagonal_block`` "nearly identical" to Alg. 3 (Section 4.2), with
+                                tolerance tol_D.
+* ``factor``                    Section 4.2's block order s = 1, 2, ... and the
+                                indefinite restart of Section 5.3 in tolerance form:
+                                tol_D <- tol_D / 1.25 per restart; after
+                                ``max_restarts`` restarts diagonal compression is
+                                switched off (Section 3.2 then guarantees success).
+
+Low-rank descendants keep U_prod = U_k^T U_k literally (Eq. "lowRankMult").
+Random test matrices come from ``oracle.philox.gaussian_block`` with block id
+(j << 12) | s (s = 0 for the off-diagonal block, s = label for diagonal blocks).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import dense
+from .dense import NotPositiveDefinite
+from .ordering import order as nd_order
+from .philox import gaussian_block
+from .scatter import gather_rows, positions, scatter_rows
+from .symbolic import symbolic
+
+
+@dataclasses.dataclass
+class Options:
+    tau_O: int = 256
+    tau_D: int = 256
+    leaf_size: int = 64
+    sample_block: int = 16
+    power_iters: int = 0
+    dof_per_node: int = 1
+    max_restarts: int = 8
+    seed: int = 0
+    diag_compress: bool = True
+
+
+class Analysis:
+    """Ordering + symbolic structure of one matrix."""
+
+    def __init__(self, n, row_ptr, col_idx, val, coords, opts: Options):
+        self.opts = opts
+        self.n = n
+        A = sp.csr_matrix((val, col_idx, row_ptr), shape=(n, n))
+        self.ordering = nd_order(coords, opts.dof_per_node, opts.leaf_size, opts.tau_O, opts.tau_D)
+        p = self.ordering.perm
+        self.A = A
+        self.Ap = sp.csr_matrix(A[p][:, p])
+        self.Ap.sort_indices()
+        self.sym = symbolic(self.Ap, self.ordering.snode_ptr)
+
+    @property
+    def nsuper(self):
+        return self.sym.nsuper
+
+    def cols(self, j):
+        return int(self.sym.snode_ptr[j]), int(self.sym.snode_ptr[j + 1])
+
+    def A_block(self, rows, cols) -> np.ndarray:
+        """Dense A(rows, cols) of the permuted matrix (rows/cols global index arrays)."""
+        return self.Ap[rows][:, cols].toarray()
+
+
+class DiagFactor:
+    """L^D_j: dense, or hierarchical over a BlockTree (Section 4.1)."""
+
+    def __init__(self, tree=None):
+        self.tree = tree
+        self.L = None          # dense case
+        self.leafL = {}        # s -> dense leaf block
+        self.V = {}            # s -> V_s
+        self.U = {}            # s -> U_s
+
+    @property
+    def hierarchical(self):
+        return self.tree is not None
+
+
+class SupernodeFactor:
+    def __init__(self):
+        self.compressed = False
+        self.D: DiagFactor | None = None
+        self.LO = None         # dense L^O_j (uncompressed)
+        self.V = None          # V_j (compressed)
+        self.U = None          # U_j
+        self.Uprod = None      # U_j^T U_j
+
+
+class Factor:
+    def __init__(self, an: Analysis):
+        self.an = an
+        self.sn = [SupernodeFactor() for _ in range(an.nsuper)]
+        self.restarts = 0
+        self.tol = 0.0
+        self.tol_D = 0.0
+        self.diag_compress = False
+
+    # ----------------------------------------------------------- descendant blocks
+    def lo_rows(self, k, pos):
+        """Rows `pos` of L^O_k (uncompressed) or of V_k (compressed)."""
+        s = self.sn[k]
+        return s.LO[pos] if not s.compressed else s.V[pos]
+
+    def lo_pair_product(self, k, pa, pb):
+        """L^O_k(pa,:) L^O_k(pb,:)^T, or V_k(pa,:) U_k^T U_k V_k(pb,:)^T (Eq. lowRankMult)."""
+        s = self.sn[k]
+        if not s.compressed:
+            return s.LO[pa] @ s.LO[pb].T
+        return s.V[pa] @ (s.Uprod @ s.V[pb].T)
+
+    def lo_apply(self, k, pa, pb, G):
+        """L^O_k(pa,:) (L^O_k(pb,:)^T G) with the low-rank form when k is compressed."""
+        s = self.sn[k]
+        if not s.compressed:
+            return s.LO[pa] @ (s.LO[pb].T @ G)
+        T = s.V[pb].T @ G
+        T = s.Uprod @ T
+        return s.V[pa] @ T
+
+    # ----------------------------------------------------------- Alg. 4
+    def diagonal_solve(self, j, G, transpose, s=None):
+        D = self.sn[j].D
+        if not D.hierarchical:
+            return dense.solve_lower_T(D.L, G) if transpose else dense.solve_lower(D.L, G)
+        t = D.tree
+        s = t.root if s is None else s
+        if t.leaf[s]:
+            L = D.leafL[s]
+            return dense.solve_lower_T(L, G) if transpose else dense.solve_lower(L, G)
+        n1 = t.mid[s] - t.lo[s]
+        G1, G2 = G[:n1], G[n1:]
+        s1, s2 = t.left[s], t.right[s]
+        if transpose:
+            G2 = self.diagonal_solve(j, G2, True, s2)
+            G1 = G1 - D.U[s] @ (D.V[s].T @ G2)
+            G1 = self.diagonal_solve(j, G1, True, s1)
+        else:
+            G1 = self.diagonal_solve(j, G1, False, s1)
+            G2 = G2 - D.V[s] @ (D.U[s].T @ G1)
+            G2 = self.diagonal_solve(j, G2, False, s2)
+        return np.vstack([G1, G2])
+
+    # ----------------------------------------------------------- Alg. 2 / transpose
+    def offdiag_multiply(self, j, G):
+        """B = L^O_j G for G in R^{|C_j| x r} (Alg. 2)."""
+        an = self.an
+        c0, c1 = an.cols(j)
+        Rj = an.sym.rows[j]
+        Cj = np.arange(c0, c1)
+        G = self.diagonal_solve(j, G, transpose=True)
+        W = an.A_block(Rj, Cj) @ G
+        for k, pD, pO in an.sym.desc[j]:
+            Rk = an.sym.rows[k]
+            G_sub = gather_rows(G, Cj, Rk[pD])
+            T = self.lo_apply(k, pO, pD, G_sub)
+            W -= scatter_rows(T, Rk[pO], Rj)
+        return W
+
+    def offdiag_multiply_T(self, j, G):
+        """B = (L^O_j)^T G for G in R^{|R_j| x r}."""
+        an = self.an
+        c0, c1 = an.cols(j)
+        Rj = an.sym.rows[j]
+        Cj = np.arange(c0, c1)
+        W = an.A_block(Rj, Cj).T @ G
+        for k, pD, pO in an.sym.desc[j]:
+            Rk = an.sym.rows[k]
+            G_sub = gather_rows(G, Rj, Rk[pO])
+            T = self.lo_apply(k, pD, pO, G_sub)
+            W -= scatter_rows(T, Rk[pD], Cj)
+        return self.diagonal_solve(j, W, transpose=False)
+
+    # ----------------------------------------------------------- adaptive range finder
+    def _range_finder(self, m, c, tol, block_id, mult, mult_T):
+        """Shared body of Alg. 3 and approximateDiagonalBlock: returns (V, U)."""
+        opts = self.an.opts
+        b = opts.sample_block
+        maxr = min(m, c)
+        U = np.zeros((c, 0))
+        y1 = None
+        t = 0
+        while U.shape[1] < maxr:
+            G = gaussian_block(m, b, opts.seed, block_id, t, self.restarts)
+            Y = mult_T(G)
+            for _ in range(opts.power_iters):
+                Y = mult_T(mult(Y))
+            if y1 is None:
+                y1 = np.linalg.norm(Y)
+            Yh = Y - U @ (U.T @ Y)
+            Yh = Yh - U @ (U.T @ Yh)
+            if np.linalg.norm(Yh) <= tol * y1:
+                break
+            Q = dense.householder_q(Yh[:, :min(b, maxr - U.shape[1])])
+            Q = Q - U @ (U.T @ Q)
+            Q = dense.householder_q(Q)
+            U = np.hstack([U, Q])
+            t += 1
+        V = mult(U)
+        return V, U
+
+    def approximate_offdiag(self, j):
+        """Alg. 3 (adaptive): L^O_j ~= V_j U_j^T with orthonormal U_j."""
+        an = self.an
+        c0, c1 = an.cols(j)
+        m = an.sym.rows[j].size
+        V, U = self._range_finder(m, c1 - c0, self.tol, (j << 12) | 0,
+                                  lambda G: self.offdiag_multiply(j, G),
+                                  lambda G: self.offdiag_multiply_T(j, G))
+        s = self.sn[j]
+        s.V, s.U, s.Uprod = V, U, U.T @ U
+
+    # ----------------------------------------------------------- Alg. 5 / transpose
+    def _desc_rows_in(self, j, k, lo, hi):
+        """Positions p in R_k whose row lies in global range [lo, hi) (inside C_j)."""
+        Rk = self.an.sym.rows[k]
+        return np.nonzero((Rk >= lo) & (Rk < hi))[0]
+
+    def _ancestor_blocks(self, j, s):
+        """Blocks p on the path from s to the root with p < s (they precede s)."""
+        t = self.sn[j].D.tree
+        p = t.parent[s]
+        out = []
+        while p:
+            if p < s:
+                out.append(p)
+            p = t.parent[p]
+        return out
+
+    def diagonal_multiply(self, j, s, G):
+        """L^D_{j,s} G for internal block s (Alg. 5); G has |C^D_{j,s}| rows."""
+        an = self.an
+        D = self.sn[j].D
+        t = D.tree
+        c0, _ = an.cols(j)
+        r0, r1 = t.rows(s)
+        q0, q1 = t.cols(s)
+        G = self.diagonal_solve(j, G, True, t.left[s])
+        W = an.A_block(np.arange(c0 + r0, c0 + r1), np.arange(c0 + q0, c0 + q1)) @ G
+        for k, _, _ in an.sym.desc[j]:
+            Rk = an.sym.rows[k]
+            pr = self._desc_rows_in(j, k, c0 + r0, c0 + r1)
+            pc = self._desc_rows_in(j, k, c0 + q0, c0 + q1)
+            if pr.size and pc.size:
+                T = self.lo_apply(k, pr, pc, G[Rk[pc] - (c0 + q0)])
+                W[Rk[pr] - (c0 + r0)] -= T
+        for p in self._ancestor_blocks(j, s):
+            pr0, _ = t.rows(p)
+            Rsub = np.arange(r0, r1) - pr0                       # alignSet(R^D_s, R^D_p)
+            Csub = np.arange(q0, q1) - pr0                       # alignSet(C^D_s, R^D_p)
+            Up = D.U[p].T @ D.U[p]
+            T = D.V[p][Csub].T @ G
+            T = Up @ T
+            W -= D.V[p][Rsub] @ T
+        return W
+
+    def diagonal_multiply_T(self, j, s, G):
+        """(L^D_{j,s})^T G for internal block s; G has |R^D_{j,s}| rows."""
+        an = self.an
+        D = self.sn[j].D
+        t = D.tree
+        c0, _ = an.cols(j)
+        r0, r1 = t.rows(s)
+        q0, q1 = t.cols(s)
+        W = an.A_block(np.arange(c0 + r0, c0 + r1), np.arange(c0 + q0, c0 + q1)).T @ G
+        for k, _, _ in an.sym.desc[j]:
+            Rk = an.sym.rows[k]
+            pr = self._desc_rows_in(j, k, c0 + r0, c0 + r1)
+            pc = self._desc_rows_in(j, k, c0 + q0, c0 + q1)
+            if pr.size and pc.size:
+                T = self.lo_apply(k, pc, pr, G[Rk[pr] - (c0 + r0)])
+                W[Rk[pc] - (c0 + q0)] -= T
+        for p in self._ancestor_blocks(j, s):
+            pr0, _ = t.rows(p)
+            Rsub = np.arange(r0, r1) - pr0
+            Csub = np.arange(q0, q1) - pr0
+            Up = D.U[p].T @ D.U[p]
+            T = D.V[p][Rsub].T @ G
+            T = Up @ T
+            W -= D.V[p][Csub] @ T
+        return self.diagonal_solve(j, W, False, t.left[s])
+
+    def approximate_diagonal_block(self, j, s):
+        D = self.sn[j].D
+        t = D.tree
+        r0, r1 = t.rows(s)
+        q0, q1 = t.cols(s)
+        V, U = self._range_finder(r1 - r0, q1 - q0, self.tol_D, (j << 12) | s,
+                                  lambda G: self.diagonal_multiply(j, s, G),
+                                  lambda G: self.diagonal_multiply_T(j, s, G))
+        D.V[s], D.U[s] = V, U
+
+    # ----------------------------------------------------------- Alg. 6
+    def factor_diagonal(self, j, s):
+        an = self.an
+        D = self.sn[j].D
+        t = D.tree
+        c0, _ = an.cols(j)
+        r0, r1 = t.rows(s)
+        gl = np.arange(c0 + r0, c0 + r1)
+        S = an.A_block(gl, gl)
+        for k, _, _ in an.sym.desc[j]:
+            Rk = an.sym.rows[k]
+            pr = self._desc_rows_in(j, k, c0 + r0, c0 + r1)
+            if pr.size:
+                loc = Rk[pr] - (c0 + r0)
+                S[np.ix_(loc, loc)] -= self.lo_pair_product(k, pr, pr)
+        for p in self._ancestor_blocks(j, s):
+            pr0, _ = t.rows(p)
+            Rsub = np.arange(r0, r1) - pr0
+            Up = D.U[p].T @ D.U[p]
+            S -= D.V[p][Rsub] @ (Up @ D.V[p][Rsub].T)
+        D.leafL[s] = dense.cholesky(S)
+
+    # ----------------------------------------------------------- Alg. 1
+    def schur_blocks(self, j, with_offdiag=True):
+        """U^D_j and U^O_j (Eqs. schurDiag / schurOffDiag)."""
+        an = self.an
+        c0, c1 = an.cols(j)
+        Cj = np.arange(c0, c1)
+        Rj = an.sym.rows[j]
+        UD = an.A_block(Cj, Cj)
+        UO = an.A_block(Rj, Cj) if with_offdiag else None
+        for k, pD, pO in an.sym.desc[j]:
+            Rk = an.sym.rows[k]
+            dloc = positions(Rk[pD], Cj)                         # scatter(., R^D_glob, C_j, R^D_glob, C_j)
+            UD[np.ix_(dloc, dloc)] -= self.lo_pair_product(k, pD, pD)
+            if with_offdiag and pO.size:
+                oloc = positions(Rk[pO], Rj)                     # scatter(., R^O_glob, R_j, R^D_glob, C_j)
+                UO[np.ix_(oloc, dloc)] -= self.lo_pair_product(k, pO, pD)
+        return UD, UO
+
+    def factor_supernode(self, j):
+        """Alg. 1: L^D_j = chol(U^D_j), L^O_j = U^O_j (L^D_j)^{-T}."""
+        UD, UO = self.schur_blocks(j)
+        s = self.sn[j]
+        s.D = DiagFactor()
+        s.D.L = dense.cholesky(UD)
+        s.LO = dense.solve_lower(s.D.L, UO.T).T
+
+    def factor_compressed(self, j):
+        an = self.an
+        s = self.sn[j]
+        s.compressed = True
+        tree = an.ordering.trees[j]
+        if self.diag_compress and tree is not None:
+            s.D = DiagFactor(tree)
+            for b in range(1, tree.nblocks + 1):
+                if tree.leaf[b]:
+                    self.factor_diagonal(j, b)
+                else:
+                    self.approximate_diagonal_block(j, b)
+        else:
+            UD, _ = self.schur_blocks(j, with_offdiag=False)
+            s.D = DiagFactor()
+            s.D.L = dense.cholesky(UD)
+        if an.sym.rows[j].size:
+            self.approximate_offdiag(j)
+        else:
+            c = an.cols(j)[1] - an.cols(j)[0]
+            s.V, s.U, s.Uprod = np.zeros((0, 0)), np.zeros((c, 0)), np.zeros((0, 0))
+
+    def is_compressed(self, j):
+        an = self.an
+        c0, c1 = an.cols(j)
+        return self.tol > 0 and an.ordering.kinds[j] == "sep" and (c1 - c0) >= an.opts.tau_O
+
+    def run(self):
+        self.sn = [SupernodeFactor() for _ in range(self.an.nsuper)]
+        for j in range(self.an.nsuper):
+            if self.is_compressed(j):
+                self.factor_compressed(j)
+            else:
+                self.factor_supernode(j)
+
+
+def factor(an: Analysis, tol: float) -> Factor:
+    """Factor with the Section 5.3 restart loop (tolerance form)."""
+    f = Factor(an)
+    f.tol = tol
+    f.tol_D = tol
+    f.diag_compress = bool(an.opts.diag_compress and tol > 0)
+    attempt = 0
+    while True:
+        f.restarts = attempt
+        try:
+            f.run()
+            return f
+        except NotPositiveDefinite:
+            if not f.diag_compress:
+                raise
+            attempt += 1
+            if attempt <= an.opts.max_restarts:
+                f.tol_D = f.tol_D / 1.25
+            else:
+                f.diag_compress = False
+
+
+# ----------------------------------------------------------------------------- solve
+
+def apply_preconditioner(f: Factor, r: np.ndarray) -> np.ndarray:
+    """z = P (L L^T)^{-1} P^T r with the approximate factor: forward, then backward
+    substitution over supernodes (Section 1: "two triangular solves")."""
+    an = f.an
+    perm = an.ordering.perm
+    y = np.array(r[perm], dtype=np.float64)
+    M = an.nsuper
+    for j in range(M):
+        c0, c1 = an.cols(j)
+        Rj = an.sym.rows[j]
+        y[c0:c1] = f.diagonal_solve(j, y[c0:c1, None], transpose=False)[:, 0]
+        if Rj.size:
+            s = f.sn[j]
+            if s.compressed:
+                y[Rj] -= s.V @ (s.U.T @ y[c0:c1])
+            else:
+                y[Rj] -= s.LO @ y[c0:c1]
+    for j in range(M - 1, -1, -1):
+        c0, c1 = an.cols(j)
+        Rj = an.sym.rows[j]
+        if Rj.size:
+            s = f.sn[j]
+            if s.compressed:
+                y[c0:c1] -= s.U @ (s.V.T @ y[Rj])
+            else:
+                y[c0:c1] -= s.LO.T @ y[Rj]
+        y[c0:c1] = f.diagonal_solve(j, y[c0:c1, None], transpose=True)[:, 0]
+    z = np.empty_like(y)
+    z[perm] = y
+    return z
+
+
+def pcg(A: sp.csr_matrix, b: np.ndarray, precond, rtol: float = 1e-8, max_iter: int = 1000):
+    """Hestenes-Stiefel PCG from x0 = 0 (Section 6.1 uses PCG to a relative l2
+    residual).  Stops when the recursive ||r||/||b|| <= rtol and the true residual
+    ||b - A x||/||b|| confirms it.  Returns (x, iterations, true relative residual,
+    converged) with iterations = number of CG steps (products with A)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, 0, 0.0, True
+    z = precond(r)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, max_iter + 1):
+        q = A @ p
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        if np.linalg.norm(r) / nb <= rtol:
+            true_rel = np.linalg.norm(b - A @ x) / nb
+            if true_rel <= rtol:
+                return x, it, true_rel, True
+        z = precond(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, max_iter, np.linalg.norm(b - A @ x) / nb, False
+
+
+def analyze(n, row_ptr, col_idx, val, coords, opts: Options | None = None) -> Analysis:
+    return Analysis(n, row_ptr, col_idx, val, coords, opts or Options())
+
+
+def solve(an: Analysis, f: Factor, b: np.ndarray, rtol=1e-8, max_iter=1000):
+    return pcg(an.A, b, lambda r: apply_preconditioner(f, r), rtol, max_iter)
+
+
+def factor_bytes(f: Factor) -> int:
+    """Bytes of the stored factor in FP64 (dense blocks, V and U factors)."""
+    tot = 0
+    for s in f.sn:
+        D = s.D
+        if D.hierarchical:
+            tot += sum(L.size for L in D.leafL.values())
+            tot += sum(D.V[b].size + D.U[b].size for b in D.V)
+        else:
+            tot += D.L.shape[0] * (D.L.shape[0] + 1) // 2
+        if s.compressed:
+            tot += s.V.size + s.U.size
+        else:
+            tot += s.LO.size
+    return 8 * tot

@@ -1,0 +1,406 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: the worked
+example of Section 2.1, published known-answer vectors, brute-force symbolic
+elimination, a library dense Cholesky of the permuted matrix, explicitly formed
+dense blocks, dense SVDs and PCG residuals.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as W
+from oracle import dense
+from oracle import factor as F
+from oracle.ordering import geometric_split, nested_dissection
+from oracle.philox import gaussian_block, philox4x32_10
+from oracle.scatter import gather_rows, scatter_rows
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _mat(txt):
+    return np.array([[float(x) for x in r.split()] for r in txt.split(";")])
+
+
+# --------------------------------------------------------------------------- scatter / gather
+
+def test_scatter_rows_worked_example():
+    rec = {}
+    for line in open(os.path.join(GOLDEN, "scatter_rows_example.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split(":", 1)
+        rec[k.strip()] = v.strip()
+    B = _mat(rec["B"])
+    R1 = [int(x) for x in rec["R1"].split()]
+    R2 = [int(x) for x in rec["R2"].split()]
+    out = scatter_rows(B, R1, R2)
+    np.testing.assert_array_equal(out, _mat(rec["OUT"]))
+    np.testing.assert_array_equal(gather_rows(out, R2, R1), B)
+
+
+def test_gather_inverts_scatter_random():
+    rng = np.random.default_rng(1)
+    R2 = np.sort(rng.choice(1000, 60, replace=False))
+    R1 = np.sort(rng.choice(R2, 25, replace=False))
+    B = rng.standard_normal((25, 3))
+    np.testing.assert_array_equal(gather_rows(scatter_rows(B, R1, R2), R2, R1), B)
+    with pytest.raises(ValueError):
+        scatter_rows(B[:1], [1001], R2)
+
+
+# --------------------------------------------------------------------------- Philox
+
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = philox4x32_10(np.array(w[:4], np.uint32), np.array(w[4:6], np.uint32))
+        assert [int(x) for x in out] == w[6:10]
+
+
+def test_gaussian_moments_and_counter_independence():
+    g = gaussian_block(20000, 16, seed=7, block_id=3, pass_=0, attempt=0)
+    assert abs(g.mean()) < 0.01
+    assert abs(g.var() - 1.0) < 0.02
+    assert abs(np.mean(g ** 4) - 3.0) < 0.1          # Gaussian kurtosis
+    c = np.corrcoef(g[:, 0], g[:, 1])[0, 1]
+    assert abs(c) < 0.03
+    g2 = gaussian_block(20000, 16, seed=7, block_id=3, pass_=1, attempt=0)
+    assert abs(np.corrcoef(g.ravel(), g2.ravel())[0, 1]) < 0.01
+    # same counters -> same numbers; a prefix of rows is a prefix of the matrix
+    np.testing.assert_array_equal(g[:100], gaussian_block(100, 16, 7, 3, 0, 0))
+
+
+# --------------------------------------------------------------------------- dense kernels
+
+def test_dense_kernels_vs_library():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((40, 40))
+    S = X @ X.T + 40 * np.eye(40)
+    L = dense.cholesky(S)
+    np.testing.assert_allclose(L, np.linalg.cholesky(S), rtol=1e-13, atol=1e-13)
+    B = rng.standard_normal((40, 5))
+    np.testing.assert_allclose(dense.solve_lower(L, B), sla.solve_triangular(L, B, lower=True), rtol=1e-12)
+    np.testing.assert_allclose(dense.solve_lower_T(L, B), sla.solve_triangular(L.T, B, lower=False),
+                               rtol=1e-12)
+    with pytest.raises(dense.NotPositiveDefinite):
+        dense.cholesky(S - 1000 * np.eye(40))
+    Y = rng.standard_normal((50, 16))
+    Q = dense.householder_q(Y)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(16), atol=1e-14)
+    np.testing.assert_allclose(Q @ (Q.T @ Y), Y, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- ordering
+
+def test_nested_dissection_grid_closed_form():
+    p = W.poisson7(32)
+    order, parts = nested_dissection(p.coords, 64)
+    assert sorted(order.tolist()) == list(range(p.n))
+    # last part = top separator: the plane x = 16 (32*32 nodes)
+    kind, top = parts[-1]
+    assert kind == "sep" and top.size == 1024
+    assert np.all(p.coords[top, 0] == 16)
+    # its in-plane order is lexicographic (z, y, x)
+    zyx = p.coords[top][:, ::-1]
+    assert all(tuple(zyx[i]) < tuple(zyx[i + 1]) for i in range(len(top) - 1))
+    assert all(ids.size <= 64 for k, ids in parts if k == "leaf")
+    # every separator is a plane (one coordinate constant)
+    for k, ids in parts:
+        if k == "sep":
+            assert any(np.ptp(p.coords[ids, a]) == 0 for a in range(3))
+
+
+def test_nested_dissection_separates():
+    """Nodes of two sibling subtrees are never adjacent in A (vertex separators)."""
+    p = W.poisson7(12)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(leaf_size=16))
+    L = _brute_structure(an.Ap.toarray() != 0)
+    # A separator property implies: columns of two different leaves never share a
+    # nonzero of L below the leaves (fill stays inside ancestor separators).
+    leaves = [j for j in range(an.nsuper) if an.ordering.kinds[j] == "leaf"]
+    for a in leaves[:6]:
+        a0, a1 = an.cols(a)
+        for b in leaves:
+            if b == a:
+                continue
+            b0, b1 = an.cols(b)
+            assert not L[b0:b1, a0:a1].any()
+
+
+def test_block_tree_inorder_labels():
+    """Section 4.1, Eq. (ldjLabel): a 4-leaf tree has 7 blocks, root 4 with
+    children 2 and 6, leaves 1, 3, 5, 7 on the diagonal in order."""
+    p = W.poisson7(32)
+    _, parts = nested_dissection(p.coords, 64)
+    top = parts[-1][1]
+    ids, t = geometric_split(top, p.coords, 256)
+    assert t.nblocks == 7 and t.root == 4
+    assert (t.left[4], t.right[4]) == (2, 6)
+    assert (t.left[2], t.right[2], t.left[6], t.right[6]) == (1, 3, 5, 7)
+    assert [s for s in range(1, 8) if t.leaf[s]] == [1, 3, 5, 7]
+    assert [t.lo[s] for s in (1, 3, 5, 7)] == [0, 256, 512, 768]
+    assert t.rows(4) == (512, 1024) and t.cols(4) == (0, 512)
+    assert t.rows(2) == (256, 512) and t.cols(2) == (0, 256)
+    # halves are split along the longest bounding-box axis: y first (plane x = 16)
+    assert np.all(p.coords[ids[:512], 1] < 16) and np.all(p.coords[ids[512:], 1] >= 16)
+    # labels of a complete in-order tree: node at height h has children s -/+ 2^(h-1)
+    _, t16 = geometric_split(top, p.coords, 64)
+    assert t16.nblocks == 31 and t16.root == 16
+    for s in range(1, 32):
+        h = (s & -s).bit_length() - 1
+        if h:
+            assert (t16.left[s], t16.right[s]) == (s - (1 << (h - 1)), s + (1 << (h - 1)))
+
+
+# --------------------------------------------------------------------------- symbolic
+
+def _brute_structure(nz):
+    """Boolean Gaussian elimination: structure of the Cholesky factor (lower)."""
+    nz = nz.copy()
+    n = nz.shape[0]
+    for k in range(n):
+        rows = np.nonzero(nz[k + 1:, k])[0] + k + 1
+        nz[np.ix_(rows, rows)] = True
+    return np.tril(nz)
+
+
+@pytest.mark.parametrize("maker", [lambda: W.poisson7(6), lambda: W.poisson7(5, 7, 4),
+                                   lambda: W.elasticity_q1(3, incl=(1, 2))])
+def test_symbolic_vs_brute_force(maker):
+    p = maker()
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=8, dof_per_node=p.dof_per_node))
+    L = _brute_structure(an.Ap.toarray() != 0)
+    sym = an.sym
+    for j in range(an.nsuper):
+        c0, c1 = an.cols(j)
+        brute = np.nonzero(L[c1:, c0:c1].any(axis=1))[0] + c1
+        np.testing.assert_array_equal(sym.rows[j], brute)
+    for j in range(an.nsuper):
+        c0, c1 = an.cols(j)
+        brute_D = [k for k in range(j) if np.any((sym.rows[k] >= c0) & (sym.rows[k] < c1))]
+        assert [k for k, _, _ in sym.desc[j]] == brute_D
+        for k, pD, pO in sym.desc[j]:
+            Rk = sym.rows[k]
+            assert pD.tolist() == [q for q in range(Rk.size) if c0 <= Rk[q] < c1]
+            assert pO.tolist() == [q for q in range(Rk.size) if Rk[q] in set(sym.rows[j].tolist())]
+            # R_k meets C^O_j only inside R_j (Section 2.1)
+            assert set(Rk[Rk >= c1].tolist()) <= set(sym.rows[j].tolist())
+
+
+# --------------------------------------------------------------------------- exact factor
+
+def _assemble_L(f):
+    """Dense approximate factor from the oracle's blocks (hierarchical blocks expanded)."""
+    an = f.an
+    n = an.n
+    L = np.zeros((n, n))
+    for j in range(an.nsuper):
+        c0, c1 = an.cols(j)
+        L[c0:c1, c0:c1] = _assemble_LD(f, j)
+        s = f.sn[j]
+        Rj = an.sym.rows[j]
+        if Rj.size:
+            L[Rj, c0:c1] = s.V @ s.U.T if s.compressed else s.LO
+    return L
+
+
+def _assemble_LD(f, j):
+    D = f.sn[j].D
+    if not D.hierarchical:
+        return D.L
+    t = D.tree
+    c = t.hi[t.root]
+    H = np.zeros((c, c))
+    for s in range(1, t.nblocks + 1):
+        r0, r1 = t.rows(s)
+        q0, q1 = t.cols(s)
+        H[r0:r1, q0:q1] = D.leafL[s] if t.leaf[s] else D.V[s] @ D.U[s].T
+    return H
+
+
+@pytest.mark.parametrize("maker", [lambda: W.poisson7(4), lambda: W.poisson7(8), lambda: W.poisson7(6, 9, 5),
+                                   lambda: W.diffusion_grf(8, 2.0, 3.0, 0),
+                                   lambda: W.elasticity_q1(4, incl=(1, 3))])
+def test_exact_factor_matches_dense_cholesky(maker):
+    p = maker()
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=8, tau_O=16, tau_D=8, dof_per_node=p.dof_per_node))
+    f = F.factor(an, 0.0)
+    L = _assemble_L(f)
+    Ap = an.Ap.toarray()
+    assert np.linalg.norm(L @ L.T - Ap) / np.linalg.norm(Ap) <= 1e-13
+    Lref = np.linalg.cholesky(Ap)
+    assert np.abs(L - Lref).max() <= 1e-12 * np.abs(Lref).max()
+    x, it, rr, ok = F.solve(an, f, p.b, 1e-8)
+    assert ok and it <= 2 and rr <= 1e-8
+
+
+# --------------------------------------------------------------------------- compressed factor
+
+@pytest.fixture(scope="module")
+def compressed8():
+    p = W.poisson7(10)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=8, tau_O=24, tau_D=16))
+    f = F.factor(an, 0.05)
+    return p, an, f
+
+
+def _prefix_schur(f, j):
+    """Dense Schur complement block column of supernode j from the dense factor of
+    all earlier supernodes: A(:, C_j) - L(:, <C_j) L(C_j, <C_j)^T."""
+    an = f.an
+    c0, c1 = an.cols(j)
+    L = _assemble_L(f)
+    Ap = an.Ap.toarray()
+    return Ap[:, c0:c1] - L[:, :c0] @ L[c0:c1, :c0].T
+
+
+def test_offdiag_multiply_vs_explicit(compressed8):
+    p, an, f = compressed8
+    js = [j for j in range(an.nsuper) if f.sn[j].compressed and an.sym.rows[j].size]
+    assert js
+    rng = np.random.default_rng(2)
+    for j in js:
+        c0, c1 = an.cols(j)
+        Rj = an.sym.rows[j]
+        S = _prefix_schur(f, j)
+        LD = _assemble_LD(f, j)
+        LO = sla.solve_triangular(LD, S[Rj].T, lower=True).T        # U^O_j (L^D_j)^{-T}
+        G = rng.standard_normal((c1 - c0, 5))
+        np.testing.assert_allclose(f.offdiag_multiply(j, G), LO @ G, rtol=1e-10, atol=1e-11)
+        H = rng.standard_normal((Rj.size, 5))
+        np.testing.assert_allclose(f.offdiag_multiply_T(j, H), LO.T @ H, rtol=1e-10, atol=1e-11)
+        # the stored compression meets its tolerance against the explicit block
+        s = f.sn[j]
+        err = np.linalg.norm(LO - s.V @ s.U.T) / np.linalg.norm(LO)
+        assert err <= 2 * f.tol
+        np.testing.assert_allclose(s.U.T @ s.U, np.eye(s.U.shape[1]), atol=1e-13)
+        # rank is at most one 16-column pass beyond the passes that reach the SVD
+        # rank needed for tol/2 in Frobenius norm
+        sv = np.linalg.svd(LO, compute_uv=False)
+        tail = np.sqrt(np.cumsum((sv ** 2)[::-1]))[::-1] / np.linalg.norm(sv)
+        need = int(np.sum(tail > f.tol / 2))
+        assert s.U.shape[1] <= 16 * ((need + 15) // 16) + 16
+
+
+def test_diagonal_blocks_vs_explicit(compressed8):
+    p, an, f = compressed8
+    rng = np.random.default_rng(3)
+    js = [j for j in range(an.nsuper) if f.sn[j].compressed and f.sn[j].D.hierarchical]
+    assert js
+    for j in js:
+        D = f.sn[j].D
+        t = D.tree
+        c0, c1 = an.cols(j)
+        S = _prefix_schur(f, j)[c0:c1]                  # U^D_j as a dense matrix
+        H = _assemble_LD(f, j)
+        # Alg. 4: hierarchical solves equal dense triangular solves with the assembled block
+        G = rng.standard_normal((c1 - c0, 3))
+        np.testing.assert_allclose(f.diagonal_solve(j, G, False), sla.solve_triangular(H, G, lower=True),
+                                   rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(f.diagonal_solve(j, G, True),
+                                   sla.solve_triangular(H.T, G, lower=False), rtol=1e-10, atol=1e-10)
+        for s in range(1, t.nblocks + 1):
+            r0, r1 = t.rows(s)
+            q0, q1 = t.cols(s)
+            # block Cholesky relation: L_s = (S(rows,cols) - H(rows,:lo) H(cols,:lo)^T) H(cols,cols)^{-T}
+            rhs = S[r0:r1, q0:q1] - H[r0:r1, :q0] @ H[q0:q1, :q0].T
+            if t.leaf[s]:
+                np.testing.assert_allclose(D.leafL[s], np.linalg.cholesky(rhs), rtol=1e-10, atol=1e-12)
+                continue
+            Ls = sla.solve_triangular(H[q0:q1, q0:q1], rhs.T, lower=True).T
+            Gs = rng.standard_normal((q1 - q0, 4))
+            np.testing.assert_allclose(f.diagonal_multiply(j, s, Gs), Ls @ Gs, rtol=1e-9, atol=1e-11)
+            Gr = rng.standard_normal((r1 - r0, 4))
+            np.testing.assert_allclose(f.diagonal_multiply_T(j, s, Gr), Ls.T @ Gr, rtol=1e-9, atol=1e-11)
+            assert np.linalg.norm(Ls - D.V[s] @ D.U[s].T) <= 2 * f.tol_D * np.linalg.norm(Ls) + 1e-14
+
+
+def test_preconditioner_apply_vs_dense(compressed8):
+    p, an, f = compressed8
+    L = _assemble_L(f)
+    r = np.random.default_rng(4).standard_normal(p.n)
+    z = F.apply_preconditioner(f, r)
+    P = an.ordering.perm
+    y = np.linalg.solve(L @ L.T, r[P])
+    zz = np.empty_like(y)
+    zz[P] = y
+    np.testing.assert_allclose(z, zz, rtol=1e-9, atol=1e-12)
+
+
+def test_offdiag_compression_keeps_schur_pd():
+    """Section 3.2 (Eq. scPlusPos): with diagonal blocks exact, the Schur complement
+    after a compressed supernode exceeds the exact one by L^O (I - U U^T) L^O^T >= 0,
+    and the factorization never needs a restart."""
+    for maker in (lambda: W.poisson7(10), lambda: W.diffusion_grf(10, 2.0, 3.0, 1)):
+        p = maker()
+        an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                       F.Options(leaf_size=8, tau_O=24, tau_D=16, diag_compress=False))
+        f = F.factor(an, 0.5)
+        assert f.restarts == 0
+        for j in range(an.nsuper):
+            s = f.sn[j]
+            if not (s.compressed and an.sym.rows[j].size):
+                continue
+            S = _prefix_schur(f, j)
+            c0, c1 = an.cols(j)
+            LO = sla.solve_triangular(s.D.L, S[an.sym.rows[j]].T, lower=True).T
+            diff = LO @ LO.T - s.V @ s.V.T
+            assert np.linalg.eigvalsh(diff).min() >= -1e-12 * np.abs(LO @ LO.T).max()
+
+
+def test_restart_path(monkeypatch):
+    """Section 5.3: an indefinite diagonal block restarts with a tighter diagonal
+    tolerance (tol_D / 1.25); the planted failure is in the oracle, on the CPU."""
+    p = W.poisson7(10)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(leaf_size=8, tau_O=24, tau_D=16))
+    calls = {"n": 0}
+    orig = F.Factor.factor_diagonal
+
+    def failing(self, j, s):
+        if self.restarts == 0 and calls["n"] == 0:
+            calls["n"] += 1
+            raise dense.NotPositiveDefinite("planted")
+        return orig(self, j, s)
+
+    monkeypatch.setattr(F.Factor, "factor_diagonal", failing)
+    f = F.factor(an, 0.1)
+    assert f.restarts == 1 and abs(f.tol_D - 0.1 / 1.25) < 1e-15 and f.diag_compress
+
+
+def test_restart_switches_diag_compression_off(monkeypatch):
+    p = W.poisson7(10)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=8, tau_O=24, tau_D=16, max_restarts=2))
+    orig = F.Factor.factor_diagonal
+
+    def always_fail(self, j, s):
+        raise dense.NotPositiveDefinite("planted")
+
+    monkeypatch.setattr(F.Factor, "factor_diagonal", always_fail)
+    f = F.factor(an, 0.1)
+    assert f.restarts == 3 and not f.diag_compress
+    x, it, rr, ok = F.solve(an, f, p.b)
+    assert ok
+
+
+# --------------------------------------------------------------------------- PCG
+
+@pytest.mark.parametrize("tol", [0.3, 0.1, 0.01])
+def test_pcg_reaches_tolerance(tol):
+    p = W.diffusion_grf(12, 2.0, 3.0, 0)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(leaf_size=16, tau_O=40, tau_D=32))
+    f = F.factor(an, tol)
+    assert any(s.compressed for s in f.sn)
+    x, it, rr, ok = F.solve(an, f, p.b, 1e-8)
+    assert ok and rr <= 1e-8
+    A = p.scipy()
+    assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= 1e-8
