@@ -1,0 +1,171 @@
+/*
+ * rsc.h -- C ABI of a GB300 (sm_103a) implementation of the rank-structured
+ * supernodal Cholesky preconditioner of Chadwick & Bindel, "An efficient solver
+ * for sparse linear systems based on rank-structured Cholesky factorization"
+ * (arXiv 1507.05593).
+ *
+ * The problem is A x = b with A symmetric positive definite (Section 1, Eq. "main").
+ * rsc_analyze orders A by nested dissection and computes the supernodal structure
+ * (Sections 2.1, 2.2, 3.1, 4.1); rsc_factor builds the approximate factor
+ * L ~ chol(P A P^T) with compressed off-diagonal and diagonal blocks (Algorithms
+ * 1-6, Sections 3-5); rsc_solve runs PCG preconditioned by the two triangular
+ * solves with L (Section 1; Section 6.1 uses PCG to a relative residual).
+ *
+ * Conventions for every call:
+ *  - indices are 0-based; the matrix is the FULL symmetric CSR (both triangles),
+ *    column indices sorted and unique within each row, the diagonal present;
+ *  - pointers named d_* are device pointers of the current CUDA device, all
+ *    others are host pointers; the caller owns every buffer it passes and the
+ *    library copies what it keeps;
+ *  - no C++ exception crosses this boundary; a failing call returns a status
+ *    and rsc_last_error(handle) describes it (NULL handle: last global error);
+ *  - a handle is not thread safe and issues its GPU work on one stream.
+ */
+#ifndef RSC_H
+#define RSC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsc_handle rsc_handle;
+
+typedef enum {
+    RSC_OK = 0,
+    RSC_ERR_INVALID_ARG = 1,    /* malformed input (sizes, pattern, NaN, NULL) */
+    RSC_ERR_NOT_SPD = 2,        /* a pivot <= 0 after every restart (Section 5.3) */
+    RSC_ERR_NO_CONVERGENCE = 3, /* PCG hit max_iter; x holds the last iterate */
+    RSC_ERR_OOM = 4,            /* device or host allocation failed */
+    RSC_ERR_CUDA = 5,           /* a CUDA runtime error (no device, launch failure) */
+    RSC_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    RSC_ERR_STATE = 7           /* call order: factor before analyze, solve before factor */
+} rsc_status;
+
+typedef enum {
+    RSC_PREC_FP64 = 0,   /* every step in FP64 */
+    RSC_PREC_FP32 = 1,   /* Schur updates, sampling and the preconditioner apply in FP32
+                            (FP64 kept for diagonal Cholesky factorizations and PCG) */
+    RSC_PREC_TF32 = 2,   /* as FP32, Schur-update GEMMs on tensor cores in TF32 */
+    RSC_PREC_BF16 = 3    /* as FP32, Schur-update GEMMs on tensor cores in BF16 */
+} rsc_precision;
+
+/* Parameters of the method (Sections 3.1, 4.1, 5.2, 5.3). */
+typedef struct {
+    int32_t tau_O;         /* separators with >= tau_O unknowns are compressed (Section 3.1); 256 */
+    int32_t tau_D;         /* largest dense diagonal block (Section 4.1); 256 */
+    int32_t leaf_size;     /* nested-dissection leaf: at most this many nodes; 64 */
+    int32_t sample_block;  /* columns per randomized sampling pass; 16 (only 16 supported) */
+    int32_t power_iters;   /* power iterations in Alg. 3; 0 */
+    int32_t dof_per_node;  /* unknowns per node kept adjacent (3 for elasticity); 1 */
+    int32_t max_restarts;  /* indefinite restarts before diagonal compression is switched off; 8 */
+    int32_t precision;     /* rsc_precision; RSC_PREC_FP64 */
+    int32_t diag_compress; /* 1: compress diagonal blocks hierarchically (Section 4); 1 */
+    int32_t reserved;      /* must be 0 */
+    uint64_t seed;         /* key of the Philox4x32-10 stream of the random test matrices; 0 */
+} rsc_options;
+
+typedef struct {
+    double factor_bytes;      /* bytes of the stored factor (dense blocks + V, U) */
+    double factor_flops;      /* algorithmic flops of the last rsc_factor */
+    double factor_seconds;    /* device time of the last rsc_factor (CUDA events) */
+    double solve_seconds;     /* device time of the last solve */
+    int32_t restarts;         /* restarts taken by the last rsc_factor (Section 5.3) */
+    int32_t n_supernodes;
+    int32_t n_compressed;     /* supernodes with compressed blocks */
+    int32_t n_levels;         /* levels of the supernodal elimination tree */
+    int32_t max_rank;         /* largest off-diagonal rank */
+    int32_t last_iters;       /* PCG iterations of the last solve */
+    double last_relres;       /* true relative residual of the last solve */
+    int64_t gpu_launches;     /* kernels launched by the last factor + solve */
+} rsc_stats_t;
+
+/* Fill *opts with the defaults listed above.  Returns RSC_INVALID_ARG on NULL. */
+rsc_status rsc_options_default(rsc_options* opts);
+
+/*
+ * Symbolic analysis on the host (Sections 2.1, 2.2, 3.1, 4.1): nested-dissection
+ * ordering of the nodes by recursive coordinate bisection, one supernode per
+ * nested-dissection leaf or separator, supernodal row structures R_j, the
+ * supernodal elimination tree and its levels, and the within-separator
+ * geometric ordering and block tree of every separator with more than tau_D
+ * unknowns that is large enough to be compressed.
+ *   n        unknowns; row_ptr[n+1] (int64), col_idx[nnz] (int32), val[nnz] (FP64);
+ *   coords   n x 3 row-major lattice coordinates of each unknown (unknowns of one
+ *            node repeat the node's coordinates); required;
+ *   opts     NULL for defaults.
+ * The values are copied and used by rsc_factor.  No GPU work is done here.
+ * Errors: RSC_ERR_INVALID_ARG (pattern not symmetric, unsorted, missing
+ * diagonal, non-finite value, n not a multiple of dof_per_node, NULL coords).
+ */
+rsc_status rsc_analyze(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                       const double* coords, const rsc_options* opts, rsc_handle** out);
+
+/* perm[n]: perm[new] = old unknown; *n_snodes = M; snode_ptr[M+1] column boundaries
+ * (each output may be NULL). */
+rsc_status rsc_get_ordering(const rsc_handle* h, int32_t* perm, int32_t* n_snodes, int64_t* snode_ptr);
+
+/* Supernodal structure: rows_ptr[M+1] and rows[rows_ptr[M]] hold R_j (sorted
+ * permuted row indices after C_j); parent[M] (-1 for roots); level[M]; kind[M]
+ * (0 leaf, 1 separator).  Pass rows == NULL to query rows_ptr only. */
+rsc_status rsc_get_structure(const rsc_handle* h, int64_t* rows_ptr, int32_t* rows, int32_t* parent,
+                             int32_t* level, int32_t* kind);
+
+/*
+ * Numeric factorization on the GPU (Algorithms 1-6).  tol <= 0: compression off,
+ * the exact supernodal Cholesky factor (Alg. 1).  tol > 0: supernodes that are
+ * separators with >= tau_O unknowns get off-diagonal blocks L^O_j ~ V_j U_j^T
+ * (Alg. 2, 3; adaptive: stop when the sampled residual falls to tol relative)
+ * and, above tau_D unknowns, hierarchically compressed diagonal blocks (Alg. 4-6)
+ * at tolerance tol_D = tol / 1.25^restart.  On an indefinite diagonal block the
+ * factorization restarts (Section 5.3); after max_restarts restarts diagonal
+ * compression is switched off.  Errors: RSC_ERR_STATE, RSC_ERR_NOT_SPD,
+ * RSC_ERR_OOM, RSC_ERR_CUDA, RSC_ERR_TIMEOUT.  Synchronous.
+ */
+rsc_status rsc_factor(rsc_handle* h, double tol);
+
+/* New values for the same pattern (val[nnz] as in rsc_analyze); the next
+ * rsc_factor uses them. */
+rsc_status rsc_refactor_values(rsc_handle* h, const double* val);
+
+/*
+ * PCG from x0 = 0 on the original (unpermuted) system, preconditioned by
+ * M^{-1} = P (L L^T)^{-1} P^T, until ||r||/||b|| <= rtol (recursive residual,
+ * confirmed by the true residual).  b[n], x[n] host FP64.  *iters = CG steps;
+ * *final_relres = true relative residual.  RSC_ERR_NO_CONVERGENCE leaves the
+ * last iterate in x.  Synchronous.
+ */
+rsc_status rsc_solve(rsc_handle* h, const double* b, double* x, double rtol, int32_t max_iter,
+                     int32_t* iters, double* final_relres);
+
+/* As rsc_solve with device vectors d_b[n], d_x[n] (FP64) on cuda_stream
+ * (a cudaStream_t, NULL = the handle's stream). */
+rsc_status rsc_solve_device(rsc_handle* h, const double* d_b, double* d_x, double rtol, int32_t max_iter,
+                            int32_t* iters, double* final_relres, void* cuda_stream);
+
+/* One application of the preconditioner: d_z = P (L L^T)^{-1} P^T d_r (device FP64, n). */
+rsc_status rsc_apply_preconditioner_device(rsc_handle* h, const double* d_r, double* d_z, void* cuda_stream);
+
+/* Per-supernode results of the last factor.  info[8] = {c_j, |R_j|, compressed,
+ * rank of L^O_j (0 if uncompressed), hierarchical diagonal, blocks in L^D_j,
+ * level, kind}. */
+rsc_status rsc_get_supernode_info(const rsc_handle* h, int32_t j, int32_t* info);
+
+/* Dense blocks of supernode j (FP64, column-major): LD[c*c] the diagonal block
+ * (hierarchical blocks expanded, V_s U_s^T in the off-diagonal blocks), LO[r*c]
+ * L^O_j or V_j U_j^T (either may be NULL). */
+rsc_status rsc_get_supernode_blocks(const rsc_handle* h, int32_t j, double* LD, double* LO);
+
+rsc_status rsc_get_stats(const rsc_handle* h, rsc_stats_t* out);
+
+/* Message of the last error on h (or of the last failed rsc_analyze if h is NULL). */
+const char* rsc_last_error(const rsc_handle* h);
+
+void rsc_destroy(rsc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSC_H */

@@ -1,0 +1,1554 @@
+// GPU engine: plan building, the level-scheduled factorization (Algorithms 1-6)
+// and the PCG solve with the two triangular solves as preconditioner.
+//
+// Factorization schedule (one pass per level of the supernodal elimination tree):
+//   1. uncompressed supernodes (and compressed ones with a dense diagonal) of the
+//      level factor their dense panels [L^D_j; L^O_j] by a blocked tall-panel
+//      Cholesky (diagonal-tile POTRF, TRSM of the rows below, trailing update),
+//      batched over the level;
+//   2. compressed supernodes of the level build their hierarchical diagonal
+//      blocks (Alg. 6 for leaves, Alg. 5 + adaptive range finder for the others)
+//      and their off-diagonal low-rank blocks (Alg. 2, 3), one supernode at a time;
+//   3. every supernode of the level pushes its Schur update
+//      L^O_k L^O_k^T (or V_k V_k^T) into its ancestors' dense storage (the
+//      extend-add of Eqs. "schurDiag"/"schurOffDiag", Alg. 1) with atomic adds.
+// The uncompressed target of supernode j therefore holds U^D_j and U^O_j of Alg. 1
+// when step 1 reaches it; compressed targets only receive the entries of their
+// dense diagonal storage, the rest is applied implicitly by Alg. 2 / Alg. 5.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace rsc {
+
+#define CK(x)                                                                                    \
+    do {                                                                                         \
+        cudaError_t e_ = (x);                                                                    \
+        if (e_ != cudaSuccess)                                                                   \
+            throw Error(e_ == cudaErrorMemoryAllocation ? RSC_ERR_OOM : RSC_ERR_CUDA,             \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+#define LAUNCH_CHECK() CK(cudaGetLastError())
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ device memory
+class DeviceMem {
+public:
+    ~DeviceMem() { release(); }
+    void* alloc(size_t bytes) {
+        void* p = nullptr;
+        if (bytes == 0) bytes = 16;
+        CK(cudaMalloc(&p, bytes));
+        ptrs_.push_back(p);
+        total_ += bytes;
+        return p;
+    }
+    template <class X> X* upload(const std::vector<X>& v, cudaStream_t s) {
+        X* p = (X*)alloc(sizeof(X) * std::max<size_t>(v.size(), 1));
+        if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, s));
+        return p;
+    }
+    void release() {
+        for (void* p : ptrs_) cudaFree(p);
+        ptrs_.clear();
+        total_ = 0;
+    }
+    size_t total() const { return total_; }
+
+private:
+    std::vector<void*> ptrs_;
+    size_t total_ = 0;
+};
+
+// growable device scratch
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~Scratch() { if (p) cudaFree(p); }
+    void* get(size_t b) {
+        if (b > bytes) {
+            if (p) CK(cudaFree(p));
+            p = nullptr;
+            size_t nb = std::max(b, bytes * 3 / 2);
+            CK(cudaMalloc(&p, nb));
+            bytes = nb;
+        }
+        return p;
+    }
+};
+
+// ------------------------------------------------------------------ engine base
+struct EngineImpl {
+    virtual ~EngineImpl() = default;
+    virtual rsc_status factor(const double* val, double tol) = 0;
+    virtual bool factored() const = 0;
+    virtual void apply(const double* d_r, double* d_z, cudaStream_t s) = 0;
+    virtual void node_info(int j, int32_t* info) const = 0;
+    virtual rsc_status node_blocks(int j, double* LD, double* LO) = 0;
+    virtual void stats(rsc_stats_t* out) const = 0;
+    // PCG state shared by every precision
+    rsc_status pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
+                   const double* d_b, double* d_x, double rtol, int max_iter, int* iters, double* relres,
+                   cudaStream_t s);
+    cudaStream_t stream = nullptr;
+    DeviceMem amem;   // matrix for SpMV
+    int* d_rp32 = nullptr;   // unused placeholder
+    long long* d_rp = nullptr;
+    int32_t* d_ci = nullptr;
+    double* d_val = nullptr;
+    bool a_uploaded = false;
+    std::vector<double> a_val_cache;
+    Scratch pcg_vec, red;
+    double solve_seconds = 0.0;
+    int last_iters = 0;
+    double last_relres = 0.0;
+    long long launches = 0;
+};
+
+// ------------------------------------------------------------------ PCG vector kernels (FP64)
+__global__ void k_spmv(long long n, const long long* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
+    // 8 lanes per row
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long row = t >> 3;
+    int sub = threadIdx.x & 7;
+    double s = 0.0;
+    if (row < n) {
+        for (long long e = rp[row] + sub; e < rp[row + 1]; e += 8) s = fma(v[e], x[ci[e]], s);
+    }
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (row < n && sub == 0) y[row] = s;
+}
+
+// deterministic dot: per-block partials, then one block sums them in order
+__global__ void k_dot_partial(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                              double* __restrict__ part) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s = fma(a[i], b[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void k_dot_final(int nparts, const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double ws[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    ws[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) ws[threadIdx.x] += ws[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = ws[0];
+}
+// y = a*x + b*y
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+// y = x - y (residual from A x)
+__global__ void k_xmy(long long n, const double* __restrict__ x, double* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i] - y[i];
+}
+
+static constexpr int DOT_BLOCKS = 304;
+
+rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                           const std::vector<double>& val, const double* d_b, double* d_x, double rtol, int max_iter,
+                           int* iters_out, double* relres_out, cudaStream_t s) {
+    const long long n = (long long)rp.size() - 1;
+    if (!a_uploaded || a_val_cache != val) {
+        amem.release();
+        d_rp = (long long*)amem.alloc(sizeof(long long) * (n + 1));
+        CK(cudaMemcpyAsync(d_rp, rp.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, s));
+        d_ci = (int32_t*)amem.alloc(sizeof(int32_t) * ci.size());
+        CK(cudaMemcpyAsync(d_ci, ci.data(), sizeof(int32_t) * ci.size(), cudaMemcpyHostToDevice, s));
+        d_val = (double*)amem.alloc(sizeof(double) * val.size());
+        CK(cudaMemcpyAsync(d_val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, s));
+        a_val_cache = val;
+        a_uploaded = true;
+    }
+    double* V = (double*)pcg_vec.get(sizeof(double) * 5 * n);
+    double *r = V, *z = V + n, *p = V + 2 * n, *q = V + 3 * n, *t = V + 4 * n;
+    double* part = (double*)red.get(sizeof(double) * (DOT_BLOCKS + 8));
+    double* scal = part + DOT_BLOCKS;
+    double h_s[4];
+    auto dot = [&](const double* a, const double* b) -> double {
+        k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(n, a, b, part);
+        k_dot_final<<<1, 256, 0, s>>>(DOT_BLOCKS, part, scal);
+        launches += 2;
+        CK(cudaMemcpyAsync(h_s, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return h_s[0];
+    };
+    const int vb = (int)std::min<long long>(cdiv(n, 256), 4 * 152);
+    auto spmv = [&](const double* x, double* y) {
+        k_spmv<<<cdiv(n * 8, 256), 256, 0, s>>>(n, d_rp, d_ci, d_val, x, y);
+        launches++;
+    };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    CK(cudaMemsetAsync(d_x, 0, sizeof(double) * n, s));
+    CK(cudaMemcpyAsync(r, d_b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    const double nb = std::sqrt(dot(d_b, d_b));
+    rsc_status st = RSC_OK;
+    int it = 0;
+    double rel = 0.0;
+    if (nb == 0.0) {
+        rel = 0.0;
+    } else {
+        apply(r, z, s);
+        CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        double rz = dot(r, z);
+        bool done = false;
+        for (it = 1; it <= max_iter; ++it) {
+            spmv(p, q);
+            const double pq = dot(p, q);
+            const double alpha = rz / pq;
+            k_axpby<<<vb, 256, 0, s>>>(n, alpha, p, 1.0, d_x);
+            k_axpby<<<vb, 256, 0, s>>>(n, -alpha, q, 1.0, r);
+            launches += 2;
+            const double rn = std::sqrt(dot(r, r));
+            if (!std::isfinite(rn)) { st = RSC_ERR_NOT_SPD; break; }
+            if (rn / nb <= rtol) {
+                spmv(d_x, t);
+                k_xmy<<<vb, 256, 0, s>>>(n, d_b, t);
+                launches++;
+                rel = std::sqrt(dot(t, t)) / nb;
+                if (rel <= rtol) { done = true; break; }
+            }
+            apply(r, z, s);
+            const double rz_new = dot(r, z);
+            const double beta = rz_new / rz;
+            rz = rz_new;
+            k_axpby<<<vb, 256, 0, s>>>(n, 1.0, z, beta, p);
+            launches++;
+        }
+        if (!done) {
+            if (it > max_iter) it = max_iter;
+            spmv(d_x, t);
+            k_xmy<<<vb, 256, 0, s>>>(n, d_b, t);
+            launches++;
+            rel = std::sqrt(dot(t, t)) / nb;
+            if (st == RSC_OK) st = RSC_ERR_NO_CONVERGENCE;
+        }
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    solve_seconds = ms * 1e-3;
+    last_iters = it;
+    last_relres = rel;
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = rel;
+    return st;
+}
+
+// ------------------------------------------------------------------ typed engine
+template <class T>
+struct EngineT final : EngineImpl {
+    struct NodeRT {
+        int c = 0, r = 0;
+        long long c0 = 0;
+        bool compressed = false, hier = false;
+        long long off = -1;     // panel or dense-diagonal offset in the arena
+        int ld = 0;
+        std::vector<long long> leaf_off;   // by block label (leaves only)
+        int rank = 0;
+        T* V = nullptr;          // |R_j| x rank, column-major
+        T* U = nullptr;          // c x rank, column-major (ld c)
+        std::vector<int> brank;            // by label
+        std::vector<T*> bV, bU;
+        // sparse A blocks for the implicit products (compressed nodes)
+        CsrBlock aR{}, aC{};               // A(R_j, C_j) by R rows / by C rows (transposed)
+        std::vector<CsrBlock> bR, bC;      // per internal block: A(rows_s, cols_s) by rows / by cols
+        int32_t* tailpos = nullptr;        // per descendant: positions of R_k's tail rows inside R_j
+        std::vector<long long> tail_off;   // offset of descendant d's tail map inside tailpos
+    };
+
+    const Symbolic& S;
+    rsc_options o;
+    DeviceMem pmem;      // plan (per layout)
+    DeviceMem fmem;      // factor arena + low-rank storage
+    T* arena = nullptr;
+    long long arena_elems = 0;
+    T* lr_base = nullptr;
+    long long lr_cap = 0, lr_used = 0;
+    std::vector<NodeRT> nd;
+    bool plan_compress = false, plan_diag = false, have_plan = false;
+    bool is_factored = false;
+    double tol = 0.0, tol_D = 0.0;
+    int restarts = 0;
+    bool diag_on = false;
+    // device tables
+    int32_t* d_rows = nullptr;
+    long long* d_rows_ptr = nullptr;
+    int32_t* d_perm = nullptr;
+    NodeTgt* d_tgt = nullptr;
+    LeafMap* d_leaf = nullptr;
+    LoOp* d_lo = nullptr;
+    std::vector<LoOp> h_lo;
+    long long* d_asm_src = nullptr;
+    long long* d_asm_dst = nullptr;
+    long long asm_cnt = 0;
+    double* d_valbuf = nullptr;
+    int* d_status = nullptr;
+    double* d_norms = nullptr;     // [0] y1, [1] current
+    double* d_small = nullptr;     // gram (256) + rinv (256)
+    int* d_qstatus = nullptr;
+    // per level task lists
+    struct PanelStep { PotrfTask* potrf; int npotrf; TrsmTask* trsm; int ntrsm; GemmTask* gemm; int ngemm; };
+    std::vector<std::vector<PanelStep>> panel_steps;   // [level][step]
+    std::vector<PushTask*> push_tasks;
+    std::vector<int> push_count;
+    // sparse block values are gathered at factor time from these source indices
+    std::vector<long long> sp_src;     // concatenated value sources of all CsrBlocks
+    double* d_spval = nullptr;
+    // scratch
+    Scratch sG, sY, sUr, sVr, sX, sZ, sT, sTv, sTask, sTask2, sT2;
+    double flops = 0.0;
+    double factor_seconds = 0.0;
+    // solve scratch
+    Scratch sy, stmp;
+
+    EngineT(const Symbolic& S_, const rsc_options& o_) : S(S_), o(o_) {
+        CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+        nd.resize(S.M);
+    }
+    ~EngineT() override {
+        if (stream) cudaStreamDestroy(stream);
+    }
+
+    bool factored() const override { return is_factored; }
+
+    // ---------------------------------------------------------------- plan
+    void build_plan(bool compress, bool diag) {
+        pmem.release();
+        fmem.release();
+        have_plan = false;
+        const int M = S.M;
+        long long off = 0;
+        for (int j = 0; j < M; ++j) {
+            NodeRT& n = nd[j];
+            n = NodeRT();
+            n.c = S.ncols(j);
+            n.r = S.nrows(j);
+            n.c0 = S.sn_ptr[j];
+            n.compressed = compress && S.kind[j] == 1 && n.c >= o.tau_O;
+            n.hier = n.compressed && diag && S.tree[j].nblocks > 0;
+            if (!n.compressed) {
+                n.off = off;
+                n.ld = n.c + n.r;
+                off += (long long)n.ld * n.c;
+            } else if (!n.hier) {
+                n.off = off;
+                n.ld = n.c;
+                off += (long long)n.c * n.c;
+            } else {
+                const BlockTree& t = S.tree[j];
+                n.leaf_off.assign(t.nblocks + 1, -1);
+                for (int s = 1; s <= t.nblocks; ++s)
+                    if (t.leaf[s]) {
+                        long long sz = t.hi[s] - t.lo[s];
+                        n.leaf_off[s] = off;
+                        off += sz * sz;
+                    }
+                n.brank.assign(t.nblocks + 1, 0);
+                n.bV.assign(t.nblocks + 1, nullptr);
+                n.bU.assign(t.nblocks + 1, nullptr);
+            }
+        }
+        arena_elems = off;
+        arena = (T*)fmem.alloc(sizeof(T) * std::max<long long>(off, 1));
+        // low-rank storage bound: U (c x maxr) + V (r x maxr) per compressed block
+        long long lr = 0;
+        for (int j = 0; j < M; ++j) {
+            const NodeRT& n = nd[j];
+            if (!n.compressed) continue;
+            long long mr = std::min(n.c, n.r);
+            lr += (long long)(n.c + n.r) * mr + 64;
+            if (n.hier) {
+                const BlockTree& t = S.tree[j];
+                for (int s = 1; s <= t.nblocks; ++s)
+                    if (!t.leaf[s]) {
+                        long long a = t.hi[s] - t.mid[s], b = t.mid[s] - t.lo[s];
+                        lr += (a + b) * std::min(a, b) + 64;
+                    }
+            }
+        }
+        lr_cap = lr;
+        lr_base = (T*)fmem.alloc(sizeof(T) * std::max<long long>(lr, 1));
+
+        // device structure tables
+        d_rows = pmem.upload(S.rows, stream);
+        std::vector<long long> rptr(S.rows_ptr.begin(), S.rows_ptr.end());
+        d_rows_ptr = pmem.upload(rptr, stream);
+        d_perm = pmem.upload(S.perm, stream);
+        d_status = (int*)pmem.alloc(sizeof(int) * 4);
+        d_norms = (double*)pmem.alloc(sizeof(double) * 4);
+        d_small = (double*)pmem.alloc(sizeof(double) * 512);
+        d_qstatus = (int*)pmem.alloc(sizeof(int) * 4);
+
+        // targets and leaf maps
+        std::vector<NodeTgt> tg(M);
+        std::vector<LeafMap> lm(S.n, LeafMap{0, 0, 0, 0});
+        for (int j = 0; j < M; ++j) {
+            const NodeRT& n = nd[j];
+            NodeTgt t{};
+            t.c = n.c;
+            t.r = n.r;
+            t.c0 = n.c0;
+            t.rows_off = S.rows_ptr[j];
+            if (!n.compressed) { t.kind = 0; t.base = arena + n.off; t.ld = n.ld; }
+            else if (!n.hier) { t.kind = 1; t.base = arena + n.off; t.ld = n.c; }
+            else {
+                t.kind = 2;
+                t.base = nullptr;
+                t.ld = 0;
+                const BlockTree& bt = S.tree[j];
+                for (int s = 1; s <= bt.nblocks; ++s)
+                    if (bt.leaf[s])
+                        for (int q = bt.lo[s]; q < bt.hi[s]; ++q)
+                            lm[n.c0 + q] = LeafMap{n.c0 + bt.lo[s], n.leaf_off[s], bt.hi[s] - bt.lo[s], 0};
+            }
+            tg[j] = t;
+        }
+        d_tgt = pmem.upload(tg, stream);
+        d_leaf = pmem.upload(lm, stream);
+        h_lo.assign(M, LoOp{nullptr, 1, 0});
+        for (int j = 0; j < M; ++j)
+            if (!nd[j].compressed) h_lo[j] = LoOp{arena + nd[j].off + nd[j].c, nd[j].ld, nd[j].c};
+        d_lo = (LoOp*)pmem.alloc(sizeof(LoOp) * M);
+
+        // assembly map and sparse blocks
+        std::vector<long long> src, dst;
+        src.reserve(S.li.size());
+        dst.reserve(S.li.size());
+        sp_src.clear();
+        struct Coo { int r, c; long long s; };
+        std::vector<std::vector<Coo>> offA(M);
+        std::vector<std::vector<std::vector<Coo>>> blkA(M);
+        for (int j = 0; j < M; ++j)
+            if (nd[j].hier) blkA[j].assign(S.tree[j].nblocks + 1, {});
+        for (long long c = 0; c < S.n; ++c) {
+            const int j = S.snode_of[c];
+            const NodeRT& n = nd[j];
+            const int lc = (int)(c - n.c0);
+            const int32_t* Rj = S.R(j);
+            for (long long e = S.lp[c]; e < S.lp[c + 1]; ++e) {
+                const long long g = S.li[e];
+                const bool inC = g < n.c0 + n.c;
+                const int lr = inC ? (int)(g - n.c0) : (int)(std::lower_bound(Rj, Rj + n.r, (int32_t)g) - Rj);
+                if (!n.compressed) {
+                    src.push_back(S.lsrc[e]);
+                    dst.push_back(n.off + (inC ? lr : n.c + lr) + (long long)lc * n.ld);
+                } else if (!inC) {
+                    offA[j].push_back({lr, lc, S.lsrc[e]});
+                } else if (!n.hier) {
+                    src.push_back(S.lsrc[e]);
+                    dst.push_back(n.off + lr + (long long)lc * n.c);
+                } else {
+                    const BlockTree& bt = S.tree[j];
+                    int s = bt.root;
+                    while (!bt.leaf[s]) {
+                        if (lc < bt.mid[s] && lr >= bt.mid[s]) break;
+                        s = lr < bt.mid[s] ? bt.left[s] : bt.right[s];
+                    }
+                    if (bt.leaf[s]) {
+                        const long long sz = bt.hi[s] - bt.lo[s];
+                        src.push_back(S.lsrc[e]);
+                        dst.push_back(n.leaf_off[s] + (lr - bt.lo[s]) + (lc - bt.lo[s]) * sz);
+                    } else {
+                        blkA[j][s].push_back({lr - bt.mid[s], lc - bt.lo[s], S.lsrc[e]});
+                    }
+                }
+            }
+        }
+        asm_cnt = (long long)src.size();
+        d_asm_src = pmem.upload(src, stream);
+        d_asm_dst = pmem.upload(dst, stream);
+        d_valbuf = (double*)pmem.alloc(sizeof(double) * (S.lsrc.empty() ? 1 : (size_t)(*std::max_element(S.lsrc.begin(), S.lsrc.end()) + 1)));
+
+        // CSR blocks (two orientations); values gathered per factor via sp_src
+        std::vector<int32_t> sp_rp, sp_ci;
+        struct PendingBlk { int node, label, orient; long long rp_off, ci_off, v_off; int nrows; };
+        std::vector<PendingBlk> pend;
+        auto add_csr = [&](std::vector<Coo>& coo, int nrows, bool by_row, int node, int label) {
+            std::vector<int> cnt(nrows + 1, 0);
+            for (auto& x : coo) cnt[(by_row ? x.r : x.c) + 1]++;
+            for (int i = 0; i < nrows; ++i) cnt[i + 1] += cnt[i];
+            PendingBlk pb{node, label, by_row ? 0 : 1, (long long)sp_rp.size(), (long long)sp_ci.size(),
+                          (long long)sp_src.size(), nrows};
+            std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+            std::vector<int32_t> col(coo.size());
+            std::vector<long long> sv(coo.size());
+            // stable order: sort by (row, col)
+            std::vector<size_t> idx(coo.size());
+            std::iota(idx.begin(), idx.end(), 0);
+            std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+                int ra = by_row ? coo[a].r : coo[a].c, rb = by_row ? coo[b].r : coo[b].c;
+                int ca = by_row ? coo[a].c : coo[a].r, cb = by_row ? coo[b].c : coo[b].r;
+                return ra != rb ? ra < rb : ca < cb;
+            });
+            for (size_t t = 0; t < idx.size(); ++t) {
+                const Coo& x = coo[idx[t]];
+                col[t] = by_row ? x.c : x.r;
+                sv[t] = x.s;
+            }
+            sp_rp.insert(sp_rp.end(), cnt.begin(), cnt.end());
+            sp_ci.insert(sp_ci.end(), col.begin(), col.end());
+            sp_src.insert(sp_src.end(), sv.begin(), sv.end());
+            pend.push_back(pb);
+        };
+        for (int j = 0; j < M; ++j) {
+            NodeRT& n = nd[j];
+            if (!n.compressed) continue;
+            add_csr(offA[j], n.r, true, j, 0);
+            add_csr(offA[j], n.c, false, j, 0);
+            if (n.hier) {
+                const BlockTree& bt = S.tree[j];
+                n.bR.assign(bt.nblocks + 1, CsrBlock{});
+                n.bC.assign(bt.nblocks + 1, CsrBlock{});
+                for (int s = 1; s <= bt.nblocks; ++s)
+                    if (!bt.leaf[s]) {
+                        add_csr(blkA[j][s], bt.hi[s] - bt.mid[s], true, j, s);
+                        add_csr(blkA[j][s], bt.mid[s] - bt.lo[s], false, j, s);
+                    }
+            }
+        }
+        int32_t* d_sprp = pmem.upload(sp_rp, stream);
+        int32_t* d_spci = pmem.upload(sp_ci, stream);
+        d_spval = (double*)pmem.alloc(sizeof(double) * std::max<size_t>(sp_src.size(), 1));
+        for (auto& pb : pend) {
+            CsrBlock b{d_sprp + pb.rp_off, d_spci + pb.ci_off, d_spval + pb.v_off, pb.nrows, 0};
+            NodeRT& n = nd[pb.node];
+            if (pb.label == 0) (pb.orient == 0 ? n.aR : n.aC) = b;
+            else (pb.orient == 0 ? n.bR[pb.label] : n.bC[pb.label]) = b;
+        }
+
+        // tail maps for compressed nodes: positions of R_k[p1..] inside R_j
+        {
+            std::vector<int32_t> tails;
+            std::vector<std::pair<int, long long>> where;
+            for (int j = 0; j < M; ++j) {
+                NodeRT& n = nd[j];
+                if (!n.compressed) continue;
+                const int32_t* Rj = S.R(j);
+                n.tail_off.clear();
+                for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
+                    const int k = S.desc_k[d];
+                    const int32_t* Rk = S.R(k);
+                    n.tail_off.push_back((long long)tails.size());
+                    for (int p = S.desc_p1[d]; p < S.nrows(k); ++p)
+                        tails.push_back((int32_t)(std::lower_bound(Rj, Rj + n.r, Rk[p]) - Rj));
+                }
+            }
+            int32_t* d_tails = pmem.upload(tails, stream);
+            for (int j = 0; j < M; ++j)
+                if (nd[j].compressed) nd[j].tailpos = d_tails;
+        }
+
+        // panel factorization steps per level (uncompressed panels and dense diagonals)
+        panel_steps.assign(S.nlevels, {});
+        for (int l = 0; l < S.nlevels; ++l) {
+            std::vector<int> pan;
+            for (int j : S.level_nodes[l])
+                if (!nd[j].compressed || !nd[j].hier) pan.push_back(j);
+            int maxc = 0;
+            for (int j : pan) maxc = std::max(maxc, nd[j].c);
+            for (int t0 = 0; t0 < maxc; t0 += NB) {
+                std::vector<PotrfTask> pt;
+                std::vector<TrsmTask> tt;
+                std::vector<GemmTask> gt;
+                for (int j : pan) {
+                    const NodeRT& n = nd[j];
+                    if (t0 >= n.c) continue;
+                    const int nrows_tot = n.compressed ? n.c : n.c + n.r;
+                    append_panel_step(arena + n.off, n.ld, n.c, nrows_tot, t0, j, pt, tt, gt);
+                }
+                PanelStep ps{pmem.upload(pt, stream), (int)pt.size(), pmem.upload(tt, stream), (int)tt.size(),
+                             pmem.upload(gt, stream), (int)gt.size()};
+                panel_steps[l].push_back(ps);
+            }
+        }
+
+        // push tasks per level: sources k of the level, every ancestor run, 64x64 tiles
+        push_tasks.assign(S.nlevels, nullptr);
+        push_count.assign(S.nlevels, 0);
+        {
+            std::vector<std::vector<PushTask>> byl(S.nlevels);
+            for (int j = 0; j < M; ++j)
+                for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
+                    const int k = S.desc_k[d];
+                    const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+                    for (int pc = p0; pc < p1; pc += TILE)
+                        for (int pr = pc; pr < (nd[j].compressed ? p1 : rk); pr += TILE)
+                            byl[S.level[k]].push_back(
+                                PushTask{k, j, pr, std::min(pr + TILE, nd[j].compressed ? p1 : rk), pc,
+                                         std::min(pc + TILE, p1)});
+                }
+            for (int l = 0; l < S.nlevels; ++l) {
+                push_tasks[l] = pmem.upload(byl[l], stream);
+                push_count[l] = (int)byl[l].size();
+            }
+        }
+        CK(cudaStreamSynchronize(stream));
+        plan_compress = compress;
+        plan_diag = diag;
+        have_plan = true;
+    }
+
+    // one step of the blocked tall-panel Cholesky of panel P (nrows_tot x c, ld)
+    static void append_panel_step(T* P, int ld, int c, int nrows_tot, int t0, int node, std::vector<PotrfTask>& pt,
+                                  std::vector<TrsmTask>& tt, std::vector<GemmTask>& gt) {
+        const int nb = std::min(NB, c - t0);
+        T* D = P + t0 + (size_t)t0 * ld;
+        pt.push_back(PotrfTask{D, ld, nb, node});
+        for (int r0 = t0 + nb; r0 < nrows_tot; r0 += TILE)
+            tt.push_back(TrsmTask{D, P + r0 + (size_t)t0 * ld, ld, ld, nb, std::min(TILE, nrows_tot - r0)});
+        for (int c0 = t0 + nb; c0 < c; c0 += TILE) {
+            const int ncol = std::min(TILE, c - c0);
+            for (int r0 = c0; r0 < nrows_tot; r0 += TILE) {
+                GemmTask g{};
+                g.A = P + r0 + (size_t)t0 * ld;
+                g.B = P + c0 + (size_t)t0 * ld;
+                g.C = P + r0 + (size_t)c0 * ld;
+                g.lda = ld; g.ldb = ld; g.ldc = ld;
+                g.m = std::min(TILE, nrows_tot - r0);
+                g.n = ncol;
+                g.K = nb;
+                g.moff = r0 - c0;
+                g.lower = (r0 < c0 + ncol) ? 1 : 0;
+                gt.push_back(g);
+            }
+        }
+    }
+
+    // ---------------------------------------------------------------- launch helpers
+    void run_panel_steps(const std::vector<PanelStep>& steps) {
+        for (const PanelStep& ps : steps) {
+            if (ps.npotrf) { k_potrf_tile<T><<<ps.npotrf, 256, 0, stream>>>(ps.potrf, d_status); launches++; }
+            if (ps.ntrsm) { k_trsm_tile<T><<<ps.ntrsm, 256, 0, stream>>>(ps.trsm); launches++; }
+            if (ps.ngemm) { k_gemm_tile<T><<<ps.ngemm, 256, 0, stream>>>(ps.gemm); launches++; }
+            LAUNCH_CHECK();
+        }
+    }
+
+    // factor one dense panel (nrows_tot x c) outside the level batches
+    void factor_dense(T* P, int ld, int c, int nrows_tot, int node) {
+        for (int t0 = 0; t0 < c; t0 += NB) {
+            std::vector<PotrfTask> pt;
+            std::vector<TrsmTask> tt;
+            std::vector<GemmTask> gt;
+            append_panel_step(P, ld, c, nrows_tot, t0, node, pt, tt, gt);
+            PotrfTask* dp = (PotrfTask*)upload_tmp(sTask, pt);
+            k_potrf_tile<T><<<(int)pt.size(), 256, 0, stream>>>(dp, d_status);
+            launches++;
+            if (!tt.empty()) {
+                TrsmTask* dt = (TrsmTask*)upload_tmp(sTask2, tt);
+                k_trsm_tile<T><<<(int)tt.size(), 256, 0, stream>>>(dt);
+                launches++;
+            }
+            if (!gt.empty()) {
+                GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
+                k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg);
+                launches++;
+            }
+            LAUNCH_CHECK();
+            flops += (double)nb_flops(c, nrows_tot, t0);
+        }
+    }
+    static double nb_flops(int c, int nrows_tot, int t0) {
+        const double nb = std::min(NB, c - t0);
+        const double below = nrows_tot - t0 - nb;
+        const double trail = c - t0 - nb;
+        return nb * nb * nb / 3.0 + below * nb * nb + 2.0 * nb * (trail * (below - trail) + trail * (trail + 1) / 2.0);
+    }
+
+    template <class X> void* upload_tmp(Scratch& sc, const std::vector<X>& v) {
+        void* p = sc.get(sizeof(X) * std::max<size_t>(v.size(), 1));
+        if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, stream));
+        // the staging buffer is reused by the next call: make the copy complete first
+        CK(cudaStreamSynchronize(stream));
+        return p;
+    }
+
+    // TN tasks are split here into 8-column chunks (one column per warp)
+    static std::vector<TnTask> expand_tn(const std::vector<TnTask>& tasks) {
+        std::vector<TnTask> ch;
+        for (const auto& t : tasks)
+            for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; ch.push_back(c); }
+        return ch;
+    }
+    void launch_tn(std::vector<TnTask>& tasks, const T* Y, int ldy, int N) {
+        std::vector<TnTask> ch = expand_tn(tasks);
+        if (ch.empty()) return;
+        TnTask* d = (TnTask*)upload_tmp(sTask, ch);
+        dim3 grid((unsigned)ch.size(), (unsigned)cdiv(N, 16));
+        k_tn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N);
+        launches++;
+        LAUNCH_CHECK();
+        for (auto& t : tasks) flops += 2.0 * t.nrow * t.K * N;
+    }
+    // NN tasks are given per descendant and split here into 64-row chunks
+    void launch_nn(std::vector<NnTask>& tasks, T* Y, int ldy, int N, T alpha, bool atomic) {
+        std::vector<NnTask> ch;
+        for (auto& t : tasks) {
+            if (t.K == 0 || t.nrow == 0) continue;
+            for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; ch.push_back(c); }
+            flops += 2.0 * t.nrow * t.K * N;
+        }
+        if (ch.empty()) return;
+        NnTask* d = (NnTask*)upload_tmp(sTask2, ch);
+        dim3 grid((unsigned)ch.size(), (unsigned)cdiv(N, 16));
+        k_nn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N, alpha, atomic ? 1 : 0);
+        launches++;
+        LAUNCH_CHECK();
+    }
+    void csr_mm(const CsrBlock& b, const T* X, int ldx, T* Y, int ldy, int N, T alpha, bool acc) {
+        if (b.nrows == 0) return;
+        dim3 grid((unsigned)std::min(cdiv((long long)b.nrows * 16, 256), 4096), (unsigned)cdiv(N, 16));
+        k_csr_mm<T><<<grid, 256, 0, stream>>>(b, X, ldx, Y, ldy, N, alpha, acc ? 1 : 0);
+        launches++;
+        LAUNCH_CHECK();
+    }
+    void fill(T* X, long long cnt, T v) {
+        if (cnt <= 0) return;
+        k_fill<T><<<std::min(cdiv(cnt, 256), 4096), 256, 0, stream>>>(X, cnt, v);
+        launches++;
+    }
+    void axpy_rows(const T* X, int ldx, T* Y, int ldy, int m, int nc, T alpha) {
+        if (m <= 0) return;
+        k_axpy_rows<T><<<std::min(cdiv((long long)m * nc, 256), 4096), 256, 0, stream>>>(X, ldx, Y, ldy, m, nc, alpha);
+        launches++;
+    }
+    // copy a row-major block (m x nc, ld ldx) into column-major storage (ld ldu) at column col0
+    void rows_to_cols_ld(const T* X, int ldx, int m, int nc, T* U, int ldu, int col0);
+
+    // ---------------------------------------------------------------- dense / hierarchical triangular solves
+    // X (c x N row-major, ld ldx) <- L^{-1} X or L^{-T} X for dense lower L (ld)
+    void dense_solve(const T* L, int ld, int c, T* X, int ldx, int N, bool transpose) {
+        if (c == 0) return;
+        if (c <= SOLVE_MAX) {
+            std::vector<TrsvTask> tv{TrsvTask{L, ld, c, 0, X, ldx, 0}};
+            TrsvTask* d = (TrsvTask*)upload_tmp(sTv, tv);
+            dim3 grid(1, (unsigned)cdiv(N, 16));
+            k_trsv_multi<T><<<grid, 256, 0, stream>>>(d, N, transpose ? 1 : 0);
+            launches++;
+            LAUNCH_CHECK();
+            flops += (double)c * c * N;
+            return;
+        }
+        const int bs = SOLVE_MAX;
+        if (!transpose) {
+            for (int b0 = 0; b0 < c; b0 += bs) {
+                const int b1 = std::min(c, b0 + bs);
+                dense_solve(L + b0 + (size_t)b0 * ld, ld, b1 - b0, X + (size_t)b0 * ldx, ldx, N, false);
+                if (b1 < c) {
+                    std::vector<NnTask> nn{NnTask{L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, 0, nullptr, 0,
+                                                  X + (size_t)b0 * ldx, ldx, 0}};
+                    launch_nn(nn, X + (size_t)b1 * ldx, ldx, N, T(-1), false);
+                }
+            }
+        } else {
+            const int nblk = cdiv(c, bs);
+            for (int bi = nblk - 1; bi >= 0; --bi) {
+                const int b0 = bi * bs, b1 = std::min(c, b0 + bs);
+                dense_solve(L + b0 + (size_t)b0 * ld, ld, b1 - b0, X + (size_t)b0 * ldx, ldx, N, true);
+                if (b0 > 0) {
+                    T* Z = (T*)sZ.get(sizeof(T) * (size_t)b0 * N);
+                    std::vector<TnTask> tn{TnTask{L + b0, ld, b0, b1 - b0, nullptr, 0, nullptr, 0, Z, N, 0}};
+                    launch_tn(tn, X + (size_t)b0 * ldx, ldx, N);
+                    axpy_rows(Z, N, X, ldx, b0, N, T(-1));
+                }
+            }
+        }
+    }
+
+    // Alg. 4 (branches in the corrected order): solve with the subtree of L^D_j rooted at s.
+    // X holds the rows of the subtree's range, row-major (ld ldx), N columns.
+    void diag_solve(int j, int s, T* X, int ldx, int N, bool transpose) {
+        const NodeRT& n = nd[j];
+        if (!n.hier) {
+            dense_solve(arena + n.off, n.ld, n.c, X, ldx, N, transpose);
+            return;
+        }
+        const BlockTree& t = S.tree[j];
+        if (s == 0) s = t.root;
+        if (t.leaf[s]) {
+            const int sz = t.hi[s] - t.lo[s];
+            dense_solve(arena + n.leaf_off[s], sz, sz, X, ldx, N, transpose);
+            return;
+        }
+        const int n1 = t.mid[s] - t.lo[s], n2 = t.hi[s] - t.mid[s];
+        T* X1 = X;
+        T* X2 = X + (size_t)n1 * ldx;
+        const int q = n.brank[s];
+        if (!transpose) {
+            diag_solve(j, t.left[s], X1, ldx, N, false);
+            if (q) {   // X2 -= V_s (U_s^T X1)
+                T* Z = (T*)sZ.get(sizeof(T) * (size_t)q * N);
+                std::vector<TnTask> tn{TnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, 0, Z, N, 0}};
+                launch_tn(tn, X1, ldx, N);
+                std::vector<NnTask> nn{NnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, 0, Z, N, 0}};
+                launch_nn(nn, X2, ldx, N, T(-1), false);
+            }
+            diag_solve(j, t.right[s], X2, ldx, N, false);
+        } else {
+            diag_solve(j, t.right[s], X2, ldx, N, true);
+            if (q) {   // X1 -= U_s (V_s^T X2)
+                T* Z = (T*)sZ.get(sizeof(T) * (size_t)q * N);
+                std::vector<TnTask> tn{TnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, 0, Z, N, 0}};
+                launch_tn(tn, X2, ldx, N);
+                std::vector<NnTask> nn{NnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, 0, Z, N, 0}};
+                launch_nn(nn, X1, ldx, N, T(-1), false);
+            }
+            diag_solve(j, t.left[s], X1, ldx, N, true);
+        }
+    }
+
+    // ---------------------------------------------------------------- implicit products
+    // descendant k's operand rows (L^O_k or V_k)
+    const LoOp& lo(int k) const { return h_lo[k]; }
+
+    // Alg. 2 transposed: W (c x N) = (L^O_j)^T G, G (r x N); all row-major ld N.
+    void offdiag_T(int j, const T* G, int N, T* W) {
+        const NodeRT& n = nd[j];
+        csr_mm(n.aC, G, N, W, N, N, T(1), false);
+        std::vector<TnTask> tn;
+        std::vector<NnTask> nn;
+        long long zoff = 0;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
+            const int k = S.desc_k[d];
+            const LoOp& op = lo(k);
+            const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+            if (op.K == 0) continue;
+            zoff += (long long)op.K * N;
+        }
+        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
+        zoff = 0;
+        int di = 0;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
+            const int k = S.desc_k[d];
+            const LoOp& op = lo(k);
+            const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+            if (op.K == 0) continue;
+            T* Z = Zb + zoff;
+            zoff += (long long)op.K * N;
+            // T_k = L^O_k(R^O)^T gatherRows(G, R_j, R^O)
+            if (rk > p1)
+                tn.push_back(TnTask{op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, Z, N, 0});
+            else
+                fill(Z, (long long)op.K * N, T(0));
+            // W -= scatterRows(L^O_k(R^D) T_k, R^D, C_j)
+            nn.push_back(NnTask{op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0,
+                                (int)-n.c0, Z, N, 0});
+        }
+        launch_tn(tn, G, N, N);
+        launch_nn(nn, W, N, N, T(-1), true);
+        diag_solve(j, 0, W, N, N, false);
+    }
+
+    // Alg. 2: W (r x N) = L^O_j X, X (c x N); X is left unchanged.
+    void offdiag(int j, const T* X, int N, T* W) {
+        const NodeRT& n = nd[j];
+        T* Xp = (T*)sX.get(sizeof(T) * (size_t)n.c * N);
+        CK(cudaMemcpyAsync(Xp, X, sizeof(T) * (size_t)n.c * N, cudaMemcpyDeviceToDevice, stream));
+        diag_solve(j, 0, Xp, N, N, true);
+        csr_mm(n.aR, Xp, N, W, N, N, T(1), false);
+        long long zoff = 0;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) zoff += (long long)lo(S.desc_k[d]).K * N;
+        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
+        zoff = 0;
+        std::vector<TnTask> tn;
+        std::vector<NnTask> nn;
+        int di = 0;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
+            const int k = S.desc_k[d];
+            const LoOp& op = lo(k);
+            const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+            if (op.K == 0) continue;
+            T* Z = Zb + zoff;
+            zoff += (long long)op.K * N;
+            // T_k = L^O_k(R^D)^T gatherRows(X', C_j, R^D)
+            tn.push_back(TnTask{op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0, (int)-n.c0, Z,
+                                N, 0});
+            // W -= scatterRows(L^O_k(R^O) T_k, R^O, R_j)
+            if (rk > p1) nn.push_back(NnTask{op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, Z, N, 0});
+        }
+        launch_tn(tn, Xp, N, N);
+        launch_nn(nn, W, N, N, T(-1), true);
+    }
+
+    // descendant rows of R_k inside the global range [g0, g1) (a sub-run of the C_j run)
+    void run_in(int d, long long g0, long long g1, int& a, int& b) const {
+        const int k = S.desc_k[d];
+        const int32_t* Rk = S.R(k);
+        const int p0 = S.desc_p0[d], p1 = S.desc_p1[d];
+        a = (int)(std::lower_bound(Rk + p0, Rk + p1, (int32_t)g0) - Rk);
+        b = (int)(std::lower_bound(Rk + p0, Rk + p1, (int32_t)g1) - Rk);
+    }
+
+    // Alg. 5: W (|rows_s| x N) = L^D_{j,s} X, X (|cols_s| x N).
+    void diag_mult(int j, int s, const T* X, int N, T* W) {
+        const NodeRT& n = nd[j];
+        const BlockTree& t = S.tree[j];
+        const int r0 = t.mid[s], r1 = t.hi[s], q0 = t.lo[s], q1 = t.mid[s];
+        T* Xp = (T*)sX.get(sizeof(T) * (size_t)(q1 - q0) * N);
+        CK(cudaMemcpyAsync(Xp, X, sizeof(T) * (size_t)(q1 - q0) * N, cudaMemcpyDeviceToDevice, stream));
+        diag_solve(j, t.left[s], Xp, N, N, true);
+        csr_mm(n.bR[s], Xp, N, W, N, N, T(1), false);
+        std::vector<TnTask> tn;
+        std::vector<NnTask> nn;
+        long long zoff = 0;
+        std::vector<int> A0, A1, B0, B1;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
+            int a, b, c, e;
+            run_in((int)d, n.c0 + r0, n.c0 + r1, a, b);
+            run_in((int)d, n.c0 + q0, n.c0 + q1, c, e);
+            A0.push_back(a); A1.push_back(b); B0.push_back(c); B1.push_back(e);
+            if (a < b && c < e) zoff += (long long)lo(S.desc_k[d]).K * N;
+        }
+        for (int p = t.parent[s]; p; p = t.parent[p])
+            if (p < s) zoff += (long long)n.brank[p] * N;
+        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
+        zoff = 0;
+        int di = 0;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
+            const int k = S.desc_k[d];
+            const LoOp& op = lo(k);
+            if (op.K == 0 || A0[di] >= A1[di] || B0[di] >= B1[di]) continue;
+            T* Z = Zb + zoff;
+            zoff += (long long)op.K * N;
+            tn.push_back(TnTask{op.base, op.ld, op.K, B1[di] - B0[di], nullptr, B0[di], d_rows + S.rows_ptr[k] + B0[di],
+                                (int)-(n.c0 + q0), Z, N, 0});
+            nn.push_back(NnTask{op.base, op.ld, op.K, A1[di] - A0[di], nullptr, A0[di], d_rows + S.rows_ptr[k] + A0[di],
+                                (int)-(n.c0 + r0), Z, N, 0});
+        }
+        // earlier blocks p < s on the path to the root (Uprod = U_p^T U_p = I)
+        for (int p = t.parent[s]; p; p = t.parent[p]) {
+            if (p > s || n.brank[p] == 0) continue;
+            T* Z = Zb + zoff;
+            zoff += (long long)n.brank[p] * N;
+            const int pr0 = t.mid[p], mp = t.hi[p] - t.mid[p];
+            tn.push_back(TnTask{n.bV[p], mp, n.brank[p], q1 - q0, nullptr, q0 - pr0, nullptr, 0, Z, N, 0});
+            nn.push_back(NnTask{n.bV[p], mp, n.brank[p], r1 - r0, nullptr, r0 - pr0, nullptr, 0, Z, N, 0});
+        }
+        launch_tn(tn, Xp, N, N);
+        launch_nn(nn, W, N, N, T(-1), true);
+    }
+
+    // Alg. 5 transposed: W (|cols_s| x N) = (L^D_{j,s})^T G, G (|rows_s| x N).
+    void diag_mult_T(int j, int s, const T* G, int N, T* W) {
+        const NodeRT& n = nd[j];
+        const BlockTree& t = S.tree[j];
+        const int r0 = t.mid[s], r1 = t.hi[s], q0 = t.lo[s], q1 = t.mid[s];
+        csr_mm(n.bC[s], G, N, W, N, N, T(1), false);
+        std::vector<TnTask> tn;
+        std::vector<NnTask> nn;
+        long long zoff = 0;
+        std::vector<int> A0, A1, B0, B1;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
+            int a, b, c, e;
+            run_in((int)d, n.c0 + r0, n.c0 + r1, a, b);
+            run_in((int)d, n.c0 + q0, n.c0 + q1, c, e);
+            A0.push_back(a); A1.push_back(b); B0.push_back(c); B1.push_back(e);
+            if (a < b && c < e) zoff += (long long)lo(S.desc_k[d]).K * N;
+        }
+        for (int p = t.parent[s]; p; p = t.parent[p])
+            if (p < s) zoff += (long long)n.brank[p] * N;
+        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
+        zoff = 0;
+        int di = 0;
+        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
+            const int k = S.desc_k[d];
+            const LoOp& op = lo(k);
+            if (op.K == 0 || A0[di] >= A1[di] || B0[di] >= B1[di]) continue;
+            T* Z = Zb + zoff;
+            zoff += (long long)op.K * N;
+            tn.push_back(TnTask{op.base, op.ld, op.K, A1[di] - A0[di], nullptr, A0[di], d_rows + S.rows_ptr[k] + A0[di],
+                                (int)-(n.c0 + r0), Z, N, 0});
+            nn.push_back(NnTask{op.base, op.ld, op.K, B1[di] - B0[di], nullptr, B0[di], d_rows + S.rows_ptr[k] + B0[di],
+                                (int)-(n.c0 + q0), Z, N, 0});
+        }
+        for (int p = t.parent[s]; p; p = t.parent[p]) {
+            if (p > s || n.brank[p] == 0) continue;
+            T* Z = Zb + zoff;
+            zoff += (long long)n.brank[p] * N;
+            const int pr0 = t.mid[p], mp = t.hi[p] - t.mid[p];
+            tn.push_back(TnTask{n.bV[p], mp, n.brank[p], r1 - r0, nullptr, r0 - pr0, nullptr, 0, Z, N, 0});
+            nn.push_back(NnTask{n.bV[p], mp, n.brank[p], q1 - q0, nullptr, q0 - pr0, nullptr, 0, Z, N, 0});
+        }
+        launch_tn(tn, G, N, N);
+        launch_nn(nn, W, N, N, T(-1), true);
+        diag_solve(j, t.left[s], W, N, N, false);
+    }
+
+    // ---------------------------------------------------------------- adaptive range finder (Alg. 3)
+    T* lr_alloc(long long elems) {
+        if (lr_used + elems > lr_cap) throw Error(RSC_ERR_OOM, "low-rank storage exhausted");
+        T* p = lr_base + lr_used;
+        lr_used += (elems + 31) / 32 * 32;
+        return p;
+    }
+
+    double read_norm2(const T* X, int ld, int m, int nc, int slot) {
+        CK(cudaMemsetAsync(d_norms + slot, 0, sizeof(double), stream));
+        if (m > 0) {
+            k_sqnorm<T><<<std::min(cdiv((long long)m * nc, 256), 1024), 256, 0, stream>>>(X, ld, m, nc, d_norms + slot);
+            launches++;
+        }
+        return 0.0;
+    }
+
+    // Cholesky QR of the row-major block Y (m x b, ld 16), optionally shifted; a failed
+    // factorization sets d_qstatus
+    void cholqr(T* Y, int m, int b, bool shifted) {
+        const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double coef = shifted ? 11.0 * ((double)m * b + (double)b * (b + 1)) * u : 0.0;
+        CK(cudaMemsetAsync(d_small, 0, sizeof(double) * 256, stream));
+        k_gram<T><<<cdiv(m, 256), 256, 0, stream>>>(Y, m, b, d_small);
+        k_chol_small<<<1, 32, 0, stream>>>(d_small, b, coef, d_small + 256, d_qstatus);
+        k_apply_rinv<T><<<cdiv(m, 128), 128, 0, stream>>>(Y, m, b, d_small + 256);
+        launches += 3;
+        LAUNCH_CHECK();
+        flops += 2.0 * m * b * b + (double)m * b * b;
+    }
+
+    // project Y (c x 16 row-major) against U (c x rank column-major, ld c): Y -= U (U^T Y)
+    void project(const T* U, int c, int rank, T* Y) {
+        if (rank == 0) return;
+        T* Z = (T*)sZ.get(sizeof(T) * (size_t)rank * 16);
+        std::vector<TnTask> tn{TnTask{U, c, rank, c, nullptr, 0, nullptr, 0, Z, 16, 0}};
+        launch_tn(tn, Y, 16, 16);
+        std::vector<NnTask> nn{NnTask{U, c, rank, c, nullptr, 0, nullptr, 0, Z, 16, 0}};
+        launch_nn(nn, Y, 16, 16, T(-1), false);
+    }
+
+    template <class MultT, class Mult>
+    void range_finder(int m, int c, double tolr, uint32_t block_id, MultT&& mult_T, Mult&& mult, T*& Vout, T*& Uout,
+                      int& rank) {
+        const int maxr = std::min(m, c);
+        rank = 0;
+        Vout = Uout = nullptr;
+        if (maxr == 0) return;
+        T* U = lr_alloc((long long)c * maxr);
+        T* G = (T*)sG.get(sizeof(T) * (size_t)std::max(m, c) * 16);
+        T* Y = (T*)sY.get(sizeof(T) * (size_t)std::max(m, c) * 16);
+        double y1 = -1.0;
+        for (int t = 0; rank < maxr; ++t) {
+            const uint32_t word3 = (uint32_t)t | ((uint32_t)restarts << 16);
+            k_gauss<T><<<cdiv((long long)m * 8, 256), 256, 0, stream>>>(G, m, o.seed, block_id, word3);
+            launches++;
+            mult_T(G, 16, Y);
+            for (int q = 0; q < o.power_iters; ++q) {
+                mult(Y, 16, G);
+                mult_T(G, 16, Y);
+            }
+            if (t == 0) read_norm2(Y, 16, c, 16, 0);
+            project(U, c, rank, Y);
+            project(U, c, rank, Y);
+            read_norm2(Y, 16, c, 16, 1);
+            double h[2];
+            CK(cudaMemcpyAsync(h, d_norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, stream));
+            CK(cudaStreamSynchronize(stream));
+            if (t == 0) y1 = std::sqrt(h[0]);
+            const double nrm = std::sqrt(h[1]);
+            if (!std::isfinite(nrm) || !std::isfinite(y1)) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
+            if (nrm <= tolr * y1) break;
+            const int b = std::min(16, maxr - rank);
+            // makeOrthonormal: shifted Cholesky QR, re-projection against U, then two
+            // Cholesky QR passes (shifted CholeskyQR3: stable up to cond ~ 1/u)
+            CK(cudaMemsetAsync(d_qstatus, 0, sizeof(int), stream));
+            cholqr(Y, c, b, true);
+            project(U, c, rank, Y);
+            cholqr(Y, c, b, false);
+            cholqr(Y, c, b, false);
+            int qs = 0;
+            CK(cudaMemcpyAsync(&qs, d_qstatus, sizeof(int), cudaMemcpyDeviceToHost, stream));
+            CK(cudaStreamSynchronize(stream));
+            if (qs) break;   // the remaining sample is numerically rank deficient
+            rows_to_cols_ld(Y, 16, c, b, U, c, rank);
+            rank += b;
+        }
+        Uout = U;
+        if (rank == 0) return;
+        // V = mult(U): U in row-major form first
+        T* Ur = (T*)sUr.get(sizeof(T) * (size_t)c * rank);
+        cols_to_rows(U, c, c, rank, Ur);
+        T* Vr = (T*)sVr.get(sizeof(T) * (size_t)m * rank);
+        mult(Ur, rank, Vr);
+        Vout = lr_alloc((long long)m * rank);
+        rows_to_cols_ld(Vr, rank, m, rank, Vout, m, 0);
+    }
+
+    void cols_to_rows(const T* U, int ldu, int m, int nc, T* Xr);
+
+    // ---------------------------------------------------------------- compressed supernode
+    void compressed_node(int j) {
+        NodeRT& n = nd[j];
+        if (n.hier) {
+            const BlockTree& t = S.tree[j];
+            for (int s = 1; s <= t.nblocks; ++s) {
+                if (t.leaf[s]) {
+                    // Alg. 6: subtract earlier low-rank blocks p < s, then Cholesky
+                    const int sz = t.hi[s] - t.lo[s];
+                    T* Ls = arena + n.leaf_off[s];
+                    for (int p = t.parent[s]; p; p = t.parent[p]) {
+                        if (p > s || n.brank[p] == 0) continue;
+                        std::vector<GemmTask> gt;
+                        const int mp = t.hi[p] - t.mid[p];
+                        const T* Vp = n.bV[p] + (t.lo[s] - t.mid[p]);
+                        for (int c0 = 0; c0 < sz; c0 += TILE)
+                            for (int r0 = c0; r0 < sz; r0 += TILE) {
+                                GemmTask g{};
+                                g.A = Vp + r0; g.B = Vp + c0; g.C = Ls + r0 + (size_t)c0 * sz;
+                                g.lda = mp; g.ldb = mp; g.ldc = sz;
+                                g.m = std::min(TILE, sz - r0); g.n = std::min(TILE, sz - c0);
+                                g.K = n.brank[p]; g.moff = r0 - c0; g.lower = r0 == c0;
+                                gt.push_back(g);
+                            }
+                        flops += (double)sz * (sz + 1) * n.brank[p];
+                        GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
+                        k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg);
+                        launches++;
+                        LAUNCH_CHECK();
+                    }
+                    factor_dense(Ls, sz, sz, sz, j);
+                } else {
+                    const int rs = t.hi[s] - t.mid[s], cs = t.mid[s] - t.lo[s];
+                    T *V, *U;
+                    int q;
+                    range_finder(
+                        rs, cs, tol_D, ((uint32_t)j << 12) | (uint32_t)s,
+                        [&](const T* G, int N, T* W) { diag_mult_T(j, s, G, N, W); },
+                        [&](const T* X, int N, T* W) { diag_mult(j, s, X, N, W); }, V, U, q);
+                    n.bV[s] = V;
+                    n.bU[s] = U;
+                    n.brank[s] = q;
+                }
+                check_status();
+            }
+        }
+        if (n.r > 0) {
+            T *V, *U;
+            int q;
+            range_finder(
+                n.r, n.c, tol, (uint32_t)j << 12,
+                [&](const T* G, int N, T* W) { offdiag_T(j, G, N, W); },
+                [&](const T* X, int N, T* W) { offdiag(j, X, N, W); }, V, U, q);
+            n.V = V;
+            n.U = U;
+            n.rank = q;
+        }
+        h_lo[j] = LoOp{n.V, std::max(n.r, 1), n.rank};
+    }
+
+    void check_status() {
+        int st = 0;
+        CK(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CK(cudaStreamSynchronize(stream));
+        if (st) throw Error(RSC_ERR_NOT_SPD, "indefinite diagonal block in supernode " + std::to_string(st - 1));
+    }
+
+    // ---------------------------------------------------------------- factor
+    void run_once(const double* val) {
+        lr_used = 0;
+        flops = 0.0;
+        CK(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+        CK(cudaMemsetAsync(arena, 0, sizeof(T) * std::max<long long>(arena_elems, 1), stream));
+        const size_t nval = (size_t)(S.lsrc.empty() ? 0 : *std::max_element(S.lsrc.begin(), S.lsrc.end()) + 1);
+        CK(cudaMemcpyAsync(d_valbuf, val, sizeof(double) * nval, cudaMemcpyHostToDevice, stream));
+        if (asm_cnt) {
+            k_assemble<T><<<std::min(cdiv(asm_cnt, 256), 8192), 256, 0, stream>>>(d_valbuf, d_asm_src, d_asm_dst, asm_cnt,
+                                                                                   arena);
+            launches++;
+        }
+        {
+            std::vector<double> spv(sp_src.size());
+            for (size_t e = 0; e < sp_src.size(); ++e) spv[e] = val[sp_src[e]];
+            if (!spv.empty())
+                CK(cudaMemcpyAsync(d_spval, spv.data(), sizeof(double) * spv.size(), cudaMemcpyHostToDevice, stream));
+            CK(cudaStreamSynchronize(stream));
+        }
+        for (int j = 0; j < S.M; ++j) {
+            NodeRT& n = nd[j];
+            n.rank = 0; n.V = n.U = nullptr;
+            if (n.hier) {
+                std::fill(n.brank.begin(), n.brank.end(), 0);
+                std::fill(n.bV.begin(), n.bV.end(), nullptr);
+                std::fill(n.bU.begin(), n.bU.end(), nullptr);
+            }
+            if (n.compressed) h_lo[j] = LoOp{nullptr, 1, 0};
+        }
+        for (int l = 0; l < S.nlevels; ++l) {
+            run_panel_steps(panel_steps[l]);
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& n = nd[j];
+                if (!n.compressed) {
+                    const double c = n.c, r = n.r;
+                    flops += c * c * c / 3.0 + r * c * c;
+                }
+            }
+            bool any_comp = false;
+            for (int j : S.level_nodes[l])
+                if (nd[j].compressed) {
+                    if (!any_comp) check_status();
+                    any_comp = true;
+                    compressed_node(j);
+                }
+            // extend-add of the level into its ancestors
+            CK(cudaMemcpyAsync(d_lo, h_lo.data(), sizeof(LoOp) * S.M, cudaMemcpyHostToDevice, stream));
+            if (push_count[l]) {
+                k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf,
+                                                            arena);
+                launches++;
+                LAUNCH_CHECK();
+            }
+            CK(cudaStreamSynchronize(stream));   // h_lo is rewritten by the next level
+        }
+        // push flops: lower half of L^O_k L^O_k^T per source
+        for (int k = 0; k < S.M; ++k) {
+            const double rk = S.nrows(k), K = h_lo[k].K;
+            flops += rk * (rk + 1) * K;
+        }
+        check_status();
+    }
+
+    rsc_status factor(const double* val, double tol_in) override {
+        is_factored = false;
+        tol = tol_in > 0 ? tol_in : 0.0;
+        tol_D = tol;
+        const bool compress = tol > 0;
+        diag_on = compress && o.diag_compress;
+        restarts = 0;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        launches = 0;
+        for (;;) {
+            if (!have_plan || plan_compress != compress || plan_diag != diag_on) build_plan(compress, diag_on);
+            CK(cudaEventRecord(e0, stream));
+            try {
+                run_once(val);
+            } catch (const Error& e) {
+                if (e.status != RSC_ERR_NOT_SPD || !diag_on) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    throw;
+                }
+                CK(cudaStreamSynchronize(stream));
+                ++restarts;
+                if (restarts <= o.max_restarts) tol_D /= 1.25;
+                else diag_on = false;
+                continue;
+            }
+            break;
+        }
+        CK(cudaEventRecord(e1, stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        factor_seconds = ms * 1e-3;
+        is_factored = true;
+        build_solve_plan();
+        return RSC_OK;
+    }
+
+    // ---------------------------------------------------------------- preconditioner apply
+    struct SolveLevel {
+        TrsvTask* trsv; int ntrsv;        // dense diagonal blocks up to SOLVE_MAX
+        std::vector<int> big;             // dense > SOLVE_MAX or hierarchical: per node
+        TnTask* tnf; int ntnf;            // forward: tmp_j = U_j^T y_C (compressed)
+        NnTask* nnf; int nnnf;            // forward: y_R -= L^O y_C  /  V tmp
+        TnTask* tnb; int ntnb;            // backward: tmp = V^T y_R (compressed) or y_C -= L^O^T y_R
+        NnTask* nnb; int nnnb;            // backward: y_C -= U tmp (compressed)
+        TnTask* tnb_acc; int ntnb_acc;    // backward (uncompressed): tmpc = L^O^T y_R
+        std::vector<std::pair<int, long long>> acc_nodes;   // (node, tmp offset) for y_C -= tmpc
+    };
+    std::vector<SolveLevel> slev;
+    DeviceMem smem_plan;
+    T* y_dev = nullptr;
+    T* tmp_dev = nullptr;
+
+    void build_solve_plan() {
+        smem_plan.release();
+        slev.assign(S.nlevels, SolveLevel{});
+        y_dev = (T*)smem_plan.alloc(sizeof(T) * S.n);
+        long long tmp_total = 0;
+        for (int j = 0; j < S.M; ++j) tmp_total += nd[j].compressed ? nd[j].rank : nd[j].c;
+        tmp_dev = (T*)smem_plan.alloc(sizeof(T) * std::max<long long>(tmp_total, 1));
+        long long toff = 0;
+        std::vector<long long> tmpo(S.M);
+        for (int j = 0; j < S.M; ++j) { tmpo[j] = toff; toff += nd[j].compressed ? nd[j].rank : nd[j].c; }
+        for (int l = 0; l < S.nlevels; ++l) {
+            SolveLevel& L = slev[l];
+            std::vector<TrsvTask> tv;
+            std::vector<TnTask> tnf, tnb, tnacc;
+            std::vector<NnTask> nnf, nnb;
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& n = nd[j];
+                if (!n.hier && n.c <= SOLVE_MAX) tv.push_back(TrsvTask{arena + n.off, n.ld, n.c, 0, y_dev + n.c0, 1, 0});
+                else L.big.push_back(j);
+                if (n.r == 0) continue;
+                const int32_t* Rj = d_rows + S.rows_ptr[j];
+                T* tmp = tmp_dev + tmpo[j];
+                if (!n.compressed) {
+                    const T* LO = arena + n.off + n.c;
+                    for (int r0 = 0; r0 < n.r; r0 += 64)
+                        nnf.push_back(NnTask{LO, n.ld, n.c, n.r, nullptr, 0, Rj, 0, y_dev + n.c0, 1, r0});
+                    tnacc.push_back(TnTask{LO, n.ld, n.c, n.r, nullptr, 0, Rj, 0, tmp, 1, 0});
+                    L.acc_nodes.push_back({j, tmpo[j]});
+                } else if (n.rank) {
+                    tnf.push_back(TnTask{n.U, n.c, n.rank, n.c, nullptr, 0, nullptr, (int)n.c0, tmp, 1, 0});
+                    for (int r0 = 0; r0 < n.r; r0 += 64)
+                        nnf.push_back(NnTask{n.V, n.r, n.rank, n.r, nullptr, 0, Rj, 0, tmp, 1, r0});
+                    tnb.push_back(TnTask{n.V, n.r, n.rank, n.r, nullptr, 0, Rj, 0, tmp, 1, 0});
+                    for (int r0 = 0; r0 < n.c; r0 += 64)
+                        nnb.push_back(NnTask{n.U, n.c, n.rank, n.c, nullptr, 0, nullptr, (int)n.c0, tmp, 1, r0});
+                }
+            }
+            L.trsv = smem_plan.upload(tv, stream); L.ntrsv = (int)tv.size();
+            tnf = expand_tn(tnf);
+            tnb = expand_tn(tnb);
+            tnacc = expand_tn(tnacc);
+            L.tnf = smem_plan.upload(tnf, stream); L.ntnf = (int)tnf.size();
+            L.nnf = smem_plan.upload(nnf, stream); L.nnnf = (int)nnf.size();
+            L.tnb = smem_plan.upload(tnb, stream); L.ntnb = (int)tnb.size();
+            L.nnb = smem_plan.upload(nnb, stream); L.nnnb = (int)nnb.size();
+            L.tnb_acc = smem_plan.upload(tnacc, stream); L.ntnb_acc = (int)tnacc.size();
+        }
+        CK(cudaStreamSynchronize(stream));
+    }
+
+    void apply(const double* d_r, double* d_z, cudaStream_t s) override {
+        cudaStream_t keep = stream;
+        stream = s;
+        const long long n = S.n;
+        k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(d_r, d_perm, y_dev, n);
+        launches++;
+        for (int l = 0; l < S.nlevels; ++l) {
+            const SolveLevel& L = slev[l];
+            if (L.ntrsv) { k_trsv_multi<T><<<L.ntrsv, 256, 0, s>>>(L.trsv, 1, 0); launches++; }
+            for (int j : L.big) diag_solve(j, 0, y_dev + nd[j].c0, 1, 1, false);
+            if (L.ntnf) { k_tn<T><<<L.ntnf, 256, 0, s>>>(L.tnf, y_dev, 1, 1); launches++; }
+            if (L.nnnf) { k_nn<T><<<L.nnnf, 256, 0, s>>>(L.nnf, y_dev, 1, 1, T(-1), 1); launches++; }
+        }
+        for (int l = S.nlevels - 1; l >= 0; --l) {
+            const SolveLevel& L = slev[l];
+            if (L.ntnb_acc) {
+                k_tn<T><<<L.ntnb_acc, 256, 0, s>>>(L.tnb_acc, y_dev, 1, 1);
+                launches++;
+                for (auto& pr : L.acc_nodes) axpy_rows(tmp_dev + pr.second, 1, y_dev + nd[pr.first].c0, 1, nd[pr.first].c, 1, T(-1));
+            }
+            if (L.ntnb) { k_tn<T><<<L.ntnb, 256, 0, s>>>(L.tnb, y_dev, 1, 1); launches++; }
+            if (L.nnnb) { k_nn<T><<<L.nnnb, 256, 0, s>>>(L.nnb, y_dev, 1, 1, T(-1), 0); launches++; }
+            if (L.ntrsv) { k_trsv_multi<T><<<L.ntrsv, 256, 0, s>>>(L.trsv, 1, 1); launches++; }
+            for (int j : L.big) diag_solve(j, 0, y_dev + nd[j].c0, 1, 1, true);
+        }
+        k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, d_z, n);
+        launches++;
+        LAUNCH_CHECK();
+        stream = keep;
+    }
+
+    // ---------------------------------------------------------------- introspection
+    void node_info(int j, int32_t* info) const override {
+        const NodeRT& n = nd[j];
+        info[2] = n.compressed ? 1 : 0;
+        info[3] = n.rank;
+        info[4] = n.hier ? 1 : 0;
+        info[5] = n.hier ? S.tree[j].nblocks : 1;
+    }
+
+    template <class X> std::vector<X> dl(const X* p, size_t cnt) const {
+        std::vector<X> v(cnt);
+        if (cnt) CK(cudaMemcpy(v.data(), p, sizeof(X) * cnt, cudaMemcpyDeviceToHost));
+        return v;
+    }
+
+    rsc_status node_blocks(int j, double* LD, double* LO) override {
+        CK(cudaStreamSynchronize(stream));
+        const NodeRT& n = nd[j];
+        const int c = n.c, r = n.r;
+        if (LD) {
+            std::fill(LD, LD + (size_t)c * c, 0.0);
+            if (!n.hier) {
+                auto P = dl(arena + n.off, (size_t)n.ld * c);
+                for (int q = 0; q < c; ++q)
+                    for (int i = q; i < c; ++i) LD[i + (size_t)q * c] = (double)P[i + (size_t)q * n.ld];
+            } else {
+                const BlockTree& t = S.tree[j];
+                for (int s = 1; s <= t.nblocks; ++s) {
+                    if (t.leaf[s]) {
+                        const int sz = t.hi[s] - t.lo[s];
+                        auto P = dl(arena + n.leaf_off[s], (size_t)sz * sz);
+                        for (int q = 0; q < sz; ++q)
+                            for (int i = q; i < sz; ++i)
+                                LD[(t.lo[s] + i) + (size_t)(t.lo[s] + q) * c] = (double)P[i + (size_t)q * sz];
+                    } else if (n.brank[s]) {
+                        const int rs = t.hi[s] - t.mid[s], cs = t.mid[s] - t.lo[s], q = n.brank[s];
+                        auto V = dl(n.bV[s], (size_t)rs * q);
+                        auto U = dl(n.bU[s], (size_t)cs * q);
+                        for (int b = 0; b < cs; ++b)
+                            for (int a = 0; a < rs; ++a) {
+                                double v = 0.0;
+                                for (int l = 0; l < q; ++l) v += (double)V[a + (size_t)l * rs] * (double)U[b + (size_t)l * cs];
+                                LD[(t.mid[s] + a) + (size_t)(t.lo[s] + b) * c] = v;
+                            }
+                    }
+                }
+            }
+        }
+        if (LO && r > 0) {
+            if (!n.compressed) {
+                auto P = dl(arena + n.off, (size_t)n.ld * c);
+                for (int q = 0; q < c; ++q)
+                    for (int i = 0; i < r; ++i) LO[i + (size_t)q * r] = (double)P[c + i + (size_t)q * n.ld];
+            } else {
+                std::fill(LO, LO + (size_t)r * c, 0.0);
+                if (n.rank) {
+                    auto V = dl(n.V, (size_t)r * n.rank);
+                    auto U = dl(n.U, (size_t)c * n.rank);
+                    for (int q = 0; q < c; ++q)
+                        for (int i = 0; i < r; ++i) {
+                            double v = 0.0;
+                            for (int l = 0; l < n.rank; ++l) v += (double)V[i + (size_t)l * r] * (double)U[q + (size_t)l * c];
+                            LO[i + (size_t)q * r] = v;
+                        }
+                }
+            }
+        }
+        return RSC_OK;
+    }
+
+    void stats(rsc_stats_t* out) const override {
+        double bytes = 0.0;
+        int ncomp = 0, maxr = 0;
+        for (int j = 0; j < S.M; ++j) {
+            const NodeRT& n = nd[j];
+            if (!n.compressed) bytes += (double)(n.c * (n.c + 1) / 2 + (double)n.r * n.c);
+            else {
+                ++ncomp;
+                maxr = std::max(maxr, n.rank);
+                bytes += (double)n.rank * (n.c + n.r);
+                if (!n.hier) bytes += (double)n.c * (n.c + 1) / 2;
+                else {
+                    const BlockTree& t = S.tree[j];
+                    for (int s = 1; s <= t.nblocks; ++s) {
+                        if (t.leaf[s]) { double sz = t.hi[s] - t.lo[s]; bytes += sz * (sz + 1) / 2; }
+                        else bytes += (double)n.brank[s] * (t.hi[s] - t.lo[s]);
+                    }
+                }
+            }
+        }
+        out->factor_bytes = bytes * sizeof(T);
+        out->factor_flops = flops;
+        out->factor_seconds = factor_seconds;
+        out->solve_seconds = solve_seconds;
+        out->restarts = restarts;
+        out->n_compressed = ncomp;
+        out->max_rank = maxr;
+        out->last_iters = last_iters;
+        out->last_relres = last_relres;
+        out->gpu_launches = launches;
+    }
+};
+
+template <class T>
+__global__ void k_strided_copy(const T* __restrict__ src, long long ssr, long long ssc, T* __restrict__ dst,
+                               long long dsr, long long dsc, int m, int nc) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * nc;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long i = e % m, c = e / m;
+        dst[i * dsr + c * dsc] = src[i * ssr + c * ssc];
+    }
+}
+
+template <class T>
+void EngineT<T>::rows_to_cols_ld(const T* X, int ldx, int m, int nc, T* U, int ldu, int col0) {
+    if ((long long)m * nc == 0) return;
+    k_strided_copy<T><<<std::min(cdiv((long long)m * nc, 256), 8192), 256, 0, stream>>>(X, ldx, 1, U + (size_t)col0 * ldu, 1,
+                                                                                         ldu, m, nc);
+    launches++;
+    LAUNCH_CHECK();
+}
+template <class T>
+void EngineT<T>::cols_to_rows(const T* U, int ldu, int m, int nc, T* Xr) {
+    if ((long long)m * nc == 0) return;
+    k_strided_copy<T><<<std::min(cdiv((long long)m * nc, 256), 8192), 256, 0, stream>>>(U, 1, ldu, Xr, nc, 1, m, nc);
+    launches++;
+    LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ Engine facade
+Engine::Engine(const Symbolic& S, const rsc_options& o) {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) throw Error(RSC_ERR_CUDA, "no CUDA device available");
+    if (o.precision == RSC_PREC_FP64) impl_.reset(new EngineT<double>(S, o));
+    else impl_.reset(new EngineT<float>(S, o));
+}
+Engine::~Engine() = default;
+rsc_status Engine::factor(const double* val, double tol) { return impl_->factor(val, tol); }
+bool Engine::factored() const { return impl_->factored(); }
+rsc_status Engine::solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                              const std::vector<double>& val, const double* b, double* x, double rtol,
+                              int32_t max_iter, int32_t* iters, double* relres) {
+    const long long n = (long long)rp.size() - 1;
+    cudaStream_t s = impl_->stream;
+    double* d = nullptr;
+    CK(cudaMalloc(&d, sizeof(double) * 2 * n));
+    rsc_status st;
+    try {
+        CK(cudaMemcpyAsync(d, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        st = impl_->pcg(rp, ci, val, d, d + n, rtol, max_iter, iters, relres, s);
+        CK(cudaMemcpyAsync(x, d + n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } catch (...) {
+        cudaFree(d);
+        throw;
+    }
+    cudaFree(d);
+    return st;
+}
+rsc_status Engine::solve_device(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                                const std::vector<double>& val, const double* d_b, double* d_x, double rtol,
+                                int32_t max_iter, int32_t* iters, double* relres, void* stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
+    rsc_status st = impl_->pcg(rp, ci, val, d_b, d_x, rtol, max_iter, iters, relres, s);
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+rsc_status Engine::apply_precond(const double* d_r, double* d_z, void* stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
+    impl_->apply(d_r, d_z, s);
+    CK(cudaStreamSynchronize(s));
+    return RSC_OK;
+}
+void Engine::node_info(int j, int32_t* info) const { impl_->node_info(j, info); }
+rsc_status Engine::node_blocks(int j, double* LD, double* LO) const { return impl_->node_blocks(j, LD, LO); }
+void Engine::stats(rsc_stats_t* out) const { impl_->stats(out); }
+
+}  // namespace rsc

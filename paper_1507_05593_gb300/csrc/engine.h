@@ -1,0 +1,43 @@
+// GPU engine: device memory, the factorization driver and the PCG solve.
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "rsc.h"
+#include "rsc_internal.h"
+
+namespace rsc {
+
+struct Error : std::runtime_error {
+    rsc_status status;
+    Error(rsc_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+struct EngineImpl;
+
+class Engine {
+public:
+    Engine(const Symbolic& S, const rsc_options& o);
+    ~Engine();
+    rsc_status factor(const double* val, double tol);
+    bool factored() const;
+    rsc_status solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                          const std::vector<double>& val, const double* b, double* x, double rtol,
+                          int32_t max_iter, int32_t* iters, double* relres);
+    rsc_status solve_device(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                            const std::vector<double>& val, const double* d_b, double* d_x, double rtol,
+                            int32_t max_iter, int32_t* iters, double* relres, void* stream);
+    rsc_status apply_precond(const double* d_r, double* d_z, void* stream);
+    void node_info(int j, int32_t* info) const;
+    rsc_status node_blocks(int j, double* LD, double* LO) const;
+    void stats(rsc_stats_t* out) const;
+
+private:
+    std::unique_ptr<EngineImpl> impl_;
+};
+
+}  // namespace rsc

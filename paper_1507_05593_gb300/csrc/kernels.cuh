@@ -1,0 +1,554 @@
+// Device kernels of the factorization and the solve, templated on the storage
+// type T of the factor (double for the FP64 path, float for the mixed path).
+// Diagonal-tile Cholesky always computes in FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsc {
+
+constexpr int TILE = 64;      // output tile edge of the GEMM-shaped kernels
+constexpr int KCH = 16;       // K chunk staged in shared memory
+constexpr int NB = 64;        // panel width of the blocked tall-panel Cholesky
+constexpr int SOLVE_MAX = 256;  // largest dense diagonal block solved inside one CTA
+
+// ------------------------------------------------------------------ task records
+struct PotrfTask { void* a; int ld; int nb; int node; };
+struct TrsmTask { const void* L; void* B; int ldl; int ldb; int nb; int nrows; };
+struct GemmTask {            // C[i,j] -= sum_l A[i,l] B[j,l]; lower mask i + moff >= j
+    const void* A; const void* B; void* C;
+    int lda, ldb, ldc, m, n, K, moff, lower;
+};
+struct PushTask { int k, j, pr0, pr1, pc0, pc1; };
+struct LoOp { const void* base; int ld; int K; };   // rows of L^O_k or V_k
+struct NodeTgt {             // where extend-add updates of supernode j go
+    void* base;              // panel (kind 0) or dense diagonal (kind 1)
+    int ld; int kind;        // 0 panel, 1 dense diagonal, 2 hierarchical leaves, 3 none
+    int c; int r; long long c0; long long rows_off;
+};
+struct LeafMap { long long lo; long long off; int size; int pad; };   // per column of a hierarchical node
+struct TnTask {              // Z[t, :] = sum_i A[arow_i, t] * Y[yrow_i, :]   (Z is K x N row-major)
+    const void* A; int lda; int K; int nrow;
+    const int32_t* amap; int aoff; const int32_t* ymap; int yoff;
+    void* Z; int ldz; int t0;   // t0: first column of A handled by this CTA (8 columns, one per warp)
+};
+struct NnTask {              // Y[yrow_i, :] += alpha * sum_l A[arow_i, l] * Z[l, :]
+    const void* A; int lda; int K; int nrow;
+    const int32_t* amap; int aoff; const int32_t* ymap; int yoff;
+    const void* Z; int ldz; int row0;   // row0: first row of this 64-row chunk
+};
+struct TrsvTask { const void* L; int ld; int c; int pad; void* X; int ldx; int pad2; };
+struct CsrBlock { const int32_t* rp; const int32_t* ci; const double* v; int nrows; int pad; };
+
+// ------------------------------------------------------------------ helpers
+template <class T> __device__ __forceinline__ void atomic_add(T* p, T v) { atomicAdd(p, v); }
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------ assembly
+// arena[dst[e]] = val[src[e]] : A's lower triangle into the dense factor storage.
+template <class T>
+__global__ void k_assemble(const double* __restrict__ val, const long long* __restrict__ src,
+                           const long long* __restrict__ dst, long long cnt, T* __restrict__ arena) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (; e < cnt; e += stride) arena[dst[e]] = (T)val[src[e]];
+}
+
+// ------------------------------------------------------------------ diagonal tile Cholesky (FP64)
+template <class T>
+__global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict__ tasks, int* status) {
+    __shared__ double s[NB][NB + 1];
+    const PotrfTask tk = tasks[blockIdx.x];
+    T* a = (T*)tk.a;
+    const int nb = tk.nb, ld = tk.ld;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int i = e % nb, j = e / nb;
+        s[i][j] = (i >= j) ? (double)a[i + (size_t)j * ld] : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        if (threadIdx.x == 0) {
+            double d = s[k][k];
+            if (!(d > 0.0)) {            // indefinite or NaN pivot: record, keep values finite
+                atomicCAS(status, 0, tk.node + 1);
+                d = 1.0;
+            }
+            s[k][k] = sqrt(d);
+        }
+        __syncthreads();
+        const double dk = s[k][k];
+        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) s[i][k] /= dk;
+        __syncthreads();
+        const int m = nb - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = k + 1 + e % m, j = k + 1 + e / m;
+            if (i >= j) s[i][j] -= s[i][k] * s[j][k];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int i = e % nb, j = e / nb;
+        if (i >= j) a[i + (size_t)j * ld] = (T)s[i][j];
+    }
+}
+
+// X L^T = B for a block of rows below a factored diagonal tile (in place).
+template <class T>
+__global__ void __launch_bounds__(256) k_trsm_tile(const TrsmTask* __restrict__ tasks) {
+    __shared__ T Ls[NB][NB + 1];
+    __shared__ T Xs[TILE][NB + 1];
+    const TrsmTask tk = tasks[blockIdx.x];
+    const T* L = (const T*)tk.L;
+    T* B = (T*)tk.B;
+    const int nb = tk.nb, nr = tk.nrows;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int i = e % nb, j = e / nb;
+        Ls[i][j] = (i >= j) ? L[i + (size_t)j * tk.ldl] : T(0);
+    }
+    for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
+        int i = e % nr, j = e / nr;
+        Xs[i][j] = B[i + (size_t)j * tk.ldb];
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        const T d = Ls[j][j];
+        for (int i = threadIdx.x; i < nr; i += blockDim.x) Xs[i][j] /= d;
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
+            int i = e % nr, l = j + 1 + e / nr;
+            Xs[i][l] -= Xs[i][j] * Ls[l][j];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
+        int i = e % nr, j = e / nr;
+        B[i + (size_t)j * tk.ldb] = Xs[i][j];
+    }
+}
+
+// ------------------------------------------------------------------ 64x64 tile product core
+// acc[a][b] = sum_l A[ty + 16a, l] * B[tx + 16b, l] over l < K, rows masked by m / n.
+template <class T>
+__device__ __forceinline__ void tile_nt(const T* __restrict__ A, int lda, int m, const T* __restrict__ B, int ldb,
+                                        int n, int K, T (&acc)[4][4], T (*As)[TILE + 1], T (*Bs)[TILE + 1]) {
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int k0 = 0; k0 < K; k0 += KCH) {
+        for (int e = tid; e < KCH * TILE; e += 256) {
+            int r = e % TILE, kk = e / TILE;
+            int l = k0 + kk;
+            As[kk][r] = (r < m && l < K) ? A[r + (size_t)l * lda] : T(0);
+            Bs[kk][r] = (r < n && l < K) ? B[r + (size_t)l * ldb] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KCH; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gemm_tile(const GemmTask* __restrict__ tasks) {
+    __shared__ T As[KCH][TILE + 1];
+    __shared__ T Bs[KCH][TILE + 1];
+    const GemmTask tk = tasks[blockIdx.x];
+    T acc[4][4];
+    tile_nt<T>((const T*)tk.A, tk.lda, tk.m, (const T*)tk.B, tk.ldb, tk.n, tk.K, acc, As, Bs);
+    T* C = (T*)tk.C;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int i = ty + 16 * a, j = tx + 16 * b;
+            if (i < tk.m && j < tk.n && (!tk.lower || i + tk.moff >= j)) C[i + (size_t)j * tk.ldc] -= acc[a][b];
+        }
+}
+
+// ------------------------------------------------------------------ extend-add (push form)
+// For descendant k: S = L^O_k(pr0:pr1,:) L^O_k(pc0:pc1,:)^T, lower part (row position >=
+// column position), subtracted from ancestor j's storage at (row R_k[q], column R_k[p]).
+template <class T>
+__global__ void __launch_bounds__(256) k_push(const PushTask* __restrict__ tasks, const LoOp* __restrict__ lo,
+                                              const NodeTgt* __restrict__ tgts, const int32_t* __restrict__ rows,
+                                              const long long* __restrict__ rows_ptr,
+                                              const LeafMap* __restrict__ leafmap, T* __restrict__ arena) {
+    __shared__ T As[KCH][TILE + 1];
+    __shared__ T Bs[KCH][TILE + 1];
+    __shared__ long long rpart[TILE], cpart[TILE];
+    __shared__ long long rleaf[TILE], cleaf[TILE];
+    const PushTask tk = tasks[blockIdx.x];
+    const LoOp op = lo[tk.k];
+    const NodeTgt tg = tgts[tk.j];
+    if (tg.kind == 3 || op.K == 0) return;
+    const int32_t* Rk = rows + rows_ptr[tk.k];
+    const int m = tk.pr1 - tk.pr0, n = tk.pc1 - tk.pc0;
+    for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
+        long long rp = -1, rl = -1;
+        if (i < m) {
+            long long g = Rk[tk.pr0 + i];
+            bool inC = g < tg.c0 + tg.c;
+            if (tg.kind == 0) {
+                rp = inC ? g - tg.c0 : tg.c + lower_bound_i32(rows + tg.rows_off, tg.r, (int32_t)g);
+            } else if (inC) {
+                if (tg.kind == 1) rp = g - tg.c0;
+                else { LeafMap lm = leafmap[g]; rp = g - lm.lo; rl = lm.lo; }
+            }
+        }
+        rpart[i] = rp;
+        rleaf[i] = rl;
+        long long cp = -1, cl = -1;
+        if (i < n) {
+            long long g = Rk[tk.pc0 + i];
+            if (tg.kind == 0 || tg.kind == 1) cp = (g - tg.c0) * (long long)tg.ld;
+            else { LeafMap lm = leafmap[g]; cp = lm.off + (g - lm.lo) * (long long)lm.size; cl = lm.lo; }
+        }
+        cpart[i] = cp;
+        cleaf[i] = cl;
+    }
+    __syncthreads();
+    const T* base = (const T*)op.base;
+    T acc[4][4];
+    tile_nt<T>(base + tk.pr0, op.ld, m, base + tk.pc0, op.ld, n, op.K, acc, As, Bs);
+    T* dst = tg.kind == 2 ? arena : (T*)tg.base;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int i = ty + 16 * a, j = tx + 16 * b;
+            if (i >= m || j >= n) continue;
+            if (tk.pr0 + i < tk.pc0 + j) continue;                 // upper part
+            long long rp = rpart[i];
+            if (rp < 0) continue;
+            if (tg.kind == 2 && rleaf[i] != cleaf[j]) continue;    // not inside one leaf block
+            atomic_add(dst + rp + cpart[j], -acc[a][b]);
+        }
+}
+
+// ------------------------------------------------------------------ thin products (N columns, chunks of 16)
+// One warp per (task, column t of A); lanes stride over the task's rows.
+template <class T>
+__global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks, const T* __restrict__ Y, int ldy,
+                                            int N) {
+    const TnTask tk = tasks[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.y * 16;
+    const int nc = min(16, N - c0);
+    const T* A = (const T*)tk.A;
+    T* Z = (T*)tk.Z;
+    {
+        const int t = tk.t0 + warp;
+        if (t >= tk.K) return;
+        T acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = T(0);
+        for (int i = lane; i < tk.nrow; i += 32) {
+            int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
+            int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+            T a = A[ar + (size_t)t * tk.lda];
+            const T* y = Y + (size_t)yr * ldy + c0;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < nc) acc[c] = fma(a, y[c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            T v = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[c] = v;
+        }
+        if (lane < nc) {
+            T v = acc[0];
+#pragma unroll
+            for (int c = 1; c < 16; ++c)
+                if (lane == c) v = acc[c];
+            Z[(size_t)t * tk.ldz + c0 + lane] = v;
+        }
+    }
+}
+
+// One CTA per (task, 64-row chunk); 64 rows x 4 column groups of 4.
+template <class T>
+__global__ void __launch_bounds__(256) k_nn(const NnTask* __restrict__ tasks, T* __restrict__ Y, int ldy, int N,
+                                            T alpha, int atomic) {
+    __shared__ T Zs[64][17];
+    const NnTask tk = tasks[blockIdx.x];
+    const int c0 = blockIdx.y * 16;
+    const int nc = min(16, N - c0);
+    const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int i = tk.row0 + r;
+    const bool active = i < tk.nrow;
+    const T* A = (const T*)tk.A;
+    const T* Z = (const T*)tk.Z;
+    int ar = 0;
+    if (active) ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int l0 = 0; l0 < tk.K; l0 += 64) {
+        const int lk = min(64, tk.K - l0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+            int l = e >> 4, c = e & 15;
+            Zs[l][c] = (l < lk && c < nc) ? Z[(size_t)(l0 + l) * tk.ldz + c0 + c] : T(0);
+        }
+        __syncthreads();
+        if (active) {
+            for (int l = 0; l < lk; ++l) {
+                T a = A[ar + (size_t)(l0 + l) * tk.lda];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] = fma(a, Zs[l][4 * g + c], acc[c]);
+            }
+        }
+    }
+    if (!active) return;
+    const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+    T* y = Y + (size_t)yr * ldy + c0 + 4 * g;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (4 * g + c >= nc) break;
+        if (atomic) atomic_add(y + c, alpha * acc[c]);
+        else y[c] += alpha * acc[c];
+    }
+}
+
+// Y[i, :] = (or +=) alpha * sum_e v[e] X[ci[e], :] for a small sparse block (CSR rows).
+template <class T>
+__global__ void k_csr_mm(CsrBlock blk, const T* __restrict__ X, int ldx, T* __restrict__ Y, int ldy, int N,
+                         T alpha, int accumulate) {
+    const int c0 = blockIdx.y * 16;
+    const int nc = min(16, N - c0);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < blk.nrows * 16; e += gridDim.x * blockDim.x) {
+        int i = e >> 4, c = e & 15;
+        if (c >= nc) continue;
+        T s = T(0);
+        for (int q = blk.rp[i]; q < blk.rp[i + 1]; ++q) s = fma((T)blk.v[q], X[(size_t)blk.ci[q] * ldx + c0 + c], s);
+        T* y = Y + (size_t)i * ldy + c0 + c;
+        *y = accumulate ? *y + alpha * s : alpha * s;
+    }
+}
+
+// ------------------------------------------------------------------ dense triangular solves with many RHS
+// X (c x N, row-major) <- L^{-1} X or L^{-T} X, one CTA per (task, 16-column chunk), c <= SOLVE_MAX.
+template <class T>
+__global__ void __launch_bounds__(256) k_trsv_multi(const TrsvTask* __restrict__ tasks, int N, int transpose) {
+    __shared__ T Xs[SOLVE_MAX][17];
+    const TrsvTask tk = tasks[blockIdx.x];
+    const T* L = (const T*)tk.L;
+    T* X = (T*)tk.X;
+    const int c = tk.c, ld = tk.ld;
+    const int c0 = blockIdx.y * 16;
+    const int nc = min(16, N - c0);
+    for (int e = threadIdx.x; e < c * 16; e += blockDim.x) {
+        int i = e >> 4, q = e & 15;
+        Xs[i][q] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
+    }
+    __syncthreads();
+    if (!transpose) {
+        for (int i = 0; i < c; ++i) {
+            if (threadIdx.x < 16) Xs[i][threadIdx.x] /= L[i + (size_t)i * ld];
+            __syncthreads();
+            const int m = c - i - 1;
+            for (int e = threadIdx.x; e < m * 16; e += blockDim.x) {
+                int l = i + 1 + (e >> 4), q = e & 15;
+                Xs[l][q] -= L[l + (size_t)i * ld] * Xs[i][q];
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int i = c - 1; i >= 0; --i) {
+            if (threadIdx.x < 16) Xs[i][threadIdx.x] /= L[i + (size_t)i * ld];
+            __syncthreads();
+            for (int e = threadIdx.x; e < i * 16; e += blockDim.x) {
+                int l = e >> 4, q = e & 15;
+                Xs[l][q] -= L[i + (size_t)l * ld] * Xs[i][q];
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < c * 16; e += blockDim.x) {
+        int i = e >> 4, q = e & 15;
+        if (q < nc) X[(size_t)i * tk.ldx + c0 + q] = Xs[i][q];
+    }
+}
+
+// ------------------------------------------------------------------ random test matrices
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, key bumped between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+// G (m x 16, row-major, ld 16): entry (i, c) from counter (i, c/2, block_id, word3), key = seed;
+// Box-Muller on (w0, w1) for even c and (w2, w3) for odd c.
+template <class T>
+__global__ void k_gauss(T* __restrict__ G, int m, unsigned long long seed, uint32_t block_id, uint32_t word3) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * 8) return;
+    int i = e >> 3, cp = e & 7;
+    uint32_t c[4] = {(uint32_t)i, (uint32_t)cp, block_id, word3};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+    const double two32 = 2.3283064365386963e-10;   // 2^-32
+    const double twopi = 6.283185307179586;
+    double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
+    double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
+    G[(size_t)i * 16 + 2 * cp] = (T)z0;
+    G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
+}
+
+// ------------------------------------------------------------------ small reductions / orthonormalisation
+// out += sum of squares of X(m x nc, row-major ld).
+template <class T>
+__global__ void k_sqnorm(const T* __restrict__ X, int ld, int m, int nc, double* out) {
+    double s = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * nc; e += gridDim.x * blockDim.x) {
+        double v = (double)X[(size_t)(e / nc) * ld + e % nc];
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        atomicAdd(out, t);
+    }
+}
+
+// Gram G += Y^T Y over a 256-row chunk (b <= 16 columns of a row-major ld-16 block).
+template <class T>
+__global__ void k_gram(const T* __restrict__ Y, int m, int b, double* G) {
+    __shared__ double Ys[256][17];
+    const int r0 = blockIdx.x * 256;
+    const int nr = min(256, m - r0);
+    for (int e = threadIdx.x; e < 256 * 16; e += blockDim.x) {
+        int i = e >> 4, c = e & 15;
+        Ys[i][c] = (i < nr && c < b) ? (double)Y[(size_t)(r0 + i) * 16 + c] : 0.0;
+    }
+    __syncthreads();
+    const int a = threadIdx.x >> 4, c = threadIdx.x & 15;
+    if (a < b && c < b && c >= a) {
+        double s = 0.0;
+        for (int i = 0; i < nr; ++i) s += Ys[i][a] * Ys[i][c];
+        atomicAdd(&G[a * 16 + c], s);
+    }
+}
+
+// Cholesky G + shift I = R^T R (b x b, upper R) and Rinv = R^{-1}; status = 1 if not
+// positive definite.  shift = shift_coef * trace(G): the shifted Cholesky QR of
+// Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa (SIAM J. Sci. Comput. 2020)
+// uses 11 (m b + b (b + 1)) u ||Y||_2^2; trace(G) bounds ||Y||_2^2 from above.
+__global__ void k_chol_small(const double* G, int b, double shift_coef, double* Rinv, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double R[16][16], X[16][16];
+    for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < 16; ++j) { R[i][j] = 0.0; X[i][j] = 0.0; }
+    double trace = 0.0;
+    for (int i = 0; i < b; ++i) trace += G[i * 16 + i];
+    const double shift = shift_coef * trace;
+    for (int j = 0; j < b; ++j) {
+        double d = G[j * 16 + j] + shift;
+        for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
+        if (!(d > 1e-28 * trace)) { *status = 1; d = 1.0; }
+        R[j][j] = sqrt(d);
+        for (int i = j + 1; i < b; ++i) {
+            double s = G[j * 16 + i];
+            for (int k = 0; k < j; ++k) s -= R[k][j] * R[k][i];
+            R[j][i] = s / R[j][j];
+        }
+    }
+    for (int j = 0; j < b; ++j) {     // upper-triangular inverse, column by column
+        X[j][j] = 1.0 / R[j][j];
+        for (int i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j; ++k) s += R[i][k] * X[k][j];
+            X[i][j] = -s / R[i][i];
+        }
+    }
+    for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < 16; ++j) Rinv[i * 16 + j] = X[i][j];
+}
+
+// Y <- Y Rinv (row-major ld 16, b columns).
+template <class T>
+__global__ void k_apply_rinv(T* __restrict__ Y, int m, int b, const double* __restrict__ Rinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double y[16], o[16];
+    for (int c = 0; c < 16; ++c) y[c] = c < b ? (double)Y[(size_t)i * 16 + c] : 0.0;
+    for (int c = 0; c < b; ++c) {
+        double s = 0.0;
+        for (int k = 0; k <= c; ++k) s += y[k] * Rinv[k * 16 + c];
+        o[c] = s;
+    }
+    for (int c = 0; c < b; ++c) Y[(size_t)i * 16 + c] = (T)o[c];
+}
+
+// U[:, col0 + c] = Y[:, c] for c < b (Y row-major ld 16, U column-major ld m).
+template <class T>
+__global__ void k_rows_to_cols(const T* __restrict__ Y, int m, int b, T* __restrict__ U, int ldu, int col0) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * b) return;
+    int i = e % m, c = e / m;
+    U[i + (size_t)(col0 + c) * ldu] = Y[(size_t)i * 16 + c];
+}
+
+// Row-major thin block <-> strided copies and scaled adds (vector path of the solve).
+template <class T>
+__global__ void k_axpy_rows(const T* __restrict__ X, int ldx, T* __restrict__ Y, int ldy, int m, int nc, T alpha) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * nc; e += gridDim.x * blockDim.x) {
+        int i = e / nc, c = e % nc;
+        Y[(size_t)i * ldy + c] += alpha * X[(size_t)i * ldx + c];
+    }
+}
+
+template <class T>
+__global__ void k_fill(T* __restrict__ X, long long cnt, T v) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+        X[e] = v;
+}
+
+// ------------------------------------------------------------------ permutation and PCG vectors (FP64)
+template <class T>
+__global__ void k_perm_in(const double* __restrict__ r, const int32_t* __restrict__ perm, T* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (T)r[perm[i]];
+}
+template <class T>
+__global__ void k_perm_out(const T* __restrict__ y, const int32_t* __restrict__ perm, double* __restrict__ z, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[perm[i]] = (double)y[i];
+}
+
+}  // namespace rsc

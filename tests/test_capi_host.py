@@ -1,0 +1,140 @@
+"""Host-side tests of the C-ABI library (no GPU): exported symbols, input
+validation and bit-exact symbolic parity with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1507_05593_gb300 as R
+import workloads as W
+from oracle import factor as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "rsc.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(rsc_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared_symbols()
+    assert "rsc_analyze" in names and "rsc_factor" in names and "rsc_solve" in names
+    lib = ctypes.CDLL(R.LIB_PATH)
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_options_default_values():
+    o = R.rsc_options_default()
+    assert (o.tau_O, o.tau_D, o.leaf_size, o.sample_block, o.power_iters, o.dof_per_node) == (256, 256, 64, 16, 0, 1)
+    assert (o.max_restarts, o.precision, o.diag_compress, o.seed) == (8, 0, 1, 0)
+
+
+def _bad(p, **changes):
+    rp, ci, v, xyz = p.row_ptr.copy(), p.col_idx.copy(), p.val.copy(), p.coords.copy()
+    loc = dict(rp=rp, ci=ci, v=v, xyz=xyz)
+    for k, f in changes.items():
+        loc[k] = f(loc[k])
+    return loc
+
+
+@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "nocoords", "dof", "range"])
+def test_analyze_rejects_bad_input(what):
+    p = W.poisson7(4)
+    rp, ci, v, xyz = p.row_ptr.copy(), p.col_idx.copy(), p.val.copy(), p.coords.copy()
+    opts = R.rsc_options_default()
+    n = p.n
+    if what == "asym":      # drop one off-diagonal entry of row 0
+        keep = np.ones(ci.size, bool)
+        keep[1] = False
+        ci, v = ci[keep], v[keep]
+        rp = rp.copy()
+        rp[1:] -= 1
+    elif what == "unsorted":
+        ci[[0, 1]] = ci[[1, 0]]
+    elif what == "nodiag":
+        ci, v = ci.copy(), v.copy()
+        d = np.nonzero(ci[rp[0]:rp[1]] == 0)[0][0]
+        ci[d] = 63
+    elif what == "nan":
+        v[5] = np.nan
+    elif what == "nocoords":
+        xyz = None
+    elif what == "dof":
+        opts.dof_per_node = 5
+    elif what == "range":
+        ci[3] = 10_000
+    with pytest.raises(R.RscError) as e:
+        R.rsc_analyze(n, rp, ci, v, xyz, opts)
+    assert e.value.status == 1
+    assert R.rsc_last_error()
+
+
+def _oracle_opts(o):
+    return F.Options(tau_O=o.tau_O, tau_D=o.tau_D, leaf_size=o.leaf_size, dof_per_node=o.dof_per_node)
+
+
+@pytest.mark.parametrize("maker,kw", [
+    (lambda: W.poisson7(6), dict(leaf_size=8)),
+    (lambda: W.poisson7(5, 7, 4), dict(leaf_size=8)),
+    (lambda: W.poisson7(12), dict(leaf_size=16, tau_O=40, tau_D=32)),
+    (lambda: W.poisson7(32), dict()),
+    (lambda: W.elasticity_q1(3, incl=(1, 2)), dict(leaf_size=8, dof_per_node=3)),
+    (lambda: W.elasticity_q1(8), dict(dof_per_node=3)),
+    (lambda: W.diffusion_grf(20, 2.0, 4.0, 1), dict(leaf_size=32, tau_O=64, tau_D=64)),
+])
+def test_symbolic_bit_exact_vs_oracle(maker, kw):
+    p = maker()
+    o = R.rsc_options_default(**kw)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
+    perm, sp = R.rsc_get_ordering(h)
+    rows_ptr, rows, parent, level, kind = R.rsc_get_structure(h)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, _oracle_opts(o))
+    np.testing.assert_array_equal(perm, an.ordering.perm)
+    np.testing.assert_array_equal(sp, an.ordering.snode_ptr)
+    for j in range(an.nsuper):
+        np.testing.assert_array_equal(rows[rows_ptr[j]:rows_ptr[j + 1]], an.sym.rows[j])
+    np.testing.assert_array_equal(parent, an.sym.parent)
+    assert [int(k) for k in kind] == [1 if x == "sep" else 0 for x in an.ordering.kinds]
+    # levels: children strictly below parents, leaves at 0
+    for j in range(an.nsuper):
+        if parent[j] >= 0:
+            assert level[parent[j]] > level[j]
+
+
+def test_symbolic_properties_full_size():
+    """96^3 (884,736 unknowns): properties that hold at any size."""
+    p = W.poisson7(96)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, R.rsc_options_default())
+    perm, sp = R.rsc_get_ordering(h)
+    rows_ptr, rows, parent, level, kind = R.rsc_get_structure(h)
+    assert np.array_equal(np.sort(perm), np.arange(p.n))
+    M = sp.size - 1
+    c = np.diff(sp)
+    assert c.max() == 96 * 96 and kind[-1] == 1 and parent[-1] == -1
+    assert ((kind == 1) & (c >= 256)).sum() == 165
+    snode_of = np.repeat(np.arange(M), c)
+    iperm = np.empty_like(perm)
+    iperm[perm] = np.arange(p.n)
+    # every entry of A below the diagonal block lies in R_j of its column's supernode
+    A = p.scipy().tocoo()
+    r, cc = iperm[A.row], iperm[A.col]
+    low = r > cc
+    r, cc = r[low], cc[low]
+    j = snode_of[cc]
+    outside = r >= sp[j + 1]
+    for jj, rr in zip(j[outside][::997], r[outside][::997]):
+        R_j = rows[rows_ptr[jj]:rows_ptr[jj + 1]]
+        assert R_j[np.searchsorted(R_j, rr)] == rr
+    # R_k meets C^O_j only inside R_j for j = parent(k) (Section 2.1)
+    for k in range(0, M, 97):
+        pk = parent[k]
+        if pk < 0:
+            continue
+        Rk = rows[rows_ptr[k]:rows_ptr[k + 1]]
+        tail = Rk[Rk >= sp[pk + 1]]
+        Rp = rows[rows_ptr[pk]:rows_ptr[pk + 1]]
+        assert np.all(np.isin(tail, Rp))

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (FP64 path): the exact factor agrees within 1e-12 of the factor's
+largest entry; compressed blocks agree within 1e-8 relative (the same Philox
+test matrices drive both sides; only rounding differs); ranks are equal; the
+preconditioner applications agree within 1e-8 relative; PCG reaches 1e-8 with
+iteration counts within +-2 of the oracle's.  FP32 path: blocks within 1e-4
+relative of the FP64 oracle, PCG still to 1e-8.
+"""
+import numpy as np
+import pytest
+
+import paper_1507_05593_gb300 as R
+import workloads as W
+from oracle import factor as F
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _opts(**kw):
+    return R.rsc_options_default(**kw)
+
+
+def _oracle(p, o, tol):
+    oo = F.Options(tau_O=o.tau_O, tau_D=o.tau_D, leaf_size=o.leaf_size, dof_per_node=o.dof_per_node,
+                   power_iters=o.power_iters, max_restarts=o.max_restarts, seed=o.seed,
+                   diag_compress=bool(o.diag_compress))
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, oo)
+    return an, F.factor(an, tol)
+
+
+def _oracle_blocks(f, j):
+    an = f.an
+    s = f.sn[j]
+    D = s.D
+    c0, c1 = an.cols(j)
+    c = c1 - c0
+    if D.hierarchical:
+        t = D.tree
+        LD = np.zeros((c, c))
+        for b in range(1, t.nblocks + 1):
+            r0, r1 = t.rows(b)
+            q0, q1 = t.cols(b)
+            LD[r0:r1, q0:q1] = D.leafL[b] if t.leaf[b] else D.V[b] @ D.U[b].T
+    else:
+        LD = D.L
+    r = an.sym.rows[j].size
+    if r == 0:
+        LO = np.zeros((0, c))
+    elif s.compressed:
+        LO = s.V @ s.U.T
+    else:
+        LO = s.LO
+    return LD, LO
+
+
+def _gpu(p, o, tol):
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
+    R.rsc_factor(h, tol)
+    return h
+
+
+CASES = [
+    ("poisson8", lambda: W.poisson7(8), dict(leaf_size=8, tau_O=16, tau_D=8)),
+    ("poisson_5x7x4", lambda: W.poisson7(5, 7, 4), dict(leaf_size=8, tau_O=12, tau_D=8)),
+    ("grf12", lambda: W.diffusion_grf(12, 2.0, 3.0, 0), dict(leaf_size=16, tau_O=40, tau_D=32)),
+    ("elast4", lambda: W.elasticity_q1(4, incl=(1, 3)), dict(leaf_size=8, tau_O=48, tau_D=24, dof_per_node=3)),
+    ("poisson20", lambda: W.poisson7(20), dict(leaf_size=32, tau_O=100, tau_D=64)),
+]
+
+
+@pytest.mark.parametrize("name,maker,kw", CASES, ids=[c[0] for c in CASES])
+def test_exact_factor_parity(name, maker, kw):
+    p = maker()
+    o = _opts(**kw)
+    h = _gpu(p, o, 0.0)
+    an, f = _oracle(p, o, 0.0)
+    scale = max(np.abs(_oracle_blocks(f, j)[0]).max() for j in range(an.nsuper))
+    for j in range(an.nsuper):
+        LD, LO = R.rsc_get_supernode_blocks(h, j)
+        LDo, LOo = _oracle_blocks(f, j)
+        assert np.abs(np.tril(LD) - np.tril(LDo)).max() <= 1e-12 * scale, j
+        if LOo.size:
+            assert np.abs(LO - LOo).max() <= 1e-12 * scale, j
+    x, it, rr = R.rsc_solve(h, p.b, 1e-8, 50)
+    assert it <= 2 and rr <= 1e-8
+
+
+@pytest.mark.parametrize("name,maker,kw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("tol", [0.1, 0.01])
+def test_compressed_factor_parity(name, maker, kw, tol):
+    p = maker()
+    o = _opts(**kw)
+    h = _gpu(p, o, tol)
+    an, f = _oracle(p, o, tol)
+    st = R.rsc_get_stats(h)
+    assert st["restarts"] == f.restarts
+    ncomp = 0
+    for j in range(an.nsuper):
+        info = R.rsc_get_supernode_info(h, j)
+        assert info["compressed"] == int(f.sn[j].compressed)
+        if f.sn[j].compressed:
+            ncomp += 1
+            assert info["rank"] == f.sn[j].U.shape[1], j
+            if info["hierarchical"]:
+                D = f.sn[j].D
+                assert info["nblocks"] == D.tree.nblocks
+        LD, LO = R.rsc_get_supernode_blocks(h, j)
+        LDo, LOo = _oracle_blocks(f, j)
+        sc = max(1.0, np.abs(LDo).max())
+        assert np.abs(np.tril(LD) - np.tril(LDo)).max() <= 1e-8 * sc, j
+        if LOo.size:
+            assert np.abs(LO - LOo).max() <= 1e-8 * max(1.0, np.abs(LOo).max()), j
+    assert ncomp == st["n_compressed"]
+    # one preconditioner application, element by element
+    r = np.random.default_rng(5).standard_normal(p.n)
+    z_ref = F.apply_preconditioner(f, r)
+    d_r = torch.tensor(r, device="cuda")
+    d_z = torch.empty_like(d_r)
+    R.rsc_apply_preconditioner_device(h, d_r, d_z)
+    z = d_z.cpu().numpy()
+    assert np.abs(z - z_ref).max() <= 1e-8 * np.abs(z_ref).max()
+    x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
+    _, it_ref, rr_ref, ok = F.solve(an, f, p.b, 1e-8, 500)
+    assert ok and rr <= 1e-8 and abs(it - it_ref) <= 2
+    A = p.scipy()
+    assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= 1e-8
+
+
+def test_poisson32_config_parity():
+    """32^3 Poisson, tau_O = 256, tol 1e-1, 16-column samples, PCG to 1e-8 (all FP64)."""
+    p = W.poisson7(32)
+    o = _opts()
+    h = _gpu(p, o, 0.1)
+    an, f = _oracle(p, o, 0.1)
+    for j in range(an.nsuper):
+        if f.sn[j].compressed:
+            assert R.rsc_get_supernode_info(h, j)["rank"] == f.sn[j].U.shape[1]
+    r = np.random.default_rng(6).standard_normal(p.n)
+    z_ref = F.apply_preconditioner(f, r)
+    d_r = torch.tensor(r, device="cuda")
+    d_z = torch.empty_like(d_r)
+    R.rsc_apply_preconditioner_device(h, d_r, d_z)
+    assert np.abs(d_z.cpu().numpy() - z_ref).max() <= 1e-8 * np.abs(z_ref).max()
+    x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
+    _, it_ref, _, _ = F.solve(an, f, p.b, 1e-8, 500)
+    assert rr <= 1e-8 and abs(it - it_ref) <= 2
+
+
+def test_poisson32_exact_sampled_blocks():
+    """Exact 32^3 factor (dense 1024-column top separator): sampled supernodes vs oracle."""
+    p = W.poisson7(32)
+    o = _opts()
+    h = _gpu(p, o, 0.0)
+    an, f = _oracle(p, o, 0.0)
+    for j in list(range(0, an.nsuper, 37)) + [an.nsuper - 1, an.nsuper - 2]:
+        LD, LO = R.rsc_get_supernode_blocks(h, j)
+        LDo, LOo = _oracle_blocks(f, j)
+        assert np.abs(np.tril(LD) - LDo).max() <= 1e-12 * max(1, np.abs(LDo).max())
+        if LOo.size:
+            assert np.abs(LO - LOo).max() <= 1e-12 * max(1, np.abs(LDo).max())
+    x, it, rr = R.rsc_solve(h, p.b, 1e-8, 50)
+    assert it <= 2 and rr <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_mixed_precision_parity(prec):
+    p = W.diffusion_grf(12, 2.0, 3.0, 0)
+    kw = dict(leaf_size=16, tau_O=40, tau_D=32)
+    o = _opts(precision=prec, **kw)
+    h = _gpu(p, o, 0.01)
+    an, f = _oracle(p, R.rsc_options_default(**kw), 0.01)
+    for j in range(an.nsuper):
+        LD, LO = R.rsc_get_supernode_blocks(h, j)
+        LDo, LOo = _oracle_blocks(f, j)
+        assert np.abs(np.tril(LD) - np.tril(LDo)).max() <= 1e-4 * max(1, np.abs(LDo).max()), j
+    x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
+    _, it_ref, _, _ = F.solve(an, f, p.b, 1e-8, 500)
+    assert rr <= 1e-8 and it <= it_ref + 3
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_single_unknown_and_single_leaf():
+    for p in (W.poisson7(1), W.poisson7(2), W.poisson7(4, 1, 1)):
+        h = _gpu(p, _opts(), 0.1)
+        x, it, rr = R.rsc_solve(h, p.b, 1e-8, 10)
+        np.testing.assert_allclose(p.scipy() @ x, p.b, rtol=1e-10, atol=1e-12)
+        assert it <= 2
+
+
+def test_zero_rhs_and_state_errors():
+    p = W.poisson7(6)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, _opts(leaf_size=8))
+    with pytest.raises(R.RscError) as e:
+        R.rsc_solve(h, p.b)
+    assert e.value.status == 7
+    R.rsc_factor(h, 0.1)
+    x, it, rr = R.rsc_solve(h, np.zeros(p.n))
+    assert it == 0 and np.all(x == 0)
+
+
+def test_indefinite_matrix_reports_not_spd():
+    p = W.poisson7(6)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, -p.val, p.coords, _opts(leaf_size=8))
+    with pytest.raises(R.RscError) as e:
+        R.rsc_factor(h, 0.0)
+    assert e.value.status == 2
+    # the handle stays usable: new values, factor again
+    R.rsc_refactor_values(h, p.val)
+    R.rsc_factor(h, 0.0)
+    x, it, rr = R.rsc_solve(h, p.b)
+    assert rr <= 1e-8
+
+
+def test_refactor_values_changes_factor():
+    p = W.diffusion_grf(10, 1.0, 3.0, 0)
+    q = W.diffusion_grf(10, 1.0, 3.0, 1)
+    assert np.array_equal(p.col_idx, q.col_idx)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, _opts(leaf_size=16))
+    R.rsc_factor(h, 0.0)
+    R.rsc_refactor_values(h, q.val)
+    R.rsc_factor(h, 0.0)
+    x, it, rr = R.rsc_solve(h, q.b)
+    np.testing.assert_allclose(q.scipy() @ x, q.b, rtol=0, atol=1e-8 * np.abs(q.b).max() * 10)
+
+
+def test_solve_device_matches_host():
+    p = W.poisson7(12)
+    h = _gpu(p, _opts(leaf_size=16, tau_O=40, tau_D=32), 0.1)
+    x, it, rr = R.rsc_solve(h, p.b)
+    d_b = torch.tensor(p.b, device="cuda")
+    d_x = torch.empty_like(d_b)
+    it2, rr2 = R.rsc_solve_device(h, d_b, d_x)
+    assert it2 == it
+    np.testing.assert_allclose(d_x.cpu().numpy(), x, rtol=1e-12, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- full size (96^3)
+
+@pytest.mark.slow
+def test_diffusion96_full_size_properties():
+    """96^3 FV diffusion with GRF conductivity (sigma 2, correlation length 8), tol 1e-2:
+    PCG reaches 1e-8 (true residual checked on the CPU); FP64 and FP32 forms."""
+    p = W.diffusion_grf(96, 2.0, 8.0, 0)
+    A = p.scipy()
+    for prec in ("fp64", "fp32"):
+        h = _gpu(p, _opts(precision=prec), 1e-2)
+        x, it, rr = R.rsc_solve(h, p.b, 1e-8, 1000)
+        assert rr <= 1e-8
+        assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= 1e-8
+        st = R.rsc_get_stats(h)
+        assert st["n_compressed"] == 165 and st["factor_bytes"] > 0
