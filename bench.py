@@ -1,0 +1,304 @@
+"""Benchmark: factor + PCG seconds to relative residual 1e-8.
+
+Workload: 7-point finite-volume diffusion on a 96^3 grid (884,736 unknowns) with
+cell conductivity exp(g), g a seeded Gaussian random field (sigma 2, correlation
+length 8 cells); compression tolerance 1e-2, 16-column Gaussian samples, PCG to
+||r||/||b|| <= 1e-8.  One step = rsc_factor + rsc_solve_device (b resident on the
+device); its time is the sum of the two calls' device times (CUDA events on the
+library's stream).  The best form (mixed FP32 factor, FP64 PCG) is timed for K
+steps; the plain FP64 form is timed once beside it.  L2 is flushed between steps
+(the factor storage is also larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64] [--side 96]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+For N > 1 (torchrun) every rank solves its own replica (replicas only: the method
+has no data-parallel exchange step at this size); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+PCG seconds to rel. residual 1e-8"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--side", type=int, default=96)
+    ap.add_argument("--tol", type=float, default=1e-2)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload_name(side, tol):
+    return (f"fv_diffusion_grf_{side}^3 ({side ** 3:,} unknowns), conductivity exp(GRF sigma 2, corr len 8), "
+            f"compression tol {tol:g}, 16-col Gaussian samples, PCG rtol 1e-8")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+_ORACLE_CODE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import factor as F
+g = W.grf(({side}, {side}, {side}), 2.0, 8.0, 0)
+c = {crop}
+p = W.fv_diffusion(np.exp(g[:c, :c, :c]), 0)
+t0 = time.perf_counter()
+an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords)
+t1 = time.perf_counter()
+f = F.factor(an, {tol})
+t2 = time.perf_counter()
+x, it, rr, ok = F.solve(an, f, p.b, {rtol}, 2000)
+t3 = time.perf_counter()
+print(json.dumps(dict(n=p.n, analyze=t1 - t0, factor=t2 - t1, solve=t3 - t2, iters=it, relres=rr, ok=bool(ok))))
+"""
+
+
+def run_oracle_sample(side, crop, tol, rtol):
+    """The oracle, as it stands, on a crop of the same conductivity field (single thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_CODE.format(root=ROOT, side=side, crop=crop, tol=tol, rtol=rtol)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(side, tol, rtol, crop=32):
+    r = run_oracle_sample(side, crop, tol, rtol)
+    secs = r["factor"] + r["solve"]
+    scale = (side ** 3) / r["n"]
+    return {"value": secs * scale, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle factor+PCG on the {crop}^3 corner crop of the same conductivity field "
+                       f"({r['n']:,} unknowns, tol {tol:g}, {r['iters']} iterations, measured {secs:.2f} s), "
+                       f"scaled linearly by unknowns x{scale:.1f} (a lower bound: the method is superlinear)")}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def reference_arm(a, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    rec = None
+    for i in range(a.warmup + a.steps):
+        crop = 24 if i < a.warmup else 32
+        r = run_oracle_sample(a.side, crop, a.tol, a.rtol)
+        if i >= a.warmup:
+            vals.append((r["factor"] + r["solve"]) * (a.side ** 3) / r["n"])
+            rec = r
+    v = sum(vals) / len(vals)
+    sample = (f"oracle (numpy FP64, 1 thread) factor+PCG on the 32^3 corner crop of the same conductivity field "
+              f"({rec['n']:,} unknowns, {rec['iters']} iterations), scaled linearly by unknowns to the full grid")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_name(a.side, a.tol), "form": "cpu oracle"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if a.impl == "reference":
+        reference_arm(a, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    import paper_1507_05593_gb300 as R
+    import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # cpu baseline first (host cores; a separate process) so it does not overlap the GPU timing
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(a.side, a.tol, a.rtol)
+        except Exception as e:  # reported, not fatal
+            cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+
+    p = W.diffusion_grf(a.side, 2.0, 8.0, seed=rank)
+    d_b = torch.tensor(p.b, device="cuda")
+    d_x = torch.empty_like(d_b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        t = time.perf_counter()
+        h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, R.rsc_options_default(precision=prec))
+        return h, time.perf_counter() - t
+
+    def step(h):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        R.rsc_factor(h, a.tol)
+        it, rr = R.rsc_solve_device(h, d_b, d_x, a.rtol, 2000)
+        st = R.rsc_get_stats(h)
+        return st["factor_seconds"] + st["solve_seconds"], it, rr, st
+
+    h, t_an = make(a.prec)
+    # untimed profiling pass: find the dominant kernel class
+    R.rsc_profile(h, True)
+    step(h)
+    prof_all = R.rsc_get_kernel_profile(h)
+    dom = max(prof_all.items(), key=lambda kv: kv[1]["ms"])[0] if prof_all else None
+    R.rsc_profile(h, False)
+    for _ in range(max(a.warmup - 1, 0)):
+        step(h)
+    if dom:
+        R.rsc_profile(h, True, dom)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, iters, rrs, st = [], [], [], None
+    for _ in range(a.steps):
+        t, it, rr, st = step(h)
+        times.append(t)
+        iters.append(it)
+        rrs.append(rr)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    kprof = R.rsc_get_kernel_profile(h) if dom else {}
+    R.rsc_profile(h, False)
+    t_step = sum(times) / len(times)
+    if dist:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    # end to end through the public host API: values and b copied in, x copied out
+    t0 = time.perf_counter()
+    R.rsc_factor(h, a.tol)
+    x, it_e2e, rr_e2e = R.rsc_solve(h, p.b, a.rtol, 2000)
+    t_e2e = time.perf_counter() - t0
+    res = np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
+    # plain FP64 form, once
+    fp64 = None
+    if not a.no_fp64 and a.prec != "fp64":
+        h64, _ = make("fp64")
+        t64, it64, rr64, st64 = step(h64)
+        fp64 = {"seconds": t64, "factor_s": st64["factor_seconds"], "solve_s": st64["solve_seconds"],
+                "iters": it64, "relres": rr64, "factor_bytes": st64["factor_bytes"],
+                "factor_tflops": st64["factor_flops"] / st64["factor_seconds"] / 1e12}
+        del h64
+    roof = None
+    if dom and dom in kprof and kprof[dom]["ms"] > 0:
+        k = kprof[dom]
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        per_launch_ms = k["ms"] / k["launches"]
+        achieved = k["bytes"] / k["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "launches_timed": k["launches"],
+                "avg_launch_us": per_launch_ms * 1e3,
+                "note": "algorithmic bytes per launch / CUDA-event launch time, peak of measured"}
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.prec != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": _workload_name(a.side, a.tol), "form": f"{a.prec} factor, f64 PCG",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "l2": "L2 flushed (256 MB write) before each step; factor storage larger than L2"},
+        "iters": iters[-1], "relres": rrs[-1], "true_relres_check": res,
+        "factor_s": st["factor_seconds"], "solve_s": st["solve_seconds"],
+        "factor_tflops": st["factor_flops"] / st["factor_seconds"] / 1e12, "factor_gflop": st["factor_flops"] / 1e9,
+        "factor_bytes": st["factor_bytes"], "analyze_s": t_an, "restarts": st["restarts"],
+        "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "roofline": roof, "kernel_profile_untimed": prof_all,
+        "cpu_baseline": cpu, "clocks": clk,
+        "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(8 * (p.nnz + p.n)),
+                "d2h_bytes_per_step": int(8 * p.n)},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

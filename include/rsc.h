@@ -159,6 +159,17 @@ rsc_status rsc_get_supernode_blocks(const rsc_handle* h, int32_t j, double* LD, 
 
 rsc_status rsc_get_stats(const rsc_handle* h, rsc_stats_t* out);
 
+/* Kernel profiler (measurement aid, not part of the method): enable != 0 turns on
+ * CUDA-event timing around the launches of the listed kernel classes
+ * (comma-separated names, e.g. "push,tn,nn"; NULL or "" = all) and clears the
+ * accumulated counts.  Classes: push (extend-add), potrf, trsm, panel_gemm, tn,
+ * nn, trsv, spmv, dot, axpy. */
+rsc_status rsc_profile(rsc_handle* h, int32_t enable, const char* kernels);
+
+/* JSON object {class: {launches, ms, flops, bytes}} of the profiled launches since
+ * the last rsc_profile call (algorithmic flops and bytes).  json[len] host buffer. */
+rsc_status rsc_get_kernel_profile(rsc_handle* h, char* json, int64_t len);
+
 /* Message of the last error on h (or of the last failed rsc_analyze if h is NULL). */
 const char* rsc_last_error(const rsc_handle* h);
 

@@ -64,6 +64,8 @@ _SIGS = {
     "rsc_get_supernode_info": (C.c_int, [_P, C.c_int32, _P]),
     "rsc_get_supernode_blocks": (C.c_int, [_P, C.c_int32, _P, _P]),
     "rsc_get_stats": (C.c_int, [_P, C.POINTER(rsc_stats_t)]),
+    "rsc_profile": (C.c_int, [_P, C.c_int32, C.c_char_p]),
+    "rsc_get_kernel_profile": (C.c_int, [_P, C.c_char_p, C.c_int64]),
     "rsc_last_error": (C.c_char_p, [_P]),
     "rsc_destroy": (None, [_P]),
 }
@@ -213,6 +215,17 @@ def rsc_get_stats(h: Handle) -> dict:
     s = rsc_stats_t()
     _check(lib().rsc_get_stats(h.ptr, C.byref(s)), h.ptr)
     return s.as_dict()
+
+
+def rsc_profile(h: Handle, enable: bool = True, kernels: str | None = None) -> None:
+    _check(lib().rsc_profile(h.ptr, int(bool(enable)), kernels.encode() if kernels else None), h.ptr)
+
+
+def rsc_get_kernel_profile(h: Handle) -> dict:
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().rsc_get_kernel_profile(h.ptr, buf, len(buf)), h.ptr)
+    return json.loads(buf.value.decode())
 
 
 def rsc_last_error(h: Handle | None = None) -> str:

@@ -196,6 +196,25 @@ rsc_status rsc_get_stats(const rsc_handle* h, rsc_stats_t* out) {
     return RSC_OK;
 }
 
+rsc_status rsc_profile(rsc_handle* h, int32_t enable, const char* kernels) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng) h->eng = new Engine(h->sym, h->opts);
+        h->eng->profile(enable, kernels);
+        return RSC_OK;
+    });
+}
+
+rsc_status rsc_get_kernel_profile(rsc_handle* h, char* json, int64_t len) {
+    if (!h || !json || len <= 0) return fail(h, RSC_ERR_INVALID_ARG, "NULL argument");
+    return guarded(h, [&]() -> rsc_status {
+        std::string s = h->eng ? h->eng->profile_json() : std::string("{}");
+        if ((int64_t)s.size() + 1 > len) return fail(h, RSC_ERR_INVALID_ARG, "buffer too small");
+        std::memcpy(json, s.c_str(), s.size() + 1);
+        return RSC_OK;
+    });
+}
+
 const char* rsc_last_error(const rsc_handle* h) {
     if (h) return h->err.c_str();
     return g_last_error.c_str();

@@ -17,7 +17,11 @@
 // dense diagonal storage, the rest is applied implicitly by Alg. 2 / Alg. 5.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <cstdio>
+#include <map>
+#include <functional>
 #include <numeric>
 
 #include "engine.h"
@@ -83,8 +87,74 @@ struct Scratch {
     }
 };
 
+// ------------------------------------------------------------------ kernel profiler
+// CUDA event pairs around launches of the enabled kernel classes; per class the
+// launch count, device time and the algorithmic flops and bytes of the launches.
+struct Profiler {
+    bool on = false;
+    std::string only;      // empty: every class; else a comma-separated list of class names
+    struct Pend { const char* name; cudaEvent_t a, b; double flops, bytes; };
+    struct Acc { long long n = 0; double ms = 0, flops = 0, bytes = 0; };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Pend> pend;
+    std::map<std::string, Acc> acc;
+    ~Profiler() {
+        for (auto& p : pend) { pool.push_back(p.a); pool.push_back(p.b); }
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+    bool enabled(const char* name) const {
+        if (!on) return false;
+        if (only.empty()) return true;
+        std::string key = std::string(",") + only + ",";
+        return key.find(std::string(",") + name + ",") != std::string::npos;
+    }
+    cudaEvent_t ev() {
+        if (pool.empty()) { cudaEvent_t e; CK(cudaEventCreate(&e)); return e; }
+        cudaEvent_t e = pool.back(); pool.pop_back(); return e;
+    }
+    void flush() {
+        if (pend.empty()) return;
+        CK(cudaEventSynchronize(pend.back().b));
+        for (auto& p : pend) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, p.a, p.b));
+            Acc& a = acc[p.name];
+            a.n++; a.ms += ms; a.flops += p.flops; a.bytes += p.bytes;
+            pool.push_back(p.a); pool.push_back(p.b);
+        }
+        pend.clear();
+    }
+    std::string json() {
+        flush();
+        std::string out = "{";
+        bool first = true;
+        char buf[256];
+        for (auto& kv : acc) {
+            std::snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+                          first ? "" : ", ", kv.first.c_str(), kv.second.n, kv.second.ms, kv.second.flops, kv.second.bytes);
+            out += buf;
+            first = false;
+        }
+        return out + "}";
+    }
+};
+
+#define PROF(P, NAME, STREAM, FLOPS, BYTES, ...)                                   \
+    do {                                                                       \
+        if ((P).enabled(NAME)) {                                               \
+            cudaEvent_t a_ = (P).ev(), b_ = (P).ev();                          \
+            CK(cudaEventRecord(a_, STREAM));                                   \
+            __VA_ARGS__;                                                       \
+            CK(cudaEventRecord(b_, STREAM));                                   \
+            (P).pend.push_back({NAME, a_, b_, (double)(FLOPS), (double)(BYTES)}); \
+        } else {                                                               \
+            __VA_ARGS__;                                                       \
+        }                                                                      \
+    } while (0)
+
 // ------------------------------------------------------------------ engine base
 struct EngineImpl {
+    Profiler prof;
     virtual ~EngineImpl() = default;
     virtual rsc_status factor(const double* val, double tol) = 0;
     virtual bool factored() const = 0;
@@ -188,8 +258,8 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
     double* scal = part + DOT_BLOCKS;
     double h_s[4];
     auto dot = [&](const double* a, const double* b) -> double {
-        k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(n, a, b, part);
-        k_dot_final<<<1, 256, 0, s>>>(DOT_BLOCKS, part, scal);
+        PROF(prof, "dot", s, 2.0 * n, 16.0 * n, k_dot_partial<<<DOT_BLOCKS, 256, 0, s>>>(n, a, b, part);
+             k_dot_final<<<1, 256, 0, s>>>(DOT_BLOCKS, part, scal));
         launches += 2;
         CK(cudaMemcpyAsync(h_s, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -197,7 +267,9 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
     };
     const int vb = (int)std::min<long long>(cdiv(n, 256), 4 * 152);
     auto spmv = [&](const double* x, double* y) {
-        k_spmv<<<cdiv(n * 8, 256), 256, 0, s>>>(n, d_rp, d_ci, d_val, x, y);
+        const double nnz = (double)val.size();
+        PROF(prof, "spmv", s, 2.0 * nnz, 12.0 * nnz + 8.0 * (n + 1) + 16.0 * n,
+             k_spmv<<<cdiv(n * 8, 256), 256, 0, s>>>(n, d_rp, d_ci, d_val, x, y));
         launches++;
     };
     cudaEvent_t e0, e1;
@@ -221,8 +293,8 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
             spmv(p, q);
             const double pq = dot(p, q);
             const double alpha = rz / pq;
-            k_axpby<<<vb, 256, 0, s>>>(n, alpha, p, 1.0, d_x);
-            k_axpby<<<vb, 256, 0, s>>>(n, -alpha, q, 1.0, r);
+            PROF(prof, "axpy", s, 6.0 * n, 48.0 * n, k_axpby<<<vb, 256, 0, s>>>(n, alpha, p, 1.0, d_x);
+                 k_axpby<<<vb, 256, 0, s>>>(n, -alpha, q, 1.0, r));
             launches += 2;
             const double rn = std::sqrt(dot(r, r));
             if (!std::isfinite(rn)) { st = RSC_ERR_NOT_SPD; break; }
@@ -237,7 +309,7 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
             const double rz_new = dot(r, z);
             const double beta = rz_new / rz;
             rz = rz_new;
-            k_axpby<<<vb, 256, 0, s>>>(n, 1.0, z, beta, p);
+            PROF(prof, "axpy", s, 3.0 * n, 24.0 * n, k_axpby<<<vb, 256, 0, s>>>(n, 1.0, z, beta, p));
             launches++;
         }
         if (!done) {
@@ -256,6 +328,7 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     solve_seconds = ms * 1e-3;
+    prof.flush();
     last_iters = it;
     last_relres = rel;
     if (iters_out) *iters_out = it;
@@ -316,7 +389,10 @@ struct EngineT final : EngineImpl {
     double* d_small = nullptr;     // gram (256) + rinv (256)
     int* d_qstatus = nullptr;
     // per level task lists
-    struct PanelStep { PotrfTask* potrf; int npotrf; TrsmTask* trsm; int ntrsm; GemmTask* gemm; int ngemm; };
+    struct PanelStep { PotrfTask* potrf; int npotrf; TrsmTask* trsm; int ntrsm; GemmTask* gemm; int ngemm;
+                       double fl_potrf, fl_trsm, fl_gemm; };
+    struct PushElems { int k; double elems; double rows; };
+    std::vector<std::vector<PushElems>> push_elems;   // per level: per source, lower entries pushed
     std::vector<std::vector<PanelStep>> panel_steps;   // [level][step]
     std::vector<PushTask*> push_tasks;
     std::vector<int> push_count;
@@ -332,9 +408,12 @@ struct EngineT final : EngineImpl {
 
     EngineT(const Symbolic& S_, const rsc_options& o_) : S(S_), o(o_) {
         CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+        if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
         nd.resize(S.M);
     }
     ~EngineT() override {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (arena_base) cudaFree(arena_base);
         if (stream) cudaStreamDestroy(stream);
     }
 
@@ -585,8 +664,12 @@ struct EngineT final : EngineImpl {
                     const int nrows_tot = n.compressed ? n.c : n.c + n.r;
                     append_panel_step(arena + n.off, n.ld, n.c, nrows_tot, t0, j, pt, tt, gt);
                 }
+                double fp = 0, ft = 0, fg = 0;
+                for (auto& x : pt) fp += (double)x.nb * x.nb * x.nb / 3.0;
+                for (auto& x : tt) ft += (double)x.nrows * x.nb * x.nb;
+                for (auto& x : gt) fg += x.lower ? (double)x.m * (x.n + 1) * x.K : 2.0 * x.m * x.n * x.K;
                 PanelStep ps{pmem.upload(pt, stream), (int)pt.size(), pmem.upload(tt, stream), (int)tt.size(),
-                             pmem.upload(gt, stream), (int)gt.size()};
+                             pmem.upload(gt, stream), (int)gt.size(), fp, ft, fg};
                 panel_steps[l].push_back(ps);
             }
         }
@@ -596,16 +679,23 @@ struct EngineT final : EngineImpl {
         push_count.assign(S.nlevels, 0);
         {
             std::vector<std::vector<PushTask>> byl(S.nlevels);
+            std::vector<double> elems(M, 0.0), prow(M, 0.0);
             for (int j = 0; j < M; ++j)
                 for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
                     const int k = S.desc_k[d];
                     const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+                    const int rend = nd[j].compressed ? p1 : rk;
+                    const double w = p1 - p0, h = rend - p0;
+                    elems[k] += w * (w + 1) / 2 + (h - w) * w;
+                    prow[k] += h;
                     for (int pc = p0; pc < p1; pc += TILE)
-                        for (int pr = pc; pr < (nd[j].compressed ? p1 : rk); pr += TILE)
+                        for (int pr = pc; pr < rend; pr += TILE)
                             byl[S.level[k]].push_back(
-                                PushTask{k, j, pr, std::min(pr + TILE, nd[j].compressed ? p1 : rk), pc,
-                                         std::min(pc + TILE, p1)});
+                                PushTask{k, j, pr, std::min(pr + TILE, rend), pc, std::min(pc + TILE, p1)});
                 }
+            push_elems.assign(S.nlevels, {});
+            for (int k = 0; k < M; ++k)
+                if (elems[k] > 0) push_elems[S.level[k]].push_back(PushElems{k, elems[k], prow[k]});
             for (int l = 0; l < S.nlevels; ++l) {
                 push_tasks[l] = pmem.upload(byl[l], stream);
                 push_count[l] = (int)byl[l].size();
@@ -646,9 +736,9 @@ struct EngineT final : EngineImpl {
     // ---------------------------------------------------------------- launch helpers
     void run_panel_steps(const std::vector<PanelStep>& steps) {
         for (const PanelStep& ps : steps) {
-            if (ps.npotrf) { k_potrf_tile<T><<<ps.npotrf, 256, 0, stream>>>(ps.potrf, d_status); launches++; }
-            if (ps.ntrsm) { k_trsm_tile<T><<<ps.ntrsm, 256, 0, stream>>>(ps.trsm); launches++; }
-            if (ps.ngemm) { k_gemm_tile<T><<<ps.ngemm, 256, 0, stream>>>(ps.gemm); launches++; }
+            if (ps.npotrf) { PROF(prof, "potrf", stream, ps.fl_potrf, 0, k_potrf_tile<T><<<ps.npotrf, 256, 0, stream>>>(ps.potrf, d_status)); launches++; }
+            if (ps.ntrsm) { PROF(prof, "trsm", stream, ps.fl_trsm, 0, k_trsm_tile<T><<<ps.ntrsm, 256, 0, stream>>>(ps.trsm)); launches++; }
+            if (ps.ngemm) { PROF(prof, "panel_gemm", stream, ps.fl_gemm, 0, k_gemm_tile<T><<<ps.ngemm, 256, 0, stream>>>(ps.gemm)); launches++; }
             LAUNCH_CHECK();
         }
     }
@@ -684,11 +774,28 @@ struct EngineT final : EngineImpl {
         return nb * nb * nb / 3.0 + below * nb * nb + 2.0 * nb * (trail * (below - trail) + trail * (trail + 1) / 2.0);
     }
 
-    template <class X> void* upload_tmp(Scratch& sc, const std::vector<X>& v) {
-        void* p = sc.get(sizeof(X) * std::max<size_t>(v.size(), 1));
-        if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, stream));
-        // the staging buffer is reused by the next call: make the copy complete first
+    // Task records go to a bump-allocated device arena; it is reset only when the
+    // stream is idle (sync_stream), so records of kernels in flight stay valid.
+    // cudaMemcpyAsync from pageable memory stages the data before returning.
+    char* arena_base = nullptr;
+    size_t arena_cap = 0, arena_used = 0;
+    void sync_stream() {
         CK(cudaStreamSynchronize(stream));
+        arena_used = 0;
+    }
+    template <class X> void* upload_tmp(Scratch&, const std::vector<X>& v) {
+        const size_t bytes = (sizeof(X) * std::max<size_t>(v.size(), 1) + 255) / 256 * 256;
+        if (arena_used + bytes > arena_cap) {
+            sync_stream();
+            if (bytes > arena_cap) {
+                if (arena_base) CK(cudaFree(arena_base));
+                arena_cap = std::max(bytes, (size_t)64 << 20);
+                CK(cudaMalloc(&arena_base, arena_cap));
+            }
+        }
+        void* p = arena_base + arena_used;
+        arena_used += bytes;
+        if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, stream));
         return p;
     }
 
@@ -704,23 +811,28 @@ struct EngineT final : EngineImpl {
         if (ch.empty()) return;
         TnTask* d = (TnTask*)upload_tmp(sTask, ch);
         dim3 grid((unsigned)ch.size(), (unsigned)cdiv(N, 16));
-        k_tn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N);
+        double fl = 0, by = 0;
+        for (auto& t : tasks) { fl += 2.0 * t.nrow * t.K * N; by += sizeof(T) * ((double)t.nrow * t.K + (double)t.nrow * N + (double)t.K * N); }
+        PROF(prof, "tn", stream, fl, by, k_tn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N));
         launches++;
         LAUNCH_CHECK();
-        for (auto& t : tasks) flops += 2.0 * t.nrow * t.K * N;
+        flops += fl;
     }
     // NN tasks are given per descendant and split here into 64-row chunks
     void launch_nn(std::vector<NnTask>& tasks, T* Y, int ldy, int N, T alpha, bool atomic) {
         std::vector<NnTask> ch;
+        double fl = 0, by = 0;
         for (auto& t : tasks) {
             if (t.K == 0 || t.nrow == 0) continue;
             for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; ch.push_back(c); }
-            flops += 2.0 * t.nrow * t.K * N;
+            fl += 2.0 * t.nrow * t.K * N;
+            by += sizeof(T) * ((double)t.nrow * t.K + 2.0 * t.nrow * N + (double)t.K * N);
         }
+        flops += fl;
         if (ch.empty()) return;
         NnTask* d = (NnTask*)upload_tmp(sTask2, ch);
         dim3 grid((unsigned)ch.size(), (unsigned)cdiv(N, 16));
-        k_nn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N, alpha, atomic ? 1 : 0);
+        PROF(prof, "nn", stream, fl, by, k_nn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N, alpha, atomic ? 1 : 0));
         launches++;
         LAUNCH_CHECK();
     }
@@ -752,7 +864,8 @@ struct EngineT final : EngineImpl {
             std::vector<TrsvTask> tv{TrsvTask{L, ld, c, 0, X, ldx, 0}};
             TrsvTask* d = (TrsvTask*)upload_tmp(sTv, tv);
             dim3 grid(1, (unsigned)cdiv(N, 16));
-            k_trsv_multi<T><<<grid, 256, 0, stream>>>(d, N, transpose ? 1 : 0);
+            PROF(prof, "trsv", stream, (double)c * c * N, sizeof(T) * ((double)c * c / 2 + 2.0 * c * N),
+                 k_trsv<T><<<grid, 256, 0, stream>>>(d, N, transpose ? 1 : 0));
             launches++;
             LAUNCH_CHECK();
             flops += (double)c * c * N;
@@ -1070,7 +1183,7 @@ struct EngineT final : EngineImpl {
             read_norm2(Y, 16, c, 16, 1);
             double h[2];
             CK(cudaMemcpyAsync(h, d_norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, stream));
-            CK(cudaStreamSynchronize(stream));
+            sync_stream();
             if (t == 0) y1 = std::sqrt(h[0]);
             const double nrm = std::sqrt(h[1]);
             if (!std::isfinite(nrm) || !std::isfinite(y1)) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
@@ -1085,7 +1198,7 @@ struct EngineT final : EngineImpl {
             cholqr(Y, c, b, false);
             int qs = 0;
             CK(cudaMemcpyAsync(&qs, d_qstatus, sizeof(int), cudaMemcpyDeviceToHost, stream));
-            CK(cudaStreamSynchronize(stream));
+            sync_stream();
             if (qs) break;   // the remaining sample is numerically rank deficient
             rows_to_cols_ld(Y, 16, c, b, U, c, rank);
             rank += b;
@@ -1166,7 +1279,7 @@ struct EngineT final : EngineImpl {
     void check_status() {
         int st = 0;
         CK(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        CK(cudaStreamSynchronize(stream));
+        sync_stream();
         if (st) throw Error(RSC_ERR_NOT_SPD, "indefinite diagonal block in supernode " + std::to_string(st - 1));
     }
 
@@ -1219,12 +1332,18 @@ struct EngineT final : EngineImpl {
             // extend-add of the level into its ancestors
             CK(cudaMemcpyAsync(d_lo, h_lo.data(), sizeof(LoOp) * S.M, cudaMemcpyHostToDevice, stream));
             if (push_count[l]) {
-                k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf,
-                                                            arena);
+                double pf = 0, pb = 0;
+                for (auto& e : push_elems[l]) {
+                    pf += 2.0 * e.elems * h_lo[e.k].K;
+                    pb += sizeof(T) * ((double)e.rows * h_lo[e.k].K + 2.0 * e.elems);
+                }
+                PROF(prof, "push", stream, pf, pb,
+                     k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf,
+                                                                 arena));
                 launches++;
                 LAUNCH_CHECK();
             }
-            CK(cudaStreamSynchronize(stream));   // h_lo is rewritten by the next level
+            sync_stream();   // h_lo is rewritten by the next level
         }
         // push flops: lower half of L^O_k L^O_k^T per source
         for (int k = 0; k < S.M; ++k) {
@@ -1256,7 +1375,8 @@ struct EngineT final : EngineImpl {
                     cudaEventDestroy(e1);
                     throw;
                 }
-                CK(cudaStreamSynchronize(stream));
+                sync_stream();
+                prof.flush();
                 ++restarts;
                 if (restarts <= o.max_restarts) tol_D /= 1.25;
                 else diag_on = false;
@@ -1271,106 +1391,255 @@ struct EngineT final : EngineImpl {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         factor_seconds = ms * 1e-3;
+        prof.flush();
         is_factored = true;
         build_solve_plan();
         return RSC_OK;
     }
 
     // ---------------------------------------------------------------- preconditioner apply
-    struct SolveLevel {
-        TrsvTask* trsv; int ntrsv;        // dense diagonal blocks up to SOLVE_MAX
-        std::vector<int> big;             // dense > SOLVE_MAX or hierarchical: per node
-        TnTask* tnf; int ntnf;            // forward: tmp_j = U_j^T y_C (compressed)
-        NnTask* nnf; int nnnf;            // forward: y_R -= L^O y_C  /  V tmp
-        TnTask* tnb; int ntnb;            // backward: tmp = V^T y_R (compressed) or y_C -= L^O^T y_R
-        NnTask* nnb; int nnnb;            // backward: y_C -= U tmp (compressed)
-        TnTask* tnb_acc; int ntnb_acc;    // backward (uncompressed): tmpc = L^O^T y_R
-        std::vector<std::pair<int, long long>> acc_nodes;   // (node, tmp offset) for y_C -= tmpc
-    };
-    std::vector<SolveLevel> slev;
+    // The apply is a fixed list of batched launches built once per factor:
+    //   forward, level by level: dense diagonal solves (TRSV, all small nodes of the
+    //   level in one launch), the in-order actions of hierarchical / large dense
+    //   diagonal blocks batched across the level's nodes by action index, then the
+    //   off-diagonal updates y_R -= L^O y_C (or V (U^T y_C));
+    //   backward, levels in reverse: y_C -= L^O^T y_R (or U (V^T y_R)), the actions
+    //   in reverse order, the transposed small dense solves.
+    // It is captured once into a CUDA graph reading g_in and writing g_out.
+    enum LKind { L_PERM_IN, L_PERM_OUT, L_TRSV, L_TN, L_NN };
+    struct Launch { int kind; int count; size_t off; int flag; };
+    std::vector<Launch> seq;
     DeviceMem smem_plan;
     T* y_dev = nullptr;
     T* tmp_dev = nullptr;
+    double* g_in = nullptr;
+    double* g_out = nullptr;
+    TrsvTask* d_trsv_all = nullptr;
+    TnTask* d_tn_all = nullptr;
+    NnTask* d_nn_all = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    double apply_flops = 0, apply_bytes = 0;
+
+    struct SolveBuild {
+        std::vector<TrsvTask> trsv;
+        std::vector<TnTask> tn;
+        std::vector<NnTask> nn;
+    };
+    struct Act { std::vector<TrsvTask> trsv; std::vector<TnTask> tn; std::vector<NnTask> nn; };
+
+    static void push_nn_chunks(std::vector<NnTask>& v, NnTask t) {
+        for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; v.push_back(c); }
+    }
+    static void push_tn_chunks(std::vector<TnTask>& v, const TnTask& t) {
+        for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; v.push_back(c); }
+    }
+
+    // In-order actions of one diagonal block (vector right-hand side, X = y + c0).
+    void diag_actions(int j, bool transpose, T*& zcur, std::vector<Act>& acts) {
+        const NodeRT& n = nd[j];
+        T* X = y_dev + n.c0;
+        if (!n.hier) {
+            const T* L = arena + n.off;
+            const int ld = n.ld, c = n.c, bs = SOLVE_MAX;
+            const int nblk = cdiv(c, bs);
+            for (int bi = 0; bi < nblk; ++bi) {
+                const int b = transpose ? nblk - 1 - bi : bi;
+                const int b0 = b * bs, b1 = std::min(c, b0 + bs);
+                Act a;
+                a.trsv.push_back(TrsvTask{L + b0 + (size_t)b0 * ld, ld, b1 - b0, 0, X + b0, 1, 0});
+                if (!transpose && b1 < c)
+                    push_nn_chunks(a.nn, NnTask{L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, 0, nullptr,
+                                                (int)(n.c0 + b1), X + b0, 1, 0});
+                if (transpose && b0 > 0) {
+                    TnTask t{L + b0, ld, b0, b1 - b0, nullptr, 0, nullptr, 0, X, 1, 0};
+                    t.alpha = -1.0; t.beta = 1.0;
+                    t.ymap = nullptr;
+                    // Y rows b0..b1 of X: express through yoff on the vector y
+                    t.yoff = (int)(n.c0 + b0);
+                    push_tn_chunks(a.tn, t);
+                }
+                acts.push_back(std::move(a));
+            }
+            return;
+        }
+        const BlockTree& t = S.tree[j];
+        // recursive emission in the order of Alg. 4 (corrected branches)
+        std::function<void(int)> rec = [&](int s) {
+            if (t.leaf[s]) {
+                Act a;
+                const int sz = t.hi[s] - t.lo[s];
+                a.trsv.push_back(TrsvTask{arena + n.leaf_off[s], sz, sz, 0, X + t.lo[s], 1, 0});
+                acts.push_back(std::move(a));
+                return;
+            }
+            const int n1 = t.mid[s] - t.lo[s], n2 = t.hi[s] - t.mid[s], q = n.brank[s];
+            auto lowrank = [&]() {
+                if (!q) return;
+                Act a;
+                T* Z = zcur;
+                zcur += q;
+                if (!transpose) {   // X2 -= V_s (U_s^T X1)
+                    push_tn_chunks(a.tn, TnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, (int)(n.c0 + t.lo[s]), Z, 1, 0});
+                    push_nn_chunks(a.nn, NnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, (int)(n.c0 + t.mid[s]), Z, 1, 0});
+                } else {            // X1 -= U_s (V_s^T X2)
+                    push_tn_chunks(a.tn, TnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, (int)(n.c0 + t.mid[s]), Z, 1, 0});
+                    push_nn_chunks(a.nn, NnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, (int)(n.c0 + t.lo[s]), Z, 1, 0});
+                }
+                acts.push_back(std::move(a));
+            };
+            if (!transpose) { rec(t.left[s]); lowrank(); rec(t.right[s]); }
+            else { rec(t.right[s]); lowrank(); rec(t.left[s]); }
+        };
+        rec(t.root);
+    }
 
     void build_solve_plan() {
+        if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
         smem_plan.release();
-        slev.assign(S.nlevels, SolveLevel{});
-        y_dev = (T*)smem_plan.alloc(sizeof(T) * S.n);
+        seq.clear();
+        apply_flops = apply_bytes = 0;
+        const long long n = S.n;
+        y_dev = (T*)smem_plan.alloc(sizeof(T) * n);
+        g_in = (double*)smem_plan.alloc(sizeof(double) * n);
+        g_out = (double*)smem_plan.alloc(sizeof(double) * n);
         long long tmp_total = 0;
-        for (int j = 0; j < S.M; ++j) tmp_total += nd[j].compressed ? nd[j].rank : nd[j].c;
+        for (int j = 0; j < S.M; ++j) {
+            const NodeRT& nn = nd[j];
+            tmp_total += nn.compressed ? nn.rank : 0;
+            if (nn.hier)
+                for (int b = 1; b <= S.tree[j].nblocks; ++b) tmp_total += 2 * nn.brank[b];
+        }
         tmp_dev = (T*)smem_plan.alloc(sizeof(T) * std::max<long long>(tmp_total, 1));
-        long long toff = 0;
-        std::vector<long long> tmpo(S.M);
-        for (int j = 0; j < S.M; ++j) { tmpo[j] = toff; toff += nd[j].compressed ? nd[j].rank : nd[j].c; }
+        T* zcur = tmp_dev;
+        SolveBuild B;
+        auto emit = [&](int kind, size_t off, size_t cnt, int flag) {
+            if (cnt) seq.push_back(Launch{kind, (int)cnt, off, flag});
+        };
+        auto emit_acts = [&](std::vector<std::vector<Act>>& per_node, bool transpose) {
+            size_t maxa = 0;
+            for (auto& v : per_node) maxa = std::max(maxa, v.size());
+            for (size_t ai = 0; ai < maxa; ++ai) {
+                size_t o1 = B.trsv.size(), o2 = B.tn.size(), o3 = B.nn.size();
+                for (auto& v : per_node) {
+                    if (ai >= v.size()) continue;
+                    Act& a = v[ai];
+                    B.trsv.insert(B.trsv.end(), a.trsv.begin(), a.trsv.end());
+                    B.tn.insert(B.tn.end(), a.tn.begin(), a.tn.end());
+                    B.nn.insert(B.nn.end(), a.nn.begin(), a.nn.end());
+                }
+                emit(L_TRSV, o1, B.trsv.size() - o1, transpose ? 1 : 0);
+                emit(L_TN, o2, B.tn.size() - o2, 0);
+                emit(L_NN, o3, B.nn.size() - o3, 0);
+            }
+        };
+        emit(L_PERM_IN, 0, 1, 0);
+        std::vector<std::vector<T*>> ztmp(S.nlevels);
         for (int l = 0; l < S.nlevels; ++l) {
-            SolveLevel& L = slev[l];
-            std::vector<TrsvTask> tv;
-            std::vector<TnTask> tnf, tnb, tnacc;
-            std::vector<NnTask> nnf, nnb;
+            size_t o = B.trsv.size();
+            std::vector<std::vector<Act>> acts;
             for (int j : S.level_nodes[l]) {
-                const NodeRT& n = nd[j];
-                if (!n.hier && n.c <= SOLVE_MAX) tv.push_back(TrsvTask{arena + n.off, n.ld, n.c, 0, y_dev + n.c0, 1, 0});
-                else L.big.push_back(j);
-                if (n.r == 0) continue;
+                const NodeRT& nn = nd[j];
+                apply_bytes += 2.0 * sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
+                if (!nn.hier && nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 0, y_dev + nn.c0, 1, 0});
+                else { acts.emplace_back(); diag_actions(j, false, zcur, acts.back()); }
+            }
+            emit(L_TRSV, o, B.trsv.size() - o, 0);
+            emit_acts(acts, false);
+            size_t o2 = B.tn.size(), o3 = B.nn.size();
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (nn.r == 0) continue;
                 const int32_t* Rj = d_rows + S.rows_ptr[j];
-                T* tmp = tmp_dev + tmpo[j];
-                if (!n.compressed) {
-                    const T* LO = arena + n.off + n.c;
-                    for (int r0 = 0; r0 < n.r; r0 += 64)
-                        nnf.push_back(NnTask{LO, n.ld, n.c, n.r, nullptr, 0, Rj, 0, y_dev + n.c0, 1, r0});
-                    tnacc.push_back(TnTask{LO, n.ld, n.c, n.r, nullptr, 0, Rj, 0, tmp, 1, 0});
-                    L.acc_nodes.push_back({j, tmpo[j]});
-                } else if (n.rank) {
-                    tnf.push_back(TnTask{n.U, n.c, n.rank, n.c, nullptr, 0, nullptr, (int)n.c0, tmp, 1, 0});
-                    for (int r0 = 0; r0 < n.r; r0 += 64)
-                        nnf.push_back(NnTask{n.V, n.r, n.rank, n.r, nullptr, 0, Rj, 0, tmp, 1, r0});
-                    tnb.push_back(TnTask{n.V, n.r, n.rank, n.r, nullptr, 0, Rj, 0, tmp, 1, 0});
-                    for (int r0 = 0; r0 < n.c; r0 += 64)
-                        nnb.push_back(NnTask{n.U, n.c, n.rank, n.c, nullptr, 0, nullptr, (int)n.c0, tmp, 1, r0});
+                if (!nn.compressed) {
+                    push_nn_chunks(B.nn, NnTask{arena + nn.off + nn.c, nn.ld, nn.c, nn.r, nullptr, 0, Rj, 0, y_dev + nn.c0, 1, 0});
+                    apply_bytes += 2.0 * sizeof(T) * nn.r * nn.c;
+                } else if (nn.rank) {
+                    T* tmp = zcur; zcur += nn.rank;
+                    ztmp[l].push_back(tmp);
+                    push_tn_chunks(B.tn, TnTask{nn.U, nn.c, nn.rank, nn.c, nullptr, 0, nullptr, (int)nn.c0, tmp, 1, 0});
+                    push_nn_chunks(B.nn, NnTask{nn.V, nn.r, nn.rank, nn.r, nullptr, 0, Rj, 0, tmp, 1, 0});
+                    apply_bytes += 2.0 * sizeof(T) * nn.rank * (nn.r + nn.c);
                 }
             }
-            L.trsv = smem_plan.upload(tv, stream); L.ntrsv = (int)tv.size();
-            tnf = expand_tn(tnf);
-            tnb = expand_tn(tnb);
-            tnacc = expand_tn(tnacc);
-            L.tnf = smem_plan.upload(tnf, stream); L.ntnf = (int)tnf.size();
-            L.nnf = smem_plan.upload(nnf, stream); L.nnnf = (int)nnf.size();
-            L.tnb = smem_plan.upload(tnb, stream); L.ntnb = (int)tnb.size();
-            L.nnb = smem_plan.upload(nnb, stream); L.nnnb = (int)nnb.size();
-            L.tnb_acc = smem_plan.upload(tnacc, stream); L.ntnb_acc = (int)tnacc.size();
+            emit(L_TN, o2, B.tn.size() - o2, 0);
+            emit(L_NN, o3, B.nn.size() - o3, 1);   // atomic: nodes of a level share rows of R
         }
-        CK(cudaStreamSynchronize(stream));
+        for (int l = S.nlevels - 1; l >= 0; --l) {
+            size_t o2 = B.tn.size();
+            size_t zi = 0;
+            std::vector<NnTask> nnb;
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (nn.r == 0) continue;
+                const int32_t* Rj = d_rows + S.rows_ptr[j];
+                if (!nn.compressed) {
+                    TnTask t{arena + nn.off + nn.c, nn.ld, nn.c, nn.r, nullptr, 0, Rj, 0, y_dev + nn.c0, 1, 0};
+                    t.alpha = -1.0; t.beta = 1.0;
+                    push_tn_chunks(B.tn, t);
+                } else if (nn.rank) {
+                    T* tmp = ztmp[l][zi++];
+                    push_tn_chunks(B.tn, TnTask{nn.V, nn.r, nn.rank, nn.r, nullptr, 0, Rj, 0, tmp, 1, 0});
+                    push_nn_chunks(nnb, NnTask{nn.U, nn.c, nn.rank, nn.c, nullptr, 0, nullptr, (int)nn.c0, tmp, 1, 0});
+                }
+            }
+            emit(L_TN, o2, B.tn.size() - o2, 0);
+            size_t o3 = B.nn.size();
+            B.nn.insert(B.nn.end(), nnb.begin(), nnb.end());
+            emit(L_NN, o3, nnb.size(), 0);
+            std::vector<std::vector<Act>> acts;
+            size_t o = B.trsv.size();
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (!nn.hier && nn.c <= SOLVE_MAX) continue;
+                acts.emplace_back();
+                diag_actions(j, true, zcur, acts.back());
+            }
+            emit_acts(acts, true);
+            o = B.trsv.size();
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (!nn.hier && nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 0, y_dev + nn.c0, 1, 0});
+            }
+            emit(L_TRSV, o, B.trsv.size() - o, 1);
+        }
+        emit(L_PERM_OUT, 0, 1, 0);
+        if (zcur > tmp_dev + std::max<long long>(tmp_total, 1)) throw Error(RSC_ERR_CUDA, "solve scratch overflow");
+        d_trsv_all = smem_plan.upload(B.trsv, stream);
+        d_tn_all = smem_plan.upload(B.tn, stream);
+        d_nn_all = smem_plan.upload(B.nn, stream);
+        for (auto& t : B.tn) apply_flops += 2.0 * t.nrow * std::min(8, t.K - t.t0);
+        for (auto& t : B.nn) apply_flops += 2.0 * std::min(64, t.nrow - t.row0) * t.K;
+        apply_bytes += 4.0 * sizeof(T) * n + 16.0 * n;
+        sync_stream();
+        // capture the launch list once
+        CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        issue_apply(stream);
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamEndCapture(stream, &g));
+        CK(cudaGraphInstantiate(&graph_exec, g, 0));
+        CK(cudaGraphDestroy(g));
+    }
+
+    void issue_apply(cudaStream_t s) {
+        const long long n = S.n;
+        for (const Launch& L : seq) {
+            switch (L.kind) {
+                case L_PERM_IN: k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(g_in, d_perm, y_dev, n); break;
+                case L_PERM_OUT: k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, g_out, n); break;
+                case L_TRSV: k_trsv<T><<<L.count, 256, 0, s>>>(d_trsv_all + L.off, 1, L.flag); break;
+                case L_TN: k_tn<T><<<L.count, 256, 0, s>>>(d_tn_all + L.off, y_dev, 1, 1); break;
+                case L_NN: k_nn<T><<<L.count, 256, 0, s>>>(d_nn_all + L.off, y_dev, 1, 1, T(-1), L.flag); break;
+            }
+        }
+        LAUNCH_CHECK();
     }
 
     void apply(const double* d_r, double* d_z, cudaStream_t s) override {
-        cudaStream_t keep = stream;
-        stream = s;
         const long long n = S.n;
-        k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(d_r, d_perm, y_dev, n);
-        launches++;
-        for (int l = 0; l < S.nlevels; ++l) {
-            const SolveLevel& L = slev[l];
-            if (L.ntrsv) { k_trsv_multi<T><<<L.ntrsv, 256, 0, s>>>(L.trsv, 1, 0); launches++; }
-            for (int j : L.big) diag_solve(j, 0, y_dev + nd[j].c0, 1, 1, false);
-            if (L.ntnf) { k_tn<T><<<L.ntnf, 256, 0, s>>>(L.tnf, y_dev, 1, 1); launches++; }
-            if (L.nnnf) { k_nn<T><<<L.nnnf, 256, 0, s>>>(L.nnf, y_dev, 1, 1, T(-1), 1); launches++; }
-        }
-        for (int l = S.nlevels - 1; l >= 0; --l) {
-            const SolveLevel& L = slev[l];
-            if (L.ntnb_acc) {
-                k_tn<T><<<L.ntnb_acc, 256, 0, s>>>(L.tnb_acc, y_dev, 1, 1);
-                launches++;
-                for (auto& pr : L.acc_nodes) axpy_rows(tmp_dev + pr.second, 1, y_dev + nd[pr.first].c0, 1, nd[pr.first].c, 1, T(-1));
-            }
-            if (L.ntnb) { k_tn<T><<<L.ntnb, 256, 0, s>>>(L.tnb, y_dev, 1, 1); launches++; }
-            if (L.nnnb) { k_nn<T><<<L.nnnb, 256, 0, s>>>(L.nnb, y_dev, 1, 1, T(-1), 0); launches++; }
-            if (L.ntrsv) { k_trsv_multi<T><<<L.ntrsv, 256, 0, s>>>(L.trsv, 1, 1); launches++; }
-            for (int j : L.big) diag_solve(j, 0, y_dev + nd[j].c0, 1, 1, true);
-        }
-        k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, d_z, n);
-        launches++;
-        LAUNCH_CHECK();
-        stream = keep;
+        if (d_r != g_in) CK(cudaMemcpyAsync(g_in, d_r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        PROF(prof, "apply", s, apply_flops, apply_bytes, CK(cudaGraphLaunch(graph_exec, s)));
+        launches += (long long)seq.size();
+        if (d_z != g_out) CK(cudaMemcpyAsync(d_z, g_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
 
     // ---------------------------------------------------------------- introspection
@@ -1550,5 +1819,12 @@ rsc_status Engine::apply_precond(const double* d_r, double* d_z, void* stream) {
 void Engine::node_info(int j, int32_t* info) const { impl_->node_info(j, info); }
 rsc_status Engine::node_blocks(int j, double* LD, double* LO) const { return impl_->node_blocks(j, LD, LO); }
 void Engine::stats(rsc_stats_t* out) const { impl_->stats(out); }
+void Engine::profile(int enable, const char* only) {
+    impl_->prof.flush();
+    impl_->prof.acc.clear();
+    impl_->prof.on = enable != 0;
+    impl_->prof.only = only ? only : "";
+}
+std::string Engine::profile_json() { return impl_->prof.json(); }
 
 }  // namespace rsc

@@ -35,6 +35,8 @@ public:
     void node_info(int j, int32_t* info) const;
     rsc_status node_blocks(int j, double* LD, double* LO) const;
     void stats(rsc_stats_t* out) const;
+    void profile(int enable, const char* only);
+    std::string profile_json();
 
 private:
     std::unique_ptr<EngineImpl> impl_;

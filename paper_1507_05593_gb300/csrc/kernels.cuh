@@ -32,6 +32,7 @@ struct TnTask {              // Z[t, :] = sum_i A[arow_i, t] * Y[yrow_i, :]   (Z
     const void* A; int lda; int K; int nrow;
     const int32_t* amap; int aoff; const int32_t* ymap; int yoff;
     void* Z; int ldz; int t0;   // t0: first column of A handled by this CTA (8 columns, one per warp)
+    double alpha = 1.0, beta = 0.0;   // Z = beta Z + alpha sum
 };
 struct NnTask {              // Y[yrow_i, :] += alpha * sum_l A[arow_i, l] * Z[l, :]
     const void* A; int lda; int K; int nrow;
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks, co
 #pragma unroll
             for (int c = 1; c < 16; ++c)
                 if (lane == c) v = acc[c];
-            Z[(size_t)t * tk.ldz + c0 + lane] = v;
+            T* z = Z + (size_t)t * tk.ldz + c0 + lane;
+            *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * v : (T)tk.alpha * v;
         }
     }
 }
@@ -354,43 +356,87 @@ __global__ void k_csr_mm(CsrBlock blk, const T* __restrict__ X, int ldx, T* __re
 
 // ------------------------------------------------------------------ dense triangular solves with many RHS
 // X (c x N, row-major) <- L^{-1} X or L^{-T} X, one CTA per (task, 16-column chunk), c <= SOLVE_MAX.
+// Blocked by 32 rows: a warp solves each column of the 32 x 32 diagonal tile with
+// shuffles, then the CTA updates the remaining rows with the solved block.
 template <class T>
-__global__ void __launch_bounds__(256) k_trsv_multi(const TrsvTask* __restrict__ tasks, int N, int transpose) {
+__global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks, int N, int transpose) {
     __shared__ T Xs[SOLVE_MAX][17];
+    __shared__ T Lt[32][33];
     const TrsvTask tk = tasks[blockIdx.x];
     const T* L = (const T*)tk.L;
     T* X = (T*)tk.X;
     const int c = tk.c, ld = tk.ld;
     const int c0 = blockIdx.y * 16;
     const int nc = min(16, N - c0);
-    for (int e = threadIdx.x; e < c * 16; e += blockDim.x) {
+    if (nc <= 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < c * 16; e += blockDim.x) {
         int i = e >> 4, q = e & 15;
         Xs[i][q] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
     }
-    __syncthreads();
-    if (!transpose) {
-        for (int i = 0; i < c; ++i) {
-            if (threadIdx.x < 16) Xs[i][threadIdx.x] /= L[i + (size_t)i * ld];
-            __syncthreads();
-            const int m = c - i - 1;
-            for (int e = threadIdx.x; e < m * 16; e += blockDim.x) {
-                int l = i + 1 + (e >> 4), q = e & 15;
-                Xs[l][q] -= L[l + (size_t)i * ld] * Xs[i][q];
-            }
-            __syncthreads();
+    const int nb = (c + 31) >> 5;
+    for (int bi = 0; bi < nb; ++bi) {
+        const int b = transpose ? nb - 1 - bi : bi;
+        const int r0 = b * 32, w = min(32, c - r0);
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += blockDim.x) {
+            int i = e & 31, j = e >> 5;
+            Lt[i][j] = (i < w && j < w && i >= j) ? L[(r0 + i) + (size_t)(r0 + j) * ld] : T(0);
         }
-    } else {
-        for (int i = c - 1; i >= 0; --i) {
-            if (threadIdx.x < 16) Xs[i][threadIdx.x] /= L[i + (size_t)i * ld];
-            __syncthreads();
-            for (int e = threadIdx.x; e < i * 16; e += blockDim.x) {
-                int l = e >> 4, q = e & 15;
-                Xs[l][q] -= L[i + (size_t)l * ld] * Xs[i][q];
+        __syncthreads();
+        for (int q = warp; q < nc; q += 8) {
+            T x = lane < w ? Xs[r0 + lane][q] : T(0);
+            if (!transpose) {
+                for (int k = 0; k < w; ++k) {
+                    if (lane == k) x /= Lt[k][k];
+                    const T xk = __shfl_sync(0xffffffffu, x, k);
+                    if (lane > k) x -= Lt[lane][k] * xk;
+                }
+            } else {
+                for (int k = w - 1; k >= 0; --k) {
+                    if (lane == k) x /= Lt[k][k];
+                    const T xk = __shfl_sync(0xffffffffu, x, k);
+                    if (lane < k) x -= Lt[k][lane] * xk;
+                }
             }
-            __syncthreads();
+            if (lane < w) Xs[r0 + lane][q] = x;
+        }
+        __syncthreads();
+        if (!transpose) {
+            // rows below: X[i,:] -= L[i, r0:r0+w] X[r0:r0+w, :]
+            const int rem = c - r0 - w;
+            for (int e = tid; e < rem * 4; e += blockDim.x) {
+                const int i = r0 + w + (e >> 2), g = (e & 3) * 4;
+                if (g >= nc) continue;
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                for (int k = 0; k < w; ++k) {
+                    const T l = L[i + (size_t)(r0 + k) * ld];
+                    a0 = fma(l, Xs[r0 + k][g], a0);
+                    a1 = fma(l, Xs[r0 + k][g + 1], a1);
+                    a2 = fma(l, Xs[r0 + k][g + 2], a2);
+                    a3 = fma(l, Xs[r0 + k][g + 3], a3);
+                }
+                Xs[i][g] -= a0; Xs[i][g + 1] -= a1; Xs[i][g + 2] -= a2; Xs[i][g + 3] -= a3;
+            }
+        } else {
+            // rows above: X[i,:] -= L[r0:r0+w, i]^T X[r0:r0+w, :]
+            for (int e = tid; e < r0 * 4; e += blockDim.x) {
+                const int i = e >> 2, g = (e & 3) * 4;
+                if (g >= nc) continue;
+                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+                for (int k = 0; k < w; ++k) {
+                    const T l = L[(r0 + k) + (size_t)i * ld];
+                    a0 = fma(l, Xs[r0 + k][g], a0);
+                    a1 = fma(l, Xs[r0 + k][g + 1], a1);
+                    a2 = fma(l, Xs[r0 + k][g + 2], a2);
+                    a3 = fma(l, Xs[r0 + k][g + 3], a3);
+                }
+                Xs[i][g] -= a0; Xs[i][g + 1] -= a1; Xs[i][g + 2] -= a2; Xs[i][g + 3] -= a3;
+            }
         }
     }
-    for (int e = threadIdx.x; e < c * 16; e += blockDim.x) {
+    __syncthreads();
+    for (int e = tid; e < c * 16; e += blockDim.x) {
         int i = e >> 4, q = e & 15;
         if (q < nc) X[(size_t)i * tk.ldx + c0 + q] = Xs[i][q];
     }
