@@ -743,28 +743,38 @@ struct EngineT final : EngineImpl {
         }
     }
 
-    // factor one dense panel (nrows_tot x c) outside the level batches
-    void factor_dense(T* P, int ld, int c, int nrows_tot, int node) {
-        for (int t0 = 0; t0 < c; t0 += NB) {
+    // factor a batch of dense panels (nrows_tot x c each) together, step by step
+    struct DensePanel { T* P; int ld; int c; int nrows_tot; int node; };
+    void factor_dense_batch(const std::vector<DensePanel>& ps) {
+        int maxc = 0;
+        for (auto& d : ps) maxc = std::max(maxc, d.c);
+        for (int t0 = 0; t0 < maxc; t0 += NB) {
             std::vector<PotrfTask> pt;
             std::vector<TrsmTask> tt;
             std::vector<GemmTask> gt;
-            append_panel_step(P, ld, c, nrows_tot, t0, node, pt, tt, gt);
+            double fp = 0, ft = 0, fg = 0;
+            for (auto& d : ps) {
+                if (t0 >= d.c) continue;
+                append_panel_step(d.P, d.ld, d.c, d.nrows_tot, t0, d.node, pt, tt, gt);
+                flops += nb_flops(d.c, d.nrows_tot, t0);
+            }
+            for (auto& x : pt) fp += (double)x.nb * x.nb * x.nb / 3.0;
+            for (auto& x : tt) ft += (double)x.nrows * x.nb * x.nb;
+            for (auto& x : gt) fg += x.lower ? (double)x.m * (x.n + 1) * x.K : 2.0 * x.m * x.n * x.K;
             PotrfTask* dp = (PotrfTask*)upload_tmp(sTask, pt);
-            k_potrf_tile<T><<<(int)pt.size(), 256, 0, stream>>>(dp, d_status);
+            PROF(prof, "potrf", stream, fp, 0, k_potrf_tile<T><<<(int)pt.size(), 256, 0, stream>>>(dp, d_status));
             launches++;
             if (!tt.empty()) {
                 TrsmTask* dt = (TrsmTask*)upload_tmp(sTask2, tt);
-                k_trsm_tile<T><<<(int)tt.size(), 256, 0, stream>>>(dt);
+                PROF(prof, "trsm", stream, ft, 0, k_trsm_tile<T><<<(int)tt.size(), 256, 0, stream>>>(dt));
                 launches++;
             }
             if (!gt.empty()) {
                 GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
-                k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg);
+                PROF(prof, "panel_gemm", stream, fg, 0, k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg));
                 launches++;
             }
             LAUNCH_CHECK();
-            flops += (double)nb_flops(c, nrows_tot, t0);
         }
     }
     static double nb_flops(int c, int nrows_tot, int t0) {
@@ -799,221 +809,236 @@ struct EngineT final : EngineImpl {
         return p;
     }
 
-    // TN tasks are split here into 8-column chunks (one column per warp)
-    static std::vector<TnTask> expand_tn(const std::vector<TnTask>& tasks) {
-        std::vector<TnTask> ch;
-        for (const auto& t : tasks)
-            for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; ch.push_back(c); }
-        return ch;
-    }
-    void launch_tn(std::vector<TnTask>& tasks, const T* Y, int ldy, int N) {
-        std::vector<TnTask> ch = expand_tn(tasks);
-        if (ch.empty()) return;
-        TnTask* d = (TnTask*)upload_tmp(sTask, ch);
-        dim3 grid((unsigned)ch.size(), (unsigned)cdiv(N, 16));
-        double fl = 0, by = 0;
-        for (auto& t : tasks) { fl += 2.0 * t.nrow * t.K * N; by += sizeof(T) * ((double)t.nrow * t.K + (double)t.nrow * N + (double)t.K * N); }
-        PROF(prof, "tn", stream, fl, by, k_tn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N));
-        launches++;
-        LAUNCH_CHECK();
-        flops += fl;
-    }
-    // NN tasks are given per descendant and split here into 64-row chunks
-    void launch_nn(std::vector<NnTask>& tasks, T* Y, int ldy, int N, T alpha, bool atomic) {
-        std::vector<NnTask> ch;
-        double fl = 0, by = 0;
-        for (auto& t : tasks) {
-            if (t.K == 0 || t.nrow == 0) continue;
-            for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; ch.push_back(c); }
-            fl += 2.0 * t.nrow * t.K * N;
-            by += sizeof(T) * ((double)t.nrow * t.K + 2.0 * t.nrow * N + (double)t.K * N);
-        }
-        flops += fl;
-        if (ch.empty()) return;
-        NnTask* d = (NnTask*)upload_tmp(sTask2, ch);
-        dim3 grid((unsigned)ch.size(), (unsigned)cdiv(N, 16));
-        PROF(prof, "nn", stream, fl, by, k_nn<T><<<grid, 256, 0, stream>>>(d, Y, ldy, N, alpha, atomic ? 1 : 0));
-        launches++;
-        LAUNCH_CHECK();
-    }
-    void csr_mm(const CsrBlock& b, const T* X, int ldx, T* Y, int ldy, int N, T alpha, bool acc) {
-        if (b.nrows == 0) return;
-        dim3 grid((unsigned)std::min(cdiv((long long)b.nrows * 16, 256), 4096), (unsigned)cdiv(N, 16));
-        k_csr_mm<T><<<grid, 256, 0, stream>>>(b, X, ldx, Y, ldy, N, alpha, acc ? 1 : 0);
-        launches++;
-        LAUNCH_CHECK();
-    }
-    void fill(T* X, long long cnt, T v) {
-        if (cnt <= 0) return;
-        k_fill<T><<<std::min(cdiv(cnt, 256), 4096), 256, 0, stream>>>(X, cnt, v);
-        launches++;
-    }
-    void axpy_rows(const T* X, int ldx, T* Y, int ldy, int m, int nc, T alpha) {
-        if (m <= 0) return;
-        k_axpy_rows<T><<<std::min(cdiv((long long)m * nc, 256), 4096), 256, 0, stream>>>(X, ldx, Y, ldy, m, nc, alpha);
-        launches++;
-    }
-    // copy a row-major block (m x nc, ld ldx) into column-major storage (ld ldu) at column col0
-    void rows_to_cols_ld(const T* X, int ldx, int m, int nc, T* U, int ldu, int col0);
+    // ---------------------------------------------------------------- stage programs
+    // An operation of one supernode (an implicit product, a hierarchical solve, ...)
+    // is a list of stages.  Stage i of every node in a batch is launched together,
+    // phase A (copies, samples, sparse products, triangular solves) before phase B
+    // (TN products) before phase C (NN products); a stage never holds two phase-A
+    // records that touch the same buffer.
+    struct Stage {
+        std::vector<GaussTask> gauss;
+        std::vector<CopyTask> copy;
+        std::vector<CsrTask> csr;
+        std::vector<TrsvTask> trsv;
+        std::vector<TnTask> tn;
+        std::vector<NnTask> nn;
+    };
+    using Program = std::vector<Stage>;
+    static constexpr int TRSV_CW = sizeof(T) == 8 ? 1 : 8;   // FP64: spread columns over more SMs
 
-    // ---------------------------------------------------------------- dense / hierarchical triangular solves
-    // X (c x N row-major, ld ldx) <- L^{-1} X or L^{-T} X for dense lower L (ld)
-    void dense_solve(const T* L, int ld, int c, T* X, int ldx, int N, bool transpose) {
+    static TnTask tn_task(const void* A, int lda, int K, int nrow, const int32_t* amap, int aoff, const int32_t* ymap,
+                          int yoff, const void* Y, int ldy, void* Z, int ldz, int N, double alpha = 1.0,
+                          double beta = 0.0) {
+        TnTask t{};
+        t.A = A; t.lda = lda; t.K = K; t.nrow = nrow; t.amap = amap; t.aoff = aoff; t.ymap = ymap; t.yoff = yoff;
+        t.Z = Z; t.ldz = ldz; t.t0 = 0; t.Y = Y; t.ldy = ldy; t.N = N; t.alpha = alpha; t.beta = beta;
+        return t;
+    }
+    static NnTask nn_task(const void* A, int lda, int K, int nrow, const int32_t* amap, int aoff, const int32_t* ymap,
+                          int yoff, const void* Z, int ldz, void* Y, int ldy, int N, double alpha, bool atomic) {
+        NnTask t{};
+        t.A = A; t.lda = lda; t.K = K; t.nrow = nrow; t.amap = amap; t.aoff = aoff; t.ymap = ymap; t.yoff = yoff;
+        t.Z = Z; t.ldz = ldz; t.row0 = 0; t.Y = Y; t.ldy = ldy; t.N = N; t.alpha = alpha; t.atomic = atomic ? 1 : 0;
+        return t;
+    }
+    void add_tn(Stage& s, const TnTask& t) {
+        if (t.K == 0 || t.nrow == 0 || t.N == 0) return;
+        for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; s.tn.push_back(c); }
+        flops += 2.0 * t.nrow * t.K * t.N;
+    }
+    void add_nn(Stage& s, const NnTask& t) {
+        if (t.K == 0 || t.nrow == 0 || t.N == 0) return;
+        for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; s.nn.push_back(c); }
+        flops += 2.0 * t.nrow * t.K * t.N;
+    }
+    void add_csr(Stage& s, const CsrBlock& b, const T* X, int ldx, T* Y, int ldy, int N) {
+        for (int r0 = 0; r0 < b.nrows; r0 += 16) s.csr.push_back(CsrTask{b, X, ldx, Y, ldy, N, r0, 1.0});
+    }
+    static void add_copy(Stage& s, const T* src, long long ssr, long long ssc, T* dst, long long dsr, long long dsc, int m,
+                         int nc) {
+        if ((long long)m * nc > 0) s.copy.push_back(CopyTask{src, ssr, ssc, dst, dsr, dsc, m, nc});
+    }
+    void add_trsv(Stage& s, const T* L, int ld, int c, T* X, int ldx, int N, bool transpose) {
+        if (c == 0 || N == 0) return;
+        s.trsv.push_back(TrsvTask{L, ld, c, N, X, ldx, transpose ? 1 : 0});
+        flops += (double)c * c * N;
+    }
+    static Stage& next(Program& P) { P.emplace_back(); return P.back(); }
+
+    template <class X, class F> void launch_kind(const char* name, std::vector<X>& all, int ychunks, F&& launch) {
+        if (all.empty()) return;
+        X* d = (X*)upload_tmp(sTask, all);
+        PROF(prof, name, stream, 0, 0, launch(d, (int)all.size(), ychunks));
+        launches++;
+        LAUNCH_CHECK();
+    }
+
+    void run(std::vector<Program>& progs) {
+        size_t len = 0;
+        for (auto& p : progs) len = std::max(len, p.size());
+        for (size_t i = 0; i < len; ++i) {
+            Stage st;
+            int yn_tn = 1, yn_nn = 1, yn_csr = 1, yn_tr = 1;
+            for (auto& p : progs) {
+                if (i >= p.size()) continue;
+                Stage& s = p[i];
+                st.gauss.insert(st.gauss.end(), s.gauss.begin(), s.gauss.end());
+                st.copy.insert(st.copy.end(), s.copy.begin(), s.copy.end());
+                st.csr.insert(st.csr.end(), s.csr.begin(), s.csr.end());
+                st.trsv.insert(st.trsv.end(), s.trsv.begin(), s.trsv.end());
+                st.tn.insert(st.tn.end(), s.tn.begin(), s.tn.end());
+                st.nn.insert(st.nn.end(), s.nn.begin(), s.nn.end());
+            }
+            for (auto& t : st.tn) yn_tn = std::max(yn_tn, cdiv(t.N, 16));
+            for (auto& t : st.nn) yn_nn = std::max(yn_nn, cdiv(t.N, 16));
+            for (auto& t : st.csr) yn_csr = std::max(yn_csr, cdiv(t.N, 16));
+            for (auto& t : st.trsv) yn_tr = std::max(yn_tr, cdiv(t.N, TRSV_CW));
+            const unsigned long long seed = o.seed;
+            cudaStream_t s = stream;
+            launch_kind("gauss", st.gauss, 1, [&](GaussTask* d, int n, int) { k_gauss<T><<<n, 256, 0, s>>>(d, seed); });
+            launch_kind("copy", st.copy, 1, [&](CopyTask* d, int n, int) { k_copy<T><<<dim3(n, 32), 256, 0, s>>>(d); });
+            launch_kind("csr", st.csr, yn_csr, [&](CsrTask* d, int n, int y) { k_csr_mm<T><<<dim3(n, y), 256, 0, s>>>(d); });
+            launch_kind("trsv", st.trsv, yn_tr,
+                        [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
+            launch_kind("tn", st.tn, yn_tn, [&](TnTask* d, int n, int y) { k_tn<T><<<dim3(n, y), 256, 0, s>>>(d); });
+            launch_kind("nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) { k_nn<T><<<dim3(n, y), 256, 0, s>>>(d); });
+        }
+        progs.clear();
+    }
+
+    // ---------------------------------------------------------------- per-batch device workspace
+    // chunked bump allocator; reset() recycles every chunk (call with the stream idle)
+    struct Workspace {
+        std::vector<std::pair<char*, size_t>> chunks;
+        size_t cur = 0, used = 0;
+        ~Workspace() { for (auto& c : chunks) cudaFree(c.first); }
+        void reset() { cur = 0; used = 0; }
+        void* getb(size_t nbytes) {
+            size_t bytes = (std::max<size_t>(nbytes, 1) + 255) / 256 * 256;
+            while (true) {
+                if (cur < chunks.size() && used + bytes <= chunks[cur].second) {
+                    char* p = chunks[cur].first + used;
+                    used += bytes;
+                    return p;
+                }
+                if (cur + 1 < chunks.size() || (cur < chunks.size() && used > 0)) {
+                    if (cur + 1 < chunks.size()) { ++cur; used = 0; continue; }
+                }
+                size_t sz = std::max(bytes, (size_t)256 << 20);
+                char* p = nullptr;
+                CK(cudaMalloc(&p, sz));
+                chunks.emplace_back(p, sz);
+                cur = chunks.size() - 1;
+                used = 0;
+            }
+        }
+    };
+    Workspace ws;
+    T* wsT(size_t n) { return (T*)ws.getb(sizeof(T) * n); }
+
+    // ---------------------------------------------------------------- dense / hierarchical triangular solves (programs)
+    // X (c x N row-major, ld ldx) <- L^{-1} X or L^{-T} X for dense lower L (ld), blocked by SOLVE_MAX
+    void prog_dense_solve(Program& P, const T* L, int ld, int c, T* X, int ldx, int N, bool transpose) {
         if (c == 0) return;
-        if (c <= SOLVE_MAX) {
-            std::vector<TrsvTask> tv{TrsvTask{L, ld, c, 0, X, ldx, 0}};
-            TrsvTask* d = (TrsvTask*)upload_tmp(sTv, tv);
-            dim3 grid(1, (unsigned)cdiv(N, 16));
-            PROF(prof, "trsv", stream, (double)c * c * N, sizeof(T) * ((double)c * c / 2 + 2.0 * c * N),
-                 k_trsv<T><<<grid, 256, 0, stream>>>(d, N, transpose ? 1 : 0));
-            launches++;
-            LAUNCH_CHECK();
-            flops += (double)c * c * N;
-            return;
-        }
-        const int bs = SOLVE_MAX;
-        if (!transpose) {
-            for (int b0 = 0; b0 < c; b0 += bs) {
-                const int b1 = std::min(c, b0 + bs);
-                dense_solve(L + b0 + (size_t)b0 * ld, ld, b1 - b0, X + (size_t)b0 * ldx, ldx, N, false);
-                if (b1 < c) {
-                    std::vector<NnTask> nn{NnTask{L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, 0, nullptr, 0,
-                                                  X + (size_t)b0 * ldx, ldx, 0}};
-                    launch_nn(nn, X + (size_t)b1 * ldx, ldx, N, T(-1), false);
-                }
-            }
-        } else {
-            const int nblk = cdiv(c, bs);
-            for (int bi = nblk - 1; bi >= 0; --bi) {
-                const int b0 = bi * bs, b1 = std::min(c, b0 + bs);
-                dense_solve(L + b0 + (size_t)b0 * ld, ld, b1 - b0, X + (size_t)b0 * ldx, ldx, N, true);
-                if (b0 > 0) {
-                    T* Z = (T*)sZ.get(sizeof(T) * (size_t)b0 * N);
-                    std::vector<TnTask> tn{TnTask{L + b0, ld, b0, b1 - b0, nullptr, 0, nullptr, 0, Z, N, 0}};
-                    launch_tn(tn, X + (size_t)b0 * ldx, ldx, N);
-                    axpy_rows(Z, N, X, ldx, b0, N, T(-1));
-                }
-            }
+        const int bs = SOLVE_MAX, nblk = cdiv(c, bs);
+        for (int bi = 0; bi < nblk; ++bi) {
+            const int b = transpose ? nblk - 1 - bi : bi;
+            const int b0 = b * bs, b1 = std::min(c, b0 + bs);
+            Stage& s = next(P);
+            add_trsv(s, L + b0 + (size_t)b0 * ld, ld, b1 - b0, X + (size_t)b0 * ldx, ldx, N, transpose);
+            if (!transpose && b1 < c)
+                add_nn(s, nn_task(L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, 0, nullptr, 0, X + (size_t)b0 * ldx,
+                                  ldx, X + (size_t)b1 * ldx, ldx, N, -1.0, false));
+            if (transpose && b0 > 0)
+                add_tn(s, tn_task(L + b0, ld, b0, b1 - b0, nullptr, 0, nullptr, 0, X + (size_t)b0 * ldx, ldx, X, ldx, N,
+                                  -1.0, 1.0));
         }
     }
 
-    // Alg. 4 (branches in the corrected order): solve with the subtree of L^D_j rooted at s.
-    // X holds the rows of the subtree's range, row-major (ld ldx), N columns.
-    void diag_solve(int j, int s, T* X, int ldx, int N, bool transpose) {
+    // Alg. 4 (branches in the corrected order) on the subtree of L^D_j rooted at s (0 = root).
+    void prog_diag_solve(Program& P, int j, int s, T* X, int ldx, int N, bool transpose) {
         const NodeRT& n = nd[j];
-        if (!n.hier) {
-            dense_solve(arena + n.off, n.ld, n.c, X, ldx, N, transpose);
-            return;
-        }
+        if (!n.hier) { prog_dense_solve(P, arena + n.off, n.ld, n.c, X, ldx, N, transpose); return; }
         const BlockTree& t = S.tree[j];
         if (s == 0) s = t.root;
         if (t.leaf[s]) {
             const int sz = t.hi[s] - t.lo[s];
-            dense_solve(arena + n.leaf_off[s], sz, sz, X, ldx, N, transpose);
+            prog_dense_solve(P, arena + n.leaf_off[s], sz, sz, X, ldx, N, transpose);
             return;
         }
-        const int n1 = t.mid[s] - t.lo[s], n2 = t.hi[s] - t.mid[s];
+        const int n1 = t.mid[s] - t.lo[s], n2 = t.hi[s] - t.mid[s], q = n.brank[s];
         T* X1 = X;
         T* X2 = X + (size_t)n1 * ldx;
-        const int q = n.brank[s];
+        auto lowrank = [&]() {
+            if (!q) return;
+            T* Z = wsT((size_t)q * N);
+            Stage& st = next(P);
+            if (!transpose) {   // X2 -= V_s (U_s^T X1)
+                add_tn(st, tn_task(n.bU[s], n1, q, n1, nullptr, 0, nullptr, 0, X1, ldx, Z, N, N));
+                add_nn(st, nn_task(n.bV[s], n2, q, n2, nullptr, 0, nullptr, 0, Z, N, X2, ldx, N, -1.0, false));
+            } else {            // X1 -= U_s (V_s^T X2)
+                add_tn(st, tn_task(n.bV[s], n2, q, n2, nullptr, 0, nullptr, 0, X2, ldx, Z, N, N));
+                add_nn(st, nn_task(n.bU[s], n1, q, n1, nullptr, 0, nullptr, 0, Z, N, X1, ldx, N, -1.0, false));
+            }
+        };
         if (!transpose) {
-            diag_solve(j, t.left[s], X1, ldx, N, false);
-            if (q) {   // X2 -= V_s (U_s^T X1)
-                T* Z = (T*)sZ.get(sizeof(T) * (size_t)q * N);
-                std::vector<TnTask> tn{TnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, 0, Z, N, 0}};
-                launch_tn(tn, X1, ldx, N);
-                std::vector<NnTask> nn{NnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, 0, Z, N, 0}};
-                launch_nn(nn, X2, ldx, N, T(-1), false);
-            }
-            diag_solve(j, t.right[s], X2, ldx, N, false);
+            prog_diag_solve(P, j, t.left[s], X1, ldx, N, false);
+            lowrank();
+            prog_diag_solve(P, j, t.right[s], X2, ldx, N, false);
         } else {
-            diag_solve(j, t.right[s], X2, ldx, N, true);
-            if (q) {   // X1 -= U_s (V_s^T X2)
-                T* Z = (T*)sZ.get(sizeof(T) * (size_t)q * N);
-                std::vector<TnTask> tn{TnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, 0, Z, N, 0}};
-                launch_tn(tn, X2, ldx, N);
-                std::vector<NnTask> nn{NnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, 0, Z, N, 0}};
-                launch_nn(nn, X1, ldx, N, T(-1), false);
-            }
-            diag_solve(j, t.left[s], X1, ldx, N, true);
+            prog_diag_solve(P, j, t.right[s], X2, ldx, N, true);
+            lowrank();
+            prog_diag_solve(P, j, t.left[s], X1, ldx, N, true);
         }
     }
 
-    // ---------------------------------------------------------------- implicit products
-    // descendant k's operand rows (L^O_k or V_k)
+    // ---------------------------------------------------------------- implicit products (programs)
     const LoOp& lo(int k) const { return h_lo[k]; }
 
-    // Alg. 2 transposed: W (c x N) = (L^O_j)^T G, G (r x N); all row-major ld N.
-    void offdiag_T(int j, const T* G, int N, T* W) {
+    // Alg. 2 transposed: W (c x N) = (L^O_j)^T G, G (r x N); row-major, ld N.
+    void prog_offdiag_T(Program& P, int j, const T* G, int N, T* W) {
         const NodeRT& n = nd[j];
-        csr_mm(n.aC, G, N, W, N, N, T(1), false);
-        std::vector<TnTask> tn;
-        std::vector<NnTask> nn;
-        long long zoff = 0;
-        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
-            const int k = S.desc_k[d];
-            const LoOp& op = lo(k);
-            const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
-            if (op.K == 0) continue;
-            zoff += (long long)op.K * N;
-        }
-        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
-        zoff = 0;
+        Stage& st = next(P);
+        add_csr(st, n.aC, G, N, W, N, N);
         int di = 0;
         for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
             const int k = S.desc_k[d];
             const LoOp& op = lo(k);
             const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
-            if (op.K == 0) continue;
-            T* Z = Zb + zoff;
-            zoff += (long long)op.K * N;
-            // T_k = L^O_k(R^O)^T gatherRows(G, R_j, R^O)
-            if (rk > p1)
-                tn.push_back(TnTask{op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, Z, N, 0});
-            else
-                fill(Z, (long long)op.K * N, T(0));
-            // W -= scatterRows(L^O_k(R^D) T_k, R^D, C_j)
-            nn.push_back(NnTask{op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0,
-                                (int)-n.c0, Z, N, 0});
+            if (op.K == 0 || rk == p1) continue;          // empty R^O: no contribution
+            T* Z = wsT((size_t)op.K * N);
+            // T_k = L^O_k(R^O)^T gatherRows(G, R_j, R^O); W -= scatterRows(L^O_k(R^D) T_k, R^D, C_j)
+            add_tn(st, tn_task(op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, G, N, Z, N, N));
+            add_nn(st, nn_task(op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0, (int)-n.c0, Z, N,
+                               W, N, N, -1.0, true));
         }
-        launch_tn(tn, G, N, N);
-        launch_nn(nn, W, N, N, T(-1), true);
-        diag_solve(j, 0, W, N, N, false);
+        prog_diag_solve(P, j, 0, W, N, N, false);
     }
 
-    // Alg. 2: W (r x N) = L^O_j X, X (c x N); X is left unchanged.
-    void offdiag(int j, const T* X, int N, T* W) {
+    // Alg. 2: W (r x N) = L^O_j X, X (c x N); Xp (c x N) is scratch.
+    void prog_offdiag(Program& P, int j, const T* X, int N, T* W, T* Xp) {
         const NodeRT& n = nd[j];
-        T* Xp = (T*)sX.get(sizeof(T) * (size_t)n.c * N);
-        CK(cudaMemcpyAsync(Xp, X, sizeof(T) * (size_t)n.c * N, cudaMemcpyDeviceToDevice, stream));
-        diag_solve(j, 0, Xp, N, N, true);
-        csr_mm(n.aR, Xp, N, W, N, N, T(1), false);
-        long long zoff = 0;
-        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) zoff += (long long)lo(S.desc_k[d]).K * N;
-        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
-        zoff = 0;
-        std::vector<TnTask> tn;
-        std::vector<NnTask> nn;
+        add_copy(next(P), X, N, 1, Xp, N, 1, n.c, N);
+        prog_diag_solve(P, j, 0, Xp, N, N, true);
+        Stage& st = next(P);
+        add_csr(st, n.aR, Xp, N, W, N, N);
         int di = 0;
         for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
             const int k = S.desc_k[d];
             const LoOp& op = lo(k);
             const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
-            if (op.K == 0) continue;
-            T* Z = Zb + zoff;
-            zoff += (long long)op.K * N;
-            // T_k = L^O_k(R^D)^T gatherRows(X', C_j, R^D)
-            tn.push_back(TnTask{op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0, (int)-n.c0, Z,
-                                N, 0});
-            // W -= scatterRows(L^O_k(R^O) T_k, R^O, R_j)
-            if (rk > p1) nn.push_back(NnTask{op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, Z, N, 0});
+            if (op.K == 0 || rk == p1) continue;
+            T* Z = wsT((size_t)op.K * N);
+            // T_k = L^O_k(R^D)^T gatherRows(X', C_j, R^D); W -= scatterRows(L^O_k(R^O) T_k, R^O, R_j)
+            add_tn(st, tn_task(op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0, (int)-n.c0, Xp, N,
+                               Z, N, N));
+            add_nn(st, nn_task(op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, Z, N, W, N, N,
+                               -1.0, true));
         }
-        launch_tn(tn, Xp, N, N);
-        launch_nn(nn, W, N, N, T(-1), true);
     }
 
-    // descendant rows of R_k inside the global range [g0, g1) (a sub-run of the C_j run)
-    void run_in(int d, long long g0, long long g1, int& a, int& b) const {
+    // positions of R_k inside the global range [g0, g1) (a sub-run of the C_j run)
+    void run_in(long long d, long long g0, long long g1, int& a, int& b) const {
         const int k = S.desc_k[d];
         const int32_t* Rk = S.R(k);
         const int p0 = S.desc_p0[d], p1 = S.desc_p1[d];
@@ -1021,102 +1046,64 @@ struct EngineT final : EngineImpl {
         b = (int)(std::lower_bound(Rk + p0, Rk + p1, (int32_t)g1) - Rk);
     }
 
-    // Alg. 5: W (|rows_s| x N) = L^D_{j,s} X, X (|cols_s| x N).
-    void diag_mult(int j, int s, const T* X, int N, T* W) {
+    // descendant and earlier-block terms of Alg. 5 (transpose = false) or its transpose
+    void diag_terms(Stage& st, int j, int s, const T* In, int N, T* W, bool transpose) {
         const NodeRT& n = nd[j];
         const BlockTree& t = S.tree[j];
         const int r0 = t.mid[s], r1 = t.hi[s], q0 = t.lo[s], q1 = t.mid[s];
-        T* Xp = (T*)sX.get(sizeof(T) * (size_t)(q1 - q0) * N);
-        CK(cudaMemcpyAsync(Xp, X, sizeof(T) * (size_t)(q1 - q0) * N, cudaMemcpyDeviceToDevice, stream));
-        diag_solve(j, t.left[s], Xp, N, N, true);
-        csr_mm(n.bR[s], Xp, N, W, N, N, T(1), false);
-        std::vector<TnTask> tn;
-        std::vector<NnTask> nn;
-        long long zoff = 0;
-        std::vector<int> A0, A1, B0, B1;
+        // In has |cols| rows (Alg. 5) or |rows| rows (transpose); W the other
+        const long long gin = n.c0 + (transpose ? r0 : q0), gout = n.c0 + (transpose ? q0 : r0);
         for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
-            int a, b, c, e;
-            run_in((int)d, n.c0 + r0, n.c0 + r1, a, b);
-            run_in((int)d, n.c0 + q0, n.c0 + q1, c, e);
-            A0.push_back(a); A1.push_back(b); B0.push_back(c); B1.push_back(e);
-            if (a < b && c < e) zoff += (long long)lo(S.desc_k[d]).K * N;
-        }
-        for (int p = t.parent[s]; p; p = t.parent[p])
-            if (p < s) zoff += (long long)n.brank[p] * N;
-        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
-        zoff = 0;
-        int di = 0;
-        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
             const int k = S.desc_k[d];
             const LoOp& op = lo(k);
-            if (op.K == 0 || A0[di] >= A1[di] || B0[di] >= B1[di]) continue;
-            T* Z = Zb + zoff;
-            zoff += (long long)op.K * N;
-            tn.push_back(TnTask{op.base, op.ld, op.K, B1[di] - B0[di], nullptr, B0[di], d_rows + S.rows_ptr[k] + B0[di],
-                                (int)-(n.c0 + q0), Z, N, 0});
-            nn.push_back(NnTask{op.base, op.ld, op.K, A1[di] - A0[di], nullptr, A0[di], d_rows + S.rows_ptr[k] + A0[di],
-                                (int)-(n.c0 + r0), Z, N, 0});
+            if (op.K == 0) continue;
+            int a0, a1, b0, b1;
+            run_in(d, n.c0 + r0, n.c0 + r1, a0, a1);    // rows of the block
+            run_in(d, n.c0 + q0, n.c0 + q1, b0, b1);    // columns of the block
+            if (a0 >= a1 || b0 >= b1) continue;
+            const int i0 = transpose ? a0 : b0, i1 = transpose ? a1 : b1;
+            const int o0 = transpose ? b0 : a0, o1 = transpose ? b1 : a1;
+            T* Z = wsT((size_t)op.K * N);
+            add_tn(st, tn_task(op.base, op.ld, op.K, i1 - i0, nullptr, i0, d_rows + S.rows_ptr[k] + i0, (int)-gin, In, N, Z,
+                               N, N));
+            add_nn(st, nn_task(op.base, op.ld, op.K, o1 - o0, nullptr, o0, d_rows + S.rows_ptr[k] + o0, (int)-gout, Z, N, W,
+                               N, N, -1.0, true));
         }
-        // earlier blocks p < s on the path to the root (Uprod = U_p^T U_p = I)
+        // earlier blocks p < s on the path to the root (U_p^T U_p = I)
         for (int p = t.parent[s]; p; p = t.parent[p]) {
             if (p > s || n.brank[p] == 0) continue;
-            T* Z = Zb + zoff;
-            zoff += (long long)n.brank[p] * N;
-            const int pr0 = t.mid[p], mp = t.hi[p] - t.mid[p];
-            tn.push_back(TnTask{n.bV[p], mp, n.brank[p], q1 - q0, nullptr, q0 - pr0, nullptr, 0, Z, N, 0});
-            nn.push_back(NnTask{n.bV[p], mp, n.brank[p], r1 - r0, nullptr, r0 - pr0, nullptr, 0, Z, N, 0});
+            const int mp = t.hi[p] - t.mid[p], pr0 = t.mid[p];
+            const int ioff = (transpose ? r0 : q0) - pr0, ooff = (transpose ? q0 : r0) - pr0;
+            const int inr = transpose ? r1 - r0 : q1 - q0, outr = transpose ? q1 - q0 : r1 - r0;
+            T* Z = wsT((size_t)n.brank[p] * N);
+            add_tn(st, tn_task(n.bV[p], mp, n.brank[p], inr, nullptr, ioff, nullptr, 0, In, N, Z, N, N));
+            add_nn(st, nn_task(n.bV[p], mp, n.brank[p], outr, nullptr, ooff, nullptr, 0, Z, N, W, N, N, -1.0, true));
         }
-        launch_tn(tn, Xp, N, N);
-        launch_nn(nn, W, N, N, T(-1), true);
+    }
+
+    // Alg. 5: W (|rows_s| x N) = L^D_{j,s} X, X (|cols_s| x N); Xp scratch.
+    void prog_diag_mult(Program& P, int j, int s, const T* X, int N, T* W, T* Xp) {
+        const NodeRT& n = nd[j];
+        const BlockTree& t = S.tree[j];
+        const int cs = t.mid[s] - t.lo[s];
+        add_copy(next(P), X, N, 1, Xp, N, 1, cs, N);
+        prog_diag_solve(P, j, t.left[s], Xp, N, N, true);
+        Stage& st = next(P);
+        add_csr(st, n.bR[s], Xp, N, W, N, N);
+        diag_terms(st, j, s, Xp, N, W, false);
     }
 
     // Alg. 5 transposed: W (|cols_s| x N) = (L^D_{j,s})^T G, G (|rows_s| x N).
-    void diag_mult_T(int j, int s, const T* G, int N, T* W) {
+    void prog_diag_mult_T(Program& P, int j, int s, const T* G, int N, T* W) {
         const NodeRT& n = nd[j];
         const BlockTree& t = S.tree[j];
-        const int r0 = t.mid[s], r1 = t.hi[s], q0 = t.lo[s], q1 = t.mid[s];
-        csr_mm(n.bC[s], G, N, W, N, N, T(1), false);
-        std::vector<TnTask> tn;
-        std::vector<NnTask> nn;
-        long long zoff = 0;
-        std::vector<int> A0, A1, B0, B1;
-        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
-            int a, b, c, e;
-            run_in((int)d, n.c0 + r0, n.c0 + r1, a, b);
-            run_in((int)d, n.c0 + q0, n.c0 + q1, c, e);
-            A0.push_back(a); A1.push_back(b); B0.push_back(c); B1.push_back(e);
-            if (a < b && c < e) zoff += (long long)lo(S.desc_k[d]).K * N;
-        }
-        for (int p = t.parent[s]; p; p = t.parent[p])
-            if (p < s) zoff += (long long)n.brank[p] * N;
-        T* Zb = (T*)sT.get(sizeof(T) * std::max<long long>(zoff, 1));
-        zoff = 0;
-        int di = 0;
-        for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
-            const int k = S.desc_k[d];
-            const LoOp& op = lo(k);
-            if (op.K == 0 || A0[di] >= A1[di] || B0[di] >= B1[di]) continue;
-            T* Z = Zb + zoff;
-            zoff += (long long)op.K * N;
-            tn.push_back(TnTask{op.base, op.ld, op.K, A1[di] - A0[di], nullptr, A0[di], d_rows + S.rows_ptr[k] + A0[di],
-                                (int)-(n.c0 + r0), Z, N, 0});
-            nn.push_back(NnTask{op.base, op.ld, op.K, B1[di] - B0[di], nullptr, B0[di], d_rows + S.rows_ptr[k] + B0[di],
-                                (int)-(n.c0 + q0), Z, N, 0});
-        }
-        for (int p = t.parent[s]; p; p = t.parent[p]) {
-            if (p > s || n.brank[p] == 0) continue;
-            T* Z = Zb + zoff;
-            zoff += (long long)n.brank[p] * N;
-            const int pr0 = t.mid[p], mp = t.hi[p] - t.mid[p];
-            tn.push_back(TnTask{n.bV[p], mp, n.brank[p], r1 - r0, nullptr, r0 - pr0, nullptr, 0, Z, N, 0});
-            nn.push_back(NnTask{n.bV[p], mp, n.brank[p], q1 - q0, nullptr, q0 - pr0, nullptr, 0, Z, N, 0});
-        }
-        launch_tn(tn, G, N, N);
-        launch_nn(nn, W, N, N, T(-1), true);
-        diag_solve(j, t.left[s], W, N, N, false);
+        Stage& st = next(P);
+        add_csr(st, n.bC[s], G, N, W, N, N);
+        diag_terms(st, j, s, G, N, W, true);
+        prog_diag_solve(P, j, t.left[s], W, N, N, false);
     }
 
-    // ---------------------------------------------------------------- adaptive range finder (Alg. 3)
+    // ---------------------------------------------------------------- adaptive range finder (Alg. 3), batched
     T* lr_alloc(long long elems) {
         if (lr_used + elems > lr_cap) throw Error(RSC_ERR_OOM, "low-rank storage exhausted");
         T* p = lr_base + lr_used;
@@ -1124,113 +1111,217 @@ struct EngineT final : EngineImpl {
         return p;
     }
 
-    double read_norm2(const T* X, int ld, int m, int nc, int slot) {
-        CK(cudaMemsetAsync(d_norms + slot, 0, sizeof(double), stream));
-        if (m > 0) {
-            k_sqnorm<T><<<std::min(cdiv((long long)m * nc, 256), 1024), 256, 0, stream>>>(X, ld, m, nc, d_norms + slot);
-            launches++;
-        }
-        return 0.0;
+    struct RF {                    // one block being compressed
+        int j = 0, s = 0;          // s == 0: L^O_j; else internal block s of L^D_j
+        int m = 0, c = 0, maxr = 0;
+        double tol = 0;
+        uint32_t block_id = 0;
+        T* U = nullptr; T* V = nullptr;
+        int rank = 0, b_last = 0;
+        bool active = true, qr_pending = false;
+        double y1 = -1;
+        T *G = nullptr, *Y = nullptr, *Gp = nullptr;
+        int slot = 0;              // index into the batch's small device records
+    };
+    double* d_rf = nullptr;        // per RF: [0] y1^2, [1] nrm^2, [2..257] gram, [258..513] rinv
+    int* d_rfst = nullptr;         // per RF: QR status
+    size_t rf_cap = 0, rf_used = 0;
+    static constexpr int RFD = 520;
+
+    void mult_T_prog(Program& P, RF& r, const T* G, int N, T* W) {
+        if (r.s == 0) prog_offdiag_T(P, r.j, G, N, W);
+        else prog_diag_mult_T(P, r.j, r.s, G, N, W);
+    }
+    void mult_prog(Program& P, RF& r, const T* X, int N, T* W) {
+        T* Xp = wsT((size_t)r.c * N);
+        if (r.s == 0) prog_offdiag(P, r.j, X, N, W, Xp);
+        else prog_diag_mult(P, r.j, r.s, X, N, W, Xp);
     }
 
-    // Cholesky QR of the row-major block Y (m x b, ld 16), optionally shifted; a failed
-    // factorization sets d_qstatus
-    void cholqr(T* Y, int m, int b, bool shifted) {
+    void norms(std::vector<RF*>& rs, int slot) {
+        std::vector<NormTask> nt;
+        for (RF* r : rs) nt.push_back(NormTask{r->Y, 16, r->c, 16, d_rf + (size_t)r->slot * RFD + slot});
+        if (nt.empty()) return;
+        NormTask* d = (NormTask*)upload_tmp(sTask, nt);
+        k_sqnorm<T><<<dim3((unsigned)nt.size(), 16), 256, 0, stream>>>(d);
+        launches++;
+        LAUNCH_CHECK();
+    }
+    void project(std::vector<RF*>& rs) {
+        std::vector<Program> progs;
+        for (RF* r : rs) {
+            if (r->rank == 0) continue;
+            progs.emplace_back();
+            T* Z = wsT((size_t)r->rank * 16);
+            Stage& st = next(progs.back());
+            add_tn(st, tn_task(r->U, r->c, r->rank, r->c, nullptr, 0, nullptr, 0, r->Y, 16, Z, 16, 16));
+            add_nn(st, nn_task(r->U, r->c, r->rank, r->c, nullptr, 0, nullptr, 0, Z, 16, r->Y, 16, 16, -1.0, false));
+        }
+        run(progs);
+    }
+    void cholqr(std::vector<RF*>& rs, bool shifted) {
         const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
-        const double coef = shifted ? 11.0 * ((double)m * b + (double)b * (b + 1)) * u : 0.0;
-        CK(cudaMemsetAsync(d_small, 0, sizeof(double) * 256, stream));
-        k_gram<T><<<cdiv(m, 256), 256, 0, stream>>>(Y, m, b, d_small);
-        k_chol_small<<<1, 32, 0, stream>>>(d_small, b, coef, d_small + 256, d_qstatus);
-        k_apply_rinv<T><<<cdiv(m, 128), 128, 0, stream>>>(Y, m, b, d_small + 256);
+        std::vector<QrTask> qt, q256, q128;
+        for (RF* r : rs) {
+            double* base = d_rf + (size_t)r->slot * RFD;
+            const int b = r->b_last;
+            const double coef = shifted ? 11.0 * ((double)r->c * b + (double)b * (b + 1)) * u : 0.0;
+            QrTask t{r->Y, r->c, b, 0, base + 2, base + 258, d_rfst + r->slot, coef};
+            qt.push_back(t);
+            for (int r0 = 0; r0 < r->c; r0 += 256) { t.row0 = r0; q256.push_back(t); }
+            for (int r0 = 0; r0 < r->c; r0 += 128) { t.row0 = r0; q128.push_back(t); }
+            flops += 3.0 * r->c * b * b;
+        }
+        if (qt.empty()) return;
+        CK(cudaMemset2DAsync(d_rf + 2, sizeof(double) * RFD, 0, sizeof(double) * 256, rf_used, stream));
+        QrTask* d1 = (QrTask*)upload_tmp(sTask, q256);
+        QrTask* d2 = (QrTask*)upload_tmp(sTask, qt);
+        QrTask* d3 = (QrTask*)upload_tmp(sTask, q128);
+        k_gram<T><<<(unsigned)q256.size(), 256, 0, stream>>>(d1);
+        k_chol_small<<<cdiv((long long)qt.size(), 32), 32, 0, stream>>>(d2, (int)qt.size());
+        k_apply_rinv<T><<<(unsigned)q128.size(), 128, 0, stream>>>(d3);
         launches += 3;
         LAUNCH_CHECK();
-        flops += 2.0 * m * b * b + (double)m * b * b;
     }
 
-    // project Y (c x 16 row-major) against U (c x rank column-major, ld c): Y -= U (U^T Y)
-    void project(const T* U, int c, int rank, T* Y) {
-        if (rank == 0) return;
-        T* Z = (T*)sZ.get(sizeof(T) * (size_t)rank * 16);
-        std::vector<TnTask> tn{TnTask{U, c, rank, c, nullptr, 0, nullptr, 0, Z, 16, 0}};
-        launch_tn(tn, Y, 16, 16);
-        std::vector<NnTask> nn{NnTask{U, c, rank, c, nullptr, 0, nullptr, 0, Z, 16, 0}};
-        launch_nn(nn, Y, 16, 16, T(-1), false);
-    }
-
-    template <class MultT, class Mult>
-    void range_finder(int m, int c, double tolr, uint32_t block_id, MultT&& mult_T, Mult&& mult, T*& Vout, T*& Uout,
-                      int& rank) {
-        const int maxr = std::min(m, c);
-        rank = 0;
-        Vout = Uout = nullptr;
-        if (maxr == 0) return;
-        T* U = lr_alloc((long long)c * maxr);
-        T* G = (T*)sG.get(sizeof(T) * (size_t)std::max(m, c) * 16);
-        T* Y = (T*)sY.get(sizeof(T) * (size_t)std::max(m, c) * 16);
-        double y1 = -1.0;
-        for (int t = 0; rank < maxr; ++t) {
-            const uint32_t word3 = (uint32_t)t | ((uint32_t)restarts << 16);
-            k_gauss<T><<<cdiv((long long)m * 8, 256), 256, 0, stream>>>(G, m, o.seed, block_id, word3);
-            launches++;
-            mult_T(G, 16, Y);
-            for (int q = 0; q < o.power_iters; ++q) {
-                mult(Y, 16, G);
-                mult_T(G, 16, Y);
-            }
-            if (t == 0) read_norm2(Y, 16, c, 16, 0);
-            project(U, c, rank, Y);
-            project(U, c, rank, Y);
-            read_norm2(Y, 16, c, 16, 1);
-            double h[2];
-            CK(cudaMemcpyAsync(h, d_norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, stream));
-            sync_stream();
-            if (t == 0) y1 = std::sqrt(h[0]);
-            const double nrm = std::sqrt(h[1]);
-            if (!std::isfinite(nrm) || !std::isfinite(y1)) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
-            if (nrm <= tolr * y1) break;
-            const int b = std::min(16, maxr - rank);
-            // makeOrthonormal: shifted Cholesky QR, re-projection against U, then two
-            // Cholesky QR passes (shifted CholeskyQR3: stable up to cond ~ 1/u)
-            CK(cudaMemsetAsync(d_qstatus, 0, sizeof(int), stream));
-            cholqr(Y, c, b, true);
-            project(U, c, rank, Y);
-            cholqr(Y, c, b, false);
-            cholqr(Y, c, b, false);
-            int qs = 0;
-            CK(cudaMemcpyAsync(&qs, d_qstatus, sizeof(int), cudaMemcpyDeviceToHost, stream));
-            sync_stream();
-            if (qs) break;   // the remaining sample is numerically rank deficient
-            rows_to_cols_ld(Y, 16, c, b, U, c, rank);
-            rank += b;
+    void range_finder_batch(std::vector<RF>& R) {
+        if (R.empty()) return;
+        ws.reset();
+        if (R.size() > rf_cap) {
+            if (d_rf) CK(cudaFree(d_rf));
+            if (d_rfst) CK(cudaFree(d_rfst));
+            rf_cap = std::max<size_t>(R.size(), 64);
+            CK(cudaMalloc(&d_rf, sizeof(double) * RFD * rf_cap));
+            CK(cudaMalloc(&d_rfst, sizeof(int) * rf_cap));
         }
-        Uout = U;
-        if (rank == 0) return;
-        // V = mult(U): U in row-major form first
-        T* Ur = (T*)sUr.get(sizeof(T) * (size_t)c * rank);
-        cols_to_rows(U, c, c, rank, Ur);
-        T* Vr = (T*)sVr.get(sizeof(T) * (size_t)m * rank);
-        mult(Ur, rank, Vr);
-        Vout = lr_alloc((long long)m * rank);
-        rows_to_cols_ld(Vr, rank, m, rank, Vout, m, 0);
+        CK(cudaMemsetAsync(d_rfst, 0, sizeof(int) * R.size(), stream));
+        rf_used = R.size();
+        for (size_t i = 0; i < R.size(); ++i) {
+            RF& r = R[i];
+            r.slot = (int)i;
+            r.maxr = std::min(r.m, r.c);
+            r.rank = 0;
+            r.active = r.maxr > 0;
+            r.U = r.maxr ? lr_alloc((long long)r.c * r.maxr) : nullptr;
+            r.G = wsT((size_t)std::max(r.m, r.c) * 16);
+            r.Y = wsT((size_t)std::max(r.m, r.c) * 16);
+            r.Gp = wsT((size_t)std::max(r.m, r.c) * 16);
+        }
+        std::vector<double> h(R.size() * 2);
+        std::vector<int> hs(R.size());
+        for (int t = 0;; ++t) {
+            std::vector<RF*> act;
+            for (RF& r : R)
+                if (r.active) act.push_back(&r);
+            if (act.empty()) break;
+            // sample: Y = mult_T(G) (with power iterations)
+            std::vector<Program> progs;
+            for (RF* r : act) {
+                progs.emplace_back();
+                Program& P = progs.back();
+                Stage& g = next(P);
+                const uint32_t word3 = (uint32_t)t | ((uint32_t)restarts << 16);
+                for (int r0 = 0; r0 < r->m; r0 += 32) g.gauss.push_back(GaussTask{r->G, r->m, r0, r->block_id, word3});
+                mult_T_prog(P, *r, r->G, 16, r->Y);
+                for (int q = 0; q < o.power_iters; ++q) {
+                    mult_prog(P, *r, r->Y, 16, r->Gp);
+                    mult_T_prog(P, *r, r->Gp, 16, r->Y);
+                }
+            }
+            run(progs);
+            CK(cudaMemset2DAsync(d_rf, sizeof(double) * RFD, 0, sizeof(double) * 2, R.size(), stream));
+            if (t == 0) norms(act, 0);
+            project(act);
+            project(act);
+            norms(act, 1);
+            // one readback per pass: norms of every block and QR status of the previous pass
+            CK(cudaMemcpy2DAsync(h.data(), sizeof(double) * 2, d_rf, sizeof(double) * RFD, sizeof(double) * 2, R.size(),
+                                 cudaMemcpyDeviceToHost, stream));
+            CK(cudaMemcpyAsync(hs.data(), d_rfst, sizeof(int) * R.size(), cudaMemcpyDeviceToHost, stream));
+            sync_stream();
+            std::vector<RF*> go;
+            for (RF* r : act) {
+                if (r->qr_pending && hs[r->slot]) {   // previous orthonormalisation failed: drop it
+                    r->rank -= r->b_last;
+                    r->active = false;
+                    continue;
+                }
+                r->qr_pending = false;
+                if (t == 0) r->y1 = std::sqrt(h[2 * r->slot]);
+                const double nrm = std::sqrt(h[2 * r->slot + 1]);
+                if (!std::isfinite(nrm) || !std::isfinite(r->y1)) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
+                if (nrm <= r->tol * r->y1) { r->active = false; continue; }
+                r->b_last = std::min(16, r->maxr - r->rank);
+                go.push_back(r);
+            }
+            if (go.empty()) continue;
+            // makeOrthonormal: shifted Cholesky QR, re-projection against U, two Cholesky QR
+            // passes (shifted CholeskyQR3: stable up to cond ~ 1/u)
+            cholqr(go, true);
+            project(go);
+            cholqr(go, false);
+            cholqr(go, false);
+            std::vector<Program> cp;
+            for (RF* r : go) {
+                cp.emplace_back();
+                add_copy(next(cp.back()), r->Y, 16, 1, r->U + (size_t)r->rank * r->c, 1, r->c, r->c, r->b_last);
+                r->rank += r->b_last;
+                r->qr_pending = true;
+                if (r->rank >= r->maxr) r->active = false;
+            }
+            run(cp);
+        }
+        // status of the last orthonormalisation of blocks that stopped at full rank
+        CK(cudaMemcpyAsync(hs.data(), d_rfst, sizeof(int) * R.size(), cudaMemcpyDeviceToHost, stream));
+        sync_stream();
+        for (RF& r : R)
+            if (r.qr_pending && hs[r.slot]) r.rank -= r.b_last;
+        // V = mult(U): U to row-major, product, back to column-major
+        std::vector<Program> progs;
+        std::vector<T*> vr(R.size(), nullptr);
+        for (size_t i = 0; i < R.size(); ++i) {
+            RF& r = R[i];
+            if (r.rank == 0) continue;
+            progs.emplace_back();
+            Program& P = progs.back();
+            T* Ur = wsT((size_t)r.c * r.rank);
+            vr[i] = wsT((size_t)r.m * r.rank);
+            add_copy(next(P), r.U, 1, r.c, Ur, r.rank, 1, r.c, r.rank);
+            mult_prog(P, r, Ur, r.rank, vr[i]);
+            r.V = lr_alloc((long long)r.m * r.rank);
+            add_copy(next(P), vr[i], r.rank, 1, r.V, 1, r.m, r.m, r.rank);
+        }
+        run(progs);
+        sync_stream();   // the workspace is recycled by the next batch
     }
 
-    void cols_to_rows(const T* U, int ldu, int m, int nc, T* Xr);
-
-    // ---------------------------------------------------------------- compressed supernode
-    void compressed_node(int j) {
-        NodeRT& n = nd[j];
-        if (n.hier) {
-            const BlockTree& t = S.tree[j];
-            for (int s = 1; s <= t.nblocks; ++s) {
-                if (t.leaf[s]) {
-                    // Alg. 6: subtract earlier low-rank blocks p < s, then Cholesky
-                    const int sz = t.hi[s] - t.lo[s];
-                    T* Ls = arena + n.leaf_off[s];
-                    for (int p = t.parent[s]; p; p = t.parent[p]) {
-                        if (p > s || n.brank[p] == 0) continue;
-                        std::vector<GemmTask> gt;
-                        const int mp = t.hi[p] - t.mid[p];
+    // ---------------------------------------------------------------- compressed supernodes of one level
+    void compressed_level(const std::vector<int>& comp) {
+        std::vector<int> hier;
+        int maxnb = 0;
+        for (int j : comp)
+            if (nd[j].hier) { hier.push_back(j); maxnb = std::max(maxnb, S.tree[j].nblocks); }
+        for (int s = 1; s <= maxnb; ++s) {
+            std::vector<int> leaves, internals;
+            for (int j : hier)
+                if (S.tree[j].nblocks >= s) (S.tree[j].leaf[s] ? leaves : internals).push_back(j);
+            if (!leaves.empty()) {
+                // Alg. 6: subtract earlier low-rank blocks p < s (one launch per ancestor depth,
+                // since the tiles of one leaf receive several ancestors), then Cholesky
+                for (int depth = 0;; ++depth) {
+                    std::vector<GemmTask> gt;
+                    bool any = false;
+                    for (int j : leaves) {
+                        NodeRT& n = nd[j];
+                        const BlockTree& t = S.tree[j];
+                        int p = t.parent[s], d = 0;
+                        for (; p; p = t.parent[p])
+                            if (p < s && n.brank[p] > 0) { if (d == depth) break; ++d; }
+                        if (!p) continue;
+                        any = true;
+                        const int sz = t.hi[s] - t.lo[s], mp = t.hi[p] - t.mid[p];
                         const T* Vp = n.bV[p] + (t.lo[s] - t.mid[p]);
+                        T* Ls = arena + n.leaf_off[s];
                         for (int c0 = 0; c0 < sz; c0 += TILE)
                             for (int r0 = c0; r0 < sz; r0 += TILE) {
                                 GemmTask g{};
@@ -1241,39 +1332,57 @@ struct EngineT final : EngineImpl {
                                 gt.push_back(g);
                             }
                         flops += (double)sz * (sz + 1) * n.brank[p];
-                        GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
-                        k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg);
-                        launches++;
-                        LAUNCH_CHECK();
                     }
-                    factor_dense(Ls, sz, sz, sz, j);
-                } else {
-                    const int rs = t.hi[s] - t.mid[s], cs = t.mid[s] - t.lo[s];
-                    T *V, *U;
-                    int q;
-                    range_finder(
-                        rs, cs, tol_D, ((uint32_t)j << 12) | (uint32_t)s,
-                        [&](const T* G, int N, T* W) { diag_mult_T(j, s, G, N, W); },
-                        [&](const T* X, int N, T* W) { diag_mult(j, s, X, N, W); }, V, U, q);
-                    n.bV[s] = V;
-                    n.bU[s] = U;
-                    n.brank[s] = q;
+                    if (!any) break;
+                    GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
+                    k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg);
+                    launches++;
+                    LAUNCH_CHECK();
                 }
+                std::vector<DensePanel> dp;
+                for (int j : leaves) {
+                    const BlockTree& t = S.tree[j];
+                    const int sz = t.hi[s] - t.lo[s];
+                    dp.push_back(DensePanel{arena + nd[j].leaf_off[s], sz, sz, sz, j});
+                }
+                factor_dense_batch(dp);
                 check_status();
             }
+            if (!internals.empty()) {
+                std::vector<RF> R;
+                for (int j : internals) {
+                    const BlockTree& t = S.tree[j];
+                    RF r;
+                    r.j = j; r.s = s;
+                    r.m = t.hi[s] - t.mid[s];
+                    r.c = t.mid[s] - t.lo[s];
+                    r.tol = tol_D;
+                    r.block_id = ((uint32_t)j << 12) | (uint32_t)s;
+                    R.push_back(r);
+                }
+                range_finder_batch(R);
+                for (RF& r : R) {
+                    NodeRT& n = nd[r.j];
+                    n.bV[s] = r.V; n.bU[s] = r.U; n.brank[s] = r.rank;
+                }
+            }
         }
-        if (n.r > 0) {
-            T *V, *U;
-            int q;
-            range_finder(
-                n.r, n.c, tol, (uint32_t)j << 12,
-                [&](const T* G, int N, T* W) { offdiag_T(j, G, N, W); },
-                [&](const T* X, int N, T* W) { offdiag(j, X, N, W); }, V, U, q);
-            n.V = V;
-            n.U = U;
-            n.rank = q;
+        std::vector<RF> R;
+        for (int j : comp)
+            if (nd[j].r > 0) {
+                RF r;
+                r.j = j; r.s = 0;
+                r.m = nd[j].r; r.c = nd[j].c;
+                r.tol = tol;
+                r.block_id = (uint32_t)j << 12;
+                R.push_back(r);
+            }
+        range_finder_batch(R);
+        for (RF& r : R) {
+            NodeRT& n = nd[r.j];
+            n.V = r.V; n.U = r.U; n.rank = r.rank;
         }
-        h_lo[j] = LoOp{n.V, std::max(n.r, 1), n.rank};
+        for (int j : comp) h_lo[j] = LoOp{nd[j].V, std::max(nd[j].r, 1), nd[j].rank};
     }
 
     void check_status() {
@@ -1322,13 +1431,13 @@ struct EngineT final : EngineImpl {
                     flops += c * c * c / 3.0 + r * c * c;
                 }
             }
-            bool any_comp = false;
+            std::vector<int> comp;
             for (int j : S.level_nodes[l])
-                if (nd[j].compressed) {
-                    if (!any_comp) check_status();
-                    any_comp = true;
-                    compressed_node(j);
-                }
+                if (nd[j].compressed) comp.push_back(j);
+            if (!comp.empty()) {
+                check_status();
+                compressed_level(comp);
+            }
             // extend-add of the level into its ancestors
             CK(cudaMemcpyAsync(d_lo, h_lo.data(), sizeof(LoOp) * S.M, cudaMemcpyHostToDevice, stream));
             if (push_count[l]) {
@@ -1433,8 +1542,16 @@ struct EngineT final : EngineImpl {
     static void push_tn_chunks(std::vector<TnTask>& v, const TnTask& t) {
         for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; v.push_back(c); }
     }
+    // vector forms on y (ld 1, one column); yoff / ymap index rows of y
+    TnTask vtn(const void* A, int lda, int K, int nrow, const int32_t* ymap, int yoff, T* Z, double alpha = 1.0,
+               double beta = 0.0) {
+        return tn_task(A, lda, K, nrow, nullptr, 0, ymap, yoff, y_dev, 1, Z, 1, 1, alpha, beta);
+    }
+    NnTask vnn(const void* A, int lda, int K, int nrow, const int32_t* ymap, int yoff, const T* Z, bool atomic) {
+        return nn_task(A, lda, K, nrow, nullptr, 0, ymap, yoff, Z, 1, y_dev, 1, 1, -1.0, atomic);
+    }
 
-    // In-order actions of one diagonal block (vector right-hand side, X = y + c0).
+    // In-order actions of one diagonal block (vector right-hand side, rows c0.. of y).
     void diag_actions(int j, bool transpose, T*& zcur, std::vector<Act>& acts) {
         const NodeRT& n = nd[j];
         T* X = y_dev + n.c0;
@@ -1446,29 +1563,22 @@ struct EngineT final : EngineImpl {
                 const int b = transpose ? nblk - 1 - bi : bi;
                 const int b0 = b * bs, b1 = std::min(c, b0 + bs);
                 Act a;
-                a.trsv.push_back(TrsvTask{L + b0 + (size_t)b0 * ld, ld, b1 - b0, 0, X + b0, 1, 0});
+                a.trsv.push_back(TrsvTask{L + b0 + (size_t)b0 * ld, ld, b1 - b0, 1, X + b0, 1, transpose ? 1 : 0});
                 if (!transpose && b1 < c)
-                    push_nn_chunks(a.nn, NnTask{L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, 0, nullptr,
-                                                (int)(n.c0 + b1), X + b0, 1, 0});
-                if (transpose && b0 > 0) {
-                    TnTask t{L + b0, ld, b0, b1 - b0, nullptr, 0, nullptr, 0, X, 1, 0};
-                    t.alpha = -1.0; t.beta = 1.0;
-                    t.ymap = nullptr;
-                    // Y rows b0..b1 of X: express through yoff on the vector y
-                    t.yoff = (int)(n.c0 + b0);
-                    push_tn_chunks(a.tn, t);
-                }
+                    push_nn_chunks(a.nn, vnn(L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, (int)(n.c0 + b1),
+                                             X + b0, false));
+                if (transpose && b0 > 0)   // y[c0 : c0+b0] -= L[b0:b1, 0:b0]^T y[c0+b0 : c0+b1]
+                    push_tn_chunks(a.tn, vtn(L + b0, ld, b0, b1 - b0, nullptr, (int)(n.c0 + b0), X, -1.0, 1.0));
                 acts.push_back(std::move(a));
             }
             return;
         }
         const BlockTree& t = S.tree[j];
-        // recursive emission in the order of Alg. 4 (corrected branches)
         std::function<void(int)> rec = [&](int s) {
             if (t.leaf[s]) {
                 Act a;
                 const int sz = t.hi[s] - t.lo[s];
-                a.trsv.push_back(TrsvTask{arena + n.leaf_off[s], sz, sz, 0, X + t.lo[s], 1, 0});
+                a.trsv.push_back(TrsvTask{arena + n.leaf_off[s], sz, sz, 1, X + t.lo[s], 1, transpose ? 1 : 0});
                 acts.push_back(std::move(a));
                 return;
             }
@@ -1479,11 +1589,11 @@ struct EngineT final : EngineImpl {
                 T* Z = zcur;
                 zcur += q;
                 if (!transpose) {   // X2 -= V_s (U_s^T X1)
-                    push_tn_chunks(a.tn, TnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, (int)(n.c0 + t.lo[s]), Z, 1, 0});
-                    push_nn_chunks(a.nn, NnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, (int)(n.c0 + t.mid[s]), Z, 1, 0});
+                    push_tn_chunks(a.tn, vtn(n.bU[s], n1, q, n1, nullptr, (int)(n.c0 + t.lo[s]), Z));
+                    push_nn_chunks(a.nn, vnn(n.bV[s], n2, q, n2, nullptr, (int)(n.c0 + t.mid[s]), Z, false));
                 } else {            // X1 -= U_s (V_s^T X2)
-                    push_tn_chunks(a.tn, TnTask{n.bV[s], n2, q, n2, nullptr, 0, nullptr, (int)(n.c0 + t.mid[s]), Z, 1, 0});
-                    push_nn_chunks(a.nn, NnTask{n.bU[s], n1, q, n1, nullptr, 0, nullptr, (int)(n.c0 + t.lo[s]), Z, 1, 0});
+                    push_tn_chunks(a.tn, vtn(n.bV[s], n2, q, n2, nullptr, (int)(n.c0 + t.mid[s]), Z));
+                    push_nn_chunks(a.nn, vnn(n.bU[s], n1, q, n1, nullptr, (int)(n.c0 + t.lo[s]), Z, false));
                 }
                 acts.push_back(std::move(a));
             };
@@ -1515,7 +1625,7 @@ struct EngineT final : EngineImpl {
         auto emit = [&](int kind, size_t off, size_t cnt, int flag) {
             if (cnt) seq.push_back(Launch{kind, (int)cnt, off, flag});
         };
-        auto emit_acts = [&](std::vector<std::vector<Act>>& per_node, bool transpose) {
+        auto emit_acts = [&](std::vector<std::vector<Act>>& per_node) {
             size_t maxa = 0;
             for (auto& v : per_node) maxa = std::max(maxa, v.size());
             for (size_t ai = 0; ai < maxa; ++ai) {
@@ -1527,7 +1637,7 @@ struct EngineT final : EngineImpl {
                     B.tn.insert(B.tn.end(), a.tn.begin(), a.tn.end());
                     B.nn.insert(B.nn.end(), a.nn.begin(), a.nn.end());
                 }
-                emit(L_TRSV, o1, B.trsv.size() - o1, transpose ? 1 : 0);
+                emit(L_TRSV, o1, B.trsv.size() - o1, 0);
                 emit(L_TN, o2, B.tn.size() - o2, 0);
                 emit(L_NN, o3, B.nn.size() - o3, 0);
             }
@@ -1540,29 +1650,30 @@ struct EngineT final : EngineImpl {
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 apply_bytes += 2.0 * sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
-                if (!nn.hier && nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 0, y_dev + nn.c0, 1, 0});
+                if (!nn.hier && nn.c <= SOLVE_MAX)
+                    B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 1, y_dev + nn.c0, 1, 0});
                 else { acts.emplace_back(); diag_actions(j, false, zcur, acts.back()); }
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
-            emit_acts(acts, false);
+            emit_acts(acts);
             size_t o2 = B.tn.size(), o3 = B.nn.size();
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 if (nn.r == 0) continue;
                 const int32_t* Rj = d_rows + S.rows_ptr[j];
-                if (!nn.compressed) {
-                    push_nn_chunks(B.nn, NnTask{arena + nn.off + nn.c, nn.ld, nn.c, nn.r, nullptr, 0, Rj, 0, y_dev + nn.c0, 1, 0});
+                if (!nn.compressed) {   // y_R -= L^O_j y_C (atomic: nodes of a level share rows of R)
+                    push_nn_chunks(B.nn, vnn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, Rj, 0, y_dev + nn.c0, true));
                     apply_bytes += 2.0 * sizeof(T) * nn.r * nn.c;
-                } else if (nn.rank) {
+                } else if (nn.rank) {   // y_R -= V_j (U_j^T y_C)
                     T* tmp = zcur; zcur += nn.rank;
                     ztmp[l].push_back(tmp);
-                    push_tn_chunks(B.tn, TnTask{nn.U, nn.c, nn.rank, nn.c, nullptr, 0, nullptr, (int)nn.c0, tmp, 1, 0});
-                    push_nn_chunks(B.nn, NnTask{nn.V, nn.r, nn.rank, nn.r, nullptr, 0, Rj, 0, tmp, 1, 0});
+                    push_tn_chunks(B.tn, vtn(nn.U, nn.c, nn.rank, nn.c, nullptr, (int)nn.c0, tmp));
+                    push_nn_chunks(B.nn, vnn(nn.V, nn.r, nn.rank, nn.r, Rj, 0, tmp, true));
                     apply_bytes += 2.0 * sizeof(T) * nn.rank * (nn.r + nn.c);
                 }
             }
             emit(L_TN, o2, B.tn.size() - o2, 0);
-            emit(L_NN, o3, B.nn.size() - o3, 1);   // atomic: nodes of a level share rows of R
+            emit(L_NN, o3, B.nn.size() - o3, 0);
         }
         for (int l = S.nlevels - 1; l >= 0; --l) {
             size_t o2 = B.tn.size();
@@ -1572,14 +1683,12 @@ struct EngineT final : EngineImpl {
                 const NodeRT& nn = nd[j];
                 if (nn.r == 0) continue;
                 const int32_t* Rj = d_rows + S.rows_ptr[j];
-                if (!nn.compressed) {
-                    TnTask t{arena + nn.off + nn.c, nn.ld, nn.c, nn.r, nullptr, 0, Rj, 0, y_dev + nn.c0, 1, 0};
-                    t.alpha = -1.0; t.beta = 1.0;
-                    push_tn_chunks(B.tn, t);
-                } else if (nn.rank) {
+                if (!nn.compressed) {   // y_C -= L^O_j^T y_R
+                    push_tn_chunks(B.tn, vtn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, Rj, 0, y_dev + nn.c0, -1.0, 1.0));
+                } else if (nn.rank) {   // y_C -= U_j (V_j^T y_R)
                     T* tmp = ztmp[l][zi++];
-                    push_tn_chunks(B.tn, TnTask{nn.V, nn.r, nn.rank, nn.r, nullptr, 0, Rj, 0, tmp, 1, 0});
-                    push_nn_chunks(nnb, NnTask{nn.U, nn.c, nn.rank, nn.c, nullptr, 0, nullptr, (int)nn.c0, tmp, 1, 0});
+                    push_tn_chunks(B.tn, vtn(nn.V, nn.r, nn.rank, nn.r, Rj, 0, tmp));
+                    push_nn_chunks(nnb, vnn(nn.U, nn.c, nn.rank, nn.c, nullptr, (int)nn.c0, tmp, false));
                 }
             }
             emit(L_TN, o2, B.tn.size() - o2, 0);
@@ -1587,20 +1696,20 @@ struct EngineT final : EngineImpl {
             B.nn.insert(B.nn.end(), nnb.begin(), nnb.end());
             emit(L_NN, o3, nnb.size(), 0);
             std::vector<std::vector<Act>> acts;
-            size_t o = B.trsv.size();
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 if (!nn.hier && nn.c <= SOLVE_MAX) continue;
                 acts.emplace_back();
                 diag_actions(j, true, zcur, acts.back());
             }
-            emit_acts(acts, true);
-            o = B.trsv.size();
+            emit_acts(acts);
+            size_t o = B.trsv.size();
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
-                if (!nn.hier && nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 0, y_dev + nn.c0, 1, 0});
+                if (!nn.hier && nn.c <= SOLVE_MAX)
+                    B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 1, y_dev + nn.c0, 1, 1});
             }
-            emit(L_TRSV, o, B.trsv.size() - o, 1);
+            emit(L_TRSV, o, B.trsv.size() - o, 0);
         }
         emit(L_PERM_OUT, 0, 1, 0);
         if (zcur > tmp_dev + std::max<long long>(tmp_total, 1)) throw Error(RSC_ERR_CUDA, "solve scratch overflow");
@@ -1626,9 +1735,9 @@ struct EngineT final : EngineImpl {
             switch (L.kind) {
                 case L_PERM_IN: k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(g_in, d_perm, y_dev, n); break;
                 case L_PERM_OUT: k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, g_out, n); break;
-                case L_TRSV: k_trsv<T><<<L.count, 256, 0, s>>>(d_trsv_all + L.off, 1, L.flag); break;
-                case L_TN: k_tn<T><<<L.count, 256, 0, s>>>(d_tn_all + L.off, y_dev, 1, 1); break;
-                case L_NN: k_nn<T><<<L.count, 256, 0, s>>>(d_nn_all + L.off, y_dev, 1, 1, T(-1), L.flag); break;
+                case L_TRSV: k_trsv<T, 1><<<L.count, 256, 0, s>>>(d_trsv_all + L.off); break;
+                case L_TN: k_tn<T><<<L.count, 256, 0, s>>>(d_tn_all + L.off); break;
+                case L_NN: k_nn<T><<<L.count, 256, 0, s>>>(d_nn_all + L.off); break;
             }
         }
         LAUNCH_CHECK();
@@ -1753,22 +1862,6 @@ __global__ void k_strided_copy(const T* __restrict__ src, long long ssr, long lo
         long long i = e % m, c = e / m;
         dst[i * dsr + c * dsc] = src[i * ssr + c * ssc];
     }
-}
-
-template <class T>
-void EngineT<T>::rows_to_cols_ld(const T* X, int ldx, int m, int nc, T* U, int ldu, int col0) {
-    if ((long long)m * nc == 0) return;
-    k_strided_copy<T><<<std::min(cdiv((long long)m * nc, 256), 8192), 256, 0, stream>>>(X, ldx, 1, U + (size_t)col0 * ldu, 1,
-                                                                                         ldu, m, nc);
-    launches++;
-    LAUNCH_CHECK();
-}
-template <class T>
-void EngineT<T>::cols_to_rows(const T* U, int ldu, int m, int nc, T* Xr) {
-    if ((long long)m * nc == 0) return;
-    k_strided_copy<T><<<std::min(cdiv((long long)m * nc, 256), 8192), 256, 0, stream>>>(U, 1, ldu, Xr, nc, 1, m, nc);
-    launches++;
-    LAUNCH_CHECK();
 }
 
 // ------------------------------------------------------------------ Engine facade

@@ -28,19 +28,27 @@ struct NodeTgt {             // where extend-add updates of supernode j go
     int c; int r; long long c0; long long rows_off;
 };
 struct LeafMap { long long lo; long long off; int size; int pad; };   // per column of a hierarchical node
-struct TnTask {              // Z[t, :] = sum_i A[arow_i, t] * Y[yrow_i, :]   (Z is K x N row-major)
+struct TnTask {              // Z[t, :] = beta Z[t, :] + alpha sum_i A[arow_i, t] Y[yrow_i, :]  (N columns)
     const void* A; int lda; int K; int nrow;
     const int32_t* amap; int aoff; const int32_t* ymap; int yoff;
-    void* Z; int ldz; int t0;   // t0: first column of A handled by this CTA (8 columns, one per warp)
-    double alpha = 1.0, beta = 0.0;   // Z = beta Z + alpha sum
+    void* Z; int ldz; int t0;          // t0: first column of A of this CTA (8 columns, one per warp)
+    const void* Y; int ldy; int N;
+    double alpha, beta;
 };
-struct NnTask {              // Y[yrow_i, :] += alpha * sum_l A[arow_i, l] * Z[l, :]
+struct NnTask {              // Y[yrow_i, :] += alpha sum_l A[arow_i, l] Z[l, :]  (N columns)
     const void* A; int lda; int K; int nrow;
     const int32_t* amap; int aoff; const int32_t* ymap; int yoff;
-    const void* Z; int ldz; int row0;   // row0: first row of this 64-row chunk
+    const void* Z; int ldz; int row0;  // row0: first row of this CTA's 64-row chunk
+    void* Y; int ldy; int N;
+    double alpha; int atomic;
 };
-struct TrsvTask { const void* L; int ld; int c; int pad; void* X; int ldx; int pad2; };
+struct TrsvTask { const void* L; int ld; int c; int N; void* X; int ldx; int transpose; };
 struct CsrBlock { const int32_t* rp; const int32_t* ci; const double* v; int nrows; int pad; };
+struct CsrTask { CsrBlock blk; const void* X; int ldx; void* Y; int ldy; int N; int row0; double alpha; };
+struct GaussTask { void* G; int m; int row0; uint32_t block_id; uint32_t word3; };
+struct NormTask { const void* X; int ld; int m; int nc; double* out; };
+struct QrTask { void* Y; int m; int b; int row0; double* G; double* Rinv; int* status; double coef; };
+struct CopyTask { const void* src; long long ssr, ssc; void* dst; long long dsr, dsc; int m, nc; };
 
 // ------------------------------------------------------------------ helpers
 template <class T> __device__ __forceinline__ void atomic_add(T* p, T v) { atomicAdd(p, v); }
@@ -254,55 +262,52 @@ __global__ void __launch_bounds__(256) k_push(const PushTask* __restrict__ tasks
 // ------------------------------------------------------------------ thin products (N columns, chunks of 16)
 // One warp per (task, column t of A); lanes stride over the task's rows.
 template <class T>
-__global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks, const T* __restrict__ Y, int ldy,
-                                            int N) {
+__global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     const TnTask tk = tasks[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = blockIdx.y * 16;
-    const int nc = min(16, N - c0);
+    const int nc = min(16, tk.N - c0);
+    const int t = tk.t0 + warp;
+    if (nc <= 0 || t >= tk.K) return;
     const T* A = (const T*)tk.A;
-    T* Z = (T*)tk.Z;
-    {
-        const int t = tk.t0 + warp;
-        if (t >= tk.K) return;
-        T acc[16];
+    const T* Y = (const T*)tk.Y;
+    T acc[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[c] = T(0);
-        for (int i = lane; i < tk.nrow; i += 32) {
-            int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
-            int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
-            T a = A[ar + (size_t)t * tk.lda];
-            const T* y = Y + (size_t)yr * ldy + c0;
+    for (int c = 0; c < 16; ++c) acc[c] = T(0);
+    for (int i = lane; i < tk.nrow; i += 32) {
+        const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
+        const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+        const T a = A[ar + (size_t)t * tk.lda];
+        const T* y = Y + (size_t)yr * tk.ldy + c0;
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (c < nc) acc[c] = fma(a, y[c], acc[c]);
-        }
+        for (int c = 0; c < 16; ++c)
+            if (c < nc) acc[c] = fma(a, y[c], acc[c]);
+    }
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            T v = acc[c];
+    for (int c = 0; c < 16; ++c) {
+        T v = acc[c];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc[c] = v;
-        }
-        if (lane < nc) {
-            T v = acc[0];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[c] = v;
+    }
+    if (lane < nc) {
+        T v = acc[0];
 #pragma unroll
-            for (int c = 1; c < 16; ++c)
-                if (lane == c) v = acc[c];
-            T* z = Z + (size_t)t * tk.ldz + c0 + lane;
-            *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * v : (T)tk.alpha * v;
-        }
+        for (int c = 1; c < 16; ++c)
+            if (lane == c) v = acc[c];
+        T* z = (T*)tk.Z + (size_t)t * tk.ldz + c0 + lane;
+        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * v : (T)tk.alpha * v;
     }
 }
 
-// One CTA per (task, 64-row chunk); 64 rows x 4 column groups of 4.
+// One CTA per (task, 64-row chunk, 16-column chunk); 64 rows x 4 column groups of 4.
 template <class T>
-__global__ void __launch_bounds__(256) k_nn(const NnTask* __restrict__ tasks, T* __restrict__ Y, int ldy, int N,
-                                            T alpha, int atomic) {
+__global__ void __launch_bounds__(256) k_nn(const NnTask* __restrict__ tasks) {
     __shared__ T Zs[64][17];
     const NnTask tk = tasks[blockIdx.x];
     const int c0 = blockIdx.y * 16;
-    const int nc = min(16, N - c0);
+    const int nc = min(16, tk.N - c0);
+    if (nc <= 0) return;
     const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
     const int i = tk.row0 + r;
     const bool active = i < tk.nrow;
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(256) k_nn(const NnTask* __restrict__ tasks, T*
         __syncthreads();
         if (active) {
             for (int l = 0; l < lk; ++l) {
-                T a = A[ar + (size_t)(l0 + l) * tk.lda];
+                const T a = A[ar + (size_t)(l0 + l) * tk.lda];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[c] = fma(a, Zs[l][4 * g + c], acc[c]);
             }
@@ -329,52 +334,55 @@ __global__ void __launch_bounds__(256) k_nn(const NnTask* __restrict__ tasks, T*
     }
     if (!active) return;
     const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
-    T* y = Y + (size_t)yr * ldy + c0 + 4 * g;
+    T* y = (T*)tk.Y + (size_t)yr * tk.ldy + c0 + 4 * g;
+    const T alpha = (T)tk.alpha;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         if (4 * g + c >= nc) break;
-        if (atomic) atomic_add(y + c, alpha * acc[c]);
+        if (tk.atomic) atomic_add(y + c, alpha * acc[c]);
         else y[c] += alpha * acc[c];
     }
 }
 
-// Y[i, :] = (or +=) alpha * sum_e v[e] X[ci[e], :] for a small sparse block (CSR rows).
+// Y[i, :] = alpha * sum_e v[e] X[ci[e], :] for 16 rows x 16 columns per CTA.
 template <class T>
-__global__ void k_csr_mm(CsrBlock blk, const T* __restrict__ X, int ldx, T* __restrict__ Y, int ldy, int N,
-                         T alpha, int accumulate) {
+__global__ void k_csr_mm(const CsrTask* __restrict__ tasks) {
+    const CsrTask tk = tasks[blockIdx.x];
     const int c0 = blockIdx.y * 16;
-    const int nc = min(16, N - c0);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < blk.nrows * 16; e += gridDim.x * blockDim.x) {
-        int i = e >> 4, c = e & 15;
-        if (c >= nc) continue;
-        T s = T(0);
-        for (int q = blk.rp[i]; q < blk.rp[i + 1]; ++q) s = fma((T)blk.v[q], X[(size_t)blk.ci[q] * ldx + c0 + c], s);
-        T* y = Y + (size_t)i * ldy + c0 + c;
-        *y = accumulate ? *y + alpha * s : alpha * s;
-    }
+    const int nc = min(16, tk.N - c0);
+    if (nc <= 0) return;
+    const int i = tk.row0 + (threadIdx.x >> 4), c = threadIdx.x & 15;
+    if (i >= tk.blk.nrows || c >= nc) return;
+    const T* X = (const T*)tk.X;
+    T s = T(0);
+    for (int q = tk.blk.rp[i]; q < tk.blk.rp[i + 1]; ++q)
+        s = fma((T)tk.blk.v[q], X[(size_t)tk.blk.ci[q] * tk.ldx + c0 + c], s);
+    ((T*)tk.Y)[(size_t)i * tk.ldy + c0 + c] = (T)tk.alpha * s;
 }
 
 // ------------------------------------------------------------------ dense triangular solves with many RHS
-// X (c x N, row-major) <- L^{-1} X or L^{-T} X, one CTA per (task, 16-column chunk), c <= SOLVE_MAX.
+// X (c x N, row-major) <- L^{-1} X or L^{-T} X, one CTA per (task, CW-column chunk), c <= SOLVE_MAX.
 // Blocked by 32 rows: a warp solves each column of the 32 x 32 diagonal tile with
 // shuffles, then the CTA updates the remaining rows with the solved block.
-template <class T>
-__global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks, int N, int transpose) {
-    __shared__ T Xs[SOLVE_MAX][17];
+template <class T, int CW>
+__global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks) {
+    __shared__ T Xs[SOLVE_MAX][CW + 1];
     __shared__ T Lt[32][33];
     const TrsvTask tk = tasks[blockIdx.x];
     const T* L = (const T*)tk.L;
     T* X = (T*)tk.X;
-    const int c = tk.c, ld = tk.ld;
-    const int c0 = blockIdx.y * 16;
-    const int nc = min(16, N - c0);
+    const int c = tk.c, ld = tk.ld, transpose = tk.transpose;
+    const int c0 = blockIdx.y * CW;
+    const int nc = min(CW, tk.N - c0);
     if (nc <= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < c * 16; e += blockDim.x) {
-        int i = e >> 4, q = e & 15;
+    for (int e = tid; e < c * CW; e += blockDim.x) {
+        int i = e / CW, q = e % CW;
         Xs[i][q] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
     }
     const int nb = (c + 31) >> 5;
+    constexpr int G = CW >= 4 ? 4 : CW;          // columns per thread in the update
+    constexpr int NG = CW / G;                    // column groups
     for (int bi = 0; bi < nb; ++bi) {
         const int b = transpose ? nb - 1 - bi : bi;
         const int r0 = b * 32, w = min(32, c - r0);
@@ -387,57 +395,41 @@ __global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks
         for (int q = warp; q < nc; q += 8) {
             T x = lane < w ? Xs[r0 + lane][q] : T(0);
             if (!transpose) {
-                for (int k = 0; k < w; ++k) {
-                    if (lane == k) x /= Lt[k][k];
-                    const T xk = __shfl_sync(0xffffffffu, x, k);
-                    if (lane > k) x -= Lt[lane][k] * xk;
+                for (int k2 = 0; k2 < w; ++k2) {
+                    if (lane == k2) x /= Lt[k2][k2];
+                    const T xk = __shfl_sync(0xffffffffu, x, k2);
+                    if (lane > k2) x -= Lt[lane][k2] * xk;
                 }
             } else {
-                for (int k = w - 1; k >= 0; --k) {
-                    if (lane == k) x /= Lt[k][k];
-                    const T xk = __shfl_sync(0xffffffffu, x, k);
-                    if (lane < k) x -= Lt[k][lane] * xk;
+                for (int k2 = w - 1; k2 >= 0; --k2) {
+                    if (lane == k2) x /= Lt[k2][k2];
+                    const T xk = __shfl_sync(0xffffffffu, x, k2);
+                    if (lane < k2) x -= Lt[k2][lane] * xk;
                 }
             }
             if (lane < w) Xs[r0 + lane][q] = x;
         }
         __syncthreads();
-        if (!transpose) {
-            // rows below: X[i,:] -= L[i, r0:r0+w] X[r0:r0+w, :]
-            const int rem = c - r0 - w;
-            for (int e = tid; e < rem * 4; e += blockDim.x) {
-                const int i = r0 + w + (e >> 2), g = (e & 3) * 4;
-                if (g >= nc) continue;
-                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-                for (int k = 0; k < w; ++k) {
-                    const T l = L[i + (size_t)(r0 + k) * ld];
-                    a0 = fma(l, Xs[r0 + k][g], a0);
-                    a1 = fma(l, Xs[r0 + k][g + 1], a1);
-                    a2 = fma(l, Xs[r0 + k][g + 2], a2);
-                    a3 = fma(l, Xs[r0 + k][g + 3], a3);
-                }
-                Xs[i][g] -= a0; Xs[i][g + 1] -= a1; Xs[i][g + 2] -= a2; Xs[i][g + 3] -= a3;
+        const int lo = transpose ? 0 : r0 + w;
+        const int cnt = transpose ? r0 : c - r0 - w;
+        for (int e = tid; e < cnt * NG; e += blockDim.x) {
+            const int i = lo + e / NG, g0 = (e % NG) * G;
+            if (g0 >= nc) continue;
+            T a[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) a[u] = T(0);
+            for (int k2 = 0; k2 < w; ++k2) {
+                const T l = transpose ? L[(r0 + k2) + (size_t)i * ld] : L[i + (size_t)(r0 + k2) * ld];
+#pragma unroll
+                for (int u = 0; u < G; ++u) a[u] = fma(l, Xs[r0 + k2][g0 + u], a[u]);
             }
-        } else {
-            // rows above: X[i,:] -= L[r0:r0+w, i]^T X[r0:r0+w, :]
-            for (int e = tid; e < r0 * 4; e += blockDim.x) {
-                const int i = e >> 2, g = (e & 3) * 4;
-                if (g >= nc) continue;
-                T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-                for (int k = 0; k < w; ++k) {
-                    const T l = L[(r0 + k) + (size_t)i * ld];
-                    a0 = fma(l, Xs[r0 + k][g], a0);
-                    a1 = fma(l, Xs[r0 + k][g + 1], a1);
-                    a2 = fma(l, Xs[r0 + k][g + 2], a2);
-                    a3 = fma(l, Xs[r0 + k][g + 3], a3);
-                }
-                Xs[i][g] -= a0; Xs[i][g + 1] -= a1; Xs[i][g + 2] -= a2; Xs[i][g + 3] -= a3;
-            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) Xs[i][g0 + u] -= a[u];
         }
     }
     __syncthreads();
-    for (int e = tid; e < c * 16; e += blockDim.x) {
-        int i = e >> 4, q = e & 15;
+    for (int e = tid; e < c * CW; e += blockDim.x) {
+        int i = e / CW, q = e % CW;
         if (q < nc) X[(size_t)i * tk.ldx + c0 + q] = Xs[i][q];
     }
 }
@@ -456,29 +448,33 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 }
 
 // G (m x 16, row-major, ld 16): entry (i, c) from counter (i, c/2, block_id, word3), key = seed;
-// Box-Muller on (w0, w1) for even c and (w2, w3) for odd c.
+// Box-Muller on (w0, w1) for even c and (w2, w3) for odd c.  32 rows per CTA.
 template <class T>
-__global__ void k_gauss(T* __restrict__ G, int m, unsigned long long seed, uint32_t block_id, uint32_t word3) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * 8) return;
-    int i = e >> 3, cp = e & 7;
-    uint32_t c[4] = {(uint32_t)i, (uint32_t)cp, block_id, word3};
+__global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long seed) {
+    const GaussTask tk = tasks[blockIdx.x];
+    const int i = tk.row0 + (threadIdx.x >> 3), cp = threadIdx.x & 7;
+    if (i >= tk.m) return;
+    uint32_t c[4] = {(uint32_t)i, (uint32_t)cp, tk.block_id, tk.word3};
     philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
     const double two32 = 2.3283064365386963e-10;   // 2^-32
     const double twopi = 6.283185307179586;
-    double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
-    double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
+    const double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
+    const double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
+    T* G = (T*)tk.G;
     G[(size_t)i * 16 + 2 * cp] = (T)z0;
     G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
 }
 
 // ------------------------------------------------------------------ small reductions / orthonormalisation
-// out += sum of squares of X(m x nc, row-major ld).
+// *out += sum of squares of X (m x nc, row-major ld); grid (tasks, 16).
 template <class T>
-__global__ void k_sqnorm(const T* __restrict__ X, int ld, int m, int nc, double* out) {
+__global__ void k_sqnorm(const NormTask* __restrict__ tasks) {
+    const NormTask tk = tasks[blockIdx.x];
+    const T* X = (const T*)tk.X;
     double s = 0.0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * nc; e += gridDim.x * blockDim.x) {
-        double v = (double)X[(size_t)(e / nc) * ld + e % nc];
+    const long long cnt = (long long)tk.m * tk.nc;
+    for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.y * blockDim.x) {
+        const double v = (double)X[(size_t)(e / tk.nc) * tk.ld + e % tk.nc];
         s += v * v;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -488,49 +484,55 @@ __global__ void k_sqnorm(const T* __restrict__ X, int ld, int m, int nc, double*
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        atomicAdd(out, t);
+        atomicAdd(tk.out, t);
     }
 }
 
 // Gram G += Y^T Y over a 256-row chunk (b <= 16 columns of a row-major ld-16 block).
 template <class T>
-__global__ void k_gram(const T* __restrict__ Y, int m, int b, double* G) {
+__global__ void k_gram(const QrTask* __restrict__ tasks) {
     __shared__ double Ys[256][17];
-    const int r0 = blockIdx.x * 256;
-    const int nr = min(256, m - r0);
+    const QrTask tk = tasks[blockIdx.x];
+    const T* Y = (const T*)tk.Y;
+    const int nr = min(256, tk.m - tk.row0);
     for (int e = threadIdx.x; e < 256 * 16; e += blockDim.x) {
         int i = e >> 4, c = e & 15;
-        Ys[i][c] = (i < nr && c < b) ? (double)Y[(size_t)(r0 + i) * 16 + c] : 0.0;
+        Ys[i][c] = (i < nr && c < tk.b) ? (double)Y[(size_t)(tk.row0 + i) * 16 + c] : 0.0;
     }
     __syncthreads();
     const int a = threadIdx.x >> 4, c = threadIdx.x & 15;
-    if (a < b && c < b && c >= a) {
+    if (a < tk.b && c < tk.b && c >= a) {
         double s = 0.0;
         for (int i = 0; i < nr; ++i) s += Ys[i][a] * Ys[i][c];
-        atomicAdd(&G[a * 16 + c], s);
+        atomicAdd(&tk.G[a * 16 + c], s);
     }
 }
 
-// Cholesky G + shift I = R^T R (b x b, upper R) and Rinv = R^{-1}; status = 1 if not
-// positive definite.  shift = shift_coef * trace(G): the shifted Cholesky QR of
-// Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa (SIAM J. Sci. Comput. 2020)
-// uses 11 (m b + b (b + 1)) u ||Y||_2^2; trace(G) bounds ||Y||_2^2 from above.
-__global__ void k_chol_small(const double* G, int b, double shift_coef, double* Rinv, int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Cholesky G + shift I = R^T R (b x b, upper R) and Rinv = R^{-1}; *status = 1 if not
+// positive definite.  shift = coef * trace(G): the shifted Cholesky QR of Fukaya,
+// Kannan, Nakatsukasa, Yamamoto, Yanagisawa (SIAM J. Sci. Comput. 2020) uses
+// 11 (m b + b (b + 1)) u ||Y||_2^2, and trace(G) bounds ||Y||_2^2 from above.
+// One thread per task.
+__global__ void k_chol_small(const QrTask* __restrict__ tasks, int ntasks) {
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= ntasks) return;
+    const QrTask tk = tasks[ti];
+    const double* G = tk.G;
+    const int b = tk.b;
     double R[16][16], X[16][16];
     for (int i = 0; i < 16; ++i)
         for (int j = 0; j < 16; ++j) { R[i][j] = 0.0; X[i][j] = 0.0; }
     double trace = 0.0;
     for (int i = 0; i < b; ++i) trace += G[i * 16 + i];
-    const double shift = shift_coef * trace;
+    const double shift = tk.coef * trace;
     for (int j = 0; j < b; ++j) {
         double d = G[j * 16 + j] + shift;
-        for (int k = 0; k < j; ++k) d -= R[k][j] * R[k][j];
-        if (!(d > 1e-28 * trace)) { *status = 1; d = 1.0; }
+        for (int k2 = 0; k2 < j; ++k2) d -= R[k2][j] * R[k2][j];
+        if (!(d > 1e-28 * trace)) { *tk.status = 1; d = 1.0; }
         R[j][j] = sqrt(d);
         for (int i = j + 1; i < b; ++i) {
             double s = G[j * 16 + i];
-            for (int k = 0; k < j; ++k) s -= R[k][j] * R[k][i];
+            for (int k2 = 0; k2 < j; ++k2) s -= R[k2][j] * R[k2][i];
             R[j][i] = s / R[j][j];
         }
     }
@@ -538,36 +540,39 @@ __global__ void k_chol_small(const double* G, int b, double shift_coef, double* 
         X[j][j] = 1.0 / R[j][j];
         for (int i = j - 1; i >= 0; --i) {
             double s = 0.0;
-            for (int k = i + 1; k <= j; ++k) s += R[i][k] * X[k][j];
+            for (int k2 = i + 1; k2 <= j; ++k2) s += R[i][k2] * X[k2][j];
             X[i][j] = -s / R[i][i];
         }
     }
     for (int i = 0; i < 16; ++i)
-        for (int j = 0; j < 16; ++j) Rinv[i * 16 + j] = X[i][j];
+        for (int j = 0; j < 16; ++j) tk.Rinv[i * 16 + j] = X[i][j];
 }
 
-// Y <- Y Rinv (row-major ld 16, b columns).
+// Y <- Y Rinv (row-major ld 16, b columns), 128 rows per CTA.
 template <class T>
-__global__ void k_apply_rinv(T* __restrict__ Y, int m, int b, const double* __restrict__ Rinv) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    double y[16], o[16];
-    for (int c = 0; c < 16; ++c) y[c] = c < b ? (double)Y[(size_t)i * 16 + c] : 0.0;
-    for (int c = 0; c < b; ++c) {
+__global__ void k_apply_rinv(const QrTask* __restrict__ tasks) {
+    const QrTask tk = tasks[blockIdx.x];
+    const int i = tk.row0 + threadIdx.x;
+    if (i >= tk.m) return;
+    T* Y = (T*)tk.Y;
+    double y[16];
+    for (int c = 0; c < 16; ++c) y[c] = c < tk.b ? (double)Y[(size_t)i * 16 + c] : 0.0;
+    for (int c = 0; c < tk.b; ++c) {
         double s = 0.0;
-        for (int k = 0; k <= c; ++k) s += y[k] * Rinv[k * 16 + c];
-        o[c] = s;
+        for (int k2 = 0; k2 <= c; ++k2) s += y[k2] * tk.Rinv[k2 * 16 + c];
+        Y[(size_t)i * 16 + c] = (T)s;
     }
-    for (int c = 0; c < b; ++c) Y[(size_t)i * 16 + c] = (T)o[c];
 }
 
-// U[:, col0 + c] = Y[:, c] for c < b (Y row-major ld 16, U column-major ld m).
+// dst[i*dsr + c*dsc] = src[i*ssr + c*ssc]; grid (tasks, 32).
 template <class T>
-__global__ void k_rows_to_cols(const T* __restrict__ Y, int m, int b, T* __restrict__ U, int ldu, int col0) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * b) return;
-    int i = e % m, c = e / m;
-    U[i + (size_t)(col0 + c) * ldu] = Y[(size_t)i * 16 + c];
+__global__ void k_copy(const CopyTask* __restrict__ tasks) {
+    const CopyTask tk = tasks[blockIdx.x];
+    const long long cnt = (long long)tk.m * tk.nc;
+    for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.y * blockDim.x) {
+        const long long i = e % tk.m, c = e / tk.m;
+        ((T*)tk.dst)[i * tk.dsr + c * tk.dsc] = ((const T*)tk.src)[i * tk.ssr + c * tk.ssc];
+    }
 }
 
 // Row-major thin block <-> strided copies and scaled adds (vector path of the solve).
