@@ -346,6 +346,8 @@ struct EngineT final : EngineImpl {
         long long off = -1;     // panel or dense-diagonal offset in the arena
         int ld = 0;
         std::vector<long long> leaf_off;   // by block label (leaves only)
+        long long inv_off = -1;            // row-major inverses of the SOLVE_MAX diagonal sub-blocks
+        std::vector<long long> leaf_inv;   // by label: row-major inverse of each leaf
         int rank = 0;
         T* V = nullptr;          // |R_j| x rank, column-major
         T* U = nullptr;          // c x rank, column-major (ld c)
@@ -364,6 +366,39 @@ struct EngineT final : EngineImpl {
     DeviceMem fmem;      // factor arena + low-rank storage
     T* arena = nullptr;
     long long arena_elems = 0;
+    T* invs = nullptr;            // inverses of dense diagonal (sub-)blocks, row-major
+    long long inv_elems = 0;
+    std::vector<TrsvTask*> inv_tasks;   // per level: inverse computations of the level's dense blocks
+    std::vector<int> inv_count, inv_maxc;
+    // inverse of the b-th SOLVE_MAX diagonal sub-block of a non-hierarchical node
+    const T* inv_block(int j, int b0) const {
+        const NodeRT& n = nd[j];
+        long long o = n.inv_off;
+        for (int x = 0; x < b0; x += SOLVE_MAX) { const long long bs = std::min(SOLVE_MAX, n.c - x); o += bs * bs; }
+        return invs + o;
+    }
+    std::vector<TrsvTask> inverse_tasks_dense(int j) const {
+        const NodeRT& n = nd[j];
+        std::vector<TrsvTask> v;
+        for (int b0 = 0; b0 < n.c; b0 += SOLVE_MAX) {
+            const int bs = std::min(SOLVE_MAX, n.c - b0);
+            v.push_back(TrsvTask{arena + n.off + b0 + (size_t)b0 * n.ld, n.ld, bs, bs, (void*)inv_block(j, b0), bs, 2});
+        }
+        return v;
+    }
+    void launch_inverses(std::vector<TrsvTask>& tv, const TrsvTask* dev = nullptr) {
+        if (tv.empty()) return;
+        int maxc = 0;
+        for (auto& t : tv) maxc = std::max(maxc, t.c);
+        const TrsvTask* d = dev ? dev : (const TrsvTask*)upload_tmp(sTask, tv);
+        const dim3 grid((unsigned)tv.size(), (unsigned)cdiv(maxc, TRSV_CW));
+        double fl = 0;
+        for (auto& t : tv) fl += (double)t.c * t.c * t.c / 3.0;
+        flops += fl;
+        PROF(prof, "trinv", stream, fl, 0, k_trsv_subst<T, TRSV_CW><<<grid, 256, 0, stream>>>(d));
+        launches++;
+        LAUNCH_CHECK();
+    }
     T* lr_base = nullptr;
     long long lr_cap = 0, lr_used = 0;
     std::vector<NodeRT> nd;
@@ -409,11 +444,16 @@ struct EngineT final : EngineImpl {
     EngineT(const Symbolic& S_, const rsc_options& o_) : S(S_), o(o_) {
         CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
+        hs_attr<8>();
+        hs_attr<4>();
+        hs_attr<2>();
+        hs_attr<1>();
         nd.resize(S.M);
     }
     ~EngineT() override {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (arena_base) cudaFree(arena_base);
+        if (arena_host) cudaFreeHost(arena_host);
         if (stream) cudaStreamDestroy(stream);
     }
 
@@ -458,6 +498,28 @@ struct EngineT final : EngineImpl {
         }
         arena_elems = off;
         arena = (T*)fmem.alloc(sizeof(T) * std::max<long long>(off, 1));
+        long long ioff = 0;
+        for (int j = 0; j < M; ++j) {
+            NodeRT& n = nd[j];
+            if (!n.hier) {
+                n.inv_off = ioff;
+                for (int b0 = 0; b0 < n.c; b0 += SOLVE_MAX) {
+                    const long long bs = std::min(SOLVE_MAX, n.c - b0);
+                    ioff += bs * bs;
+                }
+            } else {
+                const BlockTree& t = S.tree[j];
+                n.leaf_inv.assign(t.nblocks + 1, -1);
+                for (int b = 1; b <= t.nblocks; ++b)
+                    if (t.leaf[b]) {
+                        const long long sz = t.hi[b] - t.lo[b];
+                        n.leaf_inv[b] = ioff;
+                        ioff += sz * sz;
+                    }
+            }
+        }
+        invs = (T*)fmem.alloc(sizeof(T) * std::max<long long>(ioff, 1));
+        inv_elems = ioff;
         // low-rank storage bound: U (c x maxr) + V (r x maxr) per compressed block
         long long lr = 0;
         for (int j = 0; j < M; ++j) {
@@ -674,6 +736,21 @@ struct EngineT final : EngineImpl {
             }
         }
 
+        // inverses of the dense diagonal blocks factored by the level's panel steps
+        inv_tasks.assign(S.nlevels, nullptr);
+        inv_count.assign(S.nlevels, 0);
+        inv_maxc.assign(S.nlevels, 0);
+        for (int l = 0; l < S.nlevels; ++l) {
+            std::vector<TrsvTask> tv;
+            for (int j : S.level_nodes[l])
+                if (!nd[j].hier) {
+                    auto v = inverse_tasks_dense(j);
+                    tv.insert(tv.end(), v.begin(), v.end());
+                }
+            for (auto& t : tv) inv_maxc[l] = std::max(inv_maxc[l], t.c);
+            inv_tasks[l] = pmem.upload(tv, stream);
+            inv_count[l] = (int)tv.size();
+        }
         // push tasks per level: sources k of the level, every ancestor run, 64x64 tiles
         push_tasks.assign(S.nlevels, nullptr);
         push_count.assign(S.nlevels, 0);
@@ -788,6 +865,7 @@ struct EngineT final : EngineImpl {
     // stream is idle (sync_stream), so records of kernels in flight stay valid.
     // cudaMemcpyAsync from pageable memory stages the data before returning.
     char* arena_base = nullptr;
+    char* arena_host = nullptr;     // pinned staging mirror of the device arena
     size_t arena_cap = 0, arena_used = 0;
     void sync_stream() {
         CK(cudaStreamSynchronize(stream));
@@ -799,13 +877,18 @@ struct EngineT final : EngineImpl {
             sync_stream();
             if (bytes > arena_cap) {
                 if (arena_base) CK(cudaFree(arena_base));
+                if (arena_host) CK(cudaFreeHost(arena_host));
                 arena_cap = std::max(bytes, (size_t)64 << 20);
                 CK(cudaMalloc(&arena_base, arena_cap));
+                CK(cudaMallocHost(&arena_host, arena_cap));
             }
         }
         void* p = arena_base + arena_used;
+        if (!v.empty()) {
+            std::memcpy(arena_host + arena_used, v.data(), sizeof(X) * v.size());
+            CK(cudaMemcpyAsync(p, arena_host + arena_used, sizeof(X) * v.size(), cudaMemcpyHostToDevice, stream));
+        }
         arena_used += bytes;
-        if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, stream));
         return p;
     }
 
@@ -816,6 +899,8 @@ struct EngineT final : EngineImpl {
     // (TN products) before phase C (NN products); a stage never holds two phase-A
     // records that touch the same buffer.
     struct Stage {
+        std::vector<HAct> hacts;           // actions of the hsolve tasks (acts holds an index here)
+        std::vector<HTask> hs;
         std::vector<GaussTask> gauss;
         std::vector<CopyTask> copy;
         std::vector<CsrTask> csr;
@@ -843,12 +928,12 @@ struct EngineT final : EngineImpl {
     }
     void add_tn(Stage& s, const TnTask& t) {
         if (t.K == 0 || t.nrow == 0 || t.N == 0) return;
-        for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; s.tn.push_back(c); }
+        for (int t0 = 0; t0 < t.K; t0 += TN_COLS) { TnTask c = t; c.t0 = t0; s.tn.push_back(c); }
         flops += 2.0 * t.nrow * t.K * t.N;
     }
     void add_nn(Stage& s, const NnTask& t) {
         if (t.K == 0 || t.nrow == 0 || t.N == 0) return;
-        for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; s.nn.push_back(c); }
+        for (int r0 = 0; r0 < t.nrow; r0 += NN_ROWS) { NnTask c = t; c.row0 = r0; s.nn.push_back(c); }
         flops += 2.0 * t.nrow * t.K * t.N;
     }
     void add_csr(Stage& s, const CsrBlock& b, const T* X, int ldx, T* Y, int ldy, int N) {
@@ -865,10 +950,27 @@ struct EngineT final : EngineImpl {
     }
     static Stage& next(Program& P) { P.emplace_back(); return P.back(); }
 
+    static double task_flops(const TnTask& t) { return 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0) * t.N; }
+    static double task_flops(const NnTask& t) { return 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K * t.N; }
+    static double task_flops(const TrsvTask& t) { return (double)t.c * t.c * t.N; }
+    template <class X> static double task_flops(const X&) { return 0.0; }
+    static double task_bytes(const TnTask& t) {
+        const double cols = std::min(TN_COLS, t.K - t.t0);
+        return sizeof(T) * (t.nrow * cols + t.nrow * (double)t.N + cols * t.N);
+    }
+    static double task_bytes(const NnTask& t) {
+        const double rows = std::min(NN_ROWS, t.nrow - t.row0);
+        return sizeof(T) * (rows * t.K + 2.0 * rows * t.N + (double)t.K * t.N);
+    }
+    static double task_bytes(const TrsvTask& t) { return sizeof(T) * ((double)t.c * (t.c + 1) / 2 + 2.0 * t.c * t.N); }
+    template <class X> static double task_bytes(const X&) { return 0.0; }
     template <class X, class F> void launch_kind(const char* name, std::vector<X>& all, int ychunks, F&& launch) {
         if (all.empty()) return;
         X* d = (X*)upload_tmp(sTask, all);
-        PROF(prof, name, stream, 0, 0, launch(d, (int)all.size(), ychunks));
+        double fl = 0, by = 0;
+        if (prof.enabled(name))
+            for (const X& t : all) { fl += task_flops(t); by += task_bytes(t); }
+        PROF(prof, name, stream, fl, by, launch(d, (int)all.size(), ychunks));
         launches++;
         LAUNCH_CHECK();
     }
@@ -882,6 +984,9 @@ struct EngineT final : EngineImpl {
             for (auto& p : progs) {
                 if (i >= p.size()) continue;
                 Stage& s = p[i];
+                const long long hb = (long long)st.hacts.size();
+                st.hacts.insert(st.hacts.end(), s.hacts.begin(), s.hacts.end());
+                for (HTask h : s.hs) { h.acts = (const HAct*)(intptr_t)((intptr_t)h.acts + hb); st.hs.push_back(h); }
                 st.gauss.insert(st.gauss.end(), s.gauss.begin(), s.gauss.end());
                 st.copy.insert(st.copy.end(), s.copy.begin(), s.copy.end());
                 st.csr.insert(st.csr.end(), s.csr.begin(), s.csr.end());
@@ -895,13 +1000,18 @@ struct EngineT final : EngineImpl {
             for (auto& t : st.trsv) yn_tr = std::max(yn_tr, cdiv(t.N, TRSV_CW));
             const unsigned long long seed = o.seed;
             cudaStream_t s = stream;
+            if (!st.hs.empty()) {
+                HAct* dacts = (HAct*)upload_tmp(sTask, st.hacts);
+                for (auto& h : st.hs) h.acts = dacts + (intptr_t)h.acts;
+                run_hsolve(st.hs, s);
+            }
             launch_kind("gauss", st.gauss, 1, [&](GaussTask* d, int n, int) { k_gauss<T><<<n, 256, 0, s>>>(d, seed); });
             launch_kind("copy", st.copy, 1, [&](CopyTask* d, int n, int) { k_copy<T><<<dim3(n, 32), 256, 0, s>>>(d); });
             launch_kind("csr", st.csr, yn_csr, [&](CsrTask* d, int n, int y) { k_csr_mm<T><<<dim3(n, y), 256, 0, s>>>(d); });
             launch_kind("trsv", st.trsv, yn_tr,
                         [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
             launch_kind("tn", st.tn, yn_tn, [&](TnTask* d, int n, int y) { k_tn<T><<<dim3(n, y), 256, 0, s>>>(d); });
-            launch_kind("nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) { k_nn<T><<<dim3(n, y), 256, 0, s>>>(d); });
+            launch_kind("nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) { k_nn<T><<<dim3(n, y), NN_ROWS, 0, s>>>(d); });
         }
         progs.clear();
     }
@@ -937,15 +1047,98 @@ struct EngineT final : EngineImpl {
     T* wsT(size_t n) { return (T*)ws.getb(sizeof(T) * n); }
 
     // ---------------------------------------------------------------- dense / hierarchical triangular solves (programs)
+    // Action list of the solve with the subtree of L^D_j rooted at s (0: whole block),
+    // rows relative to the subtree's first row (Alg. 4, branches in the corrected order).
+    void hacts(int j, int s, bool transpose, std::vector<HAct>& out) {
+        const NodeRT& n = nd[j];
+        if (!n.hier) {
+            const T* L = arena + n.off;
+            const int ld = n.ld, c = n.c, bs = SOLVE_MAX, nblk = cdiv(c, bs);
+            for (int bi = 0; bi < nblk; ++bi) {
+                const int b = transpose ? nblk - 1 - bi : bi;
+                const int b0 = b * bs, b1 = std::min(c, b0 + bs);
+                out.push_back(HAct{HA_TRSV, 0, 0, b0, b1 - b0, 0, inv_block(j, b0), b1 - b0, nullptr, 0});
+                if (!transpose && b1 < c)
+                    out.push_back(HAct{HA_GEMV, b0, 0, b1, c - b1, b1 - b0, nullptr, 0, L + b1 + (size_t)b0 * ld, ld});
+                if (transpose && b0 > 0)
+                    out.push_back(HAct{HA_GEMVT, b0, b1 - b0, 0, b0, 0, L + b0, ld, nullptr, 0});
+                flops += (double)(b1 - b0) * (b1 - b0) + 2.0 * (b1 - b0) * (transpose ? b0 : c - b1);
+            }
+            return;
+        }
+        const BlockTree& t = S.tree[j];
+        if (s == 0) s = t.root;
+        const int base = t.lo[s];
+        std::function<void(int)> rec = [&](int b) {
+            if (t.leaf[b]) {
+                const int sz = t.hi[b] - t.lo[b];
+                out.push_back(HAct{HA_TRSV, 0, 0, t.lo[b] - base, sz, 0, invs + n.leaf_inv[b], sz, nullptr, 0});
+                flops += (double)sz * sz;
+                return;
+            }
+            const int n1 = t.mid[b] - t.lo[b], n2 = t.hi[b] - t.mid[b], q = n.brank[b];
+            auto lowrank = [&]() {
+                if (!q) return;
+                if (!transpose)
+                    out.push_back(HAct{HA_LR, t.lo[b] - base, n1, t.mid[b] - base, n2, q, n.bU[b], n1, n.bV[b], n2});
+                else
+                    out.push_back(HAct{HA_LR, t.mid[b] - base, n2, t.lo[b] - base, n1, q, n.bV[b], n2, n.bU[b], n1});
+                flops += 2.0 * q * (n1 + n2);
+            };
+            if (!transpose) { rec(t.left[b]); lowrank(); rec(t.right[b]); }
+            else { rec(t.right[b]); lowrank(); rec(t.left[b]); }
+        };
+        rec(s);
+    }
+    // column chunk of the persistent solve so that (c + Z rows) x CW fits in shared memory
+    static int pick_cw(int c) {
+        const size_t cap = 200 * 1024;
+        for (int cw : {8, 4, 2, 1})
+            if ((size_t)(c + HS_ZROWS) * cw * sizeof(T) <= cap) return cw;
+        return 0;
+    }
+    static size_t hs_smem(int c, int cw) { return (size_t)(c + HS_ZROWS) * cw * sizeof(T); }
+    template <int CW> static void hs_attr() {
+        CK(cudaFuncSetAttribute(k_hsolve<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 256));
+    }
+    // launch persistent solves, one launch per column chunk width; tasks' acts are device pointers
+    void run_hsolve(std::vector<HTask>& tasks, cudaStream_t s, int force_cw = 0) {
+        for (int cw : {8, 4, 2, 1}) {
+            std::vector<HTask> g;
+            int maxc = 0, ych = 1;
+            for (auto& t : tasks) {
+                const int w = force_cw ? force_cw : pick_cw(t.c);
+                if (w != cw) continue;
+                g.push_back(t);
+                maxc = std::max(maxc, t.c);
+                ych = std::max(ych, cdiv(t.N, cw));
+            }
+            if (g.empty()) continue;
+            HTask* d = (HTask*)upload_tmp(sTask, g);
+            const dim3 grid((unsigned)g.size(), (unsigned)ych);
+            const size_t sm = hs_smem(maxc, cw);
+            switch (cw) {
+                case 8: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 8><<<grid, HS_THREADS, sm, s>>>(d)); break;
+                case 4: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 4><<<grid, HS_THREADS, sm, s>>>(d)); break;
+                case 2: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 2><<<grid, HS_THREADS, sm, s>>>(d)); break;
+                default: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 1><<<grid, HS_THREADS, sm, s>>>(d)); break;
+            }
+            launches++;
+            LAUNCH_CHECK();
+        }
+    }
     // X (c x N row-major, ld ldx) <- L^{-1} X or L^{-T} X for dense lower L (ld), blocked by SOLVE_MAX
-    void prog_dense_solve(Program& P, const T* L, int ld, int c, T* X, int ldx, int N, bool transpose) {
+    void prog_dense_solve(Program& P, int j, T* X, int ldx, int N, bool transpose) {
+        const NodeRT& n = nd[j];
+        const T* L = arena + n.off;
+        const int ld = n.ld, c = n.c;
         if (c == 0) return;
         const int bs = SOLVE_MAX, nblk = cdiv(c, bs);
         for (int bi = 0; bi < nblk; ++bi) {
             const int b = transpose ? nblk - 1 - bi : bi;
             const int b0 = b * bs, b1 = std::min(c, b0 + bs);
             Stage& s = next(P);
-            add_trsv(s, L + b0 + (size_t)b0 * ld, ld, b1 - b0, X + (size_t)b0 * ldx, ldx, N, transpose);
+            add_trsv(s, inv_block(j, b0), b1 - b0, b1 - b0, X + (size_t)b0 * ldx, ldx, N, transpose);
             if (!transpose && b1 < c)
                 add_nn(s, nn_task(L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, 0, nullptr, 0, X + (size_t)b0 * ldx,
                                   ldx, X + (size_t)b1 * ldx, ldx, N, -1.0, false));
@@ -958,12 +1151,22 @@ struct EngineT final : EngineImpl {
     // Alg. 4 (branches in the corrected order) on the subtree of L^D_j rooted at s (0 = root).
     void prog_diag_solve(Program& P, int j, int s, T* X, int ldx, int N, bool transpose) {
         const NodeRT& n = nd[j];
-        if (!n.hier) { prog_dense_solve(P, arena + n.off, n.ld, n.c, X, ldx, N, transpose); return; }
+        if (!n.hier && n.c <= SOLVE_MAX) { prog_dense_solve(P, j, X, ldx, N, transpose); return; }
+        const int c = n.hier ? (s == 0 ? n.c : S.tree[j].hi[s] - S.tree[j].lo[s]) : n.c;
+        if (pick_cw(c) > 0) {
+            Stage& st = next(P);
+            const long long first = (long long)st.hacts.size();
+            hacts(j, s, transpose, st.hacts);
+            st.hs.push_back(HTask{(const HAct*)(intptr_t)first, (long long)st.hacts.size() - first, X, ldx, N, c,
+                                  transpose ? 1 : 0});
+            return;
+        }
+        if (!n.hier) { prog_dense_solve(P, j, X, ldx, N, transpose); return; }
         const BlockTree& t = S.tree[j];
         if (s == 0) s = t.root;
         if (t.leaf[s]) {
             const int sz = t.hi[s] - t.lo[s];
-            prog_dense_solve(P, arena + n.leaf_off[s], sz, sz, X, ldx, N, transpose);
+            add_trsv(next(P), invs + n.leaf_inv[s], sz, sz, X, ldx, N, transpose);
             return;
         }
         const int n1 = t.mid[s] - t.lo[s], n2 = t.hi[s] - t.mid[s], q = n.brank[s];
@@ -1346,7 +1549,13 @@ struct EngineT final : EngineImpl {
                     dp.push_back(DensePanel{arena + nd[j].leaf_off[s], sz, sz, sz, j});
                 }
                 factor_dense_batch(dp);
-                check_status();
+                std::vector<TrsvTask> tv;
+                for (int j : leaves) {
+                    const BlockTree& t = S.tree[j];
+                    const int sz = t.hi[s] - t.lo[s];
+                    tv.push_back(TrsvTask{arena + nd[j].leaf_off[s], sz, sz, sz, invs + nd[j].leaf_inv[s], sz, 2});
+                }
+                launch_inverses(tv);
             }
             if (!internals.empty()) {
                 std::vector<RF> R;
@@ -1424,6 +1633,16 @@ struct EngineT final : EngineImpl {
         }
         for (int l = 0; l < S.nlevels; ++l) {
             run_panel_steps(panel_steps[l]);
+            if (inv_count[l]) {
+                double fl = 0;
+                for (int j : S.level_nodes[l])
+                    if (!nd[j].hier) fl += (double)nd[j].c * std::min(nd[j].c, SOLVE_MAX) * std::min(nd[j].c, SOLVE_MAX) / 3.0;
+                flops += fl;
+                const dim3 grid((unsigned)inv_count[l], (unsigned)cdiv(inv_maxc[l], TRSV_CW));
+                PROF(prof, "trinv", stream, fl, 0, k_trsv_subst<T, TRSV_CW><<<grid, 256, 0, stream>>>(inv_tasks[l]));
+                launches++;
+                LAUNCH_CHECK();
+            }
             for (int j : S.level_nodes[l]) {
                 const NodeRT& n = nd[j];
                 if (!n.compressed) {
@@ -1515,8 +1734,10 @@ struct EngineT final : EngineImpl {
     //   backward, levels in reverse: y_C -= L^O^T y_R (or U (V^T y_R)), the actions
     //   in reverse order, the transposed small dense solves.
     // It is captured once into a CUDA graph reading g_in and writing g_out.
-    enum LKind { L_PERM_IN, L_PERM_OUT, L_TRSV, L_TN, L_NN };
+    enum LKind { L_PERM_IN, L_PERM_OUT, L_TRSV, L_TN, L_NN, L_HSOLVE };
     struct Launch { int kind; int count; size_t off; int flag; };
+    HTask* d_hs_all = nullptr;
+    HAct* d_hacts_all = nullptr;
     std::vector<Launch> seq;
     DeviceMem smem_plan;
     T* y_dev = nullptr;
@@ -1537,10 +1758,10 @@ struct EngineT final : EngineImpl {
     struct Act { std::vector<TrsvTask> trsv; std::vector<TnTask> tn; std::vector<NnTask> nn; };
 
     static void push_nn_chunks(std::vector<NnTask>& v, NnTask t) {
-        for (int r0 = 0; r0 < t.nrow; r0 += 64) { NnTask c = t; c.row0 = r0; v.push_back(c); }
+        for (int r0 = 0; r0 < t.nrow; r0 += NN_ROWS) { NnTask c = t; c.row0 = r0; v.push_back(c); }
     }
     static void push_tn_chunks(std::vector<TnTask>& v, const TnTask& t) {
-        for (int t0 = 0; t0 < t.K; t0 += 8) { TnTask c = t; c.t0 = t0; v.push_back(c); }
+        for (int t0 = 0; t0 < t.K; t0 += TN_COLS) { TnTask c = t; c.t0 = t0; v.push_back(c); }
     }
     // vector forms on y (ld 1, one column); yoff / ymap index rows of y
     TnTask vtn(const void* A, int lda, int K, int nrow, const int32_t* ymap, int yoff, T* Z, double alpha = 1.0,
@@ -1563,7 +1784,7 @@ struct EngineT final : EngineImpl {
                 const int b = transpose ? nblk - 1 - bi : bi;
                 const int b0 = b * bs, b1 = std::min(c, b0 + bs);
                 Act a;
-                a.trsv.push_back(TrsvTask{L + b0 + (size_t)b0 * ld, ld, b1 - b0, 1, X + b0, 1, transpose ? 1 : 0});
+                a.trsv.push_back(TrsvTask{inv_block(j, b0), b1 - b0, b1 - b0, 1, X + b0, 1, transpose ? 1 : 0});
                 if (!transpose && b1 < c)
                     push_nn_chunks(a.nn, vnn(L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, (int)(n.c0 + b1),
                                              X + b0, false));
@@ -1578,7 +1799,7 @@ struct EngineT final : EngineImpl {
             if (t.leaf[s]) {
                 Act a;
                 const int sz = t.hi[s] - t.lo[s];
-                a.trsv.push_back(TrsvTask{arena + n.leaf_off[s], sz, sz, 1, X + t.lo[s], 1, transpose ? 1 : 0});
+                a.trsv.push_back(TrsvTask{invs + n.leaf_inv[s], sz, sz, 1, X + t.lo[s], 1, transpose ? 1 : 0});
                 acts.push_back(std::move(a));
                 return;
             }
@@ -1642,19 +1863,40 @@ struct EngineT final : EngineImpl {
                 emit(L_NN, o3, B.nn.size() - o3, 0);
             }
         };
+        // persistent solves: actions and tasks (acts as offsets until upload)
+        std::vector<HAct> HA;
+        std::vector<HTask> HT;
+        auto emit_hsolve = [&](std::vector<int>& nodes, bool transpose, std::vector<std::vector<Act>>& rest) {
+            size_t o = HT.size();
+            int maxc = 0;
+            for (int j : nodes) {
+                const NodeRT& nn = nd[j];
+                if (pick_cw(nn.c) == 0) { rest.emplace_back(); T* zc = zcur; diag_actions(j, transpose, zc, rest.back()); zcur = zc; continue; }
+                const long long first = (long long)HA.size();
+                const double keep = flops;
+                hacts(j, 0, transpose, HA);
+                flops = keep;
+                HT.push_back(HTask{(const HAct*)(intptr_t)first, (long long)HA.size() - first, y_dev + nn.c0, 1, 1, nn.c,
+                                   transpose ? 1 : 0});
+                maxc = std::max(maxc, nn.c);
+            }
+            if (HT.size() > o) seq.push_back(Launch{L_HSOLVE, (int)(HT.size() - o), o, maxc});
+        };
         emit(L_PERM_IN, 0, 1, 0);
         std::vector<std::vector<T*>> ztmp(S.nlevels);
         for (int l = 0; l < S.nlevels; ++l) {
             size_t o = B.trsv.size();
             std::vector<std::vector<Act>> acts;
+            std::vector<int> big;
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 apply_bytes += 2.0 * sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
                 if (!nn.hier && nn.c <= SOLVE_MAX)
-                    B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 1, y_dev + nn.c0, 1, 0});
-                else { acts.emplace_back(); diag_actions(j, false, zcur, acts.back()); }
+                    B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 0});
+                else big.push_back(j);
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
+            emit_hsolve(big, false, acts);
             emit_acts(acts);
             size_t o2 = B.tn.size(), o3 = B.nn.size();
             for (int j : S.level_nodes[l]) {
@@ -1696,28 +1938,32 @@ struct EngineT final : EngineImpl {
             B.nn.insert(B.nn.end(), nnb.begin(), nnb.end());
             emit(L_NN, o3, nnb.size(), 0);
             std::vector<std::vector<Act>> acts;
+            std::vector<int> big;
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 if (!nn.hier && nn.c <= SOLVE_MAX) continue;
-                acts.emplace_back();
-                diag_actions(j, true, zcur, acts.back());
+                big.push_back(j);
             }
+            emit_hsolve(big, true, acts);
             emit_acts(acts);
             size_t o = B.trsv.size();
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 if (!nn.hier && nn.c <= SOLVE_MAX)
-                    B.trsv.push_back(TrsvTask{arena + nn.off, nn.ld, nn.c, 1, y_dev + nn.c0, 1, 1});
+                    B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 1});
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
         }
         emit(L_PERM_OUT, 0, 1, 0);
         if (zcur > tmp_dev + std::max<long long>(tmp_total, 1)) throw Error(RSC_ERR_CUDA, "solve scratch overflow");
+        d_hacts_all = smem_plan.upload(HA, stream);
+        for (auto& h : HT) h.acts = d_hacts_all + (intptr_t)h.acts;
+        d_hs_all = smem_plan.upload(HT, stream);
         d_trsv_all = smem_plan.upload(B.trsv, stream);
         d_tn_all = smem_plan.upload(B.tn, stream);
         d_nn_all = smem_plan.upload(B.nn, stream);
-        for (auto& t : B.tn) apply_flops += 2.0 * t.nrow * std::min(8, t.K - t.t0);
-        for (auto& t : B.nn) apply_flops += 2.0 * std::min(64, t.nrow - t.row0) * t.K;
+        for (auto& t : B.tn) apply_flops += 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0);
+        for (auto& t : B.nn) apply_flops += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K;
         apply_bytes += 4.0 * sizeof(T) * n + 16.0 * n;
         sync_stream();
         // capture the launch list once
@@ -1729,15 +1975,21 @@ struct EngineT final : EngineImpl {
         CK(cudaGraphDestroy(g));
     }
 
-    void issue_apply(cudaStream_t s) {
+    bool no_graph = std::getenv("RSC_NO_GRAPH") != nullptr;   // measurement aid: per-kernel apply profile
+    void issue_apply(cudaStream_t s, bool profiled = false) {
         const long long n = S.n;
+        Profiler off;
+        Profiler& P = profiled ? prof : off;
         for (const Launch& L : seq) {
             switch (L.kind) {
-                case L_PERM_IN: k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(g_in, d_perm, y_dev, n); break;
-                case L_PERM_OUT: k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, g_out, n); break;
-                case L_TRSV: k_trsv<T, 1><<<L.count, 256, 0, s>>>(d_trsv_all + L.off); break;
-                case L_TN: k_tn<T><<<L.count, 256, 0, s>>>(d_tn_all + L.off); break;
-                case L_NN: k_nn<T><<<L.count, 256, 0, s>>>(d_nn_all + L.off); break;
+                case L_PERM_IN: PROF(P, "ap_perm", s, 0, 0, k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(g_in, d_perm, y_dev, n)); break;
+                case L_PERM_OUT: PROF(P, "ap_perm", s, 0, 0, k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, g_out, n)); break;
+                case L_TRSV: PROF(P, "ap_trsv", s, 0, 0, k_trsv<T, 1><<<L.count, 256, 0, s>>>(d_trsv_all + L.off)); break;
+                case L_TN: PROF(P, "ap_tn", s, 0, 0, k_tn1<T><<<L.count, 256, 0, s>>>(d_tn_all + L.off)); break;
+                case L_NN: PROF(P, "ap_nn", s, 0, 0, k_nn<T><<<L.count, NN_ROWS, 0, s>>>(d_nn_all + L.off)); break;
+                case L_HSOLVE:
+                    PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 1><<<L.count, HS_THREADS, hs_smem(L.flag, 1), s>>>(d_hs_all + L.off));
+                    break;
             }
         }
         LAUNCH_CHECK();
@@ -1746,7 +1998,8 @@ struct EngineT final : EngineImpl {
     void apply(const double* d_r, double* d_z, cudaStream_t s) override {
         const long long n = S.n;
         if (d_r != g_in) CK(cudaMemcpyAsync(g_in, d_r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        PROF(prof, "apply", s, apply_flops, apply_bytes, CK(cudaGraphLaunch(graph_exec, s)));
+        if (no_graph) issue_apply(s, true);
+        else PROF(prof, "apply", s, apply_flops, apply_bytes, CK(cudaGraphLaunch(graph_exec, s)));
         launches += (long long)seq.size();
         if (d_z != g_out) CK(cudaMemcpyAsync(d_z, g_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }

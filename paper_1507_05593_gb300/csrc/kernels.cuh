@@ -49,6 +49,14 @@ struct GaussTask { void* G; int m; int row0; uint32_t block_id; uint32_t word3; 
 struct NormTask { const void* X; int ld; int m; int nc; double* out; };
 struct QrTask { void* Y; int m; int b; int row0; double* G; double* Rinv; int* status; double coef; };
 struct CopyTask { const void* src; long long ssr, ssc; void* dst; long long dsr, dsc; int m, nc; };
+// One action of a hierarchical (or blocked dense) diagonal solve, rows local to the block:
+//   HA_TRSV   X[o0:o0+no] <- L^{-1} X[..] or L^{-T} X[..]   (A1 = row-major L^{-1}, no <= SOLVE_MAX)
+//   HA_LR     X[o0:o0+no] -= A2 (A1^T X[i0:i0+ni])          (A1 ni x K, A2 no x K; low rank)
+//   HA_GEMV   X[o0:o0+no] -= A2 X[i0:i0+K]                  (A2 no x K)
+//   HA_GEMVT  X[o0:o0+no] -= A1^T X[i0:i0+ni]               (A1 ni x no)
+enum { HA_TRSV = 0, HA_LR = 1, HA_GEMV = 2, HA_GEMVT = 3 };
+struct HAct { int type, i0, ni, o0, no, K; const void* A1; int lda1; const void* A2; int lda2; };
+struct HTask { const HAct* acts; long long nact; void* X; int ldx; int N; int c; int transpose; };
 
 // ------------------------------------------------------------------ helpers
 template <class T> __device__ __forceinline__ void atomic_add(T* p, T v) { atomicAdd(p, v); }
@@ -260,87 +268,134 @@ __global__ void __launch_bounds__(256) k_push(const PushTask* __restrict__ tasks
 }
 
 // ------------------------------------------------------------------ thin products (N columns, chunks of 16)
-// One warp per (task, column t of A); lanes stride over the task's rows.
+// One CTA per (task, 32-column tile of A, 16-column chunk of Y).  Lane l owns column
+// t0 + l; the 8 warps take contiguous row ranges (so each lane's column of A is read
+// line by line through L1) and every Y row is read once per 32 columns; the warps'
+// partial sums are reduced in shared memory in a fixed order.
+constexpr int TN_COLS = 32;
 template <class T>
 __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
+    __shared__ T red[8][16][33];
     const TnTask tk = tasks[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = blockIdx.y * 16;
     const int nc = min(16, tk.N - c0);
-    const int t = tk.t0 + warp;
-    if (nc <= 0 || t >= tk.K) return;
-    const T* A = (const T*)tk.A;
-    const T* Y = (const T*)tk.Y;
+    if (nc <= 0) return;
+    const int t = tk.t0 + lane;
+    const bool tok = t < tk.K;
+    const T* A = (const T*)tk.A + (size_t)(tok ? t : 0) * tk.lda;
+    const T* Y = (const T*)tk.Y + c0;
     T acc[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = T(0);
-    for (int i = lane; i < tk.nrow; i += 32) {
+    for (int q = 0; q < 16; ++q) acc[q] = T(0);
+    const int chunk = (tk.nrow + 7) >> 3;
+    const int i0 = warp * chunk, i1 = min(tk.nrow, i0 + chunk);
+    for (int i = i0; i < i1; ++i) {
         const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
         const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
-        const T a = A[ar + (size_t)t * tk.lda];
-        const T* y = Y + (size_t)yr * tk.ldy + c0;
+        const T a = tok ? A[ar] : T(0);
+        const T* y = Y + (size_t)yr * tk.ldy;
+        if (nc == 16) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-            if (c < nc) acc[c] = fma(a, y[c], acc[c]);
+            for (int q = 0; q < 16; ++q) acc[q] = fma(a, y[q], acc[q]);
+        } else if (nc == 1) {
+            acc[0] = fma(a, y[0], acc[0]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (q < nc) acc[q] = fma(a, y[q], acc[q]);
+        }
     }
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        T v = acc[c];
+    for (int q = 0; q < 16; ++q) red[warp][q][lane] = acc[q];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
+        const int q = e >> 5, l = e & 31;
+        if (q >= nc || tk.t0 + l >= tk.K) continue;
+        T s = T(0);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[c] = v;
-    }
-    if (lane < nc) {
-        T v = acc[0];
-#pragma unroll
-        for (int c = 1; c < 16; ++c)
-            if (lane == c) v = acc[c];
-        T* z = (T*)tk.Z + (size_t)t * tk.ldz + c0 + lane;
-        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * v : (T)tk.alpha * v;
+        for (int w = 0; w < 8; ++w) s += red[w][q][l];
+        T* z = (T*)tk.Z + (size_t)(tk.t0 + l) * tk.ldz + c0 + q;
+        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * s : (T)tk.alpha * s;
     }
 }
 
-// One CTA per (task, 64-row chunk, 16-column chunk); 64 rows x 4 column groups of 4.
+// Vector form of k_tn (N = 1): one CTA per (task, 32-column tile), a warp per column,
+// lanes down the rows (coalesced column reads of A).
 template <class T>
-__global__ void __launch_bounds__(256) k_nn(const NnTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
+    const TnTask tk = tasks[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T* Y = (const T*)tk.Y;
+    for (int tt = warp; tt < TN_COLS; tt += 8) {
+        const int t = tk.t0 + tt;
+        if (t >= tk.K) break;
+        const T* A = (const T*)tk.A + (size_t)t * tk.lda;
+        T acc = T(0);
+#pragma unroll 4
+        for (int i = lane; i < tk.nrow; i += 32) {
+            const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
+            const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+            acc = fma(A[ar], Y[(size_t)yr * tk.ldy], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            T* z = (T*)tk.Z + (size_t)t * tk.ldz;
+            *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc : (T)tk.alpha * acc;
+        }
+    }
+}
+
+// One CTA of 128 threads per (task, 128-row chunk, 16-column chunk); a thread owns one
+// row and its 16 outputs, so each element of A is loaded once.
+constexpr int NN_ROWS = 128;
+template <class T>
+__global__ void __launch_bounds__(NN_ROWS) k_nn(const NnTask* __restrict__ tasks) {
     __shared__ T Zs[64][17];
     const NnTask tk = tasks[blockIdx.x];
     const int c0 = blockIdx.y * 16;
     const int nc = min(16, tk.N - c0);
     if (nc <= 0) return;
-    const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
-    const int i = tk.row0 + r;
+    const int i = tk.row0 + threadIdx.x;
     const bool active = i < tk.nrow;
     const T* A = (const T*)tk.A;
     const T* Z = (const T*)tk.Z;
     int ar = 0;
     if (active) ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    T acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = T(0);
     for (int l0 = 0; l0 < tk.K; l0 += 64) {
         const int lk = min(64, tk.K - l0);
         __syncthreads();
         for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
-            int l = e >> 4, c = e & 15;
+            const int l = e >> 4, c = e & 15;
             Zs[l][c] = (l < lk && c < nc) ? Z[(size_t)(l0 + l) * tk.ldz + c0 + c] : T(0);
         }
         __syncthreads();
         if (active) {
-            for (int l = 0; l < lk; ++l) {
-                const T a = A[ar + (size_t)(l0 + l) * tk.lda];
+            if (nc == 1) {
+                for (int l = 0; l < lk; ++l) acc[0] = fma(A[ar + (size_t)(l0 + l) * tk.lda], Zs[l][0], acc[0]);
+            } else {
+#pragma unroll 4
+                for (int l = 0; l < lk; ++l) {
+                    const T a = A[ar + (size_t)(l0 + l) * tk.lda];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[c] = fma(a, Zs[l][4 * g + c], acc[c]);
+                    for (int q = 0; q < 16; ++q) acc[q] = fma(a, Zs[l][q], acc[q]);
+                }
             }
         }
     }
     if (!active) return;
     const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
-    T* y = (T*)tk.Y + (size_t)yr * tk.ldy + c0 + 4 * g;
+    T* y = (T*)tk.Y + (size_t)yr * tk.ldy + c0;
     const T alpha = (T)tk.alpha;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (4 * g + c >= nc) break;
-        if (tk.atomic) atomic_add(y + c, alpha * acc[c]);
-        else y[c] += alpha * acc[c];
+    for (int q = 0; q < 16; ++q) {
+        if (q >= nc) break;
+        if (tk.atomic) atomic_add(y + q, alpha * acc[q]);
+        else y[q] += alpha * acc[q];
     }
 }
 
@@ -365,20 +420,21 @@ __global__ void k_csr_mm(const CsrTask* __restrict__ tasks) {
 // Blocked by 32 rows: a warp solves each column of the 32 x 32 diagonal tile with
 // shuffles, then the CTA updates the remaining rows with the solved block.
 template <class T, int CW>
-__global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(256) k_trsv_subst(const TrsvTask* __restrict__ tasks) {
     __shared__ T Xs[SOLVE_MAX][CW + 1];
     __shared__ T Lt[32][33];
     const TrsvTask tk = tasks[blockIdx.x];
     const T* L = (const T*)tk.L;
     T* X = (T*)tk.X;
-    const int c = tk.c, ld = tk.ld, transpose = tk.transpose;
+    const int c = tk.c, ld = tk.ld, transpose = tk.transpose == 1;
     const int c0 = blockIdx.y * CW;
     const int nc = min(CW, tk.N - c0);
     if (nc <= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < c * CW; e += blockDim.x) {
         int i = e / CW, q = e % CW;
-        Xs[i][q] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
+        if (tk.transpose == 2) Xs[i][q] = (q < nc && i == c0 + q) ? T(1) : T(0);   // invert: X = L^{-1} I
+        else Xs[i][q] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
     }
     const int nb = (c + 31) >> 5;
     constexpr int G = CW >= 4 ? 4 : CW;          // columns per thread in the update
@@ -434,6 +490,178 @@ __global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks
     }
 }
 
+// ------------------------------------------------------------------ triangular solves by explicit inverse
+// Xb (c x CW rows in shared memory) <- Linv Xb or Linv^T Xb, Linv the row-major inverse
+// of a lower-triangular diagonal block (c <= SOLVE_MAX); the result goes through Zs.
+// Forward: a warp per output row, lanes along the row (coalesced); transposed: a
+// thread per output, reading one row of Linv per step (coalesced).  Ends synced.
+template <class T, int CW>
+__device__ __forceinline__ void trmv_inv(const T* __restrict__ Li, int c, T* Xb, T* Zs, bool transpose) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (!transpose) {
+        for (int i = warp; i < c; i += blockDim.x >> 5) {
+            T acc[CW];
+#pragma unroll
+            for (int q = 0; q < CW; ++q) acc[q] = T(0);
+            const T* row = Li + (size_t)i * c;
+            for (int kk = lane; kk <= i; kk += 32) {
+                const T v = row[kk];
+#pragma unroll
+                for (int q = 0; q < CW; ++q) acc[q] = fma(v, Xb[(size_t)kk * CW + q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < CW; ++q) {
+                T v = acc[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                acc[q] = v;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < CW; ++q) Zs[(size_t)i * CW + q] = acc[q];
+            }
+        }
+    } else {
+        for (int i = tid; i < c; i += blockDim.x) {
+            T acc[CW];
+#pragma unroll
+            for (int q = 0; q < CW; ++q) acc[q] = T(0);
+            for (int kk = i; kk < c; ++kk) {
+                const T v = Li[(size_t)kk * c + i];
+#pragma unroll
+                for (int q = 0; q < CW; ++q) acc[q] = fma(v, Xb[(size_t)kk * CW + q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < CW; ++q) Zs[(size_t)i * CW + q] = acc[q];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < c * CW; e += blockDim.x) Xb[e] = Zs[e];
+    __syncthreads();
+}
+
+// X (c x N, row-major) <- Linv X or Linv^T X for a batch of small diagonal blocks
+// (TrsvTask.L = row-major inverse), one CTA per (task, CW-column chunk).
+template <class T, int CW>
+__global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks) {
+    __shared__ T Xs[SOLVE_MAX * CW];
+    __shared__ T Zs[SOLVE_MAX * CW];
+    const TrsvTask tk = tasks[blockIdx.x];
+    const int c0 = blockIdx.y * CW;
+    const int nc = min(CW, tk.N - c0);
+    if (nc <= 0) return;
+    T* X = (T*)tk.X;
+    for (int e = threadIdx.x; e < tk.c * CW; e += blockDim.x) {
+        const int i = e / CW, q = e % CW;
+        Xs[e] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
+    }
+    __syncthreads();
+    trmv_inv<T, CW>((const T*)tk.L, tk.c, Xs, Zs, tk.transpose == 1);
+    for (int e = threadIdx.x; e < tk.c * CW; e += blockDim.x) {
+        const int i = e / CW, q = e % CW;
+        if (q < nc) X[(size_t)i * tk.ldx + c0 + q] = Xs[e];
+    }
+}
+
+// ------------------------------------------------------------------ persistent hierarchical solve
+// One CTA per (task, CW-column chunk) walks a diagonal block's whole action list
+// (Alg. 4 in order) with the right-hand side block (c x CW) staged in dynamic
+// shared memory; the low-rank products go through a shared Z of 512 x CW.
+constexpr int HS_ZROWS = 512;
+constexpr int HS_THREADS = 512;
+template <class T, int CW>
+__global__ void __launch_bounds__(HS_THREADS) k_hsolve(const HTask* __restrict__ tasks) {
+    extern __shared__ __align__(16) unsigned char hs_smem[];
+    const HTask tk = tasks[blockIdx.x];
+    const int c0 = blockIdx.y * CW;
+    const int nc = min(CW, tk.N - c0);
+    if (nc <= 0) return;
+    T* Xs = (T*)hs_smem;                       // c x CW
+    T* Zs = Xs + (size_t)tk.c * CW;            // HS_ZROWS x CW
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* X = (T*)tk.X;
+    for (int e = tid; e < tk.c * CW; e += blockDim.x) {
+        const int i = e / CW, q = e % CW;
+        Xs[e] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
+    }
+    __syncthreads();
+    for (long long ai = 0; ai < tk.nact; ++ai) {
+        const HAct a = tk.acts[ai];
+        if (a.type == HA_TRSV) {
+            trmv_inv<T, CW>((const T*)a.A1, a.no, Xs + (size_t)a.o0 * CW, Zs, tk.transpose != 0);
+        } else if (a.type == HA_LR || a.type == HA_GEMVT) {
+            // Zs[t] = A1[:, t]^T X[i0:i0+ni] (LR) or X[o0 + t] -= A1[:, t]^T X[i0:i0+ni] (GEMVT)
+            const T* A1 = (const T*)a.A1;
+            const int K = a.type == HA_LR ? a.K : a.no;
+            for (int t0 = 0; t0 < K; t0 += HS_ZROWS) {
+                const int kt = min(HS_ZROWS, K - t0);
+                for (int t = warp; t < kt; t += (int)(blockDim.x >> 5)) {
+                    T acc[CW];
+#pragma unroll
+                    for (int q = 0; q < CW; ++q) acc[q] = T(0);
+                    const T* col = A1 + (size_t)(t0 + t) * a.lda1;
+                    for (int i = lane; i < a.ni; i += 32) {
+                        const T v = col[i];
+#pragma unroll
+                        for (int q = 0; q < CW; ++q) acc[q] = fma(v, Xs[(size_t)(a.i0 + i) * CW + q], acc[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < CW; ++q) {
+                        T v = acc[q];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        acc[q] = v;
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int q = 0; q < CW; ++q) {
+                            if (a.type == HA_LR) Zs[(size_t)t * CW + q] = acc[q];
+                            else Xs[(size_t)(a.o0 + t0 + t) * CW + q] -= acc[q];
+                        }
+                    }
+                }
+                __syncthreads();
+                if (a.type == HA_LR) {
+                    // X[o0:o0+no] -= A2[:, t0:t0+kt] Zs
+                    const T* A2 = (const T*)a.A2;
+                    for (int i = tid; i < a.no; i += blockDim.x) {
+                        T acc[CW];
+#pragma unroll
+                        for (int q = 0; q < CW; ++q) acc[q] = T(0);
+                        for (int t = 0; t < kt; ++t) {
+                            const T v = A2[i + (size_t)(t0 + t) * a.lda2];
+#pragma unroll
+                            for (int q = 0; q < CW; ++q) acc[q] = fma(v, Zs[(size_t)t * CW + q], acc[q]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < CW; ++q) Xs[(size_t)(a.o0 + i) * CW + q] -= acc[q];
+                    }
+                    __syncthreads();
+                }
+            }
+        } else {   // HA_GEMV: X[o0:o0+no] -= A2 X[i0:i0+K]
+            const T* A2 = (const T*)a.A2;
+            for (int i = tid; i < a.no; i += blockDim.x) {
+                T acc[CW];
+#pragma unroll
+                for (int q = 0; q < CW; ++q) acc[q] = T(0);
+                for (int t = 0; t < a.K; ++t) {
+                    const T v = A2[i + (size_t)t * a.lda2];
+#pragma unroll
+                    for (int q = 0; q < CW; ++q) acc[q] = fma(v, Xs[(size_t)(a.i0 + t) * CW + q], acc[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < CW; ++q) Xs[(size_t)(a.o0 + i) * CW + q] -= acc[q];
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < tk.c * CW; e += blockDim.x) {
+        const int i = e / CW, q = e % CW;
+        if (q < nc) X[(size_t)i * tk.ldx + c0 + q] = Xs[e];
+    }
+}
+
 // ------------------------------------------------------------------ random test matrices
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, key bumped between rounds.
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
@@ -458,11 +686,19 @@ __global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long 
     philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
     const double two32 = 2.3283064365386963e-10;   // 2^-32
     const double twopi = 6.283185307179586;
-    const double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
-    const double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
     T* G = (T*)tk.G;
-    G[(size_t)i * 16 + 2 * cp] = (T)z0;
-    G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
+    if (sizeof(T) == 8) {
+        const double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
+        const double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
+        G[(size_t)i * 16 + 2 * cp] = (T)z0;
+        G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
+    } else {   // FP32 form: single-precision transforms of the same Philox words
+        const float f32 = 2.3283064365386963e-10f, tp = 6.2831853071795865f;
+        const float z0 = sqrtf(-2.0f * logf(((float)c[0] + 1.0f) * f32)) * cosf(tp * ((float)c[1] * f32));
+        const float z1 = sqrtf(-2.0f * logf(((float)c[2] + 1.0f) * f32)) * cosf(tp * ((float)c[3] * f32));
+        G[(size_t)i * 16 + 2 * cp] = (T)z0;
+        G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
+    }
 }
 
 // ------------------------------------------------------------------ small reductions / orthonormalisation
