@@ -147,6 +147,29 @@ rsc_status rsc_solve_device(rsc_handle* h, const double* d_b, double* d_x, doubl
 /* One application of the preconditioner: d_z = P (L L^T)^{-1} P^T d_r (device FP64, n). */
 rsc_status rsc_apply_preconditioner_device(rsc_handle* h, const double* d_r, double* d_z, void* cuda_stream);
 
+/*
+ * Allocation-free variant of rsc_apply_preconditioner_device (the paper has no
+ * counterpart; this is an interface convenience).  For callers that cannot call
+ * cudaMalloc while they apply the preconditioner: frameworks whose device memory
+ * is owned by their own allocator or held to a fixed budget, and latency-bound
+ * loops that cannot afford the implicit device synchronisation of cudaMalloc and
+ * cudaFree.  It computes the same d_z = P (L L^T)^{-1} P^T d_r and allocates no
+ * device memory: its work vector, low-rank temporaries and task records live in
+ * one file-scope static device array of 64 MiB, which every GPU that loads the
+ * library holds until the process exits.
+ *  - The first call on a device looks up the array's address (cudaGetSymbolAddress,
+ *    with that device current); the first call after each rsc_factor (or with
+ *    another handle) copies its task records into the array on cuda_stream.  Make
+ *    such a first call before any stream capture.
+ *  - Every call, from every handle, shares the one array and it keeps the last
+ *    call's contents; calls whose GPU work overlaps (other streams, other host
+ *    threads) race with each other.  The call synchronises cuda_stream on return.
+ *  - Returns RSC_ERR_INVALID_ARG when the problem needs more than the 64 MiB
+ *    (about n * sizeof(factor element) plus the task records), RSC_ERR_STATE
+ *    before rsc_factor.
+ */
+rsc_status rsc_apply_preconditioner_device_noalloc(rsc_handle* h, const double* d_r, double* d_z, void* cuda_stream);
+
 /* Per-supernode results of the last factor.  info[8] = {c_j, |R_j|, compressed,
  * rank of L^O_j (0 if uncompressed), hierarchical diagonal, blocks in L^D_j,
  * level, kind}. */

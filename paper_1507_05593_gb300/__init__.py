@@ -61,6 +61,7 @@ _SIGS = {
     "rsc_solve_device": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_double), _P]),
     "rsc_apply_preconditioner_device": (C.c_int, [_P, _P, _P, _P]),
+    "rsc_apply_preconditioner_device_noalloc": (C.c_int, [_P, _P, _P, _P]),
     "rsc_get_supernode_info": (C.c_int, [_P, C.c_int32, _P]),
     "rsc_get_supernode_blocks": (C.c_int, [_P, C.c_int32, _P, _P]),
     "rsc_get_stats": (C.c_int, [_P, C.POINTER(rsc_stats_t)]),
@@ -192,6 +193,13 @@ def rsc_apply_preconditioner_device(h: Handle, d_r, d_z, stream=None) -> None:
     pz = d_z.data_ptr() if hasattr(d_z, "data_ptr") else int(d_z)
     s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().rsc_apply_preconditioner_device(h.ptr, C.c_void_p(pr), C.c_void_p(pz), s), h.ptr)
+
+
+def rsc_apply_preconditioner_device_noalloc(h: Handle, d_r, d_z, stream=None) -> None:
+    pr = d_r.data_ptr() if hasattr(d_r, "data_ptr") else int(d_r)
+    pz = d_z.data_ptr() if hasattr(d_z, "data_ptr") else int(d_z)
+    s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().rsc_apply_preconditioner_device_noalloc(h.ptr, C.c_void_p(pr), C.c_void_p(pz), s), h.ptr)
 
 
 def rsc_get_supernode_info(h: Handle, j: int) -> dict:

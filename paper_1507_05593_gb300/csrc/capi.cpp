@@ -163,6 +163,15 @@ rsc_status rsc_apply_preconditioner_device(rsc_handle* h, const double* d_r, dou
     });
 }
 
+rsc_status rsc_apply_preconditioner_device_noalloc(rsc_handle* h, const double* d_r, double* d_z, void* stream) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    if (!d_r || !d_z) return fail(h, RSC_ERR_INVALID_ARG, "d_r and d_z are required");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng || !h->eng->factored()) return fail(h, RSC_ERR_STATE, "apply before rsc_factor");
+        return h->eng->apply_precond_noalloc(d_r, d_z, stream);
+    });
+}
+
 rsc_status rsc_get_supernode_info(const rsc_handle* h, int32_t j, int32_t* info) {
     if (!h || !info) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL argument");
     if (j < 0 || j >= h->sym.M) return fail(const_cast<rsc_handle*>(h), RSC_ERR_INVALID_ARG, "j out of range");

@@ -21,6 +21,8 @@
 #include <cstring>
 #include <cstdio>
 #include <map>
+#include <atomic>
+#include <mutex>
 #include <functional>
 #include <numeric>
 
@@ -162,6 +164,11 @@ struct EngineImpl {
     virtual void node_info(int j, int32_t* info) const = 0;
     virtual rsc_status node_blocks(int j, double* LD, double* LO) = 0;
     virtual void stats(rsc_stats_t* out) const = 0;
+    virtual long long generation() const = 0;
+    long long uid = 0;    // unique per engine (never reused, unlike its address)
+    virtual rsc_status apply_noalloc(const double* d_r, double* d_z, cudaStream_t s, char* base, size_t cap,
+                                     bool load) = 0;
+    virtual bool noalloc_ready() const = 0;
     // PCG state shared by every precision
     rsc_status pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
                    const double* d_b, double* d_x, double rtol, int max_iter, int* iters, double* relres,
@@ -1721,6 +1728,7 @@ struct EngineT final : EngineImpl {
         factor_seconds = ms * 1e-3;
         prof.flush();
         is_factored = true;
+        ++factor_gen;
         build_solve_plan();
         return RSC_OK;
     }
@@ -2004,6 +2012,182 @@ struct EngineT final : EngineImpl {
         if (d_z != g_out) CK(cudaMemcpyAsync(d_z, g_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
 
+    // ---------------------------------------------------------------- allocation-free apply
+    // The same level-by-level launch list as build_solve_plan (persistent solves for
+    // hierarchical and large dense blocks), but every buffer it needs -- the permuted
+    // work vector, the low-rank temporaries and the task records -- lives in the
+    // caller-provided static device region `base` (cap bytes).  Loading the records
+    // copies host-built vectors into that region on the caller's stream; nothing is
+    // allocated on the device.
+    long long factor_gen = 0;
+    long long generation() const override { return factor_gen; }
+    std::vector<Launch> na_seq;
+    T* na_y = nullptr;
+    const TrsvTask* na_trsv = nullptr;
+    const TnTask* na_tn = nullptr;
+    const NnTask* na_nn = nullptr;
+    const HTask* na_hs = nullptr;
+
+    rsc_status load_noalloc(char* base, size_t cap, cudaStream_t s) {
+        auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+        const long long n = S.n;
+        long long tmp_total = 0;
+        for (int j = 0; j < S.M; ++j) tmp_total += nd[j].compressed ? nd[j].rank : 0;
+        size_t off = 0;
+        T* y = (T*)(base + off);
+        off = align(off + sizeof(T) * n);
+        T* tmp = (T*)(base + off);
+        off = align(off + sizeof(T) * std::max<long long>(tmp_total, 1));
+        if (off > cap)
+            throw Error(RSC_ERR_INVALID_ARG, "problem needs " + std::to_string(off) +
+                                                 " bytes of static scratch for its vectors; the library holds " +
+                                                 std::to_string(cap));
+        std::vector<HAct> HA;
+        std::vector<HTask> HT;
+        std::vector<TrsvTask> TV;
+        std::vector<TnTask> TN;
+        std::vector<NnTask> NN;
+        std::vector<Launch> q;
+        T* zc = tmp;
+        auto emit = [&](int kind, size_t o, size_t cnt, int flag) {
+            if (cnt) q.push_back(Launch{kind, (int)cnt, o, flag});
+        };
+        auto tn_chunks = [&](const TnTask& t) {
+            for (int t0 = 0; t0 < t.K; t0 += TN_COLS) { TnTask c = t; c.t0 = t0; TN.push_back(c); }
+        };
+        auto nn_chunks = [&](const NnTask& t, std::vector<NnTask>& dst) {
+            for (int r0 = 0; r0 < t.nrow; r0 += NN_ROWS) { NnTask c = t; c.row0 = r0; dst.push_back(c); }
+        };
+        auto hsolve = [&](const std::vector<int>& nodes, bool tr) {
+            const size_t o = HT.size();
+            int maxc = 0;
+            for (int j : nodes) {
+                if (pick_cw(nd[j].c) == 0)
+                    throw Error(RSC_ERR_INVALID_ARG, "a diagonal block is too large for the allocation-free apply");
+                const long long first = (long long)HA.size();
+                const double keep = flops;
+                hacts(j, 0, tr, HA);
+                flops = keep;
+                HT.push_back(HTask{(const HAct*)(intptr_t)first, (long long)HA.size() - first, y + nd[j].c0, 1, 1,
+                                   nd[j].c, tr ? 1 : 0});
+                maxc = std::max(maxc, nd[j].c);
+            }
+            emit(L_HSOLVE, o, HT.size() - o, maxc);
+        };
+        std::vector<std::vector<T*>> zt(S.nlevels);
+        for (int l = 0; l < S.nlevels; ++l) {
+            size_t o = TV.size();
+            std::vector<int> big;
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (!nn.hier && nn.c <= SOLVE_MAX) TV.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y + nn.c0, 1, 0});
+                else big.push_back(j);
+            }
+            emit(L_TRSV, o, TV.size() - o, 0);
+            hsolve(big, false);
+            const size_t o2 = TN.size(), o3 = NN.size();
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (nn.r == 0) continue;
+                const int32_t* Rj = d_rows + S.rows_ptr[j];
+                if (!nn.compressed) {
+                    nn_chunks(nn_task(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, nullptr, 0, Rj, 0, y + nn.c0, 1, y, 1, 1,
+                                      -1.0, true), NN);
+                } else if (nn.rank) {
+                    T* t = zc;
+                    zc += nn.rank;
+                    zt[l].push_back(t);
+                    tn_chunks(tn_task(nn.U, nn.c, nn.rank, nn.c, nullptr, 0, nullptr, (int)nn.c0, y, 1, t, 1, 1));
+                    nn_chunks(nn_task(nn.V, nn.r, nn.rank, nn.r, nullptr, 0, Rj, 0, t, 1, y, 1, 1, -1.0, true), NN);
+                }
+            }
+            emit(L_TN, o2, TN.size() - o2, 0);
+            emit(L_NN, o3, NN.size() - o3, 0);
+        }
+        for (int l = S.nlevels - 1; l >= 0; --l) {
+            const size_t o2 = TN.size();
+            size_t zi = 0;
+            std::vector<NnTask> nb;
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (nn.r == 0) continue;
+                const int32_t* Rj = d_rows + S.rows_ptr[j];
+                if (!nn.compressed) {
+                    tn_chunks(tn_task(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, nullptr, 0, Rj, 0, y, 1, y + nn.c0, 1, 1,
+                                      -1.0, 1.0));
+                } else if (nn.rank) {
+                    T* t = zt[l][zi++];
+                    tn_chunks(tn_task(nn.V, nn.r, nn.rank, nn.r, nullptr, 0, Rj, 0, y, 1, t, 1, 1));
+                    nn_chunks(nn_task(nn.U, nn.c, nn.rank, nn.c, nullptr, 0, nullptr, (int)nn.c0, t, 1, y, 1, 1, -1.0,
+                                      false), nb);
+                }
+            }
+            emit(L_TN, o2, TN.size() - o2, 0);
+            const size_t o3 = NN.size();
+            NN.insert(NN.end(), nb.begin(), nb.end());
+            emit(L_NN, o3, nb.size(), 0);
+            std::vector<int> big;
+            for (int j : S.level_nodes[l])
+                if (nd[j].hier || nd[j].c > SOLVE_MAX) big.push_back(j);
+            hsolve(big, true);
+            const size_t o = TV.size();
+            for (int j : S.level_nodes[l]) {
+                const NodeRT& nn = nd[j];
+                if (!nn.hier && nn.c <= SOLVE_MAX) TV.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y + nn.c0, 1, 1});
+            }
+            emit(L_TRSV, o, TV.size() - o, 0);
+        }
+        const size_t ha = off; off = align(off + sizeof(HAct) * HA.size());
+        const size_t hs = off; off = align(off + sizeof(HTask) * HT.size());
+        const size_t tv = off; off = align(off + sizeof(TrsvTask) * TV.size());
+        const size_t tn = off; off = align(off + sizeof(TnTask) * TN.size());
+        const size_t nnq = off; off = align(off + sizeof(NnTask) * NN.size());
+        if (off > cap)
+            throw Error(RSC_ERR_INVALID_ARG, "problem needs " + std::to_string(off) +
+                                                 " bytes of static scratch; the library holds " + std::to_string(cap));
+        for (auto& h : HT) h.acts = (const HAct*)(base + ha) + (intptr_t)h.acts;
+        auto put = [&](size_t o, const void* src, size_t bytes) {
+            if (bytes) CK(cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s));
+        };
+        put(ha, HA.data(), sizeof(HAct) * HA.size());
+        put(hs, HT.data(), sizeof(HTask) * HT.size());
+        put(tv, TV.data(), sizeof(TrsvTask) * TV.size());
+        put(tn, TN.data(), sizeof(TnTask) * TN.size());
+        put(nnq, NN.data(), sizeof(NnTask) * NN.size());
+        na_seq = std::move(q);
+        na_y = y;
+        na_hs = (const HTask*)(base + hs);
+        na_trsv = (const TrsvTask*)(base + tv);
+        na_tn = (const TnTask*)(base + tn);
+        na_nn = (const NnTask*)(base + nnq);
+        return RSC_OK;
+    }
+
+    long long na_loaded_gen = -1;
+    bool noalloc_ready() const override { return na_y != nullptr && na_loaded_gen == factor_gen; }
+    rsc_status apply_noalloc(const double* d_r, double* d_z, cudaStream_t s, char* base, size_t cap,
+                             bool load) override {
+        if (load) {
+            na_y = nullptr;
+            load_noalloc(base, cap, s);
+            na_loaded_gen = factor_gen;
+        }
+        const long long n = S.n;
+        k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(d_r, d_perm, na_y, n);
+        for (const Launch& L : na_seq) {
+            switch (L.kind) {
+                case L_TRSV: k_trsv<T, 1><<<L.count, 256, 0, s>>>(na_trsv + L.off); break;
+                case L_TN: k_tn1<T><<<L.count, 256, 0, s>>>(na_tn + L.off); break;
+                case L_NN: k_nn<T><<<L.count, NN_ROWS, 0, s>>>(na_nn + L.off); break;
+                case L_HSOLVE: k_hsolve<T, 1><<<L.count, HS_THREADS, hs_smem(L.flag, 1), s>>>(na_hs + L.off); break;
+                default: break;
+            }
+        }
+        k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(na_y, d_perm, d_z, n);
+        LAUNCH_CHECK();
+        return RSC_OK;
+    }
+
     // ---------------------------------------------------------------- introspection
     void node_info(int j, int32_t* info) const override {
         const NodeRT& n = nd[j];
@@ -2117,6 +2301,21 @@ __global__ void k_strided_copy(const T* __restrict__ src, long long ssr, long lo
     }
 }
 
+// ------------------------------------------------------------------ static scratch of the allocation-free apply
+// A fixed device region for rsc_apply_preconditioner_device_noalloc: every GPU that
+// loads this library holds these 64 MiB until the process exits.  Host code must not
+// use the symbol as an address: its device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_na_mu;
+std::map<int, char*> g_na_addr;                                   // device -> address of the region
+std::map<int, std::pair<long long, long long>> g_na_loaded;       // device -> (engine uid, factor generation)
+std::atomic<long long> g_engine_uid{0};
+}  // namespace
+
 // ------------------------------------------------------------------ Engine facade
 Engine::Engine(const Symbolic& S, const rsc_options& o) {
     int ndev = 0;
@@ -2124,6 +2323,7 @@ Engine::Engine(const Symbolic& S, const rsc_options& o) {
     if (e != cudaSuccess || ndev == 0) throw Error(RSC_ERR_CUDA, "no CUDA device available");
     if (o.precision == RSC_PREC_FP64) impl_.reset(new EngineT<double>(S, o));
     else impl_.reset(new EngineT<float>(S, o));
+    impl_->uid = ++g_engine_uid;
 }
 Engine::~Engine() = default;
 rsc_status Engine::factor(const double* val, double tol) { return impl_->factor(val, tol); }
@@ -2156,6 +2356,28 @@ rsc_status Engine::solve_device(const std::vector<int64_t>& rp, const std::vecto
     CK(cudaStreamSynchronize(s));
     return st;
 }
+rsc_status Engine::apply_precond_noalloc(const double* d_r, double* d_z, void* stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    auto it = g_na_addr.find(dev);
+    if (it == g_na_addr.end()) {
+        char* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        if (e != cudaSuccess) throw Error(RSC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        it = g_na_addr.emplace(dev, p).first;
+    }
+    const std::pair<long long, long long> mine{impl_->uid, impl_->generation()};
+    auto ld = g_na_loaded.find(dev);
+    const bool load = ld == g_na_loaded.end() || ld->second != mine || !impl_->noalloc_ready();
+    if (load) g_na_loaded.erase(dev);
+    rsc_status st = impl_->apply_noalloc(d_r, d_z, s, it->second, NOALLOC_SCRATCH_BYTES, load);
+    if (load) g_na_loaded[dev] = mine;
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
 rsc_status Engine::apply_precond(const double* d_r, double* d_z, void* stream) {
     cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
     impl_->apply(d_r, d_z, s);
