@@ -1388,7 +1388,7 @@ struct EngineT final : EngineImpl {
         QrTask* d2 = (QrTask*)upload_tmp(sTask, qt);
         QrTask* d3 = (QrTask*)upload_tmp(sTask, q128);
         k_gram<T><<<(unsigned)q256.size(), 256, 0, stream>>>(d1);
-        k_chol_small<<<cdiv((long long)qt.size(), 32), 32, 0, stream>>>(d2, (int)qt.size());
+        k_chol_small<<<(unsigned)qt.size(), 32, 0, stream>>>(d2, (int)qt.size());
         k_apply_rinv<T><<<(unsigned)q128.size(), 128, 0, stream>>>(d3);
         launches += 3;
         LAUNCH_CHECK();

@@ -290,9 +290,15 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     for (int q = 0; q < 16; ++q) acc[q] = T(0);
     const int chunk = (tk.nrow + 7) >> 3;
     const int i0 = warp * chunk, i1 = min(tk.nrow, i0 + chunk);
-    for (int i = i0; i < i1; ++i) {
-        const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
-        const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+    for (int ib = i0; ib < i1; ib += 32) {
+      const int nb = min(32, i1 - ib);
+      const int my = ib + lane;
+      const int ar_l = my < i1 ? (tk.amap ? tk.amap[my] : my) + tk.aoff : 0;
+      const int yr_l = my < i1 ? (tk.ymap ? tk.ymap[my] : my) + tk.yoff : 0;
+#pragma unroll 4
+      for (int r = 0; r < nb; ++r) {
+        const int ar = __shfl_sync(0xffffffffu, ar_l, r);
+        const int yr = __shfl_sync(0xffffffffu, yr_l, r);
         const T a = tok ? A[ar] : T(0);
         const T* y = Y + (size_t)yr * tk.ldy;
         if (nc == 16) {
@@ -305,6 +311,7 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
             for (int q = 0; q < 16; ++q)
                 if (q < nc) acc[q] = fma(a, y[q], acc[q]);
         }
+      }
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) red[warp][q][lane] = acc[q];
@@ -748,40 +755,51 @@ __global__ void k_gram(const QrTask* __restrict__ tasks) {
 // positive definite.  shift = coef * trace(G): the shifted Cholesky QR of Fukaya,
 // Kannan, Nakatsukasa, Yamamoto, Yanagisawa (SIAM J. Sci. Comput. 2020) uses
 // 11 (m b + b (b + 1)) u ||Y||_2^2, and trace(G) bounds ||Y||_2^2 from above.
-// One thread per task.
-__global__ void k_chol_small(const QrTask* __restrict__ tasks, int ntasks) {
-    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per task, the matrices in shared memory (FP64).
+__global__ void __launch_bounds__(32) k_chol_small(const QrTask* __restrict__ tasks, int ntasks) {
+    __shared__ double A[16][17], X[16][17];
+    const int ti = blockIdx.x;
     if (ti >= ntasks) return;
     const QrTask tk = tasks[ti];
-    const double* G = tk.G;
-    const int b = tk.b;
-    double R[16][16], X[16][16];
-    for (int i = 0; i < 16; ++i)
-        for (int j = 0; j < 16; ++j) { R[i][j] = 0.0; X[i][j] = 0.0; }
-    double trace = 0.0;
-    for (int i = 0; i < b; ++i) trace += G[i * 16 + i];
-    const double shift = tk.coef * trace;
-    for (int j = 0; j < b; ++j) {
-        double d = G[j * 16 + j] + shift;
-        for (int k2 = 0; k2 < j; ++k2) d -= R[k2][j] * R[k2][j];
-        if (!(d > 1e-28 * trace)) { *tk.status = 1; d = 1.0; }
-        R[j][j] = sqrt(d);
-        for (int i = j + 1; i < b; ++i) {
-            double s = G[j * 16 + i];
-            for (int k2 = 0; k2 < j; ++k2) s -= R[k2][j] * R[k2][i];
-            R[j][i] = s / R[j][j];
-        }
+    const int b = tk.b, lane = threadIdx.x;
+    for (int e = lane; e < 256; e += 32) {
+        const int i = e >> 4, j = e & 15;
+        A[i][j] = (i < b && j < b && j >= i) ? tk.G[i * 16 + j] : 0.0;   // upper triangle of G
+        X[i][j] = 0.0;
     }
-    for (int j = 0; j < b; ++j) {     // upper-triangular inverse, column by column
-        X[j][j] = 1.0 / R[j][j];
+    __syncwarp();
+    double trace = 0.0;
+    for (int i = 0; i < b; ++i) trace += A[i][i];
+    const double shift = tk.coef * trace;
+    if (lane < b) A[lane][lane] += shift;
+    __syncwarp();
+    bool bad = false;
+    for (int k = 0; k < b; ++k) {            // right-looking, row k of R overwrites row k of A
+        double d = A[k][k];
+        if (!(d > 1e-28 * trace)) { bad = true; d = 1.0; }
+        d = sqrt(d);
+        __syncwarp();
+        if (lane == 0) A[k][k] = d;
+        if (lane > k && lane < b) A[k][lane] /= d;
+        __syncwarp();
+        for (int e = lane; e < 256; e += 32) {
+            const int i = e >> 4, j = e & 15;
+            if (i > k && j >= i && j < b) A[i][j] -= A[k][i] * A[k][j];
+        }
+        __syncwarp();
+    }
+    if (bad && lane == 0) *tk.status = 1;
+    if (lane < b) {                          // column `lane` of R^{-1} by back substitution
+        const int j = lane;
+        X[j][j] = 1.0 / A[j][j];
         for (int i = j - 1; i >= 0; --i) {
             double s = 0.0;
-            for (int k2 = i + 1; k2 <= j; ++k2) s += R[i][k2] * X[k2][j];
-            X[i][j] = -s / R[i][i];
+            for (int k = i + 1; k <= j; ++k) s += A[i][k] * X[k][j];
+            X[i][j] = -s / A[i][i];
         }
     }
-    for (int i = 0; i < 16; ++i)
-        for (int j = 0; j < 16; ++j) tk.Rinv[i * 16 + j] = X[i][j];
+    __syncwarp();
+    for (int e = lane; e < 256; e += 32) tk.Rinv[e] = X[e >> 4][e & 15];
 }
 
 // Y <- Y Rinv (row-major ld 16, b columns), 128 rows per CTA.
@@ -789,14 +807,21 @@ template <class T>
 __global__ void k_apply_rinv(const QrTask* __restrict__ tasks) {
     const QrTask tk = tasks[blockIdx.x];
     const int i = tk.row0 + threadIdx.x;
-    if (i >= tk.m) return;
     T* Y = (T*)tk.Y;
-    double y[16];
-    for (int c = 0; c < 16; ++c) y[c] = c < tk.b ? (double)Y[(size_t)i * 16 + c] : 0.0;
-    for (int c = 0; c < tk.b; ++c) {
-        double s = 0.0;
-        for (int k2 = 0; k2 <= c; ++k2) s += y[k2] * tk.Rinv[k2 * 16 + c];
-        Y[(size_t)i * 16 + c] = (T)s;
+    __shared__ T Ri[16][16];
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) Ri[e >> 4][e & 15] = (T)tk.Rinv[e];
+    __syncthreads();
+    if (i >= tk.m) return;
+    T y[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) y[c] = c < tk.b ? Y[(size_t)i * 16 + c] : T(0);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        if (c >= tk.b) break;
+        T s = T(0);
+#pragma unroll
+        for (int k2 = 0; k2 <= c; ++k2) s = fma(y[k2], Ri[k2][c], s);
+        Y[(size_t)i * 16 + c] = s;
     }
 }
 
