@@ -148,6 +148,16 @@ rsc_status rsc_solve_device(rsc_handle* h, const double* d_b, double* d_x, doubl
 rsc_status rsc_apply_preconditioner_device(rsc_handle* h, const double* d_r, double* d_z, void* cuda_stream);
 
 /*
+ * Sparse outer product over A's pattern (the paper has no counterpart; it serves
+ * the adjoint gradient of x = A^{-1} b): d_out[e] = alpha * d_u[i] * d_v[j] for every
+ * stored entry e = (i, j) of the CSR given to rsc_analyze, in its order.  With
+ * u = lambda (the adjoint solution of A lambda = dL/dx), v = x and alpha = -1 this is
+ * dL/dA restricted to the pattern.  d_u[n], d_v[n], d_out[nnz] device FP64.
+ */
+rsc_status rsc_pattern_outer_device(rsc_handle* h, const double* d_u, const double* d_v, double alpha,
+                                    double* d_out, void* cuda_stream);
+
+/*
  * Allocation-free variant of rsc_apply_preconditioner_device (the paper has no
  * counterpart; this is an interface convenience).  For callers that cannot call
  * cudaMalloc while they apply the preconditioner: frameworks whose device memory

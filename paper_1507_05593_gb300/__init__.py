@@ -62,6 +62,7 @@ _SIGS = {
                                    C.POINTER(C.c_double), _P]),
     "rsc_apply_preconditioner_device": (C.c_int, [_P, _P, _P, _P]),
     "rsc_apply_preconditioner_device_noalloc": (C.c_int, [_P, _P, _P, _P]),
+    "rsc_pattern_outer_device": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
     "rsc_get_supernode_info": (C.c_int, [_P, C.c_int32, _P]),
     "rsc_get_supernode_blocks": (C.c_int, [_P, C.c_int32, _P, _P]),
     "rsc_get_stats": (C.c_int, [_P, C.POINTER(rsc_stats_t)]),
@@ -200,6 +201,15 @@ def rsc_apply_preconditioner_device_noalloc(h: Handle, d_r, d_z, stream=None) ->
     pz = d_z.data_ptr() if hasattr(d_z, "data_ptr") else int(d_z)
     s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().rsc_apply_preconditioner_device_noalloc(h.ptr, C.c_void_p(pr), C.c_void_p(pz), s), h.ptr)
+
+
+def rsc_pattern_outer_device(h: Handle, d_u, d_v, alpha: float, d_out, stream=None) -> None:
+    pu = d_u.data_ptr() if hasattr(d_u, "data_ptr") else int(d_u)
+    pv = d_v.data_ptr() if hasattr(d_v, "data_ptr") else int(d_v)
+    po = d_out.data_ptr() if hasattr(d_out, "data_ptr") else int(d_out)
+    s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().rsc_pattern_outer_device(h.ptr, C.c_void_p(pu), C.c_void_p(pv), float(alpha), C.c_void_p(po), s),
+           h.ptr)
 
 
 def rsc_get_supernode_info(h: Handle, j: int) -> dict:

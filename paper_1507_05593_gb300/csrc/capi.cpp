@@ -172,6 +172,16 @@ rsc_status rsc_apply_preconditioner_device_noalloc(rsc_handle* h, const double* 
     });
 }
 
+rsc_status rsc_pattern_outer_device(rsc_handle* h, const double* d_u, const double* d_v, double alpha,
+                                    double* d_out, void* stream) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    if (!d_u || !d_v || !d_out) return fail(h, RSC_ERR_INVALID_ARG, "d_u, d_v and d_out are required");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng) h->eng = new Engine(h->sym, h->opts);
+        return h->eng->pattern_outer(h->row_ptr, h->col_idx, h->val, d_u, d_v, alpha, d_out, stream);
+    });
+}
+
 rsc_status rsc_get_supernode_info(const rsc_handle* h, int32_t j, int32_t* info) {
     if (!h || !info) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL argument");
     if (j < 0 || j >= h->sym.M) return fail(const_cast<rsc_handle*>(h), RSC_ERR_INVALID_ARG, "j out of range");

@@ -170,6 +170,10 @@ struct EngineImpl {
                                      bool load) = 0;
     virtual bool noalloc_ready() const = 0;
     // PCG state shared by every precision
+    void ensure_matrix(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
+                       cudaStream_t s);
+    void pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
+                       const double* d_u, const double* d_v, double alpha, double* d_out, cudaStream_t s);
     rsc_status pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
                    const double* d_b, double* d_x, double rtol, int max_iter, int* iters, double* relres,
                    cudaStream_t s);
@@ -244,9 +248,20 @@ __global__ void k_xmy(long long n, const double* __restrict__ x, double* __restr
 
 static constexpr int DOT_BLOCKS = 304;
 
-rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                           const std::vector<double>& val, const double* d_b, double* d_x, double rtol, int max_iter,
-                           int* iters_out, double* relres_out, cudaStream_t s) {
+// out[e] = alpha * u[i] * v[j] for every stored entry e = (i, j) of the CSR pattern
+__global__ void k_pattern_outer(long long n, const long long* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ u, const double* __restrict__ v, double alpha,
+                                double* __restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long row = t >> 3;
+    const int sub = threadIdx.x & 7;
+    if (row >= n) return;
+    const double ui = alpha * u[row];
+    for (long long e = rp[row] + sub; e < rp[row + 1]; e += 8) out[e] = ui * v[ci[e]];
+}
+
+void EngineImpl::ensure_matrix(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                               const std::vector<double>& val, cudaStream_t s) {
     const long long n = (long long)rp.size() - 1;
     if (!a_uploaded || a_val_cache != val) {
         amem.release();
@@ -259,6 +274,23 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
         a_val_cache = val;
         a_uploaded = true;
     }
+}
+
+void EngineImpl::pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                               const std::vector<double>& val, const double* d_u, const double* d_v, double alpha,
+                               double* d_out, cudaStream_t s) {
+    const long long n = (long long)rp.size() - 1;
+    ensure_matrix(rp, ci, val, s);
+    k_pattern_outer<<<cdiv(n * 8, 256), 256, 0, s>>>(n, d_rp, d_ci, d_u, d_v, alpha, d_out);
+    launches++;
+    CK(cudaGetLastError());
+}
+
+rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                           const std::vector<double>& val, const double* d_b, double* d_x, double rtol, int max_iter,
+                           int* iters_out, double* relres_out, cudaStream_t s) {
+    const long long n = (long long)rp.size() - 1;
+    ensure_matrix(rp, ci, val, s);
     double* V = (double*)pcg_vec.get(sizeof(double) * 5 * n);
     double *r = V, *z = V + n, *p = V + 2 * n, *q = V + 3 * n, *t = V + 4 * n;
     double* part = (double*)red.get(sizeof(double) * (DOT_BLOCKS + 8));
@@ -2356,6 +2388,15 @@ rsc_status Engine::solve_device(const std::vector<int64_t>& rp, const std::vecto
     CK(cudaStreamSynchronize(s));
     return st;
 }
+rsc_status Engine::pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                                 const std::vector<double>& val, const double* d_u, const double* d_v, double alpha,
+                                 double* d_out, void* stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
+    impl_->pattern_outer(rp, ci, val, d_u, d_v, alpha, d_out, s);
+    CK(cudaStreamSynchronize(s));
+    return RSC_OK;
+}
+
 rsc_status Engine::apply_precond_noalloc(const double* d_r, double* d_z, void* stream) {
     cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
     int dev = 0;

@@ -33,6 +33,9 @@ public:
                             int32_t max_iter, int32_t* iters, double* relres, void* stream);
     rsc_status apply_precond(const double* d_r, double* d_z, void* stream);
     rsc_status apply_precond_noalloc(const double* d_r, double* d_z, void* stream);
+    rsc_status pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                             const std::vector<double>& val, const double* d_u, const double* d_v, double alpha,
+                             double* d_out, void* stream);
     void node_info(int j, int32_t* info) const;
     rsc_status node_blocks(int j, double* LD, double* LO) const;
     void stats(rsc_stats_t* out) const;

@@ -244,3 +244,52 @@ def elasticity_q1(ne: int = 40, nu: float = 0.3, e_soft: float = 1.0, e_stiff: f
     nc = np.stack([nx_.ravel(), ny_.ravel(), nz_.ravel()], axis=1)[free].astype(np.float64)
     coords = np.repeat(nc, 3, axis=0)
     return Problem(f"elasticity_q1_{ne}^3", n, rp, ci, v, coords, f, 3, (ne, ne, ne))
+
+
+# ----------------------------------------------------------------------------- differentiable values
+
+class FVValues:
+    """CSR values of ``fv_diffusion`` as a torch function of the log-conductivity.
+
+    ``FVValues(shape)(theta)`` returns the values of ``fv_diffusion(exp(theta))`` in its
+    CSR order (the pattern is fixed by the grid), built from torch operations so that
+    autograd can differentiate them with respect to theta[nz, ny, nx].
+    """
+
+    def __init__(self, shape):
+        nz, ny, nx = shape
+        self.shape = shape
+        n = nx * ny * nz
+        a, b = _face_pairs(nx, ny, nz)
+        ref = fv_diffusion(np.ones(shape))          # pattern and entry order
+        rp, ci = ref.row_ptr, ref.col_idx
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        face_of = {}
+        for f, (p, q) in enumerate(zip(a.tolist(), b.tolist())):
+            face_of[(p, q)] = f
+            face_of[(q, p)] = f
+        self.is_diag = rows == ci
+        self.face = np.array([0 if d else face_of[(int(r), int(c))] for r, c, d in zip(rows, ci, self.is_diag)])
+        self.rows = rows
+        self.a, self.b = a, b
+        nb = np.zeros(shape)
+        nb[:, :, 0] += 1; nb[:, :, -1] += 1
+        nb[:, 0, :] += 1; nb[:, -1, :] += 1
+        nb[0, :, :] += 1; nb[-1, :, :] += 1
+        self.nbound = nb.ravel()
+        self.row_ptr, self.col_idx, self.n = rp, ci, n
+        self.coords = ref.coords
+
+    def __call__(self, theta):
+        import torch
+        dev = theta.device
+        k = torch.exp(theta.reshape(-1).to(torch.float64))
+        a = torch.as_tensor(self.a, device=dev)
+        b = torch.as_tensor(self.b, device=dev)
+        t = 2.0 * k[a] * k[b] / (k[a] + k[b])
+        diag = 2.0 * k * torch.as_tensor(self.nbound, device=dev, dtype=torch.float64)
+        diag = diag.index_add(0, a, t).index_add(0, b, t)
+        is_diag = torch.as_tensor(self.is_diag, device=dev)
+        off = -t[torch.as_tensor(self.face, device=dev)]
+        on = diag[torch.as_tensor(self.rows, device=dev)]
+        return torch.where(is_diag, on, off)
