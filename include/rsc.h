@@ -148,6 +148,28 @@ rsc_status rsc_solve_device(rsc_handle* h, const double* d_b, double* d_x, doubl
 rsc_status rsc_apply_preconditioner_device(rsc_handle* h, const double* d_r, double* d_z, void* cuda_stream);
 
 /*
+ * Independent systems (batching form; the paper solves one system at a time): a
+ * matrix that is block diagonal up to ordering -- several systems stacked, each a
+ * connected component of A's graph -- is analysed one component at a time, so the
+ * supernodal elimination tree is a forest and every level of the factorization runs
+ * the supernodes of all systems together.  *n_systems = number of components;
+ * sys_ptr[n_systems+1] (may be NULL) their row ranges.  RSC_ERR_INVALID_ARG if the
+ * components are not contiguous row ranges of the original numbering.
+ */
+rsc_status rsc_get_systems(const rsc_handle* h, int32_t* n_systems, int64_t* sys_ptr);
+
+/*
+ * Batched PCG: every (system, right-hand side) pair runs its own PCG recurrence
+ * (own alpha, beta and stopping test, Section 6.1's relative residual) on the
+ * stacked system, preconditioned by the factor of the stacked matrix (which does
+ * not couple systems).  d_B, d_X: n x nrhs column-major device FP64.  iters[q],
+ * final_relres[q] for pair q = column * n_systems + system.  RSC_ERR_NO_CONVERGENCE
+ * if some pair did not reach rtol within max_iter (X holds the last iterates).
+ */
+rsc_status rsc_solve_batch_device(rsc_handle* h, int32_t nrhs, const double* d_B, double* d_X, double rtol,
+                                  int32_t max_iter, int32_t* iters, double* final_relres, void* cuda_stream);
+
+/*
  * Sparse outer product over A's pattern (the paper has no counterpart; it serves
  * the adjoint gradient of x = A^{-1} b): d_out[e] = alpha * d_u[i] * d_v[j] for every
  * stored entry e = (i, j) of the CSR given to rsc_analyze, in its order.  With

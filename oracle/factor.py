@@ -49,6 +49,7 @@ import dataclasses
 
 import numpy as np
 import scipy.sparse as sp
+from scipy.sparse import csgraph
 
 from . import dense
 from .dense import NotPositiveDefinite
@@ -78,7 +79,13 @@ class Analysis:
         self.opts = opts
         self.n = n
         A = sp.csr_matrix((val, col_idx, row_ptr), shape=(n, n))
-        self.ordering = nd_order(coords, opts.dof_per_node, opts.leaf_size, opts.tau_O, opts.tau_D)
+        # connected components of the node graph (independent systems are ordered apart)
+        dof = opts.dof_per_node
+        Pn = sp.csr_matrix((np.ones(len(col_idx)), (np.repeat(np.arange(n), np.diff(row_ptr)) // dof,
+                                                      np.asarray(col_idx) // dof)), shape=(n // dof, n // dof))
+        ncomp, labels = csgraph.connected_components(Pn, directed=False)
+        self.ordering = nd_order(coords, dof, opts.leaf_size, opts.tau_O, opts.tau_D,
+                                 labels if ncomp > 1 else None)
         p = self.ordering.perm
         self.A = A
         self.Ap = sp.csr_matrix(A[p][:, p])

@@ -35,9 +35,14 @@ from __future__ import annotations
 import numpy as np
 
 
-def nested_dissection(coords: np.ndarray, leaf_size: int = 64, dof: int = 1):
+def nested_dissection(coords: np.ndarray, leaf_size: int = 64, dof: int = 1, components=None):
     """Return (node_order, parts): node_order lists node ids in elimination order and
-    parts is a list of (kind, node_ids) per supernode, kind in {"leaf", "sep"}."""
+    parts is a list of (kind, node_ids) per supernode, kind in {"leaf", "sep"}.
+
+    ``components`` (optional, one label per node): the nodes of each connected
+    component of the matrix graph are dissected on their own, components in order of
+    their smallest node id (a block-diagonal stack of independent systems becomes a
+    forest of elimination trees)."""
     P = np.rint(np.asarray(coords)[::dof]).astype(np.int64)
     parts: list[tuple[str, np.ndarray]] = []
 
@@ -62,7 +67,15 @@ def nested_dissection(coords: np.ndarray, leaf_size: int = 64, dof: int = 1):
         if sep.size:
             parts.append(("sep", lex(sep)))
 
-    rec(np.arange(P.shape[0], dtype=np.int64))
+    if components is None:
+        rec(np.arange(P.shape[0], dtype=np.int64))
+    else:
+        comp = np.asarray(components)
+        first = {}
+        for i, c in enumerate(comp.tolist()):
+            first.setdefault(c, i)
+        for c in sorted(first, key=first.get):
+            rec(np.nonzero(comp == c)[0].astype(np.int64))
     order = np.concatenate([p[1] for p in parts])
     return order, parts
 
@@ -153,11 +166,11 @@ class Ordering:
 
 
 def order(coords: np.ndarray, dof: int = 1, leaf_size: int = 64, tau_O: int = 256,
-          tau_D: int = 256) -> Ordering:
+          tau_D: int = 256, components=None) -> Ordering:
     """Nested dissection, then the Section 4.1 reorder of every separator that will
     be compressed (>= tau_O unknowns, Section 3.1: "at least tau_O") and whose
     diagonal block is larger than tau_D."""
-    _, parts = nested_dissection(coords, leaf_size, dof)
+    _, parts = nested_dissection(coords, leaf_size, dof, components)
     node_blocks = []
     trees = []
     for kind, ids in parts:

@@ -63,6 +63,8 @@ _SIGS = {
     "rsc_apply_preconditioner_device": (C.c_int, [_P, _P, _P, _P]),
     "rsc_apply_preconditioner_device_noalloc": (C.c_int, [_P, _P, _P, _P]),
     "rsc_pattern_outer_device": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
+    "rsc_get_systems": (C.c_int, [_P, C.POINTER(C.c_int32), _P]),
+    "rsc_solve_batch_device": (C.c_int, [_P, C.c_int32, _P, _P, C.c_double, C.c_int32, _P, _P, _P]),
     "rsc_get_supernode_info": (C.c_int, [_P, C.c_int32, _P]),
     "rsc_get_supernode_blocks": (C.c_int, [_P, C.c_int32, _P, _P]),
     "rsc_get_stats": (C.c_int, [_P, C.POINTER(rsc_stats_t)]),
@@ -201,6 +203,31 @@ def rsc_apply_preconditioner_device_noalloc(h: Handle, d_r, d_z, stream=None) ->
     pz = d_z.data_ptr() if hasattr(d_z, "data_ptr") else int(d_z)
     s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib().rsc_apply_preconditioner_device_noalloc(h.ptr, C.c_void_p(pr), C.c_void_p(pz), s), h.ptr)
+
+
+def rsc_get_systems(h: Handle):
+    """Returns sys_ptr (n_systems + 1 row offsets of the independent systems)."""
+    m = C.c_int32()
+    _check(lib().rsc_get_systems(h.ptr, C.byref(m), None), h.ptr)
+    ptr = np.empty(m.value + 1, np.int64)
+    _check(lib().rsc_get_systems(h.ptr, C.byref(m), _ptr(ptr)), h.ptr)
+    return ptr
+
+
+def rsc_solve_batch_device(h: Handle, d_B, d_X, rtol: float = 1e-8, max_iter: int = 1000, stream=None,
+                           raise_on_no_convergence: bool = True):
+    """d_B, d_X: CUDA float64 tensors of shape (nrhs, n) (each row one right-hand side).
+    Returns (iters, relres) arrays of shape (nrhs, n_systems)."""
+    nrhs = int(d_B.shape[0]) if d_B.dim() == 2 else 1
+    nsys = rsc_get_systems(h).size - 1
+    it = np.zeros(nrhs * nsys, np.int32)
+    rr = np.zeros(nrhs * nsys, np.float64)
+    s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = lib().rsc_solve_batch_device(h.ptr, nrhs, C.c_void_p(d_B.data_ptr()), C.c_void_p(d_X.data_ptr()),
+                                      float(rtol), int(max_iter), _ptr(it), _ptr(rr), s)
+    if st != RSC_OK and not (st == 3 and not raise_on_no_convergence):
+        _check(st, h.ptr)
+    return it.reshape(nrhs, nsys), rr.reshape(nrhs, nsys)
 
 
 def rsc_pattern_outer_device(h: Handle, d_u, d_v, alpha: float, d_out, stream=None) -> None:

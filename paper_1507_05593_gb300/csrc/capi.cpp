@@ -172,6 +172,52 @@ rsc_status rsc_apply_preconditioner_device_noalloc(rsc_handle* h, const double* 
     });
 }
 
+// independent systems = connected components; each must be a contiguous row range
+static bool system_ranges(const rsc::Symbolic& S, std::vector<long long>& seg) {
+    const int dof = S.dof;
+    const int64_t nodes = S.n / dof;
+    seg.assign(1, 0);
+    // components are numbered by their smallest node: contiguous ranges step by one
+    for (int64_t v = 1; v < nodes; ++v)
+        if (S.comp_of[v] != S.comp_of[v - 1]) {
+            if (S.comp_of[v] != S.comp_of[v - 1] + 1) return false;
+            seg.push_back(v * dof);
+        }
+    seg.push_back(S.n);
+    return (int)seg.size() - 1 == S.ncomp;
+}
+
+rsc_status rsc_get_systems(const rsc_handle* h, int32_t* n_systems, int64_t* sys_ptr) {
+    if (!h || !n_systems) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL argument");
+    std::vector<long long> seg;
+    if (!system_ranges(h->sym, seg))
+        return fail(const_cast<rsc_handle*>(h), RSC_ERR_INVALID_ARG,
+                    "independent systems do not occupy contiguous row ranges");
+    *n_systems = (int32_t)seg.size() - 1;
+    if (sys_ptr)
+        for (size_t i = 0; i < seg.size(); ++i) sys_ptr[i] = seg[i];
+    return RSC_OK;
+}
+
+rsc_status rsc_solve_batch_device(rsc_handle* h, int32_t nrhs, const double* d_B, double* d_X, double rtol,
+                                  int32_t max_iter, int32_t* iters, double* final_relres, void* stream) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    if (!d_B || !d_X || !iters || !final_relres || nrhs < 1)
+        return fail(h, RSC_ERR_INVALID_ARG, "d_B, d_X, iters, final_relres and nrhs >= 1 are required");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng || !h->eng->factored()) return fail(h, RSC_ERR_STATE, "rsc_solve_batch_device before rsc_factor");
+        std::vector<long long> seg;
+        if (!system_ranges(h->sym, seg))
+            return fail(h, RSC_ERR_INVALID_ARG, "independent systems do not occupy contiguous row ranges");
+        std::vector<int> it(seg.size() - 1 > 0 ? (seg.size() - 1) * nrhs : 0);
+        rsc_status st = h->eng->solve_batch_device(h->row_ptr, h->col_idx, h->val, seg, d_B, d_X, nrhs, rtol, max_iter,
+                                                   it.data(), final_relres, stream);
+        for (size_t q = 0; q < it.size(); ++q) iters[q] = it[q];
+        if (st == RSC_ERR_NO_CONVERGENCE) return fail(h, st, "some systems did not reach rtol");
+        return st;
+    });
+}
+
 rsc_status rsc_pattern_outer_device(rsc_handle* h, const double* d_u, const double* d_v, double alpha,
                                     double* d_out, void* stream) {
     if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");

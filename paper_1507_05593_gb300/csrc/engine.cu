@@ -174,6 +174,9 @@ struct EngineImpl {
                        cudaStream_t s);
     void pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
                        const double* d_u, const double* d_v, double alpha, double* d_out, cudaStream_t s);
+    rsc_status pcg_batch(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
+                         const std::vector<long long>& seg_ptr, const double* d_B, double* d_X, int nrhs, double rtol,
+                         int max_iter, int* iters, double* relres, cudaStream_t s);
     rsc_status pcg(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci, const std::vector<double>& val,
                    const double* d_b, double* d_x, double rtol, int max_iter, int* iters, double* relres,
                    cudaStream_t s);
@@ -247,6 +250,179 @@ __global__ void k_xmy(long long n, const double* __restrict__ x, double* __restr
 }
 
 static constexpr int DOT_BLOCKS = 304;
+
+// ------------------------------------------------------------------ batched PCG (systems x right-hand sides)
+// Vectors are n x nrhs, column-major; a segment is one (system, column) pair, systems being
+// contiguous row ranges seg_ptr[s] .. seg_ptr[s+1].  Pair index = column * nseg + system.
+__global__ void k_spmv_multi(long long n, const long long* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, const double* __restrict__ X, double* __restrict__ Y) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long row = t >> 3;
+    const int sub = threadIdx.x & 7;
+    const double* x = X + (size_t)blockIdx.y * n;
+    double s = 0.0;
+    if (row < n)
+        for (long long e = rp[row] + sub; e < rp[row + 1]; e += 8) s = fma(v[e], x[ci[e]], s);
+    for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (row < n && sub == 0) Y[(size_t)blockIdx.y * n + row] = s;
+}
+// out[pair] = <A, B> over the pair's segment: one CTA per pair, fixed reduction order
+__global__ void k_seg_dot(long long n, int nseg, const long long* __restrict__ seg_ptr, const double* __restrict__ A,
+                          const double* __restrict__ B, double* __restrict__ out) {
+    const int sgi = blockIdx.x, col = blockIdx.y;
+    const double* a = A + (size_t)col * n;
+    const double* b = B + (size_t)col * n;
+    double s = 0.0;
+    for (long long i = seg_ptr[sgi] + threadIdx.x; i < seg_ptr[sgi + 1]; i += blockDim.x) s = fma(a[i], b[i], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        out[(size_t)col * nseg + sgi] = t;
+    }
+}
+// Y = a_pair X + b_pair Y over every column (coef arrays indexed by pair; nullptr = 1)
+__global__ void k_seg_axpby(long long n, int nseg, const int32_t* __restrict__ seg_of, const double* __restrict__ a,
+                            const double* __restrict__ X, const double* __restrict__ b, double* __restrict__ Y,
+                            double sa, double sb) {
+    const int col = blockIdx.y;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int pr = col * nseg + seg_of[i];
+        const double ca = a ? sa * a[pr] : sa, cb = b ? sb * b[pr] : sb;
+        const size_t k = (size_t)col * n + i;
+        Y[k] = ca * X[k] + cb * Y[k];
+    }
+}
+
+rsc_status EngineImpl::pcg_batch(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                                 const std::vector<double>& val, const std::vector<long long>& seg_ptr,
+                                 const double* d_B, double* d_X, int nrhs, double rtol, int max_iter, int* iters,
+                                 double* relres, cudaStream_t s) {
+    const long long n = (long long)rp.size() - 1;
+    const int nseg = (int)seg_ptr.size() - 1;
+    const int np = nseg * nrhs;
+    ensure_matrix(rp, ci, val, s);
+    const size_t vbytes = sizeof(double) * (size_t)n * nrhs;
+    char* W = (char*)pcg_vec.get(5 * vbytes + sizeof(double) * 8 * np + sizeof(long long) * (nseg + 1) +
+                                 sizeof(int32_t) * n + 4096);
+    double* R = (double*)W;
+    double* Z = (double*)(W + vbytes);
+    double* P = (double*)(W + 2 * vbytes);
+    double* Q = (double*)(W + 3 * vbytes);
+    double* T = (double*)(W + 4 * vbytes);
+    double* sc = (double*)(W + 5 * vbytes);            // 8 np scalars
+    long long* d_seg = (long long*)(sc + 8 * np);
+    int32_t* d_segof = (int32_t*)(d_seg + nseg + 1);
+    std::vector<int32_t> segof(n);
+    for (int g = 0; g < nseg; ++g)
+        for (long long i = seg_ptr[g]; i < seg_ptr[g + 1]; ++i) segof[i] = g;
+    CK(cudaMemcpyAsync(d_seg, seg_ptr.data(), sizeof(long long) * (nseg + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_segof, segof.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    const dim3 vg((unsigned)std::min(cdiv(n, 256), 2048), (unsigned)nrhs);
+    auto seg_dot = [&](const double* A, const double* B, std::vector<double>& out) {
+        k_seg_dot<<<dim3((unsigned)nseg, (unsigned)nrhs), 256, 0, s>>>(n, nseg, d_seg, A, B, sc);
+        launches++;
+        out.resize(np);
+        CK(cudaMemcpyAsync(out.data(), sc, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    };
+    auto put = [&](double* dst, const std::vector<double>& v) {
+        CK(cudaMemcpyAsync(dst, v.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    };
+    auto spmv = [&](const double* X, double* Y) {
+        k_spmv_multi<<<dim3((unsigned)cdiv(n * 8, 256), (unsigned)nrhs), 256, 0, s>>>(n, d_rp, d_ci, d_val, X, Y);
+        launches++;
+    };
+    auto precond = [&](const double* Rv, double* Zv) {
+        for (int c = 0; c < nrhs; ++c) apply(Rv + (size_t)c * n, Zv + (size_t)c * n, s);
+    };
+    double* d_alpha = sc + np;
+    double* d_beta = sc + 2 * np;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    CK(cudaMemsetAsync(d_X, 0, vbytes, s));
+    CK(cudaMemcpyAsync(R, d_B, vbytes, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> nb, rz, pq, rn, tr, alpha(np), beta(np);
+    seg_dot(d_B, d_B, nb);
+    for (auto& v : nb) v = std::sqrt(v);
+    std::vector<char> active(np);
+    for (int q = 0; q < np; ++q) {
+        active[q] = nb[q] > 0.0;
+        iters[q] = 0;
+        relres[q] = 0.0;
+    }
+    precond(R, Z);
+    CK(cudaMemcpyAsync(P, Z, vbytes, cudaMemcpyDeviceToDevice, s));
+    seg_dot(R, Z, rz);
+    int nact = 0;
+    for (char a : active) nact += a;
+    rsc_status st = RSC_OK;
+    for (int it = 1; it <= max_iter && nact > 0; ++it) {
+        spmv(P, Q);
+        seg_dot(P, Q, pq);
+        for (int q = 0; q < np; ++q) alpha[q] = active[q] ? rz[q] / pq[q] : 0.0;
+        put(d_alpha, alpha);
+        k_seg_axpby<<<vg, 256, 0, s>>>(n, nseg, d_segof, d_alpha, P, nullptr, d_X, 1.0, 1.0);
+        k_seg_axpby<<<vg, 256, 0, s>>>(n, nseg, d_segof, d_alpha, Q, nullptr, R, -1.0, 1.0);
+        launches += 2;
+        seg_dot(R, R, rn);
+        bool any = false;
+        for (int q = 0; q < np; ++q) {
+            if (!std::isfinite(rn[q])) { st = RSC_ERR_NOT_SPD; active[q] = 0; }
+            else if (active[q] && std::sqrt(rn[q]) / nb[q] <= rtol) any = true;
+        }
+        if (any) {   // confirm with the true residual
+            spmv(d_X, T);
+            k_seg_axpby<<<vg, 256, 0, s>>>(n, nseg, d_segof, nullptr, d_B, nullptr, T, 1.0, -1.0);
+            launches++;
+            seg_dot(T, T, tr);
+            for (int q = 0; q < np; ++q)
+                if (active[q] && std::sqrt(rn[q]) / nb[q] <= rtol && std::sqrt(tr[q]) / nb[q] <= rtol) {
+                    active[q] = 0;
+                    iters[q] = it;
+                    relres[q] = std::sqrt(tr[q]) / nb[q];
+                }
+        }
+        nact = 0;
+        for (int q = 0; q < np; ++q) {
+            nact += active[q];
+            if (active[q]) iters[q] = it;
+        }
+        if (nact == 0) break;
+        precond(R, Z);
+        std::vector<double> rz_new;
+        seg_dot(R, Z, rz_new);
+        for (int q = 0; q < np; ++q) beta[q] = active[q] ? rz_new[q] / rz[q] : 0.0;
+        put(d_beta, beta);
+        k_seg_axpby<<<vg, 256, 0, s>>>(n, nseg, d_segof, nullptr, Z, d_beta, P, 1.0, 1.0);
+        launches++;
+        rz = rz_new;
+    }
+    if (nact > 0) {
+        spmv(d_X, T);
+        k_seg_axpby<<<vg, 256, 0, s>>>(n, nseg, d_segof, nullptr, d_B, nullptr, T, 1.0, -1.0);
+        seg_dot(T, T, tr);
+        for (int q = 0; q < np; ++q)
+            if (active[q]) relres[q] = nb[q] > 0 ? std::sqrt(tr[q]) / nb[q] : 0.0;
+        if (st == RSC_OK) st = RSC_ERR_NO_CONVERGENCE;
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    solve_seconds = ms * 1e-3;
+    int mx = 0;
+    for (int q = 0; q < np; ++q) mx = std::max(mx, iters[q]);
+    last_iters = mx;
+    return st;
+}
 
 // out[e] = alpha * u[i] * v[j] for every stored entry e = (i, j) of the CSR pattern
 __global__ void k_pattern_outer(long long n, const long long* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -2388,6 +2564,16 @@ rsc_status Engine::solve_device(const std::vector<int64_t>& rp, const std::vecto
     CK(cudaStreamSynchronize(s));
     return st;
 }
+rsc_status Engine::solve_batch_device(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                                      const std::vector<double>& val, const std::vector<long long>& seg_ptr,
+                                      const double* d_B, double* d_X, int nrhs, double rtol, int max_iter, int* iters,
+                                      double* relres, void* stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
+    rsc_status st = impl_->pcg_batch(rp, ci, val, seg_ptr, d_B, d_X, nrhs, rtol, max_iter, iters, relres, s);
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
 rsc_status Engine::pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                                  const std::vector<double>& val, const double* d_u, const double* d_v, double alpha,
                                  double* d_out, void* stream) {

@@ -33,6 +33,10 @@ public:
                             int32_t max_iter, int32_t* iters, double* relres, void* stream);
     rsc_status apply_precond(const double* d_r, double* d_z, void* stream);
     rsc_status apply_precond_noalloc(const double* d_r, double* d_z, void* stream);
+    rsc_status solve_batch_device(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                                  const std::vector<double>& val, const std::vector<long long>& seg_ptr,
+                                  const double* d_B, double* d_X, int nrhs, double rtol, int max_iter, int* iters,
+                                  double* relres, void* stream);
     rsc_status pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                              const std::vector<double>& val, const double* d_u, const double* d_v, double alpha,
                              double* d_out, void* stream);

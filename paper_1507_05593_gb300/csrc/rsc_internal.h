@@ -26,6 +26,8 @@ struct Symbolic {
     int dof = 1;
     int M = 0;                              // supernodes
     std::vector<int32_t> perm, iperm;       // perm[new] = old
+    int ncomp = 1;                          // connected components of the node graph
+    std::vector<int32_t> comp_of;           // [n / dof] component of each node (original order)
     std::vector<int64_t> sn_ptr;            // [M+1] column boundaries
     std::vector<int32_t> snode_of;          // [n] supernode of each (new) column
     std::vector<uint8_t> kind;              // 0 leaf, 1 separator

@@ -172,8 +172,10 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
                 ++pos[j];
             }
     }
-    for (int64_t i = 0; i < 3 * n; ++i)
+    for (int64_t i = 0; i < 3 * n; ++i) {
         if (!std::isfinite(coords[i])) return "non-finite coordinate";
+        if (std::fabs(coords[i]) >= 2147483648.0) return "coordinates must be lattice positions below 2^31 in magnitude";
+    }
 
     const int dof = o.dof_per_node;
     const int64_t nodes = n / dof;
@@ -181,13 +183,42 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
     for (int64_t v = 0; v < nodes; ++v)
         for (int a = 0; a < 3; ++a) P[3 * v + a] = (int64_t)std::llround(coords[3 * (v * dof) + a]);
 
-    std::vector<std::pair<uint8_t, std::vector<int32_t>>> parts;
+    // connected components of the node graph: each is dissected on its own, in order of
+    // its smallest node (independent systems stacked block-diagonally become a forest)
+    std::vector<int32_t> comp(nodes, -1);
+    std::vector<std::vector<int32_t>> comps;
     {
-        std::vector<int32_t> all(nodes);
-        std::iota(all.begin(), all.end(), 0);
-        nd_recurse(all, P.data(), o.leaf_size, parts);
+        std::vector<int32_t> stack;
+        for (int64_t v0 = 0; v0 < nodes; ++v0) {
+            if (comp[v0] >= 0) continue;
+            const int32_t cid = (int32_t)comps.size();
+            comps.emplace_back();
+            comp[v0] = cid;
+            stack.assign(1, (int32_t)v0);
+            while (!stack.empty()) {
+                const int32_t v = stack.back();
+                stack.pop_back();
+                comps[cid].push_back(v);
+                for (int d = 0; d < dof; ++d) {
+                    const int64_t row = (int64_t)v * dof + d;
+                    for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+                        const int32_t w = ci[e] / dof;
+                        if (comp[w] < 0) { comp[w] = cid; stack.push_back(w); }
+                    }
+                }
+            }
+            std::sort(comps[cid].begin(), comps[cid].end());
+        }
     }
+    std::vector<std::pair<uint8_t, std::vector<int32_t>>> parts;
+    for (auto& cnodes : comps) nd_recurse(cnodes, P.data(), o.leaf_size, parts);
+    S.ncomp = (int)comps.size();
+    S.comp_of = std::move(comp);
+    const int ncomp_saved = S.ncomp;
+    std::vector<int32_t> comp_saved = std::move(S.comp_of);
     S = Symbolic();
+    S.ncomp = ncomp_saved;
+    S.comp_of = std::move(comp_saved);
     S.n = n;
     S.dof = dof;
     S.M = (int)parts.size();

@@ -41,7 +41,7 @@ def _bad(p, **changes):
     return loc
 
 
-@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "nocoords", "dof", "range"])
+@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "nocoords", "dof", "range", "hugecoord"])
 def test_analyze_rejects_bad_input(what):
     p = W.poisson7(4)
     rp, ci, v, xyz = p.row_ptr.copy(), p.col_idx.copy(), p.val.copy(), p.coords.copy()
@@ -67,6 +67,8 @@ def test_analyze_rejects_bad_input(what):
         opts.dof_per_node = 5
     elif what == "range":
         ci[3] = 10_000
+    elif what == "hugecoord":
+        xyz[5, 0] = 1e12
     with pytest.raises(R.RscError) as e:
         R.rsc_analyze(n, rp, ci, v, xyz, opts)
     assert e.value.status == 1
