@@ -1539,8 +1539,11 @@ struct EngineT final : EngineImpl {
         bool active = true, qr_pending = false;
         double y1 = -1;
         T *G = nullptr, *Y = nullptr, *Gp = nullptr;
+        T *Gb = nullptr, *Yb = nullptr;   // prefetched samples of PREFETCH passes (16 PREFETCH columns)
+        int pref_base = 0, pref_n = 0;
         int slot = 0;              // index into the batch's small device records
     };
+    static constexpr int PREFETCH = 4;   // sampling passes whose products are formed together
     double* d_rf = nullptr;        // per RF: [0] y1^2, [1] nrm^2, [2..257] gram, [258..513] rinv
     int* d_rfst = nullptr;         // per RF: QR status
     size_t rf_cap = 0, rf_used = 0;
@@ -1623,7 +1626,11 @@ struct EngineT final : EngineImpl {
             r.U = r.maxr ? lr_alloc((long long)r.c * r.maxr) : nullptr;
             r.G = wsT((size_t)std::max(r.m, r.c) * 16);
             r.Y = wsT((size_t)std::max(r.m, r.c) * 16);
-            r.Gp = wsT((size_t)std::max(r.m, r.c) * 16);
+            r.Gp = wsT((size_t)std::max(r.m, r.c) * 16 * PREFETCH);
+            r.Gb = wsT((size_t)r.m * 16 * PREFETCH);
+            r.Yb = wsT((size_t)r.c * 16 * PREFETCH);
+            r.pref_base = 0;
+            r.pref_n = 0;
         }
         std::vector<double> h(R.size() * 2);
         std::vector<int> hs(R.size());
@@ -1632,21 +1639,39 @@ struct EngineT final : EngineImpl {
             for (RF& r : R)
                 if (r.active) act.push_back(&r);
             if (act.empty()) break;
-            // sample: Y = mult_T(G) (with power iterations)
+            // samples of passes t .. t + PREFETCH - 1 are formed together: pass p's block of
+            // Y = (L^T L)^q L^T G_p depends only on its own G_p (Philox counter word3 = p)
             std::vector<Program> progs;
             for (RF* r : act) {
+                if (t < r->pref_base + r->pref_n) continue;
+                const int np_ = std::min(PREFETCH, std::max(1, cdiv(r->maxr - r->rank, 16) + 1));
+                const int N = 16 * np_;
+                r->pref_base = t;
+                r->pref_n = np_;
                 progs.emplace_back();
                 Program& P = progs.back();
                 Stage& g = next(P);
-                const uint32_t word3 = (uint32_t)t | ((uint32_t)restarts << 16);
-                for (int r0 = 0; r0 < r->m; r0 += 32) g.gauss.push_back(GaussTask{r->G, r->m, r0, r->block_id, word3});
-                mult_T_prog(P, *r, r->G, 16, r->Y);
+                for (int b = 0; b < np_; ++b) {
+                    const uint32_t word3 = (uint32_t)(t + b) | ((uint32_t)restarts << 16);
+                    for (int r0 = 0; r0 < r->m; r0 += 32)
+                        g.gauss.push_back(GaussTask{r->Gb, r->m, r0, r->block_id, word3, N, 16 * b});
+                }
+                mult_T_prog(P, *r, r->Gb, N, r->Yb);
                 for (int q = 0; q < o.power_iters; ++q) {
-                    mult_prog(P, *r, r->Y, 16, r->Gp);
-                    mult_T_prog(P, *r, r->Gp, 16, r->Y);
+                    mult_prog(P, *r, r->Yb, N, r->Gp);
+                    mult_T_prog(P, *r, r->Gp, N, r->Yb);
                 }
             }
             run(progs);
+            {   // this pass's block into Y
+                std::vector<Program> cp;
+                for (RF* r : act) {
+                    cp.emplace_back();
+                    const int N = 16 * r->pref_n;
+                    add_copy(next(cp.back()), r->Yb + 16 * (t - r->pref_base), N, 1, r->Y, 16, 1, r->c, 16);
+                }
+                run(cp);
+            }
             CK(cudaMemset2DAsync(d_rf, sizeof(double) * RFD, 0, sizeof(double) * 2, R.size(), stream));
             if (t == 0) norms(act, 0);
             project(act);

@@ -45,7 +45,7 @@ struct NnTask {              // Y[yrow_i, :] += alpha sum_l A[arow_i, l] Z[l, :]
 struct TrsvTask { const void* L; int ld; int c; int N; void* X; int ldx; int transpose; };
 struct CsrBlock { const int32_t* rp; const int32_t* ci; const double* v; int nrows; int pad; };
 struct CsrTask { CsrBlock blk; const void* X; int ldx; void* Y; int ldy; int N; int row0; double alpha; };
-struct GaussTask { void* G; int m; int row0; uint32_t block_id; uint32_t word3; };
+struct GaussTask { void* G; int m; int row0; uint32_t block_id; uint32_t word3; int ld; int col0; };
 struct NormTask { const void* X; int ld; int m; int nc; double* out; };
 struct QrTask { void* Y; int m; int b; int row0; double* G; double* Rinv; int* status; double coef; };
 struct CopyTask { const void* src; long long ssr, ssc; void* dst; long long dsr, dsc; int m, nc; };
@@ -682,7 +682,7 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
-// G (m x 16, row-major, ld 16): entry (i, c) from counter (i, c/2, block_id, word3), key = seed;
+// G (m x 16 at columns col0.., row-major, ld): entry (i, c) from counter (i, c/2, block_id, word3), key = seed;
 // Box-Muller on (w0, w1) for even c and (w2, w3) for odd c.  32 rows per CTA.
 template <class T>
 __global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long seed) {
@@ -697,14 +697,14 @@ __global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long 
     if (sizeof(T) == 8) {
         const double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
         const double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
-        G[(size_t)i * 16 + 2 * cp] = (T)z0;
-        G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
+        G[(size_t)i * tk.ld + tk.col0 + 2 * cp] = (T)z0;
+        G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = (T)z1;
     } else {   // FP32 form: single-precision transforms of the same Philox words
         const float f32 = 2.3283064365386963e-10f, tp = 6.2831853071795865f;
         const float z0 = sqrtf(-2.0f * logf(((float)c[0] + 1.0f) * f32)) * cosf(tp * ((float)c[1] * f32));
         const float z1 = sqrtf(-2.0f * logf(((float)c[2] + 1.0f) * f32)) * cosf(tp * ((float)c[3] * f32));
-        G[(size_t)i * 16 + 2 * cp] = (T)z0;
-        G[(size_t)i * 16 + 2 * cp + 1] = (T)z1;
+        G[(size_t)i * tk.ld + tk.col0 + 2 * cp] = (T)z0;
+        G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = (T)z1;
     }
 }
 
