@@ -28,6 +28,7 @@
 
 #include "engine.h"
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace rsc {
 
@@ -646,6 +647,9 @@ struct EngineT final : EngineImpl {
     std::vector<std::vector<PanelStep>> panel_steps;   // [level][step]
     std::vector<PushTask*> push_tasks;
     std::vector<int> push_count;
+    bool tc = false;                      // BF16 form: extend-add on tcgen05 tensor cores
+    std::vector<PushTask*> push_tasks_tc; // 128 x 64 tiles
+    std::vector<int> push_count_tc;
     // sparse block values are gathered at factor time from these source indices
     std::vector<long long> sp_src;     // concatenated value sources of all CsrBlocks
     double* d_spval = nullptr;
@@ -657,7 +661,9 @@ struct EngineT final : EngineImpl {
     Scratch sy, stmp;
 
     EngineT(const Symbolic& S_, const rsc_options& o_) : S(S_), o(o_) {
+        tc = sizeof(T) == 4 && o.precision == RSC_PREC_BF16;
         CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+        if (tc) CK(cudaFuncSetAttribute(k_push_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
         hs_attr<8>();
         hs_attr<4>();
@@ -991,6 +997,25 @@ struct EngineT final : EngineImpl {
             for (int l = 0; l < S.nlevels; ++l) {
                 push_tasks[l] = pmem.upload(byl[l], stream);
                 push_count[l] = (int)byl[l].size();
+            }
+            push_tasks_tc.assign(S.nlevels, nullptr);
+            push_count_tc.assign(S.nlevels, 0);
+            if (tc) {
+                std::vector<std::vector<PushTask>> bt(S.nlevels);
+                for (int j = 0; j < M; ++j)
+                    for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
+                        const int k = S.desc_k[d];
+                        const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+                        const int rend = nd[j].compressed ? p1 : rk;
+                        for (int pc = p0; pc < p1; pc += TC_N)
+                            for (int pr = pc; pr < rend; pr += TC_M)
+                                bt[S.level[k]].push_back(
+                                    PushTask{k, j, pr, std::min(pr + TC_M, rend), pc, std::min(pc + TC_N, p1)});
+                    }
+                for (int l = 0; l < S.nlevels; ++l) {
+                    push_tasks_tc[l] = pmem.upload(bt[l], stream);
+                    push_count_tc[l] = (int)bt[l].size();
+                }
             }
         }
         CK(cudaStreamSynchronize(stream));
@@ -1835,17 +1860,18 @@ struct EngineT final : EngineImpl {
     }
 
     void check_status() {
-        int st = 0;
-        CK(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        int st[2] = {0, 0};
+        CK(cudaMemcpyAsync(st, d_status, sizeof(int) * 2, cudaMemcpyDeviceToHost, stream));
         sync_stream();
-        if (st) throw Error(RSC_ERR_NOT_SPD, "indefinite diagonal block in supernode " + std::to_string(st - 1));
+        if (st[1]) throw Error(RSC_ERR_TIMEOUT, "a tensor-core completion wait expired");
+        if (st[0]) throw Error(RSC_ERR_NOT_SPD, "indefinite diagonal block in supernode " + std::to_string(st[0] - 1));
     }
 
     // ---------------------------------------------------------------- factor
     void run_once(const double* val) {
         lr_used = 0;
         flops = 0.0;
-        CK(cudaMemsetAsync(d_status, 0, sizeof(int), stream));
+        CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 2, stream));
         CK(cudaMemsetAsync(arena, 0, sizeof(T) * std::max<long long>(arena_elems, 1), stream));
         const size_t nval = (size_t)(S.lsrc.empty() ? 0 : *std::max_element(S.lsrc.begin(), S.lsrc.end()) + 1);
         CK(cudaMemcpyAsync(d_valbuf, val, sizeof(double) * nval, cudaMemcpyHostToDevice, stream));
@@ -1905,9 +1931,15 @@ struct EngineT final : EngineImpl {
                     pf += 2.0 * e.elems * h_lo[e.k].K;
                     pb += sizeof(T) * ((double)e.rows * h_lo[e.k].K + 2.0 * e.elems);
                 }
-                PROF(prof, "push", stream, pf, pb,
-                     k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf,
-                                                                 arena));
+                if (tc && push_count_tc[l]) {
+                    PROF(prof, "push_tc", stream, pf, pb,
+                         k_push_tc<<<push_count_tc[l], 128, TC_PAD_SMEM, stream>>>(
+                             push_tasks_tc[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf, (float*)arena, d_status + 1));
+                } else {
+                    PROF(prof, "push", stream, pf, pb,
+                         k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr,
+                                                                     d_leaf, arena));
+                }
                 launches++;
                 LAUNCH_CHECK();
             }
