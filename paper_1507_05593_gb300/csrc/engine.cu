@@ -26,9 +26,12 @@
 #include <functional>
 #include <numeric>
 
+#include <chrono>
+
 #include "engine.h"
 #include "kernels.cuh"
 #include "tcgen05.cuh"
+#include "rfpass.cuh"
 
 namespace rsc {
 
@@ -103,6 +106,7 @@ struct Profiler {
     std::map<std::string, Acc> acc;
     ~Profiler() {
         for (auto& p : pend) { pool.push_back(p.a); pool.push_back(p.b); }
+        if (lastb) pool.push_back(lastb);
         for (cudaEvent_t e : pool) cudaEventDestroy(e);
     }
     bool enabled(const char* name) const {
@@ -115,6 +119,11 @@ struct Profiler {
         if (pool.empty()) { cudaEvent_t e; CK(cudaEventCreate(&e)); return e; }
         cudaEvent_t e = pool.back(); pool.pop_back(); return e;
     }
+    cudaEvent_t lastb = nullptr;   // end of the previous recorded launch (idle-gap accounting)
+    void mark() {                  // forget the previous launch: the next gap is not counted
+        if (lastb) pool.push_back(lastb);
+        lastb = nullptr;
+    }
     void flush() {
         if (pend.empty()) return;
         CK(cudaEventSynchronize(pend.back().b));
@@ -123,9 +132,23 @@ struct Profiler {
             CK(cudaEventElapsedTime(&ms, p.a, p.b));
             Acc& a = acc[p.name];
             a.n++; a.ms += ms; a.flops += p.flops; a.bytes += p.bytes;
-            pool.push_back(p.a); pool.push_back(p.b);
+            if (lastb) {   // device idle (or other work) between the previous launch and this one
+                float g = 0.f;
+                CK(cudaEventElapsedTime(&g, lastb, p.a));
+                Acc& ga = acc[std::string("gap>") + p.name];
+                ga.n++; ga.ms += g;
+                pool.push_back(lastb);
+            }
+            pool.push_back(p.a);
+            lastb = p.b;
         }
         pend.clear();
+    }
+    // host wall time of a phase (stream drained at both ends), kept beside the kernel classes
+    void wall(const std::string& name, double ms) {
+        if (!on) return;
+        Acc& a = acc[name];
+        a.n++; a.ms += ms;
     }
     std::string json() {
         flush();
@@ -636,6 +659,11 @@ struct EngineT final : EngineImpl {
     long long asm_cnt = 0;
     double* d_valbuf = nullptr;
     int* d_status = nullptr;
+    // arrival counters of row-split TN products; every counter is back at zero when the
+    // launch that used it ends, so each launch numbers its counters from 0
+    static constexpr int TN_CNT_CAP = 1 << 16;
+    static constexpr int TN_SPLIT_MIN = 512, TN_SPLIT_ROWS = 256, TN_SPLIT_MAX = 64;
+    unsigned* d_tncnt = nullptr;
     double* d_norms = nullptr;     // [0] y1, [1] current
     double* d_small = nullptr;     // gram (256) + rinv (256)
     int* d_qstatus = nullptr;
@@ -675,6 +703,9 @@ struct EngineT final : EngineImpl {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (arena_base) cudaFree(arena_base);
         if (arena_host) cudaFreeHost(arena_host);
+        if (rf_host) cudaFreeHost(rf_host);
+        if (d_rfp_time) cudaFree(d_rfp_time);
+        if (st_host) cudaFreeHost(st_host);
         if (stream) cudaStreamDestroy(stream);
     }
 
@@ -766,6 +797,10 @@ struct EngineT final : EngineImpl {
         d_rows_ptr = pmem.upload(rptr, stream);
         d_perm = pmem.upload(S.perm, stream);
         d_status = (int*)pmem.alloc(sizeof(int) * 4);
+        d_tncnt = (unsigned*)pmem.alloc(sizeof(unsigned) * TN_CNT_CAP);
+        CK(cudaMemsetAsync(d_tncnt, 0, sizeof(unsigned) * TN_CNT_CAP, stream));
+        d_rfbar = (RfBarrier*)pmem.alloc(sizeof(RfBarrier));
+        CK(cudaMemsetAsync(d_rfbar, 0, sizeof(RfBarrier), stream));
         d_norms = (double*)pmem.alloc(sizeof(double) * 4);
         d_small = (double*)pmem.alloc(sizeof(double) * 512);
         d_qstatus = (int*)pmem.alloc(sizeof(int) * 4);
@@ -1108,10 +1143,25 @@ struct EngineT final : EngineImpl {
     char* arena_host = nullptr;     // pinned staging mirror of the device arena
     size_t arena_cap = 0, arena_used = 0;
     void sync_stream() {
-        CK(cudaStreamSynchronize(stream));
+        if (prof.on) {
+            const double t0 = now_ms();
+            CK(cudaStreamSynchronize(stream));
+            prof.wall("host_sync_wait", now_ms() - t0);
+        } else {
+            CK(cudaStreamSynchronize(stream));
+        }
         arena_used = 0;
     }
+    struct HostTimer {           // host time of a region, profile mode only
+        EngineT* e; const char* name; double t0;
+        HostTimer(EngineT* e_, const char* n) : e(e_), name(n), t0(e_->prof.on ? now_ms() : 0.0) {}
+        ~HostTimer() { if (e->prof.on) e->prof.wall(name, now_ms() - t0); }
+    };
+    static double now_ms() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    }
     template <class X> void* upload_tmp(Scratch&, const std::vector<X>& v) {
+        HostTimer ht_(this, "h_upload");
         const size_t bytes = (sizeof(X) * std::max<size_t>(v.size(), 1) + 255) / 256 * 256;
         if (arena_used + bytes > arena_cap) {
             sync_stream();
@@ -1216,6 +1266,7 @@ struct EngineT final : EngineImpl {
     }
 
     void run(std::vector<Program>& progs) {
+        HostTimer ht_(this, "h_run");
         size_t len = 0;
         for (auto& p : progs) len = std::max(len, p.size());
         for (size_t i = 0; i < len; ++i) {
@@ -1250,7 +1301,22 @@ struct EngineT final : EngineImpl {
             launch_kind("csr", st.csr, yn_csr, [&](CsrTask* d, int n, int y) { k_csr_mm<T><<<dim3(n, y), 256, 0, s>>>(d); });
             launch_kind("trsv", st.trsv, yn_tr,
                         [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
-            launch_kind("tn", st.tn, yn_tn, [&](TnTask* d, int n, int y) { k_tn<T><<<dim3(n, y), 256, 0, s>>>(d); });
+            int zs_tn = 1;
+            {   // long row ranges: split the rows over CTAs (deterministic fixed-order reduction)
+                int coff = 0;
+                for (auto& t : st.tn) {
+                    const int ych = cdiv(t.N, 16);
+                    if (t.nrow < TN_SPLIT_MIN || coff + ych > TN_CNT_CAP) continue;
+                    t.nsplit = std::min(cdiv(t.nrow, TN_SPLIT_ROWS), TN_SPLIT_MAX);
+                    t.rps = cdiv(t.nrow, t.nsplit);
+                    t.part = wsT((size_t)t.nsplit * 32 * t.N);
+                    t.cnt = d_tncnt + coff;
+                    coff += ych;
+                    zs_tn = std::max(zs_tn, t.nsplit);
+                }
+            }
+            launch_kind("tn", st.tn, yn_tn,
+                        [&](TnTask* d, int n, int y) { k_tn<T><<<dim3(n, y, zs_tn), 256, 0, s>>>(d); });
             launch_kind("nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) { k_nn<T><<<dim3(n, y), NN_ROWS, 0, s>>>(d); });
         }
         progs.clear();
@@ -1560,19 +1626,20 @@ struct EngineT final : EngineImpl {
         double tol = 0;
         uint32_t block_id = 0;
         T* U = nullptr; T* V = nullptr;
-        int rank = 0, b_last = 0;
-        bool active = true, qr_pending = false;
-        double y1 = -1;
-        T *G = nullptr, *Y = nullptr, *Gp = nullptr;
+        int rank = 0;
+        bool active = true;        // as last read back from the device
+        T *Y = nullptr, *Gp = nullptr;
         T *Gb = nullptr, *Yb = nullptr;   // prefetched samples of PREFETCH passes (16 PREFETCH columns)
         int pref_base = 0, pref_n = 0;
-        int slot = 0;              // index into the batch's small device records
+        int passes = 0;
     };
     static constexpr int PREFETCH = 4;   // sampling passes whose products are formed together
-    double* d_rf = nullptr;        // per RF: [0] y1^2, [1] nrm^2, [2..257] gram, [258..513] rinv
-    int* d_rfst = nullptr;         // per RF: QR status
-    size_t rf_cap = 0, rf_used = 0;
-    static constexpr int RFD = 520;
+    RfBarrier* d_rfbar = nullptr;
+    RfDev<T>* rf_host = nullptr;         // pinned: upload of the batch records, read-back of their state
+    size_t rf_host_cap = 0;
+    int* st_host = nullptr;              // pinned: status words read back with the state
+    int coop_max = 0;                    // co-resident CTAs of k_rf_pass
+    unsigned long long* d_rfp_time = nullptr;   // profile mode: time per k_rf_pass phase (ns)
 
     void mult_T_prog(Program& P, RF& r, const T* G, int N, T* W) {
         if (r.s == 0) prog_offdiag_T(P, r.j, G, N, W);
@@ -1584,166 +1651,139 @@ struct EngineT final : EngineImpl {
         else prog_diag_mult(P, r.j, r.s, X, N, W, Xp);
     }
 
-    void norms(std::vector<RF*>& rs, int slot) {
-        std::vector<NormTask> nt;
-        for (RF* r : rs) nt.push_back(NormTask{r->Y, 16, r->c, 16, d_rf + (size_t)r->slot * RFD + slot});
-        if (nt.empty()) return;
-        NormTask* d = (NormTask*)upload_tmp(sTask, nt);
-        k_sqnorm<T><<<dim3((unsigned)nt.size(), 16), 256, 0, stream>>>(d);
-        launches++;
-        LAUNCH_CHECK();
-    }
-    void project(std::vector<RF*>& rs) {
-        std::vector<Program> progs;
-        for (RF* r : rs) {
-            if (r->rank == 0) continue;
-            progs.emplace_back();
-            T* Z = wsT((size_t)r->rank * 16);
-            Stage& st = next(progs.back());
-            add_tn(st, tn_task(r->U, r->c, r->rank, r->c, nullptr, 0, nullptr, 0, r->Y, 16, Z, 16, 16));
-            add_nn(st, nn_task(r->U, r->c, r->rank, r->c, nullptr, 0, nullptr, 0, Z, 16, r->Y, 16, 16, -1.0, false));
+    // state of every block of the batch after the launched passes (one host round trip)
+    void rf_readback(std::vector<RF>& R, const RfDev<T>* d_rfd) {
+        CK(cudaMemcpyAsync(rf_host, d_rfd, sizeof(RfDev<T>) * R.size(), cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(st_host, d_status + 1, sizeof(int) * 2, cudaMemcpyDeviceToHost, stream));
+        sync_stream();
+        if (st_host[0]) throw Error(RSC_ERR_TIMEOUT, "a grid barrier wait of the range finder expired");
+        if (st_host[1]) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
+        for (size_t i = 0; i < R.size(); ++i) {
+            R[i].rank = rf_host[i].rank;
+            R[i].active = rf_host[i].active != 0;
         }
-        run(progs);
-    }
-    void cholqr(std::vector<RF*>& rs, bool shifted) {
-        const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
-        std::vector<QrTask> qt, q256, q128;
-        for (RF* r : rs) {
-            double* base = d_rf + (size_t)r->slot * RFD;
-            const int b = r->b_last;
-            const double coef = shifted ? 11.0 * ((double)r->c * b + (double)b * (b + 1)) * u : 0.0;
-            QrTask t{r->Y, r->c, b, 0, base + 2, base + 258, d_rfst + r->slot, coef};
-            qt.push_back(t);
-            for (int r0 = 0; r0 < r->c; r0 += 256) { t.row0 = r0; q256.push_back(t); }
-            for (int r0 = 0; r0 < r->c; r0 += 128) { t.row0 = r0; q128.push_back(t); }
-            flops += 3.0 * r->c * b * b;
-        }
-        if (qt.empty()) return;
-        CK(cudaMemset2DAsync(d_rf + 2, sizeof(double) * RFD, 0, sizeof(double) * 256, rf_used, stream));
-        QrTask* d1 = (QrTask*)upload_tmp(sTask, q256);
-        QrTask* d2 = (QrTask*)upload_tmp(sTask, qt);
-        QrTask* d3 = (QrTask*)upload_tmp(sTask, q128);
-        k_gram<T><<<(unsigned)q256.size(), 256, 0, stream>>>(d1);
-        k_chol_small<<<(unsigned)qt.size(), 32, 0, stream>>>(d2, (int)qt.size());
-        k_apply_rinv<T><<<(unsigned)q128.size(), 128, 0, stream>>>(d3);
-        launches += 3;
-        LAUNCH_CHECK();
     }
 
+    // Alg. 3 for a batch of blocks: samples of up to PREFETCH passes are formed by one
+    // implicit product; each pass is one cooperative launch of k_rf_pass, which keeps the
+    // stopping decision and the rank on the device, so the host reads the state back
+    // only when some block runs out of samples.
     void range_finder_batch(std::vector<RF>& R) {
         if (R.empty()) return;
         ws.reset();
-        if (R.size() > rf_cap) {
-            if (d_rf) CK(cudaFree(d_rf));
-            if (d_rfst) CK(cudaFree(d_rfst));
-            rf_cap = std::max<size_t>(R.size(), 64);
-            CK(cudaMalloc(&d_rf, sizeof(double) * RFD * rf_cap));
-            CK(cudaMalloc(&d_rfst, sizeof(int) * rf_cap));
+        if (!coop_max) {
+            int dev = 0, nsm = 0, per_sm = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rf_pass<T>, RFP_THREADS, 0));
+            coop_max = std::max(1, std::min(per_sm, 2) * nsm);
+            CK(cudaMallocHost(&st_host, sizeof(int) * 2));
         }
-        CK(cudaMemsetAsync(d_rfst, 0, sizeof(int) * R.size(), stream));
-        rf_used = R.size();
+        if (R.size() > rf_host_cap) {
+            if (rf_host) CK(cudaFreeHost(rf_host));
+            rf_host_cap = std::max<size_t>(R.size(), 64);
+            CK(cudaMallocHost(&rf_host, sizeof(RfDev<T>) * rf_host_cap));
+        }
+        const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        std::vector<int2> chunks;
         for (size_t i = 0; i < R.size(); ++i) {
             RF& r = R[i];
-            r.slot = (int)i;
             r.maxr = std::min(r.m, r.c);
             r.rank = 0;
             r.active = r.maxr > 0;
+            r.passes = 0;
             r.U = r.maxr ? lr_alloc((long long)r.c * r.maxr) : nullptr;
-            r.G = wsT((size_t)std::max(r.m, r.c) * 16);
-            r.Y = wsT((size_t)std::max(r.m, r.c) * 16);
+            r.Y = wsT((size_t)r.c * 16);
             r.Gp = wsT((size_t)std::max(r.m, r.c) * 16 * PREFETCH);
             r.Gb = wsT((size_t)r.m * 16 * PREFETCH);
             r.Yb = wsT((size_t)r.c * 16 * PREFETCH);
             r.pref_base = 0;
             r.pref_n = 0;
+            RfDev<T>& d = rf_host[i];
+            std::memset(&d, 0, sizeof(d));
+            const int nchunk = r.active ? cdiv(r.c, RFP_ROWS) : 0;
+            d.U = r.U; d.Y = r.Y;
+            d.Z = wsT((size_t)std::max(r.maxr, 1) * 16);
+            d.zpart = wsT((size_t)std::max(nchunk * r.maxr, 1) * 16);
+            d.gpart = wsT((size_t)std::max(nchunk, 1) * 256);
+            d.rinv = wsT(272);
+            d.c = r.c; d.maxr = r.maxr; d.nchunk = nchunk;
+            d.tol = r.tol; d.u = u;
+            d.active = r.active ? 1 : 0;
+            for (int q = 0; q < nchunk; ++q) chunks.push_back(make_int2((int)i, q));
         }
-        std::vector<double> h(R.size() * 2);
-        std::vector<int> hs(R.size());
+        RfDev<T>* d_rfd = (RfDev<T>*)ws.getb(sizeof(RfDev<T>) * R.size());
+        CK(cudaMemcpyAsync(d_rfd, rf_host, sizeof(RfDev<T>) * R.size(), cudaMemcpyHostToDevice, stream));
+        int2* d_chunks = (int2*)ws.getb(sizeof(int2) * std::max<size_t>(chunks.size(), 1));
+        {
+            int2* staged = (int2*)upload_tmp(sTask, chunks);
+            CK(cudaMemcpyAsync(d_chunks, staged, sizeof(int2) * chunks.size(), cudaMemcpyDeviceToDevice, stream));
+        }
+        CK(cudaMemsetAsync(d_rfbar, 0, sizeof(unsigned), stream));   // arrival count
+        const int nrf = (int)R.size(), nch = (int)chunks.size();
+        const int grid = std::max(1, std::min(nch, coop_max));
         for (int t = 0;; ++t) {
-            std::vector<RF*> act;
+            bool any = false, refill = false;
             for (RF& r : R)
-                if (r.active) act.push_back(&r);
-            if (act.empty()) break;
-            // samples of passes t .. t + PREFETCH - 1 are formed together: pass p's block of
-            // Y = (L^T L)^q L^T G_p depends only on its own G_p (Philox counter word3 = p)
-            std::vector<Program> progs;
-            for (RF* r : act) {
-                if (t < r->pref_base + r->pref_n) continue;
-                const int np_ = std::min(PREFETCH, std::max(1, cdiv(r->maxr - r->rank, 16) + 1));
-                const int N = 16 * np_;
-                r->pref_base = t;
-                r->pref_n = np_;
-                progs.emplace_back();
-                Program& P = progs.back();
-                Stage& g = next(P);
-                for (int b = 0; b < np_; ++b) {
-                    const uint32_t word3 = (uint32_t)(t + b) | ((uint32_t)restarts << 16);
-                    for (int r0 = 0; r0 < r->m; r0 += 32)
-                        g.gauss.push_back(GaussTask{r->Gb, r->m, r0, r->block_id, word3, N, 16 * b});
+                if (r.active) { any = true; refill |= t >= r.pref_base + r.pref_n; }
+            if (!any) break;
+            if (refill) {
+                if (t > 0) {
+                    rf_readback(R, d_rfd);
+                    bool still = false;
+                    for (RF& r : R) still |= r.active;
+                    if (!still) break;
                 }
-                mult_T_prog(P, *r, r->Gb, N, r->Yb);
-                for (int q = 0; q < o.power_iters; ++q) {
-                    mult_prog(P, *r, r->Yb, N, r->Gp);
-                    mult_T_prog(P, *r, r->Gp, N, r->Yb);
+                // samples of passes t .. t + np - 1 are formed together: pass p's block of
+                // Y = (L^T L)^q L^T G_p depends only on its own G_p (Philox counter word3 = p)
+                std::vector<Program> progs;
+                for (RF& r : R) {
+                    if (!r.active || t < r.pref_base + r.pref_n) continue;
+                    const int np_ = std::min(PREFETCH, std::max(1, cdiv(r.maxr - r.rank, 16) + 1));
+                    const int N = 16 * np_;
+                    r.pref_base = t;
+                    r.pref_n = np_;
+                    progs.emplace_back();
+                    Program& P = progs.back();
+                    Stage& g = next(P);
+                    for (int b = 0; b < np_; ++b) {
+                        const uint32_t word3 = (uint32_t)(t + b) | ((uint32_t)restarts << 16);
+                        for (int r0 = 0; r0 < r.m; r0 += 32)
+                            g.gauss.push_back(GaussTask{r.Gb, r.m, r0, r.block_id, word3, N, 16 * b});
+                    }
+                    mult_T_prog(P, r, r.Gb, N, r.Yb);
+                    for (int q = 0; q < o.power_iters; ++q) {
+                        mult_prog(P, r, r.Yb, N, r.Gp);
+                        mult_T_prog(P, r, r.Gp, N, r.Yb);
+                    }
                 }
+                run(progs);
             }
-            run(progs);
-            {   // this pass's block into Y
-                std::vector<Program> cp;
-                for (RF* r : act) {
-                    cp.emplace_back();
-                    const int N = 16 * r->pref_n;
-                    add_copy(next(cp.back()), r->Yb + 16 * (t - r->pref_base), N, 1, r->Y, 16, 1, r->c, 16);
-                }
-                run(cp);
+            std::vector<RfPass<T>> pp(R.size(), RfPass<T>{nullptr, 0, 0});
+            for (size_t i = 0; i < R.size(); ++i) {
+                RF& r = R[i];
+                if (!r.active || t >= r.pref_base + r.pref_n) continue;
+                pp[i] = RfPass<T>{r.Yb + 16 * (t - r.pref_base), 16 * r.pref_n, t == 0 ? 1 : 0};
+                ++r.passes;
             }
-            CK(cudaMemset2DAsync(d_rf, sizeof(double) * RFD, 0, sizeof(double) * 2, R.size(), stream));
-            if (t == 0) norms(act, 0);
-            project(act);
-            project(act);
-            norms(act, 1);
-            // one readback per pass: norms of every block and QR status of the previous pass
-            CK(cudaMemcpy2DAsync(h.data(), sizeof(double) * 2, d_rf, sizeof(double) * RFD, sizeof(double) * 2, R.size(),
-                                 cudaMemcpyDeviceToHost, stream));
-            CK(cudaMemcpyAsync(hs.data(), d_rfst, sizeof(int) * R.size(), cudaMemcpyDeviceToHost, stream));
-            sync_stream();
-            std::vector<RF*> go;
-            for (RF* r : act) {
-                if (r->qr_pending && hs[r->slot]) {   // previous orthonormalisation failed: drop it
-                    r->rank -= r->b_last;
-                    r->active = false;
-                    continue;
-                }
-                r->qr_pending = false;
-                if (t == 0) r->y1 = std::sqrt(h[2 * r->slot]);
-                const double nrm = std::sqrt(h[2 * r->slot + 1]);
-                if (!std::isfinite(nrm) || !std::isfinite(r->y1)) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
-                if (nrm <= r->tol * r->y1) { r->active = false; continue; }
-                r->b_last = std::min(16, r->maxr - r->rank);
-                go.push_back(r);
-            }
-            if (go.empty()) continue;
-            // makeOrthonormal: shifted Cholesky QR, re-projection against U, two Cholesky QR
-            // passes (shifted CholeskyQR3: stable up to cond ~ 1/u)
-            cholqr(go, true);
-            project(go);
-            cholqr(go, false);
-            cholqr(go, false);
-            std::vector<Program> cp;
-            for (RF* r : go) {
-                cp.emplace_back();
-                add_copy(next(cp.back()), r->Y, 16, 1, r->U + (size_t)r->rank * r->c, 1, r->c, r->c, r->b_last);
-                r->rank += r->b_last;
-                r->qr_pending = true;
-                if (r->rank >= r->maxr) r->active = false;
-            }
-            run(cp);
+            RfPass<T>* d_pp = (RfPass<T>*)upload_tmp(sTask, pp);
+            RfBarrier* bar = d_rfbar;
+            int* err = d_status + 1;
+            int nrf_ = nrf, nch_ = nch;
+            unsigned long long* ptime = prof.on ? d_rfp_time : nullptr;
+            void* args[] = {&d_rfd, &d_pp, &nrf_, &d_chunks, &nch_, &bar, &err, &ptime};
+            PROF(prof, "rf_pass", stream, 0, 0,
+                 CK(cudaLaunchCooperativeKernel((const void*)k_rf_pass<T>, dim3(grid), dim3(RFP_THREADS), args, 0,
+                                                stream)));
+            launches++;
         }
-        // status of the last orthonormalisation of blocks that stopped at full rank
-        CK(cudaMemcpyAsync(hs.data(), d_rfst, sizeof(int) * R.size(), cudaMemcpyDeviceToHost, stream));
-        sync_stream();
-        for (RF& r : R)
-            if (r.qr_pending && hs[r.slot]) r.rank -= r.b_last;
+        for (RF& r : R) {   // projections, Gram matrices and Cholesky QR of the passes that ran
+            const double c = r.c;
+            for (int p = 0; p < r.passes; ++p) {
+                const double rk = std::min(16.0 * p, (double)r.rank);
+                flops += 3.0 * 4.0 * c * rk * 16 + 3.0 * 2.0 * c * 256 + 3.0 * c * 256;
+            }
+        }
         // V = mult(U): U to row-major, product, back to column-major
         std::vector<Program> progs;
         std::vector<T*> vr(R.size(), nullptr);
@@ -1769,11 +1809,13 @@ struct EngineT final : EngineImpl {
         int maxnb = 0;
         for (int j : comp)
             if (nd[j].hier) { hier.push_back(j); maxnb = std::max(maxnb, S.tree[j].nblocks); }
+        const double t_h0 = now_ms();
         for (int s = 1; s <= maxnb; ++s) {
             std::vector<int> leaves, internals;
             for (int j : hier)
                 if (S.tree[j].nblocks >= s) (S.tree[j].leaf[s] ? leaves : internals).push_back(j);
             if (!leaves.empty()) {
+                HostTimer ht_(this, "h_leaves");
                 // Alg. 6: subtract earlier low-rank blocks p < s (one launch per ancestor depth,
                 // since the tiles of one leaf receive several ancestors), then Cholesky
                 for (int depth = 0;; ++depth) {
@@ -1803,7 +1845,7 @@ struct EngineT final : EngineImpl {
                     }
                     if (!any) break;
                     GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
-                    k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg);
+                    PROF(prof, "leaf_gemm", stream, 0, 0, k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg));
                     launches++;
                     LAUNCH_CHECK();
                 }
@@ -1823,6 +1865,7 @@ struct EngineT final : EngineImpl {
                 launch_inverses(tv);
             }
             if (!internals.empty()) {
+                HostTimer ht_(this, "h_internal_rf");
                 std::vector<RF> R;
                 for (int j : internals) {
                     const BlockTree& t = S.tree[j];
@@ -1841,6 +1884,8 @@ struct EngineT final : EngineImpl {
                 }
             }
         }
+        if (prof.on && maxnb) { sync_stream(); prof.wall("wall_hier_diag", now_ms() - t_h0); }
+        const double t_o0 = now_ms();
         std::vector<RF> R;
         for (int j : comp)
             if (nd[j].r > 0) {
@@ -1857,13 +1902,15 @@ struct EngineT final : EngineImpl {
             n.V = r.V; n.U = r.U; n.rank = r.rank;
         }
         for (int j : comp) h_lo[j] = LoOp{nd[j].V, std::max(nd[j].r, 1), nd[j].rank};
+        if (prof.on) prof.wall("wall_offdiag_rf", now_ms() - t_o0);
     }
 
     void check_status() {
-        int st[2] = {0, 0};
-        CK(cudaMemcpyAsync(st, d_status, sizeof(int) * 2, cudaMemcpyDeviceToHost, stream));
+        int st[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync(st, d_status, sizeof(int) * 3, cudaMemcpyDeviceToHost, stream));
         sync_stream();
-        if (st[1]) throw Error(RSC_ERR_TIMEOUT, "a tensor-core completion wait expired");
+        if (st[1]) throw Error(RSC_ERR_TIMEOUT, "a bounded device wait expired");
+        if (st[2]) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
         if (st[0]) throw Error(RSC_ERR_NOT_SPD, "indefinite diagonal block in supernode " + std::to_string(st[0] - 1));
     }
 
@@ -1871,7 +1918,7 @@ struct EngineT final : EngineImpl {
     void run_once(const double* val) {
         lr_used = 0;
         flops = 0.0;
-        CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 2, stream));
+        CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 3, stream));
         CK(cudaMemsetAsync(arena, 0, sizeof(T) * std::max<long long>(arena_elems, 1), stream));
         const size_t nval = (size_t)(S.lsrc.empty() ? 0 : *std::max_element(S.lsrc.begin(), S.lsrc.end()) + 1);
         CK(cudaMemcpyAsync(d_valbuf, val, sizeof(double) * nval, cudaMemcpyHostToDevice, stream));
@@ -1898,6 +1945,7 @@ struct EngineT final : EngineImpl {
             if (n.compressed) h_lo[j] = LoOp{nullptr, 1, 0};
         }
         for (int l = 0; l < S.nlevels; ++l) {
+            const double t_l0 = now_ms();
             run_panel_steps(panel_steps[l]);
             if (inv_count[l]) {
                 double fl = 0;
@@ -1944,6 +1992,11 @@ struct EngineT final : EngineImpl {
                 LAUNCH_CHECK();
             }
             sync_stream();   // h_lo is rewritten by the next level
+            if (prof.on) {
+                char nm[32];
+                std::snprintf(nm, sizeof(nm), "wall_level%02d", l);
+                prof.wall(nm, now_ms() - t_l0);
+            }
         }
         // push flops: lower half of L^O_k L^O_k^T per source
         for (int k = 0; k < S.M; ++k) {
@@ -1964,6 +2017,12 @@ struct EngineT final : EngineImpl {
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         launches = 0;
+        prof.flush();
+        prof.mark();
+        if (prof.on) {
+            if (!d_rfp_time) CK(cudaMalloc(&d_rfp_time, sizeof(unsigned long long) * 16));
+            CK(cudaMemsetAsync(d_rfp_time, 0, sizeof(unsigned long long) * 16, stream));
+        }
         for (;;) {
             if (!have_plan || plan_compress != compress || plan_diag != diag_on) build_plan(compress, diag_on);
             CK(cudaEventRecord(e0, stream));
@@ -1992,6 +2051,14 @@ struct EngineT final : EngineImpl {
         cudaEventDestroy(e1);
         factor_seconds = ms * 1e-3;
         prof.flush();
+        if (prof.on && d_rfp_time) {
+            unsigned long long tp[16];
+            CK(cudaMemcpy(tp, d_rfp_time, sizeof(tp), cudaMemcpyDeviceToHost));
+            static const char* names[13] = {"rfp_A_copy_tn", "rfp_B_red", "rfp_C_nn_tn", "rfp_D_red", "rfp_E_nn_gram",
+                                            "rfp_F_test_chol", "rfp_G_rinv_tn", "rfp_H_red", "rfp_I_nn_gram",
+                                            "rfp_J_chol", "rfp_K_rinv_gram", "rfp_L_chol", "rfp_M_rinv_store"};
+            for (int i = 0; i < 13; ++i) prof.wall(names[i], tp[i] * 1e-6);
+        }
         is_factored = true;
         ++factor_gen;
         build_solve_plan();

@@ -34,6 +34,12 @@ struct TnTask {              // Z[t, :] = beta Z[t, :] + alpha sum_i A[arow_i, t
     void* Z; int ldz; int t0;          // t0: first column of A of this CTA (8 columns, one per warp)
     const void* Y; int ldy; int N;
     double alpha, beta;
+    // row split (k_tn only): CTA z of the task sums rows [z rps, (z + 1) rps) into
+    // part[z][32][N]; the last CTA to arrive (counter cnt[chunk]) adds the nsplit partial
+    // sums in ascending z and writes Z, then resets its counter.
+    int nsplit = 1, rps = 0;
+    void* part = nullptr;
+    unsigned* cnt = nullptr;
 };
 struct NnTask {              // Y[yrow_i, :] += alpha sum_l A[arow_i, l] Z[l, :]  (N columns)
     const void* A; int lda; int K; int nrow;
@@ -46,8 +52,6 @@ struct TrsvTask { const void* L; int ld; int c; int N; void* X; int ldx; int tra
 struct CsrBlock { const int32_t* rp; const int32_t* ci; const double* v; int nrows; int pad; };
 struct CsrTask { CsrBlock blk; const void* X; int ldx; void* Y; int ldy; int N; int row0; double alpha; };
 struct GaussTask { void* G; int m; int row0; uint32_t block_id; uint32_t word3; int ld; int col0; };
-struct NormTask { const void* X; int ld; int m; int nc; double* out; };
-struct QrTask { void* Y; int m; int b; int row0; double* G; double* Rinv; int* status; double coef; };
 struct CopyTask { const void* src; long long ssr, ssc; void* dst; long long dsr, dsc; int m, nc; };
 // One action of a hierarchical (or blocked dense) diagonal solve, rows local to the block:
 //   HA_TRSV   X[o0:o0+no] <- L^{-1} X[..] or L^{-T} X[..]   (A1 = row-major L^{-1}, no <= SOLVE_MAX)
@@ -276,11 +280,14 @@ constexpr int TN_COLS = 32;
 template <class T>
 __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     __shared__ T red[8][16][33];
+    __shared__ int last;
     const TnTask tk = tasks[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = blockIdx.y * 16;
     const int nc = min(16, tk.N - c0);
-    if (nc <= 0) return;
+    if (nc <= 0 || (int)blockIdx.z >= tk.nsplit) return;
+    const int rb = (int)blockIdx.z * tk.rps;
+    const int re = tk.nsplit > 1 ? min(tk.nrow, rb + tk.rps) : tk.nrow;
     const int t = tk.t0 + lane;
     const bool tok = t < tk.K;
     const T* A = (const T*)tk.A + (size_t)(tok ? t : 0) * tk.lda;
@@ -288,8 +295,8 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     T acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = T(0);
-    const int chunk = (tk.nrow + 7) >> 3;
-    const int i0 = warp * chunk, i1 = min(tk.nrow, i0 + chunk);
+    const int chunk = (re - rb + 7) >> 3;
+    const int i0 = rb + warp * chunk, i1 = min(re, i0 + chunk);
     for (int ib = i0; ib < i1; ib += 32) {
       const int nb = min(32, i1 - ib);
       const int my = ib + lane;
@@ -316,15 +323,42 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) red[warp][q][lane] = acc[q];
     __syncthreads();
+    if (tk.nsplit == 1) {
+        for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
+            const int q = e >> 5, l = e & 31;
+            if (q >= nc || tk.t0 + l >= tk.K) continue;
+            T s = T(0);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += red[w][q][l];
+            T* z = (T*)tk.Z + (size_t)(tk.t0 + l) * tk.ldz + c0 + q;
+            *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * s : (T)tk.alpha * s;
+        }
+        return;
+    }
+    T* part = (T*)tk.part;
+    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
+        const int q = e >> 5, l = e & 31;
+        if (q >= nc) continue;
+        T s = T(0);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += red[w][q][l];
+        part[((size_t)blockIdx.z * 32 + l) * tk.N + c0 + q] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(tk.cnt + blockIdx.y, 1u) == (unsigned)(tk.nsplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
         const int q = e >> 5, l = e & 31;
         if (q >= nc || tk.t0 + l >= tk.K) continue;
         T s = T(0);
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += red[w][q][l];
+        for (int zz = 0; zz < tk.nsplit; ++zz) s += __ldcg(part + ((size_t)zz * 32 + l) * tk.N + c0 + q);
         T* z = (T*)tk.Z + (size_t)(tk.t0 + l) * tk.ldz + c0 + q;
         *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * s : (T)tk.alpha * s;
     }
+    if (threadIdx.x == 0) tk.cnt[blockIdx.y] = 0u;
 }
 
 // Vector form of k_tn (N = 1): one CTA per (task, 32-column tile), a warp per column,
@@ -705,123 +739,6 @@ __global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long 
         const float z1 = sqrtf(-2.0f * logf(((float)c[2] + 1.0f) * f32)) * cosf(tp * ((float)c[3] * f32));
         G[(size_t)i * tk.ld + tk.col0 + 2 * cp] = (T)z0;
         G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = (T)z1;
-    }
-}
-
-// ------------------------------------------------------------------ small reductions / orthonormalisation
-// *out += sum of squares of X (m x nc, row-major ld); grid (tasks, 16).
-template <class T>
-__global__ void k_sqnorm(const NormTask* __restrict__ tasks) {
-    const NormTask tk = tasks[blockIdx.x];
-    const T* X = (const T*)tk.X;
-    double s = 0.0;
-    const long long cnt = (long long)tk.m * tk.nc;
-    for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.y * blockDim.x) {
-        const double v = (double)X[(size_t)(e / tk.nc) * tk.ld + e % tk.nc];
-        s += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double ws[8];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        atomicAdd(tk.out, t);
-    }
-}
-
-// Gram G += Y^T Y over a 256-row chunk (b <= 16 columns of a row-major ld-16 block).
-template <class T>
-__global__ void k_gram(const QrTask* __restrict__ tasks) {
-    __shared__ double Ys[256][17];
-    const QrTask tk = tasks[blockIdx.x];
-    const T* Y = (const T*)tk.Y;
-    const int nr = min(256, tk.m - tk.row0);
-    for (int e = threadIdx.x; e < 256 * 16; e += blockDim.x) {
-        int i = e >> 4, c = e & 15;
-        Ys[i][c] = (i < nr && c < tk.b) ? (double)Y[(size_t)(tk.row0 + i) * 16 + c] : 0.0;
-    }
-    __syncthreads();
-    const int a = threadIdx.x >> 4, c = threadIdx.x & 15;
-    if (a < tk.b && c < tk.b && c >= a) {
-        double s = 0.0;
-        for (int i = 0; i < nr; ++i) s += Ys[i][a] * Ys[i][c];
-        atomicAdd(&tk.G[a * 16 + c], s);
-    }
-}
-
-// Cholesky G + shift I = R^T R (b x b, upper R) and Rinv = R^{-1}; *status = 1 if not
-// positive definite.  shift = coef * trace(G): the shifted Cholesky QR of Fukaya,
-// Kannan, Nakatsukasa, Yamamoto, Yanagisawa (SIAM J. Sci. Comput. 2020) uses
-// 11 (m b + b (b + 1)) u ||Y||_2^2, and trace(G) bounds ||Y||_2^2 from above.
-// One warp per task, the matrices in shared memory (FP64).
-__global__ void __launch_bounds__(32) k_chol_small(const QrTask* __restrict__ tasks, int ntasks) {
-    __shared__ double A[16][17], X[16][17];
-    const int ti = blockIdx.x;
-    if (ti >= ntasks) return;
-    const QrTask tk = tasks[ti];
-    const int b = tk.b, lane = threadIdx.x;
-    for (int e = lane; e < 256; e += 32) {
-        const int i = e >> 4, j = e & 15;
-        A[i][j] = (i < b && j < b && j >= i) ? tk.G[i * 16 + j] : 0.0;   // upper triangle of G
-        X[i][j] = 0.0;
-    }
-    __syncwarp();
-    double trace = 0.0;
-    for (int i = 0; i < b; ++i) trace += A[i][i];
-    const double shift = tk.coef * trace;
-    if (lane < b) A[lane][lane] += shift;
-    __syncwarp();
-    bool bad = false;
-    for (int k = 0; k < b; ++k) {            // right-looking, row k of R overwrites row k of A
-        double d = A[k][k];
-        if (!(d > 1e-28 * trace)) { bad = true; d = 1.0; }
-        d = sqrt(d);
-        __syncwarp();
-        if (lane == 0) A[k][k] = d;
-        if (lane > k && lane < b) A[k][lane] /= d;
-        __syncwarp();
-        for (int e = lane; e < 256; e += 32) {
-            const int i = e >> 4, j = e & 15;
-            if (i > k && j >= i && j < b) A[i][j] -= A[k][i] * A[k][j];
-        }
-        __syncwarp();
-    }
-    if (bad && lane == 0) *tk.status = 1;
-    if (lane < b) {                          // column `lane` of R^{-1} by back substitution
-        const int j = lane;
-        X[j][j] = 1.0 / A[j][j];
-        for (int i = j - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int k = i + 1; k <= j; ++k) s += A[i][k] * X[k][j];
-            X[i][j] = -s / A[i][i];
-        }
-    }
-    __syncwarp();
-    for (int e = lane; e < 256; e += 32) tk.Rinv[e] = X[e >> 4][e & 15];
-}
-
-// Y <- Y Rinv (row-major ld 16, b columns), 128 rows per CTA.
-template <class T>
-__global__ void k_apply_rinv(const QrTask* __restrict__ tasks) {
-    const QrTask tk = tasks[blockIdx.x];
-    const int i = tk.row0 + threadIdx.x;
-    T* Y = (T*)tk.Y;
-    __shared__ T Ri[16][16];
-    for (int e = threadIdx.x; e < 256; e += blockDim.x) Ri[e >> 4][e & 15] = (T)tk.Rinv[e];
-    __syncthreads();
-    if (i >= tk.m) return;
-    T y[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) y[c] = c < tk.b ? Y[(size_t)i * 16 + c] : T(0);
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        if (c >= tk.b) break;
-        T s = T(0);
-#pragma unroll
-        for (int k2 = 0; k2 <= c; ++k2) s = fma(y[k2], Ri[k2][c], s);
-        Y[(size_t)i * 16 + c] = s;
     }
 }
 
