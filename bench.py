@@ -290,7 +290,9 @@ def main():
     R.rsc_profile(h, True)
     step(h)
     prof_all = R.rsc_get_kernel_profile(h)
-    dom = max(prof_all.items(), key=lambda kv: kv[1]["ms"])[0] if prof_all else None
+    # kernel classes only (profile mode also reports host phases, idle gaps and k_rf_pass phases)
+    kern = {k: v for k, v in prof_all.items() if not k.startswith(("wall_", "h_", "gap>", "rfp_", "host_"))}
+    dom = max(kern.items(), key=lambda kv: kv[1]["ms"])[0] if kern else None
     R.rsc_profile(h, False)
     for _ in range(max(a.warmup - 1, 0)):
         step(h)

@@ -1728,22 +1728,18 @@ struct EngineT final : EngineImpl {
                 if (r.active) { any = true; refill |= t >= r.pref_base + r.pref_n; }
             if (!any) break;
             if (refill) {
-                if (t > 0) {
-                    rf_readback(R, d_rfd);
-                    bool still = false;
-                    for (RF& r : R) still |= r.active;
-                    if (!still) break;
-                }
                 // samples of passes t .. t + np - 1 are formed together: pass p's block of
-                // Y = (L^T L)^q L^T G_p depends only on its own G_p (Philox counter word3 = p)
+                // Y = (L^T L)^q L^T G_p depends only on its own G_p (Philox counter word3 = p).
+                // The programs are planned while the passes already launched run; blocks the
+                // read-back then shows finished are dropped from the batch.
                 std::vector<Program> progs;
+                std::vector<RF*> owner;
                 for (RF& r : R) {
                     if (!r.active || t < r.pref_base + r.pref_n) continue;
                     const int np_ = std::min(PREFETCH, std::max(1, cdiv(r.maxr - r.rank, 16) + 1));
                     const int N = 16 * np_;
-                    r.pref_base = t;
-                    r.pref_n = np_;
                     progs.emplace_back();
+                    owner.push_back(&r);
                     Program& P = progs.back();
                     Stage& g = next(P);
                     for (int b = 0; b < np_; ++b) {
@@ -1756,8 +1752,23 @@ struct EngineT final : EngineImpl {
                         mult_prog(P, r, r.Yb, N, r.Gp);
                         mult_T_prog(P, r, r.Gp, N, r.Yb);
                     }
+                    r.pref_n = -np_;   // pending: set once the read-back confirms the block
                 }
-                run(progs);
+                if (t > 0) {
+                    rf_readback(R, d_rfd);
+                    bool still = false;
+                    for (RF& r : R) still |= r.active;
+                    if (!still) break;
+                }
+                std::vector<Program> keep;
+                for (size_t i = 0; i < progs.size(); ++i) {
+                    RF& r = *owner[i];
+                    const int np_ = -r.pref_n;
+                    r.pref_base = t;
+                    r.pref_n = np_;
+                    if (r.active) keep.push_back(std::move(progs[i]));
+                }
+                run(keep);
             }
             std::vector<RfPass<T>> pp(R.size(), RfPass<T>{nullptr, 0, 0});
             for (size_t i = 0; i < R.size(); ++i) {
@@ -1777,12 +1788,23 @@ struct EngineT final : EngineImpl {
                                                 stream)));
             launches++;
         }
-        for (RF& r : R) {   // projections, Gram matrices and Cholesky QR of the passes that ran
+        // algorithmic work of the passes that ran (rank of pass p taken as min(16 p, final rank)):
+        // three projections (U^T Y and U Z: U read twice each), three Gram matrices and
+        // triangular solves; bytes: the sample block read, U read six times, Q written
+        double pf = 0, pb = 0;
+        for (RF& r : R) {
             const double c = r.c;
             for (int p = 0; p < r.passes; ++p) {
                 const double rk = std::min(16.0 * p, (double)r.rank);
-                flops += 3.0 * 4.0 * c * rk * 16 + 3.0 * 2.0 * c * 256 + 3.0 * c * 256;
+                pf += 3.0 * 4.0 * c * rk * 16 + 3.0 * 2.0 * c * 256 + 3.0 * c * 256;
+                pb += sizeof(T) * (c * 16 + 6.0 * c * rk + 2.0 * c * 16);
             }
+        }
+        flops += pf;
+        if (prof.enabled("rf_pass")) {
+            auto& a = prof.acc["rf_pass"];
+            a.flops += pf;
+            a.bytes += pb;
         }
         // V = mult(U): U to row-major, product, back to column-major
         std::vector<Program> progs;
