@@ -99,7 +99,8 @@ struct Scratch {
 struct Profiler {
     bool on = false;
     std::string only;      // empty: every class; else a comma-separated list of class names
-    struct Pend { const char* name; cudaEvent_t a, b; double flops, bytes; };
+    struct Pend { std::string name; cudaEvent_t a, b; double flops, bytes; };
+    std::string tag;       // appended to the class names of later launches (e.g. the level)
     struct Acc { long long n = 0; double ms = 0, flops = 0, bytes = 0; };
     std::vector<cudaEvent_t> pool;
     std::vector<Pend> pend;
@@ -135,7 +136,7 @@ struct Profiler {
             if (lastb) {   // device idle (or other work) between the previous launch and this one
                 float g = 0.f;
                 CK(cudaEventElapsedTime(&g, lastb, p.a));
-                Acc& ga = acc[std::string("gap>") + p.name];
+                Acc& ga = acc["gap>" + p.name];
                 ga.n++; ga.ms += g;
                 pool.push_back(lastb);
             }
@@ -172,7 +173,7 @@ struct Profiler {
             CK(cudaEventRecord(a_, STREAM));                                   \
             __VA_ARGS__;                                                       \
             CK(cudaEventRecord(b_, STREAM));                                   \
-            (P).pend.push_back({NAME, a_, b_, (double)(FLOPS), (double)(BYTES)}); \
+            (P).pend.push_back({std::string(NAME) + (P).tag, a_, b_, (double)(FLOPS), (double)(BYTES)}); \
         } else {                                                               \
             __VA_ARGS__;                                                       \
         }                                                                      \
@@ -1802,7 +1803,7 @@ struct EngineT final : EngineImpl {
         }
         flops += pf;
         if (prof.enabled("rf_pass")) {
-            auto& a = prof.acc["rf_pass"];
+            auto& a = prof.acc["rf_pass" + prof.tag];
             a.flops += pf;
             a.bytes += pb;
         }
@@ -1968,6 +1969,11 @@ struct EngineT final : EngineImpl {
         }
         for (int l = 0; l < S.nlevels; ++l) {
             const double t_l0 = now_ms();
+            if (std::getenv("RSC_PROFILE_BY_LEVEL")) {
+                char tg[16];
+                std::snprintf(tg, sizeof(tg), "@%02d", l);
+                prof.tag = tg;
+            }
             run_panel_steps(panel_steps[l]);
             if (inv_count[l]) {
                 double fl = 0;
@@ -2025,6 +2031,7 @@ struct EngineT final : EngineImpl {
             const double rk = S.nrows(k), K = h_lo[k].K;
             flops += rk * (rk + 1) * K;
         }
+        prof.tag.clear();
         check_status();
     }
 

@@ -85,16 +85,21 @@ __global__ void k_assemble(const double* __restrict__ val, const long long* __re
 }
 
 // ------------------------------------------------------------------ diagonal tile Cholesky (FP64)
+// Cholesky of one nb x nb (nb <= 64) diagonal tile in FP64, lower triangle in place, in
+// shared memory (right-looking).  Thread 0 forms the pivot and its reciprocal (one division
+// per column: an FP64 division costs hundreds of cycles on this part); the column is scaled by
+// multiplication, and the trailing update runs warps over columns, lanes down the rows of
+// each column's lower part (no index division).
 template <class T>
 __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict__ tasks, int* status) {
     __shared__ double s[NB][NB + 1];
+    __shared__ double rpiv;
     const PotrfTask tk = tasks[blockIdx.x];
     T* a = (T*)tk.a;
     const int nb = tk.nb, ld = tk.ld;
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        int i = e % nb, j = e / nb;
-        s[i][j] = (i >= j) ? (double)a[i + (size_t)j * ld] : 0.0;
-    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < nb; j += 8)
+        for (int i = j + lane; i < nb; i += 32) s[i][j] = (double)a[i + (size_t)j * ld];
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
         if (threadIdx.x == 0) {
@@ -103,58 +108,83 @@ __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict_
                 atomicCAS(status, 0, tk.node + 1);
                 d = 1.0;
             }
-            s[k][k] = sqrt(d);
+            const double r = sqrt(d);
+            s[k][k] = r;
+            rpiv = 1.0 / r;
         }
         __syncthreads();
-        const double dk = s[k][k];
-        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) s[i][k] /= dk;
+        const double ri = rpiv;
+        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) s[i][k] *= ri;
         __syncthreads();
-        const int m = nb - k - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = k + 1 + e % m, j = k + 1 + e / m;
-            if (i >= j) s[i][j] -= s[i][k] * s[j][k];
+        for (int j = k + 1 + warp; j < nb; j += 8) {
+            const double ljk = s[j][k];
+            for (int i = j + lane; i < nb; i += 32) s[i][j] = fma(-s[i][k], ljk, s[i][j]);
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        int i = e % nb, j = e / nb;
-        if (i >= j) a[i + (size_t)j * ld] = (T)s[i][j];
-    }
+    for (int j = warp; j < nb; j += 8)
+        for (int i = j + lane; i < nb; i += 32) a[i + (size_t)j * ld] = (T)s[i][j];
 }
 
-// X L^T = B for a block of rows below a factored diagonal tile (in place).
+// X L^T = B for a block of rows (nrows <= 64) below a factored diagonal tile (in place).
+// Thread (ty, tx) keeps rows ty + 16 p and columns tx + 16 q of X in registers; column j is
+// scaled by the reciprocal pivot by its owners and published to shared memory, then every
+// thread subtracts its contribution from the columns right of j (one barrier per column).
 template <class T>
 __global__ void __launch_bounds__(256) k_trsm_tile(const TrsmTask* __restrict__ tasks) {
     __shared__ T Ls[NB][NB + 1];
-    __shared__ T Xs[TILE][NB + 1];
+    __shared__ T dinv[NB];
+    __shared__ T colj[2][TILE];
     const TrsmTask tk = tasks[blockIdx.x];
     const T* L = (const T*)tk.L;
     T* B = (T*)tk.B;
     const int nb = tk.nb, nr = tk.nrows;
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        int i = e % nb, j = e / nb;
-        Ls[i][j] = (i >= j) ? L[i + (size_t)j * tk.ldl] : T(0);
-    }
-    for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
-        int i = e % nr, j = e / nr;
-        Xs[i][j] = B[i + (size_t)j * tk.ldb];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e & (NB - 1), j = e >> 6;
+        Ls[i][j] = (i < nb && j < nb && i >= j) ? L[i + (size_t)j * tk.ldl] : T(0);
     }
     __syncthreads();
+    if (threadIdx.x < nb) dinv[threadIdx.x] = T(1) / Ls[threadIdx.x][threadIdx.x];
+    T x[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = ty + 16 * p, j = tx + 16 * q;
+            x[p][q] = (i < nr && j < nb) ? B[i + (size_t)j * tk.ldb] : T(0);
+        }
+    __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        const T d = Ls[j][j];
-        for (int i = threadIdx.x; i < nr; i += blockDim.x) Xs[i][j] /= d;
-        __syncthreads();
-        const int m = nb - j - 1;
-        for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
-            int i = e % nr, l = j + 1 + e / nr;
-            Xs[i][l] -= Xs[i][j] * Ls[l][j];
+        const int buf = j & 1, jq = j >> 4;
+        if (tx == (j & 15)) {
+            const T di = dinv[j];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q == jq) {
+                        x[p][q] *= di;
+                        colj[buf][ty + 16 * p] = x[p][q];
+                    }
         }
         __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (16 * q + 15 <= j) continue;           // whole warp left of column j + 1
+            const int l = tx + 16 * q;
+            const T lj = (l > j && l < nb) ? Ls[l][j] : T(0);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) x[p][q] = fma(-colj[buf][ty + 16 * p], lj, x[p][q]);
+        }
     }
-    for (int e = threadIdx.x; e < nr * nb; e += blockDim.x) {
-        int i = e % nr, j = e / nr;
-        B[i + (size_t)j * tk.ldb] = Xs[i][j];
-    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = ty + 16 * p, j = tx + 16 * q;
+            if (i < nr && j < nb) B[i + (size_t)j * tk.ldb] = x[p][q];
+        }
 }
 
 // ------------------------------------------------------------------ 64x64 tile product core
@@ -464,6 +494,7 @@ template <class T, int CW>
 __global__ void __launch_bounds__(256) k_trsv_subst(const TrsvTask* __restrict__ tasks) {
     __shared__ T Xs[SOLVE_MAX][CW + 1];
     __shared__ T Lt[32][33];
+    __shared__ T dinv[32];
     const TrsvTask tk = tasks[blockIdx.x];
     const T* L = (const T*)tk.L;
     T* X = (T*)tk.X;
@@ -489,17 +520,19 @@ __global__ void __launch_bounds__(256) k_trsv_subst(const TrsvTask* __restrict__
             Lt[i][j] = (i < w && j < w && i >= j) ? L[(r0 + i) + (size_t)(r0 + j) * ld] : T(0);
         }
         __syncthreads();
+        if (tid < w) dinv[tid] = T(1) / Lt[tid][tid];
+        __syncthreads();
         for (int q = warp; q < nc; q += 8) {
             T x = lane < w ? Xs[r0 + lane][q] : T(0);
             if (!transpose) {
                 for (int k2 = 0; k2 < w; ++k2) {
-                    if (lane == k2) x /= Lt[k2][k2];
+                    if (lane == k2) x *= dinv[k2];
                     const T xk = __shfl_sync(0xffffffffu, x, k2);
                     if (lane > k2) x -= Lt[lane][k2] * xk;
                 }
             } else {
                 for (int k2 = w - 1; k2 >= 0; --k2) {
-                    if (lane == k2) x /= Lt[k2][k2];
+                    if (lane == k2) x *= dinv[k2];
                     const T xk = __shfl_sync(0xffffffffu, x, k2);
                     if (lane < k2) x -= Lt[k2][lane] * xk;
                 }
@@ -515,6 +548,7 @@ __global__ void __launch_bounds__(256) k_trsv_subst(const TrsvTask* __restrict__
             T a[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) a[u] = T(0);
+#pragma unroll 8
             for (int k2 = 0; k2 < w; ++k2) {
                 const T l = transpose ? L[(r0 + k2) + (size_t)i * ld] : L[i + (size_t)(r0 + k2) * ld];
 #pragma unroll
