@@ -593,6 +593,10 @@ struct EngineT final : EngineImpl {
         T* U = nullptr;          // c x rank, column-major (ld c)
         std::vector<int> brank;            // by label
         std::vector<T*> bV, bU;
+        // factors of the off-diagonal blocks of the inverse, by label (internal blocks):
+        // (L^D)^{-1} holds -tV_s tU_s^T in the place of V_s U_s^T, with tV_s = L_right(s)^{-1} V_s
+        // and tU_s = L_left(s)^{-T} U_s (same shapes as V_s, U_s)
+        std::vector<T*> tV, tU;
         // sparse A blocks for the implicit products (compressed nodes)
         CsrBlock aR{}, aC{};               // A(R_j, C_j) by R rows / by C rows (transposed)
         std::vector<CsrBlock> bR, bC;      // per internal block: A(rows_s, cols_s) by rows / by cols
@@ -664,6 +668,7 @@ struct EngineT final : EngineImpl {
     // launch that used it ends, so each launch numbers its counters from 0
     static constexpr int TN_CNT_CAP = 1 << 16;
     static constexpr int TN_SPLIT_MIN = 512, TN_SPLIT_ROWS = 256, TN_SPLIT_MAX = 64;
+    static constexpr int TN1_SPLIT_ROWS = 512;   // rows per CTA of a split vector TN task (apply)
     unsigned* d_tncnt = nullptr;
     double* d_norms = nullptr;     // [0] y1, [1] current
     double* d_small = nullptr;     // gram (256) + rinv (256)
@@ -747,6 +752,8 @@ struct EngineT final : EngineImpl {
                 n.brank.assign(t.nblocks + 1, 0);
                 n.bV.assign(t.nblocks + 1, nullptr);
                 n.bU.assign(t.nblocks + 1, nullptr);
+                n.tV.assign(t.nblocks + 1, nullptr);
+                n.tU.assign(t.nblocks + 1, nullptr);
             }
         }
         arena_elems = off;
@@ -785,7 +792,7 @@ struct EngineT final : EngineImpl {
                 for (int s = 1; s <= t.nblocks; ++s)
                     if (!t.leaf[s]) {
                         long long a = t.hi[s] - t.mid[s], b = t.mid[s] - t.lo[s];
-                        lr += (a + b) * std::min(a, b) + 64;
+                        lr += 2 * ((a + b) * std::min(a, b) + 64);   // V_s, U_s and tV_s, tU_s
                     }
             }
         }
@@ -1826,6 +1833,47 @@ struct EngineT final : EngineImpl {
         sync_stream();   // the workspace is recycled by the next batch
     }
 
+    // ---------------------------------------------------------------- factors of the inverse's off-diagonal blocks
+    // For every internal block s of the hierarchical diagonal blocks of one level (Section 4's
+    // L^D_j with L21 = V_s U_s^T): tU_s = L_left(s)^{-T} U_s and tV_s = L_right(s)^{-1} V_s by the
+    // subtree solves of Alg. 4, all blocks in one staged batch.  Then
+    //   (L^D_j)^{-1} x = D^{-1} x - sum_s tV_s (tU_s^T x[cols(s)])  (placed in rows(s)),
+    // with D the block diagonal of the leaves: every term reads x, so the preconditioner
+    // applies the diagonal solve as three parallel launches instead of the in-order chain.
+    void inverse_factors(const std::vector<int>& hier) {
+        ws.reset();
+        std::vector<Program> progs;
+        for (int j : hier) {
+            NodeRT& n = nd[j];
+            const BlockTree& t = S.tree[j];
+            for (int b = 1; b <= t.nblocks; ++b) {
+                const int q = n.brank[b];
+                if (t.leaf[b] || q == 0) continue;
+                const int n1 = t.mid[b] - t.lo[b], n2 = t.hi[b] - t.mid[b];
+                {   // tU_b = L_left(b)^{-T} U_b
+                    progs.emplace_back();
+                    Program& P = progs.back();
+                    T* X = wsT((size_t)n1 * q);
+                    add_copy(next(P), n.bU[b], 1, n1, X, q, 1, n1, q);
+                    prog_diag_solve(P, j, t.left[b], X, q, q, true);
+                    n.tU[b] = lr_alloc((long long)n1 * q);
+                    add_copy(next(P), X, q, 1, n.tU[b], 1, n1, n1, q);
+                }
+                {   // tV_b = L_right(b)^{-1} V_b
+                    progs.emplace_back();
+                    Program& P = progs.back();
+                    T* X = wsT((size_t)n2 * q);
+                    add_copy(next(P), n.bV[b], 1, n2, X, q, 1, n2, q);
+                    prog_diag_solve(P, j, t.right[b], X, q, q, false);
+                    n.tV[b] = lr_alloc((long long)n2 * q);
+                    add_copy(next(P), X, q, 1, n.tV[b], 1, n2, n2, q);
+                }
+            }
+        }
+        run(progs);
+        sync_stream();   // the workspace is recycled by the next batch
+    }
+
     // ---------------------------------------------------------------- compressed supernodes of one level
     void compressed_level(const std::vector<int>& comp) {
         std::vector<int> hier;
@@ -1907,6 +1955,7 @@ struct EngineT final : EngineImpl {
                 }
             }
         }
+        if (!hier.empty()) inverse_factors(hier);
         if (prof.on && maxnb) { sync_stream(); prof.wall("wall_hier_diag", now_ms() - t_h0); }
         const double t_o0 = now_ms();
         std::vector<RF> R;
@@ -1964,6 +2013,8 @@ struct EngineT final : EngineImpl {
                 std::fill(n.brank.begin(), n.brank.end(), 0);
                 std::fill(n.bV.begin(), n.bV.end(), nullptr);
                 std::fill(n.bU.begin(), n.bU.end(), nullptr);
+                std::fill(n.tV.begin(), n.tV.end(), nullptr);
+                std::fill(n.tU.begin(), n.tU.end(), nullptr);
             }
             if (n.compressed) h_lo[j] = LoOp{nullptr, 1, 0};
         }
@@ -2253,18 +2304,62 @@ struct EngineT final : EngineImpl {
         };
         emit(L_PERM_IN, 0, 1, 0);
         std::vector<std::vector<T*>> ztmp(S.nlevels);
+        // hierarchical diagonal blocks through the factors of their inverse: per level, the
+        // low-rank products z_s = tU_s^T y[cols(s)] (TN) before the leaf solves (TRSV, in place),
+        // then y[rows(s)] -= tV_s z_s (NN, atomic: the row ranges of nested blocks overlap);
+        // the transpose exchanges the roles of tU and tV.  z_s is kept per block.
+        std::map<std::pair<int, int>, T*> hz;
+        auto hier_terms = [&](int j, bool transpose, std::vector<TnTask>& tn, std::vector<NnTask>& nnv) {
+            const NodeRT& nn = nd[j];
+            const BlockTree& t = S.tree[j];
+            for (int b = 1; b <= t.nblocks; ++b) {
+                const int q = nn.brank[b];
+                if (t.leaf[b] || q == 0) continue;
+                const int n1 = t.mid[b] - t.lo[b], n2 = t.hi[b] - t.mid[b];
+                T*& z = hz[{j, b}];
+                if (!z) { z = zcur; zcur += q; }
+                if (!transpose) {
+                    push_tn_chunks(tn, vtn(nn.tU[b], n1, q, n1, nullptr, (int)(nn.c0 + t.lo[b]), z));
+                    push_nn_chunks(nnv, vnn(nn.tV[b], n2, q, n2, nullptr, (int)(nn.c0 + t.mid[b]), z, true));
+                } else {
+                    push_tn_chunks(tn, vtn(nn.tV[b], n2, q, n2, nullptr, (int)(nn.c0 + t.mid[b]), z));
+                    push_nn_chunks(nnv, vnn(nn.tU[b], n1, q, n1, nullptr, (int)(nn.c0 + t.lo[b]), z, true));
+                }
+                apply_bytes += sizeof(T) * (double)q * (n1 + n2);
+            }
+        };
+        auto hier_leaves = [&](int j, bool transpose) {
+            const NodeRT& nn = nd[j];
+            const BlockTree& t = S.tree[j];
+            for (int b = 1; b <= t.nblocks; ++b)
+                if (t.leaf[b]) {
+                    const int sz = t.hi[b] - t.lo[b];
+                    B.trsv.push_back(
+                        TrsvTask{invs + nn.leaf_inv[b], sz, sz, 1, y_dev + nn.c0 + t.lo[b], 1, transpose ? 1 : 0});
+                    apply_bytes += sizeof(T) * (double)sz * sz;
+                }
+        };
         for (int l = 0; l < S.nlevels; ++l) {
-            size_t o = B.trsv.size();
             std::vector<std::vector<Act>> acts;
             std::vector<int> big;
+            std::vector<NnTask> hnn;
+            size_t oh = B.tn.size();
+            for (int j : S.level_nodes[l])
+                if (nd[j].hier) hier_terms(j, false, B.tn, hnn);
+            emit(L_TN, oh, B.tn.size() - oh, 0);
+            size_t o = B.trsv.size();
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
+                if (nn.hier) { hier_leaves(j, false); continue; }
                 apply_bytes += 2.0 * sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
-                if (!nn.hier && nn.c <= SOLVE_MAX)
+                if (nn.c <= SOLVE_MAX)
                     B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 0});
                 else big.push_back(j);
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
+            size_t ohn = B.nn.size();
+            B.nn.insert(B.nn.end(), hnn.begin(), hnn.end());
+            emit(L_NN, ohn, hnn.size(), 0);
             emit_hsolve(big, false, acts);
             emit_acts(acts);
             size_t o2 = B.tn.size(), o3 = B.nn.size();
@@ -2308,20 +2403,24 @@ struct EngineT final : EngineImpl {
             emit(L_NN, o3, nnb.size(), 0);
             std::vector<std::vector<Act>> acts;
             std::vector<int> big;
-            for (int j : S.level_nodes[l]) {
-                const NodeRT& nn = nd[j];
-                if (!nn.hier && nn.c <= SOLVE_MAX) continue;
-                big.push_back(j);
-            }
-            emit_hsolve(big, true, acts);
-            emit_acts(acts);
+            std::vector<NnTask> hnn;
+            size_t oh = B.tn.size();
+            for (int j : S.level_nodes[l])
+                if (nd[j].hier) hier_terms(j, true, B.tn, hnn);
+            emit(L_TN, oh, B.tn.size() - oh, 0);
             size_t o = B.trsv.size();
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
-                if (!nn.hier && nn.c <= SOLVE_MAX)
-                    B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 1});
+                if (nn.hier) hier_leaves(j, true);
+                else if (nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 1});
+                else big.push_back(j);
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
+            size_t ohn = B.nn.size();
+            B.nn.insert(B.nn.end(), hnn.begin(), hnn.end());
+            emit(L_NN, ohn, hnn.size(), 0);
+            emit_hsolve(big, true, acts);
+            emit_acts(acts);
         }
         emit(L_PERM_OUT, 0, 1, 0);
         if (zcur > tmp_dev + std::max<long long>(tmp_total, 1)) throw Error(RSC_ERR_CUDA, "solve scratch overflow");
@@ -2329,6 +2428,24 @@ struct EngineT final : EngineImpl {
         for (auto& h : HT) h.acts = d_hacts_all + (intptr_t)h.acts;
         d_hs_all = smem_plan.upload(HT, stream);
         d_trsv_all = smem_plan.upload(B.trsv, stream);
+        {   // vector TN tasks longer than TN1_SPLIT_ROWS rows: rows split over CTAs (per launch)
+            long long npart = 0, ncnt = 0;
+            for (auto& t : B.tn)
+                if (t.nrow > TN1_SPLIT_ROWS) { npart += (long long)cdiv(t.nrow, TN1_SPLIT_ROWS) * TN_COLS; ++ncnt; }
+            T* part = npart ? (T*)smem_plan.alloc(sizeof(T) * npart) : nullptr;
+            unsigned* cnt = ncnt ? (unsigned*)smem_plan.alloc(sizeof(unsigned) * ncnt) : nullptr;
+            if (ncnt) CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * ncnt, stream));
+            for (auto& t : B.tn)
+                if (t.nrow > TN1_SPLIT_ROWS) {
+                    t.nsplit = cdiv(t.nrow, TN1_SPLIT_ROWS);
+                    t.rps = TN1_SPLIT_ROWS;
+                    t.part = part; part += (size_t)t.nsplit * TN_COLS;
+                    t.cnt = cnt++;
+                }
+            for (Launch& L : seq)
+                if (L.kind == L_TN)
+                    for (int i = 0; i < L.count; ++i) L.flag = std::max(L.flag, B.tn[L.off + i].nsplit);
+        }
         d_tn_all = smem_plan.upload(B.tn, stream);
         d_nn_all = smem_plan.upload(B.nn, stream);
         for (auto& t : B.tn) apply_flops += 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0);
@@ -2354,7 +2471,10 @@ struct EngineT final : EngineImpl {
                 case L_PERM_IN: PROF(P, "ap_perm", s, 0, 0, k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(g_in, d_perm, y_dev, n)); break;
                 case L_PERM_OUT: PROF(P, "ap_perm", s, 0, 0, k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, g_out, n)); break;
                 case L_TRSV: PROF(P, "ap_trsv", s, 0, 0, k_trsv<T, 1><<<L.count, 256, 0, s>>>(d_trsv_all + L.off)); break;
-                case L_TN: PROF(P, "ap_tn", s, 0, 0, k_tn1<T><<<L.count, 256, 0, s>>>(d_tn_all + L.off)); break;
+                case L_TN:
+                    PROF(P, "ap_tn", s, 0, 0,
+                         k_tn1<T><<<dim3(L.count, 1, std::max(L.flag, 1)), 256, 0, s>>>(d_tn_all + L.off));
+                    break;
                 case L_NN: PROF(P, "ap_nn", s, 0, 0, k_nn<T><<<L.count, NN_ROWS, 0, s>>>(d_nn_all + L.off)); break;
                 case L_HSOLVE:
                     PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 1><<<L.count, HS_THREADS, hs_smem(L.flag, 1), s>>>(d_hs_all + L.off));

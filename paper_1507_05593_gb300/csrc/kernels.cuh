@@ -391,20 +391,27 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     if (threadIdx.x == 0) tk.cnt[blockIdx.y] = 0u;
 }
 
-// Vector form of k_tn (N = 1): one CTA per (task, 32-column tile), a warp per column,
-// lanes down the rows (coalesced column reads of A).
+// Vector form of k_tn (N = 1): one CTA per (task, 32-column tile, row split), a warp per
+// column, lanes down the rows (coalesced column reads).  With tk.nsplit > 1, CTA z sums rows
+// [z rps, (z + 1) rps) into part[z][32] and the last CTA to arrive adds the partial sums in
+// ascending z (deterministic) and resets its counter.
 template <class T>
 __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
+    __shared__ int last;
     const TnTask tk = tasks[blockIdx.x];
+    if ((int)blockIdx.z >= tk.nsplit) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rb = (int)blockIdx.z * tk.rps;
+    const int re = tk.nsplit > 1 ? min(tk.nrow, rb + tk.rps) : tk.nrow;
     const T* Y = (const T*)tk.Y;
+    T* part = (T*)tk.part;
     for (int tt = warp; tt < TN_COLS; tt += 8) {
         const int t = tk.t0 + tt;
         if (t >= tk.K) break;
         const T* A = (const T*)tk.A + (size_t)t * tk.lda;
         T acc = T(0);
 #pragma unroll 4
-        for (int i = lane; i < tk.nrow; i += 32) {
+        for (int i = rb + lane; i < re; i += 32) {
             const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
             const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
             acc = fma(A[ar], Y[(size_t)yr * tk.ldy], acc);
@@ -412,10 +419,28 @@ __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
-            T* z = (T*)tk.Z + (size_t)t * tk.ldz;
-            *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc : (T)tk.alpha * acc;
+            if (tk.nsplit == 1) {
+                T* z = (T*)tk.Z + (size_t)t * tk.ldz;
+                *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc : (T)tk.alpha * acc;
+            } else {
+                part[(size_t)blockIdx.z * TN_COLS + tt] = acc;
+            }
         }
     }
+    if (tk.nsplit == 1) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(tk.cnt, 1u) == (unsigned)(tk.nsplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < TN_COLS && tk.t0 + (int)threadIdx.x < tk.K) {
+        T acc = T(0);
+        for (int zz = 0; zz < tk.nsplit; ++zz) acc += __ldcg(part + (size_t)zz * TN_COLS + threadIdx.x);
+        T* z = (T*)tk.Z + (size_t)(tk.t0 + threadIdx.x) * tk.ldz;
+        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc : (T)tk.alpha * acc;
+    }
+    if (threadIdx.x == 0) *tk.cnt = 0u;
 }
 
 // One CTA of 128 threads per (task, 128-row chunk, 16-column chunk); a thread owns one
@@ -574,33 +599,42 @@ template <class T, int CW>
 __device__ __forceinline__ void trmv_inv(const T* __restrict__ Li, int c, T* Xb, T* Zs, bool transpose) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (!transpose) {
-        for (int i = warp; i < c; i += blockDim.x >> 5) {
-            T acc[CW];
+        // a warp takes four rows at a time (their loads are independent)
+        const int nw = blockDim.x >> 5;
+        for (int i0 = 4 * warp; i0 < c; i0 += 4 * nw) {
+            T acc[4][CW];
 #pragma unroll
-            for (int q = 0; q < CW; ++q) acc[q] = T(0);
-            const T* row = Li + (size_t)i * c;
-            for (int kk = lane; kk <= i; kk += 32) {
-                const T v = row[kk];
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int q = 0; q < CW; ++q) acc[q] = fma(v, Xb[(size_t)kk * CW + q], acc[q]);
+                for (int q = 0; q < CW; ++q) acc[r][q] = T(0);
+            const int iend = min(c - 1, i0 + 3);
+            for (int kk = lane; kk <= iend; kk += 32) {
+                T v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = (i0 + r <= iend && kk <= i0 + r) ? Li[(size_t)(i0 + r) * c + kk] : T(0);
+#pragma unroll
+                for (int q = 0; q < CW; ++q) {
+                    const T xq = Xb[(size_t)kk * CW + q];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][q] = fma(v[r], xq, acc[r][q]);
+                }
             }
 #pragma unroll
-            for (int q = 0; q < CW; ++q) {
-                T v = acc[q];
+            for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                acc[q] = v;
-            }
-            if (lane == 0) {
+                for (int q = 0; q < CW; ++q) {
+                    T v = acc[r][q];
 #pragma unroll
-                for (int q = 0; q < CW; ++q) Zs[(size_t)i * CW + q] = acc[q];
-            }
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && i0 + r <= iend) Zs[(size_t)(i0 + r) * CW + q] = v;
+                }
         }
     } else {
         for (int i = tid; i < c; i += blockDim.x) {
             T acc[CW];
 #pragma unroll
             for (int q = 0; q < CW; ++q) acc[q] = T(0);
+#pragma unroll 8
             for (int kk = i; kk < c; ++kk) {
                 const T v = Li[(size_t)kk * c + i];
 #pragma unroll
@@ -660,8 +694,10 @@ __global__ void __launch_bounds__(HS_THREADS) k_hsolve(const HTask* __restrict__
         Xs[e] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
     }
     __syncthreads();
+    HAct nxt = tk.nact > 0 ? tk.acts[0] : HAct{};
     for (long long ai = 0; ai < tk.nact; ++ai) {
-        const HAct a = tk.acts[ai];
+        const HAct a = nxt;                       // the next record is fetched while this one runs
+        if (ai + 1 < tk.nact) nxt = tk.acts[ai + 1];
         if (a.type == HA_TRSV) {
             trmv_inv<T, CW>((const T*)a.A1, a.no, Xs + (size_t)a.o0 * CW, Zs, tk.transpose != 0);
         } else if (a.type == HA_LR || a.type == HA_GEMVT) {
@@ -675,6 +711,7 @@ __global__ void __launch_bounds__(HS_THREADS) k_hsolve(const HTask* __restrict__
 #pragma unroll
                     for (int q = 0; q < CW; ++q) acc[q] = T(0);
                     const T* col = A1 + (size_t)(t0 + t) * a.lda1;
+#pragma unroll 4
                     for (int i = lane; i < a.ni; i += 32) {
                         const T v = col[i];
 #pragma unroll
@@ -703,6 +740,7 @@ __global__ void __launch_bounds__(HS_THREADS) k_hsolve(const HTask* __restrict__
                         T acc[CW];
 #pragma unroll
                         for (int q = 0; q < CW; ++q) acc[q] = T(0);
+#pragma unroll 8
                         for (int t = 0; t < kt; ++t) {
                             const T v = A2[i + (size_t)(t0 + t) * a.lda2];
 #pragma unroll
@@ -720,6 +758,7 @@ __global__ void __launch_bounds__(HS_THREADS) k_hsolve(const HTask* __restrict__
                 T acc[CW];
 #pragma unroll
                 for (int q = 0; q < CW; ++q) acc[q] = T(0);
+#pragma unroll 8
                 for (int t = 0; t < a.K; ++t) {
                     const T v = A2[i + (size_t)t * a.lda2];
 #pragma unroll
