@@ -1513,6 +1513,46 @@ struct EngineT final : EngineImpl {
     const LoOp& lo(int k) const { return h_lo[k]; }
 
     // Alg. 2 transposed: W (c x N) = (L^O_j)^T G, G (r x N); row-major, ld N.
+    // X (c x N, row-major ld ldx) <- (L^D_j)^{-1} X or (L^D_j)^{-T} X for a hierarchical diagonal
+    // block whose inverse factors tU_s, tV_s are formed: stage 1 the products with the input
+    // (z_s = tU_s^T X[cols(s)], or tV_s^T X[rows(s)]), stage 2 the leaf inverses in place and
+    // then X[rows(s)] -= tV_s z_s (or X[cols(s)] -= tU_s z_s), atomic over nested blocks.
+    bool inverse_ready(int j) const {
+        const NodeRT& n = nd[j];
+        if (!n.hier) return false;
+        const BlockTree& t = S.tree[j];
+        for (int b = 1; b <= t.nblocks; ++b)
+            if (!t.leaf[b] && n.brank[b] > 0 && !n.tU[b]) return false;
+        return true;
+    }
+    void prog_diag_solve_inv(Program& P, int j, T* X, int ldx, int N, bool transpose) {
+        const NodeRT& n = nd[j];
+        const BlockTree& t = S.tree[j];
+        std::vector<T*> zb(t.nblocks + 1, nullptr);
+        Stage& st1 = next(P);
+        for (int b = 1; b <= t.nblocks; ++b) {
+            const int q = n.brank[b];
+            if (t.leaf[b] || q == 0) continue;
+            const int n1 = t.mid[b] - t.lo[b], n2 = t.hi[b] - t.mid[b];
+            zb[b] = wsT((size_t)q * N);
+            if (!transpose) add_tn(st1, tn_task(n.tU[b], n1, q, n1, nullptr, 0, nullptr, t.lo[b], X, ldx, zb[b], N, N));
+            else add_tn(st1, tn_task(n.tV[b], n2, q, n2, nullptr, 0, nullptr, t.mid[b], X, ldx, zb[b], N, N));
+        }
+        Stage& st2 = next(P);
+        for (int b = 1; b <= t.nblocks; ++b) {
+            if (t.leaf[b]) {
+                const int sz = t.hi[b] - t.lo[b];
+                add_trsv(st2, invs + n.leaf_inv[b], sz, sz, X + (size_t)t.lo[b] * ldx, ldx, N, transpose);
+                continue;
+            }
+            const int q = n.brank[b];
+            if (q == 0) continue;
+            const int n1 = t.mid[b] - t.lo[b], n2 = t.hi[b] - t.mid[b];
+            if (!transpose) add_nn(st2, nn_task(n.tV[b], n2, q, n2, nullptr, 0, nullptr, t.mid[b], zb[b], N, X, ldx, N, -1.0, true));
+            else add_nn(st2, nn_task(n.tU[b], n1, q, n1, nullptr, 0, nullptr, t.lo[b], zb[b], N, X, ldx, N, -1.0, true));
+        }
+    }
+
     void prog_offdiag_T(Program& P, int j, const T* G, int N, T* W) {
         const NodeRT& n = nd[j];
         Stage& st = next(P);
@@ -1529,14 +1569,16 @@ struct EngineT final : EngineImpl {
             add_nn(st, nn_task(op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0, (int)-n.c0, Z, N,
                                W, N, N, -1.0, true));
         }
-        prog_diag_solve(P, j, 0, W, N, N, false);
+        if (inverse_ready(j)) prog_diag_solve_inv(P, j, W, N, N, false);
+        else prog_diag_solve(P, j, 0, W, N, N, false);
     }
 
     // Alg. 2: W (r x N) = L^O_j X, X (c x N); Xp (c x N) is scratch.
     void prog_offdiag(Program& P, int j, const T* X, int N, T* W, T* Xp) {
         const NodeRT& n = nd[j];
         add_copy(next(P), X, N, 1, Xp, N, 1, n.c, N);
-        prog_diag_solve(P, j, 0, Xp, N, N, true);
+        if (inverse_ready(j)) prog_diag_solve_inv(P, j, Xp, N, N, true);
+        else prog_diag_solve(P, j, 0, Xp, N, N, true);
         Stage& st = next(P);
         add_csr(st, n.aR, Xp, N, W, N, N);
         int di = 0;
