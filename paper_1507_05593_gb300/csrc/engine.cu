@@ -1736,6 +1736,10 @@ struct EngineT final : EngineImpl {
         }
         const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         std::vector<int2> chunks;
+        bool small = true;   // every block in at most RFP_SMALL chunks: the pass kernel's small-block mode
+        for (RF& r : R)
+            if (std::min(r.m, r.c) > 0 && cdiv(r.c, RFP_ROWS) > RFP_SMALL) small = false;
+        const int halves = small ? 2 : 1;
         for (size_t i = 0; i < R.size(); ++i) {
             RF& r = R[i];
             r.maxr = std::min(r.m, r.c);
@@ -1754,8 +1758,8 @@ struct EngineT final : EngineImpl {
             const int nchunk = r.active ? cdiv(r.c, RFP_ROWS) : 0;
             d.U = r.U; d.Y = r.Y;
             d.Z = wsT((size_t)std::max(r.maxr, 1) * 16);
-            d.zpart = wsT((size_t)std::max(nchunk * r.maxr, 1) * 16);
-            d.gpart = wsT((size_t)std::max(nchunk, 1) * 256);
+            d.zpart = wsT((size_t)std::max(halves * nchunk * r.maxr, 1) * 16);
+            d.gpart = wsT((size_t)std::max(halves * nchunk, 1) * 256);
             d.rinv = wsT(272);
             d.c = r.c; d.maxr = r.maxr; d.nchunk = nchunk;
             d.tol = r.tol; d.u = u;
@@ -1832,7 +1836,8 @@ struct EngineT final : EngineImpl {
             int* err = d_status + 1;
             int nrf_ = nrf, nch_ = nch;
             unsigned long long* ptime = prof.on ? d_rfp_time : nullptr;
-            void* args[] = {&d_rfd, &d_pp, &nrf_, &d_chunks, &nch_, &bar, &err, &ptime};
+            int small_ = small ? 1 : 0;
+            void* args[] = {&d_rfd, &d_pp, &nrf_, &d_chunks, &nch_, &bar, &err, &ptime, &small_};
             PROF(prof, "rf_pass", stream, 0, 0,
                  CK(cudaLaunchCooperativeKernel((const void*)k_rf_pass<T>, dim3(grid), dim3(RFP_THREADS), args, 0,
                                                 stream)));

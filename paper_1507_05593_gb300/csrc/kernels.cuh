@@ -85,11 +85,24 @@ __global__ void k_assemble(const double* __restrict__ val, const long long* __re
 }
 
 // ------------------------------------------------------------------ diagonal tile Cholesky (FP64)
+// 1 / sqrt(x) by Newton's method for f(y) = y^-2 - x (y <- y (3 - x y^2) / 2), two steps from
+// the single-precision estimate (about 22 correct bits -> 44 -> full double precision, within
+// a few ulp).  On this part a dependent FP64 operation takes about 64 cycles, the library's
+// FP64 square root about 690 and division about 440, so the pivot's square root and
+// reciprocal come from these six operations.  Outside the float range the library is used.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf((float)x);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
+
 // Cholesky of one nb x nb (nb <= 64) diagonal tile in FP64, lower triangle in place, in
-// shared memory (right-looking).  Thread 0 forms the pivot and its reciprocal (one division
-// per column: an FP64 division costs hundreds of cycles on this part); the column is scaled by
-// multiplication, and the trailing update runs warps over columns, lanes down the rows of
-// each column's lower part (no index division).
+// shared memory (right-looking).  Thread 0 forms the pivot's square root and reciprocal
+// (rsqrt_newton); the column is scaled by multiplication, and the trailing update runs warps
+// over columns, lanes down the rows of each column's lower part (no index division).
 template <class T>
 __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict__ tasks, int* status) {
     __shared__ double s[NB][NB + 1];
@@ -108,9 +121,9 @@ __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict_
                 atomicCAS(status, 0, tk.node + 1);
                 d = 1.0;
             }
-            const double r = sqrt(d);
-            s[k][k] = r;
-            rpiv = 1.0 / r;
+            const double y = rsqrt_newton(d);
+            s[k][k] = d * y;
+            rpiv = y;
         }
         __syncthreads();
         const double ri = rpiv;

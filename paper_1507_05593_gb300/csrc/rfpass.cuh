@@ -30,6 +30,7 @@ namespace rsc {
 constexpr int RFP_ROWS = 64;             // rows per chunk
 constexpr int RFP_THREADS = 256;
 constexpr unsigned long long RFP_SPIN_LIMIT = 1ull << 22;
+constexpr int RFP_SMALL = 8;             // blocks of at most this many chunks: small-block mode
 
 template <class T>
 struct RfDev {
@@ -130,8 +131,9 @@ __device__ void rfp_tn_partial(const T* U, int c, int row0, int nr, int rank, T 
 
 // Ys -= U[chunk rows, :rank] Z  (Z: rank x 16, written by other CTAs)
 template <class T>
+// (Z may also be given as nz partial sums, zst apart, added here in ascending order.)
 __device__ void rfp_nn_update(const T* U, int c, int row0, int nr, int rank, const T* Z, T (*Ys)[17], T (*Us)[33],
-                              T (*Zs)[17]) {
+                              T (*Zs)[17], int nz = 1, size_t zst = 0) {
     const int i = threadIdx.x >> 2, cq = (threadIdx.x & 3) * 4;
     T acc[4] = {T(0), T(0), T(0), T(0)};
     T v[8], zv[2];
@@ -139,7 +141,10 @@ __device__ void rfp_nn_update(const T* U, int c, int row0, int nr, int rank, con
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int e = threadIdx.x + h * RFP_THREADS, kk = e >> 4, col = e & 15;
-            zv[h] = kk < kn ? __ldcg(Z + (size_t)(k0 + kk) * 16 + col) : T(0);
+            T a = T(0);
+            if (kk < kn)
+                for (int q = 0; q < nz; ++q) a += __ldcg(Z + q * zst + (size_t)(k0 + kk) * 16 + col);
+            zv[h] = a;
         }
     };
     rfp_fetch_u(U, c, row0, nr, 0, min(32, rank), v);
@@ -183,9 +188,9 @@ __device__ __forceinline__ void rfp_gram_partial(T (*Ys)[17], T* out) {
 // Ys[:, :b] <- Ys[:, :b] R^{-1} by forward substitution along each row (thread per row);
 // rf holds R (row-major 16 x 16) and the reciprocal diagonal (zero for a dropped column).
 template <class T>
-__device__ void rfp_apply_rsolve(const T* rf, int b, T (*Ys)[17], T (*Gs)[17], T* rd) {
-    for (int e = threadIdx.x; e < 256; e += RFP_THREADS) Gs[e >> 4][e & 15] = __ldcg(rf + e);
-    if (threadIdx.x < 16) rd[threadIdx.x] = __ldcg(rf + 256 + threadIdx.x);
+__device__ void rfp_apply_rsolve(const T* rf, int b, T (*Ys)[17], T (*Gs)[17], T* rd, bool shared_src = false) {
+    for (int e = threadIdx.x; e < 256; e += RFP_THREADS) Gs[e >> 4][e & 15] = shared_src ? rf[e] : __ldcg(rf + e);
+    if (threadIdx.x < 16) rd[threadIdx.x] = shared_src ? rf[256 + threadIdx.x] : __ldcg(rf + 256 + threadIdx.x);
     __syncthreads();
     if (threadIdx.x < RFP_ROWS) {
         const int i = threadIdx.x;
@@ -255,9 +260,9 @@ __device__ bool rfp_chol(T (*G)[17], int b, double coef, double delta, T* out) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(RFP_THREADS) k_rf_pass(RfDev<T>* rf, const RfPass<T>* __restrict__ ps, int nrf,
+__global__ void __launch_bounds__(RFP_THREADS, 2) k_rf_pass(RfDev<T>* rf, const RfPass<T>* __restrict__ ps, int nrf,
                                                          const int2* __restrict__ chunks, int nchunks, RfBarrier* bar,
-                                                         int* err, unsigned long long* ptime) {
+                                                         int* err, unsigned long long* ptime, int small) {
     __shared__ T Ys[RFP_ROWS][17];
     __shared__ T Us[RFP_ROWS][33];
     __shared__ T Zs[32][17];
@@ -372,6 +377,201 @@ __global__ void __launch_bounds__(RFP_THREADS) k_rf_pass(RfDev<T>* rf, const RfP
         Gs[tid >> 4][tid & 15] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
         __syncthreads();
     };
+
+    if (small) {
+        // ------------------------------------------------------------ small blocks (nchunk <= RFP_SMALL)
+        // Every CTA adds the few partial sums it needs itself (Z of a projection, the Gram
+        // matrix) and factors the 16 x 16 Gram matrix of its block redundantly, so that the
+        // reduction and Cholesky phases disappear; the partial buffers alternate between two
+        // halves so that a phase never overwrites what another CTA of the same phase reads.
+        // All CTAs of a block reduce the same values in the same order, so their decisions
+        // agree; the CTA of chunk 0 records them.
+        auto zp = [&](const RfDev<T>& R, int h) { return R.zpart + (size_t)h * R.nchunk * R.maxr * 16; };
+        auto gp = [&](const RfDev<T>& R, int h) { return R.gpart + (size_t)h * R.nchunk * 256; };
+        auto gram_all = [&](const RfDev<T>& R, int h) {        // Gram matrix from the partials into Gs
+            T a = T(0);
+            for (int q = 0; q < R.nchunk; ++q) a += __ldcg(gp(R, h) + (size_t)q * 256 + tid);
+            Gs[tid >> 4][tid & 15] = a;
+            __syncthreads();
+        };
+        // A: samples into Y; first pass: Gram partials (half 0); U^T Y partials (half 0)
+        for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
+            const int r = chunks[g].x, q = chunks[g].y;
+            if (!live(r)) continue;
+            const RfDev<T>& R = rf[r];
+            const int row0 = q * RFP_ROWS, nr = min(RFP_ROWS, R.c - row0);
+            const RfPass<T> p = ps[r];
+            for (int e = tid; e < RFP_ROWS * 16; e += RFP_THREADS) {
+                const int i = e >> 4, col = e & 15;
+                const T v = i < nr ? p.Yb[(size_t)(row0 + i) * p.ldyb + col] : T(0);
+                Ys[i][col] = v;
+                if (i < nr) R.Y[(size_t)(row0 + i) * 16 + col] = v;
+            }
+            __syncthreads();
+            if (p.first) rfp_gram_partial(Ys, gp(R, 0) + (size_t)q * 256);
+            const int rank = rfp_ld(&R.rank);
+            if (rank > 0) rfp_tn_partial(R.U, R.c, row0, nr, rank, Ys, Us, zp(R, 0) + (size_t)q * R.maxr * 16);
+            __syncthreads();
+        }
+        if (!sync(0)) return;
+        // C: Y -= U Z (half 0); U^T Y partials (half 1)
+        for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
+            const int r = chunks[g].x, q = chunks[g].y;
+            if (!live(r)) continue;
+            const RfDev<T>& R = rf[r];
+            const int rank = rfp_ld(&R.rank);
+            if (rank == 0) continue;
+            const int row0 = q * RFP_ROWS, nr = min(RFP_ROWS, R.c - row0);
+            load_y(R, row0, nr);
+            rfp_nn_update(R.U, R.c, row0, nr, rank, zp(R, 0), Ys, Us, Zs, R.nchunk, (size_t)R.maxr * 16);
+            store_y(R, row0, nr);
+            rfp_tn_partial(R.U, R.c, row0, nr, rank, Ys, Us, zp(R, 1) + (size_t)q * R.maxr * 16);
+        }
+        if (!sync(2)) return;
+        // E: Y -= U Z (half 1); Gram partials (half 1)
+        for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
+            const int r = chunks[g].x, q = chunks[g].y;
+            if (!live(r)) continue;
+            const RfDev<T>& R = rf[r];
+            const int rank = rfp_ld(&R.rank);
+            const int row0 = q * RFP_ROWS, nr = min(RFP_ROWS, R.c - row0);
+            load_y(R, row0, nr);
+            if (rank > 0) {
+                rfp_nn_update(R.U, R.c, row0, nr, rank, zp(R, 1), Ys, Us, Zs, R.nchunk, (size_t)R.maxr * 16);
+                store_y(R, row0, nr);
+            }
+            rfp_gram_partial(Ys, gp(R, 1) + (size_t)q * 256);
+            __syncthreads();
+        }
+        if (!sync(4)) return;
+        // G: stopping test, shifted Cholesky, Y <- Y R^{-1}, U^T Y partials (half 0)
+        __shared__ T Rl[272];
+        __shared__ int go_s;
+        __shared__ double y1_s;
+        for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
+            const int r = chunks[g].x, q = chunks[g].y;
+            if (!live(r)) continue;
+            RfDev<T>& R = rf[r];
+            const int rank = rfp_ld(&R.rank);
+            const int row0 = q * RFP_ROWS, nr = min(RFP_ROWS, R.c - row0);
+            const bool first = ps[r].first != 0;
+            double y1 = 0.0;
+            if (first) {            // ||Y_1||^2 = trace of the first pass's Gram matrix (half 0)
+                gram_all(R, 0);
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int a = 0; a < 16; ++a) t += (double)Gs[a][a];
+                    y1_s = sqrt(t);
+                    if (q == 0) R.y1 = y1_s;
+                }
+                __syncthreads();
+                y1 = y1_s;
+            } else {
+                y1 = __ldcg(&R.y1);
+            }
+            gram_all(R, 1);
+            if (tid < 32) {
+                double t = 0.0;
+                for (int a = 0; a < 16; ++a) t += (double)Gs[a][a];
+                const double nrm = sqrt(t);
+                int go = 1, b = 0;
+                if (!isfinite(nrm) || !isfinite(y1)) {
+                    go = 0;
+                    if (tid == 0) atomicCAS(err + 1, 0, 1);
+                } else if (nrm <= R.tol * y1) {
+                    go = 0;
+                } else {
+                    b = min(16, R.maxr - rank);
+                    const double coef = 11.0 * ((double)R.c * b + (double)b * (b + 1)) * R.u;
+                    const bool bad = rfp_chol(Gs, b, coef, 4.0 * max(R.c, 16) * R.u, Rl);
+                    if (tid == 0 && q == 0) R.bad = bad ? 1 : 0;
+                }
+                if (tid == 0) {
+                    go_s = go ? b : 0;
+                    if (q == 0) {
+                        R.b = b;
+                        if (!go) R.active = 0;
+                    }
+                }
+            }
+            __syncthreads();
+            const int b = go_s;
+            if (b == 0) continue;
+            load_y(R, row0, nr);
+            rfp_apply_rsolve(Rl, b, Ys, Gs, rd_s, true);
+            store_y(R, row0, nr);
+            if (rank > 0) rfp_tn_partial(R.U, R.c, row0, nr, rank, Ys, Us, zp(R, 0) + (size_t)q * R.maxr * 16);
+        }
+        if (!sync(5)) return;
+        // I: Y -= U Z (half 0); Gram partials (half 0)
+        for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
+            const int r = chunks[g].x, q = chunks[g].y;
+            if (!live(r)) continue;
+            const RfDev<T>& R = rf[r];
+            const int rank = rfp_ld(&R.rank);
+            const int row0 = q * RFP_ROWS, nr = min(RFP_ROWS, R.c - row0);
+            load_y(R, row0, nr);
+            if (rank > 0) {
+                rfp_nn_update(R.U, R.c, row0, nr, rank, zp(R, 0), Ys, Us, Zs, R.nchunk, (size_t)R.maxr * 16);
+                store_y(R, row0, nr);
+            }
+            rfp_gram_partial(Ys, gp(R, 0) + (size_t)q * 256);
+            __syncthreads();
+        }
+        // JK, LM: Cholesky of the Gram matrix, Y <- Y R^{-1}, then Gram partials or the append
+        for (int pass = 0; pass < 2; ++pass) {
+            if (!sync(8 + 2 * pass)) return;
+            for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
+                const int r = chunks[g].x, q = chunks[g].y;
+                if (!live(r)) continue;
+                RfDev<T>& R = rf[r];
+                const int b = rfp_ld(&R.b);
+                const int row0 = q * RFP_ROWS, nr = min(RFP_ROWS, R.c - row0);
+                gram_all(R, pass == 0 ? 0 : 1);
+                if (tid < 32) {
+                    const bool bad = rfp_chol(Gs, b, 0.0, 4.0 * max(R.c, 16) * R.u, Rl);
+                    if (tid == 0 && q == 0 && bad) R.bad = 1;
+                }
+                __syncthreads();
+                load_y(R, row0, nr);
+                rfp_apply_rsolve(Rl, b, Ys, Gs, rd_s, true);
+                store_y(R, row0, nr);
+                if (pass == 0) {
+                    rfp_gram_partial(Ys, gp(R, 1) + (size_t)q * 256);
+                } else {   // kept columns (nonzero 1 / R_kk) appended in order; chunk 0 keeps R for the commit
+                    const int rank = rfp_ld(&R.rank);
+                    unsigned keep = 0;
+                    for (int col = 0; col < b; ++col) keep |= (rd_s[col] != T(0) ? 1u : 0u) << col;
+                    for (int e = tid; e < RFP_ROWS * 16; e += RFP_THREADS) {
+                        const int i = e % RFP_ROWS, col = e / RFP_ROWS;
+                        if (i < nr && col < b && ((keep >> col) & 1u)) {
+                            const int pos = __popc(keep & ((1u << col) - 1u));
+                            R.U[(size_t)(rank + pos) * R.c + row0 + i] = Ys[i][col];
+                        }
+                    }
+                    if (q == 0)
+                        for (int e = tid; e < 272; e += RFP_THREADS) R.rinv[e] = Rl[e];
+                }
+                __syncthreads();
+            }
+        }
+        if (!sync(12)) return;
+        for (int r = blockIdx.x; r < nrf; r += gridDim.x) {
+            if (tid != 0 || !live(r)) continue;
+            RfDev<T>& R = rf[r];
+            const int b = rfp_ld(&R.b);
+            int kept = 0;
+            for (int col = 0; col < b; ++col) kept += __ldcg(R.rinv + 256 + col) != T(0);
+            if (rfp_ld(&R.bad) || kept == 0) {
+                R.active = 0;
+            } else {
+                const int rank = rfp_ld(&R.rank) + kept;
+                R.rank = rank;
+                if (rank >= R.maxr) R.active = 0;
+            }
+        }
+        return;
+    }
 
     // A: Y <- this pass's samples; Gram partials on the first pass (for ||Y_1||); U^T Y partials
     for (int g = blockIdx.x; g < nchunks; g += gridDim.x) {
