@@ -186,6 +186,11 @@ struct EngineImpl {
     virtual rsc_status factor(const double* val, double tol) = 0;
     virtual bool factored() const = 0;
     virtual void apply(const double* d_r, double* d_z, cudaStream_t s) = 0;
+    virtual void prepare_multi(int) {}
+    virtual void apply_multi(const double* d_r, double* d_z, int nrhs, cudaStream_t s) {
+        for (int c = 0; c < nrhs; ++c) apply(d_r + (size_t)c * n_of(), d_z + (size_t)c * n_of(), s);
+    }
+    virtual long long n_of() const = 0;
     virtual void node_info(int j, int32_t* info) const = 0;
     virtual rsc_status node_blocks(int j, double* LD, double* LO) = 0;
     virtual void stats(rsc_stats_t* out) const = 0;
@@ -361,9 +366,8 @@ rsc_status EngineImpl::pcg_batch(const std::vector<int64_t>& rp, const std::vect
         k_spmv_multi<<<dim3((unsigned)cdiv(n * 8, 256), (unsigned)nrhs), 256, 0, s>>>(n, d_rp, d_ci, d_val, X, Y);
         launches++;
     };
-    auto precond = [&](const double* Rv, double* Zv) {
-        for (int c = 0; c < nrhs; ++c) apply(Rv + (size_t)c * n, Zv + (size_t)c * n, s);
-    };
+    auto precond = [&](const double* Rv, double* Zv) { apply_multi(Rv, Zv, nrhs, s); };
+    prepare_multi(nrhs);   // the N-column launch list, built once per factorization
     double* d_alpha = sc + np;
     double* d_beta = sc + 2 * np;
     cudaEvent_t e0, e1;
@@ -706,7 +710,8 @@ struct EngineT final : EngineImpl {
         nd.resize(S.M);
     }
     ~EngineT() override {
-        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        plan1.clear();
+        planN.clear();
         if (arena_base) cudaFree(arena_base);
         if (arena_host) cudaFreeHost(arena_host);
         if (rf_host) cudaFreeHost(rf_host);
@@ -2203,19 +2208,35 @@ struct EngineT final : EngineImpl {
     // It is captured once into a CUDA graph reading g_in and writing g_out.
     enum LKind { L_PERM_IN, L_PERM_OUT, L_TRSV, L_TN, L_NN, L_HSOLVE };
     struct Launch { int kind; int count; size_t off; int flag; };
-    HTask* d_hs_all = nullptr;
-    HAct* d_hacts_all = nullptr;
-    std::vector<Launch> seq;
-    DeviceMem smem_plan;
-    T* y_dev = nullptr;
-    T* tmp_dev = nullptr;
-    double* g_in = nullptr;
-    double* g_out = nullptr;
-    TrsvTask* d_trsv_all = nullptr;
-    TnTask* d_tn_all = nullptr;
-    NnTask* d_nn_all = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    double apply_flops = 0, apply_bytes = 0;
+    // one launch list (and its CUDA graph) per number of right-hand sides: plan1 for the PCG of
+    // one system, planN for the batched PCG (N columns of y, row-major)
+    struct ApplyPlan {
+        int N = 1;
+        std::vector<Launch> seq;
+        DeviceMem mem;
+        T* y = nullptr;
+        T* tmp = nullptr;
+        double* gin = nullptr;
+        double* gout = nullptr;
+        HTask* hs = nullptr;
+        HAct* hacts = nullptr;
+        TrsvTask* trsv = nullptr;
+        TnTask* tn = nullptr;
+        NnTask* nn = nullptr;
+        cudaGraphExec_t graph = nullptr;
+        long long gen = -1;              // factorization the plan was built for
+        double flops = 0, bytes = 0;
+        void clear() {
+            if (graph) cudaGraphExecDestroy(graph);
+            graph = nullptr;
+            mem.release();
+            seq.clear();
+            flops = bytes = 0;
+            gen = -1;
+        }
+    };
+    ApplyPlan plan1, planN;
+    ApplyPlan* pl = &plan1;              // the plan being built
 
     struct SolveBuild {
         std::vector<TrsvTask> trsv;
@@ -2233,16 +2254,17 @@ struct EngineT final : EngineImpl {
     // vector forms on y (ld 1, one column); yoff / ymap index rows of y
     TnTask vtn(const void* A, int lda, int K, int nrow, const int32_t* ymap, int yoff, T* Z, double alpha = 1.0,
                double beta = 0.0) {
-        return tn_task(A, lda, K, nrow, nullptr, 0, ymap, yoff, y_dev, 1, Z, 1, 1, alpha, beta);
+        return tn_task(A, lda, K, nrow, nullptr, 0, ymap, yoff, pl->y, pl->N, Z, pl->N, pl->N, alpha, beta);
     }
     NnTask vnn(const void* A, int lda, int K, int nrow, const int32_t* ymap, int yoff, const T* Z, bool atomic) {
-        return nn_task(A, lda, K, nrow, nullptr, 0, ymap, yoff, Z, 1, y_dev, 1, 1, -1.0, atomic);
+        return nn_task(A, lda, K, nrow, nullptr, 0, ymap, yoff, Z, pl->N, pl->y, pl->N, pl->N, -1.0, atomic);
     }
 
     // In-order actions of one diagonal block (vector right-hand side, rows c0.. of y).
     void diag_actions(int j, bool transpose, T*& zcur, std::vector<Act>& acts) {
         const NodeRT& n = nd[j];
-        T* X = y_dev + n.c0;
+        const int N = pl->N;
+        T* X = pl->y + n.c0 * N;
         if (!n.hier) {
             const T* L = arena + n.off;
             const int ld = n.ld, c = n.c, bs = SOLVE_MAX;
@@ -2251,10 +2273,10 @@ struct EngineT final : EngineImpl {
                 const int b = transpose ? nblk - 1 - bi : bi;
                 const int b0 = b * bs, b1 = std::min(c, b0 + bs);
                 Act a;
-                a.trsv.push_back(TrsvTask{inv_block(j, b0), b1 - b0, b1 - b0, 1, X + b0, 1, transpose ? 1 : 0});
+                a.trsv.push_back(TrsvTask{inv_block(j, b0), b1 - b0, b1 - b0, N, X + (size_t)b0 * N, N, transpose ? 1 : 0});
                 if (!transpose && b1 < c)
                     push_nn_chunks(a.nn, vnn(L + b1 + (size_t)b0 * ld, ld, b1 - b0, c - b1, nullptr, (int)(n.c0 + b1),
-                                             X + b0, false));
+                                             X + (size_t)b0 * N, false));
                 if (transpose && b0 > 0)   // y[c0 : c0+b0] -= L[b0:b1, 0:b0]^T y[c0+b0 : c0+b1]
                     push_tn_chunks(a.tn, vtn(L + b0, ld, b0, b1 - b0, nullptr, (int)(n.c0 + b0), X, -1.0, 1.0));
                 acts.push_back(std::move(a));
@@ -2266,7 +2288,7 @@ struct EngineT final : EngineImpl {
             if (t.leaf[s]) {
                 Act a;
                 const int sz = t.hi[s] - t.lo[s];
-                a.trsv.push_back(TrsvTask{invs + n.leaf_inv[s], sz, sz, 1, X + t.lo[s], 1, transpose ? 1 : 0});
+                a.trsv.push_back(TrsvTask{invs + n.leaf_inv[s], sz, sz, N, X + (size_t)t.lo[s] * N, N, transpose ? 1 : 0});
                 acts.push_back(std::move(a));
                 return;
             }
@@ -2275,7 +2297,7 @@ struct EngineT final : EngineImpl {
                 if (!q) return;
                 Act a;
                 T* Z = zcur;
-                zcur += q;
+                zcur += (size_t)q * N;
                 if (!transpose) {   // X2 -= V_s (U_s^T X1)
                     push_tn_chunks(a.tn, vtn(n.bU[s], n1, q, n1, nullptr, (int)(n.c0 + t.lo[s]), Z));
                     push_nn_chunks(a.nn, vnn(n.bV[s], n2, q, n2, nullptr, (int)(n.c0 + t.mid[s]), Z, false));
@@ -2291,15 +2313,15 @@ struct EngineT final : EngineImpl {
         rec(t.root);
     }
 
-    void build_solve_plan() {
-        if (graph_exec) { cudaGraphExecDestroy(graph_exec); graph_exec = nullptr; }
-        smem_plan.release();
-        seq.clear();
-        apply_flops = apply_bytes = 0;
+    void build_solve_plan(int N = 1) {
+        pl = N == 1 ? &plan1 : &planN;
+        pl->clear();
+        pl->N = N;
+        pl->gen = factor_gen;
         const long long n = S.n;
-        y_dev = (T*)smem_plan.alloc(sizeof(T) * n);
-        g_in = (double*)smem_plan.alloc(sizeof(double) * n);
-        g_out = (double*)smem_plan.alloc(sizeof(double) * n);
+        pl->y = (T*)pl->mem.alloc(sizeof(T) * n * N);
+        pl->gin = (double*)pl->mem.alloc(sizeof(double) * n * N);
+        pl->gout = (double*)pl->mem.alloc(sizeof(double) * n * N);
         long long tmp_total = 0;
         for (int j = 0; j < S.M; ++j) {
             const NodeRT& nn = nd[j];
@@ -2307,11 +2329,12 @@ struct EngineT final : EngineImpl {
             if (nn.hier)
                 for (int b = 1; b <= S.tree[j].nblocks; ++b) tmp_total += 2 * nn.brank[b];
         }
-        tmp_dev = (T*)smem_plan.alloc(sizeof(T) * std::max<long long>(tmp_total, 1));
-        T* zcur = tmp_dev;
+        tmp_total *= N;
+        pl->tmp = (T*)pl->mem.alloc(sizeof(T) * std::max<long long>(tmp_total, 1));
+        T* zcur = pl->tmp;
         SolveBuild B;
         auto emit = [&](int kind, size_t off, size_t cnt, int flag) {
-            if (cnt) seq.push_back(Launch{kind, (int)cnt, off, flag});
+            if (cnt) pl->seq.push_back(Launch{kind, (int)cnt, off, flag});
         };
         auto emit_acts = [&](std::vector<std::vector<Act>>& per_node) {
             size_t maxa = 0;
@@ -2343,11 +2366,11 @@ struct EngineT final : EngineImpl {
                 const double keep = flops;
                 hacts(j, 0, transpose, HA);
                 flops = keep;
-                HT.push_back(HTask{(const HAct*)(intptr_t)first, (long long)HA.size() - first, y_dev + nn.c0, 1, 1, nn.c,
+                HT.push_back(HTask{(const HAct*)(intptr_t)first, (long long)HA.size() - first, pl->y + nn.c0 * N, N, N, nn.c,
                                    transpose ? 1 : 0});
                 maxc = std::max(maxc, nn.c);
             }
-            if (HT.size() > o) seq.push_back(Launch{L_HSOLVE, (int)(HT.size() - o), o, maxc});
+            if (HT.size() > o) pl->seq.push_back(Launch{L_HSOLVE, (int)(HT.size() - o), o, maxc});
         };
         emit(L_PERM_IN, 0, 1, 0);
         std::vector<std::vector<T*>> ztmp(S.nlevels);
@@ -2364,7 +2387,7 @@ struct EngineT final : EngineImpl {
                 if (t.leaf[b] || q == 0) continue;
                 const int n1 = t.mid[b] - t.lo[b], n2 = t.hi[b] - t.mid[b];
                 T*& z = hz[{j, b}];
-                if (!z) { z = zcur; zcur += q; }
+                if (!z) { z = zcur; zcur += (size_t)q * N; }
                 if (!transpose) {
                     push_tn_chunks(tn, vtn(nn.tU[b], n1, q, n1, nullptr, (int)(nn.c0 + t.lo[b]), z));
                     push_nn_chunks(nnv, vnn(nn.tV[b], n2, q, n2, nullptr, (int)(nn.c0 + t.mid[b]), z, true));
@@ -2372,7 +2395,7 @@ struct EngineT final : EngineImpl {
                     push_tn_chunks(tn, vtn(nn.tV[b], n2, q, n2, nullptr, (int)(nn.c0 + t.mid[b]), z));
                     push_nn_chunks(nnv, vnn(nn.tU[b], n1, q, n1, nullptr, (int)(nn.c0 + t.lo[b]), z, true));
                 }
-                apply_bytes += sizeof(T) * (double)q * (n1 + n2);
+                pl->bytes += sizeof(T) * (double)q * (n1 + n2);
             }
         };
         auto hier_leaves = [&](int j, bool transpose) {
@@ -2382,8 +2405,8 @@ struct EngineT final : EngineImpl {
                 if (t.leaf[b]) {
                     const int sz = t.hi[b] - t.lo[b];
                     B.trsv.push_back(
-                        TrsvTask{invs + nn.leaf_inv[b], sz, sz, 1, y_dev + nn.c0 + t.lo[b], 1, transpose ? 1 : 0});
-                    apply_bytes += sizeof(T) * (double)sz * sz;
+                        TrsvTask{invs + nn.leaf_inv[b], sz, sz, N, pl->y + (nn.c0 + t.lo[b]) * N, N, transpose ? 1 : 0});
+                    pl->bytes += sizeof(T) * (double)sz * sz;
                 }
         };
         for (int l = 0; l < S.nlevels; ++l) {
@@ -2398,9 +2421,9 @@ struct EngineT final : EngineImpl {
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 if (nn.hier) { hier_leaves(j, false); continue; }
-                apply_bytes += 2.0 * sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
+                pl->bytes += 2.0 * sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
                 if (nn.c <= SOLVE_MAX)
-                    B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 0});
+                    B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, N, pl->y + nn.c0 * N, N, 0});
                 else big.push_back(j);
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
@@ -2415,14 +2438,14 @@ struct EngineT final : EngineImpl {
                 if (nn.r == 0) continue;
                 const int32_t* Rj = d_rows + S.rows_ptr[j];
                 if (!nn.compressed) {   // y_R -= L^O_j y_C (atomic: nodes of a level share rows of R)
-                    push_nn_chunks(B.nn, vnn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, Rj, 0, y_dev + nn.c0, true));
-                    apply_bytes += 2.0 * sizeof(T) * nn.r * nn.c;
+                    push_nn_chunks(B.nn, vnn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, Rj, 0, pl->y + nn.c0 * N, true));
+                    pl->bytes += 2.0 * sizeof(T) * nn.r * nn.c;
                 } else if (nn.rank) {   // y_R -= V_j (U_j^T y_C)
-                    T* tmp = zcur; zcur += nn.rank;
+                    T* tmp = zcur; zcur += (size_t)nn.rank * N;
                     ztmp[l].push_back(tmp);
                     push_tn_chunks(B.tn, vtn(nn.U, nn.c, nn.rank, nn.c, nullptr, (int)nn.c0, tmp));
                     push_nn_chunks(B.nn, vnn(nn.V, nn.r, nn.rank, nn.r, Rj, 0, tmp, true));
-                    apply_bytes += 2.0 * sizeof(T) * nn.rank * (nn.r + nn.c);
+                    pl->bytes += 2.0 * sizeof(T) * nn.rank * (nn.r + nn.c);
                 }
             }
             emit(L_TN, o2, B.tn.size() - o2, 0);
@@ -2437,7 +2460,7 @@ struct EngineT final : EngineImpl {
                 if (nn.r == 0) continue;
                 const int32_t* Rj = d_rows + S.rows_ptr[j];
                 if (!nn.compressed) {   // y_C -= L^O_j^T y_R
-                    push_tn_chunks(B.tn, vtn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, Rj, 0, y_dev + nn.c0, -1.0, 1.0));
+                    push_tn_chunks(B.tn, vtn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, Rj, 0, pl->y + nn.c0 * N, -1.0, 1.0));
                 } else if (nn.rank) {   // y_C -= U_j (V_j^T y_R)
                     T* tmp = ztmp[l][zi++];
                     push_tn_chunks(B.tn, vtn(nn.V, nn.r, nn.rank, nn.r, Rj, 0, tmp));
@@ -2459,7 +2482,7 @@ struct EngineT final : EngineImpl {
             for (int j : S.level_nodes[l]) {
                 const NodeRT& nn = nd[j];
                 if (nn.hier) hier_leaves(j, true);
-                else if (nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, 1, y_dev + nn.c0, 1, 1});
+                else if (nn.c <= SOLVE_MAX) B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, N, pl->y + nn.c0 * N, N, 1});
                 else big.push_back(j);
             }
             emit(L_TRSV, o, B.trsv.size() - o, 0);
@@ -2470,74 +2493,122 @@ struct EngineT final : EngineImpl {
             emit_acts(acts);
         }
         emit(L_PERM_OUT, 0, 1, 0);
-        if (zcur > tmp_dev + std::max<long long>(tmp_total, 1)) throw Error(RSC_ERR_CUDA, "solve scratch overflow");
-        d_hacts_all = smem_plan.upload(HA, stream);
-        for (auto& h : HT) h.acts = d_hacts_all + (intptr_t)h.acts;
-        d_hs_all = smem_plan.upload(HT, stream);
-        d_trsv_all = smem_plan.upload(B.trsv, stream);
-        {   // vector TN tasks longer than TN1_SPLIT_ROWS rows: rows split over CTAs (per launch)
+        if (zcur > pl->tmp + std::max<long long>(tmp_total, 1)) throw Error(RSC_ERR_CUDA, "solve scratch overflow");
+        pl->hacts = pl->mem.upload(HA, stream);
+        for (auto& h : HT) h.acts = pl->hacts + (intptr_t)h.acts;
+        pl->hs = pl->mem.upload(HT, stream);
+        pl->trsv = pl->mem.upload(B.trsv, stream);
+        {   // long TN tasks: rows split over CTAs with per-task partial sums and arrival counters
+            // (kept in the plan; each counter is back at zero when its launch ends)
+            const int ych = cdiv(N, 16);
+            auto split_of = [&](const TnTask& t) {
+                if (N == 1) return t.nrow > TN1_SPLIT_ROWS ? cdiv(t.nrow, TN1_SPLIT_ROWS) : 1;
+                return t.nrow >= TN_SPLIT_MIN ? std::min(cdiv(t.nrow, TN_SPLIT_ROWS), TN_SPLIT_MAX) : 1;
+            };
             long long npart = 0, ncnt = 0;
-            for (auto& t : B.tn)
-                if (t.nrow > TN1_SPLIT_ROWS) { npart += (long long)cdiv(t.nrow, TN1_SPLIT_ROWS) * TN_COLS; ++ncnt; }
-            T* part = npart ? (T*)smem_plan.alloc(sizeof(T) * npart) : nullptr;
-            unsigned* cnt = ncnt ? (unsigned*)smem_plan.alloc(sizeof(unsigned) * ncnt) : nullptr;
+            for (auto& t : B.tn) {
+                const int ns = split_of(t);
+                if (ns > 1) { npart += (long long)ns * TN_COLS * N; ncnt += ych; }
+            }
+            T* part = npart ? (T*)pl->mem.alloc(sizeof(T) * npart) : nullptr;
+            unsigned* cnt = ncnt ? (unsigned*)pl->mem.alloc(sizeof(unsigned) * ncnt) : nullptr;
             if (ncnt) CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * ncnt, stream));
-            for (auto& t : B.tn)
-                if (t.nrow > TN1_SPLIT_ROWS) {
-                    t.nsplit = cdiv(t.nrow, TN1_SPLIT_ROWS);
-                    t.rps = TN1_SPLIT_ROWS;
-                    t.part = part; part += (size_t)t.nsplit * TN_COLS;
-                    t.cnt = cnt++;
-                }
-            for (Launch& L : seq)
+            for (auto& t : B.tn) {
+                const int ns = split_of(t);
+                if (ns == 1) continue;
+                t.nsplit = ns;
+                t.rps = cdiv(t.nrow, ns);
+                t.part = part; part += (size_t)ns * TN_COLS * N;
+                t.cnt = cnt; cnt += ych;
+            }
+            for (Launch& L : pl->seq)
                 if (L.kind == L_TN)
                     for (int i = 0; i < L.count; ++i) L.flag = std::max(L.flag, B.tn[L.off + i].nsplit);
         }
-        d_tn_all = smem_plan.upload(B.tn, stream);
-        d_nn_all = smem_plan.upload(B.nn, stream);
-        for (auto& t : B.tn) apply_flops += 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0);
-        for (auto& t : B.nn) apply_flops += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K;
-        apply_bytes += 4.0 * sizeof(T) * n + 16.0 * n;
+        pl->tn = pl->mem.upload(B.tn, stream);
+        pl->nn = pl->mem.upload(B.nn, stream);
+        for (auto& t : B.tn) pl->flops += 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0);
+        for (auto& t : B.nn) pl->flops += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K;
+        pl->bytes += (4.0 * sizeof(T) * n + 16.0 * n) * N;
         sync_stream();
         // capture the launch list once
         CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-        issue_apply(stream);
+        issue_apply(*pl, stream);
         cudaGraph_t g = nullptr;
         CK(cudaStreamEndCapture(stream, &g));
-        CK(cudaGraphInstantiate(&graph_exec, g, 0));
+        CK(cudaGraphInstantiate(&pl->graph, g, 0));
         CK(cudaGraphDestroy(g));
     }
 
     bool no_graph = std::getenv("RSC_NO_GRAPH") != nullptr;   // measurement aid: per-kernel apply profile
-    void issue_apply(cudaStream_t s, bool profiled = false) {
+    void issue_apply(const ApplyPlan& A, cudaStream_t s, bool profiled = false) {
         const long long n = S.n;
+        const int N = A.N;
         Profiler off;
         Profiler& P = profiled ? prof : off;
-        for (const Launch& L : seq) {
+        const unsigned pg = (unsigned)std::min<long long>(cdiv(n, 256), 4096);
+        for (const Launch& L : A.seq) {
             switch (L.kind) {
-                case L_PERM_IN: PROF(P, "ap_perm", s, 0, 0, k_perm_in<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(g_in, d_perm, y_dev, n)); break;
-                case L_PERM_OUT: PROF(P, "ap_perm", s, 0, 0, k_perm_out<T><<<std::min(cdiv(n, 256), 4096), 256, 0, s>>>(y_dev, d_perm, g_out, n)); break;
-                case L_TRSV: PROF(P, "ap_trsv", s, 0, 0, k_trsv<T, 1><<<L.count, 256, 0, s>>>(d_trsv_all + L.off)); break;
+                case L_PERM_IN:
+                    if (N == 1) PROF(P, "ap_perm", s, 0, 0, k_perm_in<T><<<pg, 256, 0, s>>>(A.gin, d_perm, A.y, n));
+                    else PROF(P, "ap_perm", s, 0, 0, k_perm_in_cols<T><<<dim3(pg, N), 256, 0, s>>>(A.gin, d_perm, A.y, n, N));
+                    break;
+                case L_PERM_OUT:
+                    if (N == 1) PROF(P, "ap_perm", s, 0, 0, k_perm_out<T><<<pg, 256, 0, s>>>(A.y, d_perm, A.gout, n));
+                    else PROF(P, "ap_perm", s, 0, 0, k_perm_out_cols<T><<<dim3(pg, N), 256, 0, s>>>(A.y, d_perm, A.gout, n, N));
+                    break;
+                case L_TRSV:
+                    if (N == 1) PROF(P, "ap_trsv", s, 0, 0, k_trsv<T, 1><<<L.count, 256, 0, s>>>(A.trsv + L.off));
+                    else PROF(P, "ap_trsv", s, 0, 0,
+                              k_trsv<T, TRSV_CW><<<dim3(L.count, cdiv(N, TRSV_CW)), 256, 0, s>>>(A.trsv + L.off));
+                    break;
                 case L_TN:
-                    PROF(P, "ap_tn", s, 0, 0,
-                         k_tn1<T><<<dim3(L.count, 1, std::max(L.flag, 1)), 256, 0, s>>>(d_tn_all + L.off));
+                    if (N == 1)
+                        PROF(P, "ap_tn", s, 0, 0, k_tn1<T><<<dim3(L.count, 1, std::max(L.flag, 1)), 256, 0, s>>>(A.tn + L.off));
+                    else
+                        PROF(P, "ap_tn", s, 0, 0,
+                             k_tn<T><<<dim3(L.count, cdiv(N, 16), std::max(L.flag, 1)), 256, 0, s>>>(A.tn + L.off));
                     break;
-                case L_NN: PROF(P, "ap_nn", s, 0, 0, k_nn<T><<<L.count, NN_ROWS, 0, s>>>(d_nn_all + L.off)); break;
-                case L_HSOLVE:
-                    PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 1><<<L.count, HS_THREADS, hs_smem(L.flag, 1), s>>>(d_hs_all + L.off));
+                case L_NN:
+                    PROF(P, "ap_nn", s, 0, 0, k_nn<T><<<dim3(L.count, cdiv(N, 16)), NN_ROWS, 0, s>>>(A.nn + L.off));
                     break;
+                case L_HSOLVE: {
+                    const int cw = N == 1 ? 1 : std::max(1, std::min(pick_cw(L.flag), 8));
+                    const dim3 g((unsigned)L.count, (unsigned)cdiv(N, cw));
+                    switch (cw) {
+                        case 8: PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 8><<<g, HS_THREADS, hs_smem(L.flag, 8), s>>>(A.hs + L.off)); break;
+                        case 4: PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 4><<<g, HS_THREADS, hs_smem(L.flag, 4), s>>>(A.hs + L.off)); break;
+                        case 2: PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 2><<<g, HS_THREADS, hs_smem(L.flag, 2), s>>>(A.hs + L.off)); break;
+                        default: PROF(P, "ap_hsolve", s, 0, 0, k_hsolve<T, 1><<<g, HS_THREADS, hs_smem(L.flag, 1), s>>>(A.hs + L.off)); break;
+                    }
+                    break;
+                }
             }
         }
         LAUNCH_CHECK();
     }
 
-    void apply(const double* d_r, double* d_z, cudaStream_t s) override {
-        const long long n = S.n;
-        if (d_r != g_in) CK(cudaMemcpyAsync(g_in, d_r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        if (no_graph) issue_apply(s, true);
-        else PROF(prof, "apply", s, apply_flops, apply_bytes, CK(cudaGraphLaunch(graph_exec, s)));
-        launches += (long long)seq.size();
-        if (d_z != g_out) CK(cudaMemcpyAsync(d_z, g_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    void run_plan(const ApplyPlan& A, const double* d_r, double* d_z, cudaStream_t s) {
+        const size_t bytes = sizeof(double) * S.n * A.N;
+        if (d_r != A.gin) CK(cudaMemcpyAsync(A.gin, d_r, bytes, cudaMemcpyDeviceToDevice, s));
+        if (no_graph) issue_apply(A, s, true);
+        else PROF(prof, "apply", s, A.flops, A.bytes, CK(cudaGraphLaunch(A.graph, s)));
+        launches += (long long)A.seq.size();
+        if (d_z != A.gout) CK(cudaMemcpyAsync(d_z, A.gout, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    void apply(const double* d_r, double* d_z, cudaStream_t s) override { run_plan(plan1, d_r, d_z, s); }
+    long long n_of() const override { return S.n; }
+    // nrhs right-hand sides at once (column c at d_r + c n): one pass over the factor for all
+    void prepare_multi(int nrhs) override {
+        if (nrhs > 1 && (planN.N != nrhs || planN.gen != factor_gen || !planN.graph)) {
+            build_solve_plan(nrhs);
+            pl = &plan1;
+        }
+    }
+    void apply_multi(const double* d_r, double* d_z, int nrhs, cudaStream_t s) override {
+        if (nrhs == 1) { apply(d_r, d_z, s); return; }
+        prepare_multi(nrhs);
+        run_plan(planN, d_r, d_z, s);
     }
 
     // ---------------------------------------------------------------- allocation-free apply

@@ -866,4 +866,20 @@ __global__ void k_perm_out(const T* __restrict__ y, const int32_t* __restrict__ 
         z[perm[i]] = (double)y[i];
 }
 
+// N right-hand sides: column c of r / z at offset c n, y row-major (n x N)
+template <class T>
+__global__ void k_perm_in_cols(const double* __restrict__ r, const int32_t* __restrict__ perm, T* __restrict__ y,
+                               long long n, int N) {
+    const int c = blockIdx.y;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i * N + c] = (T)r[(size_t)c * n + perm[i]];
+}
+template <class T>
+__global__ void k_perm_out_cols(const T* __restrict__ y, const int32_t* __restrict__ perm, double* __restrict__ z,
+                                long long n, int N) {
+    const int c = blockIdx.y;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        z[(size_t)c * n + perm[i]] = (double)y[i * N + c];
+}
+
 }  // namespace rsc
