@@ -702,6 +702,7 @@ struct EngineT final : EngineImpl {
         tc = sizeof(T) == 4 && o.precision == RSC_PREC_BF16;
         CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
         if (tc) CK(cudaFuncSetAttribute(k_push_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
+        CK(cudaFuncSetAttribute(k_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM_CAP));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
         hs_attr<8>();
         hs_attr<4>();
@@ -1417,6 +1418,9 @@ struct EngineT final : EngineImpl {
         return 0;
     }
     static size_t hs_smem(int c, int cw) { return (size_t)(c + HS_ZROWS) * cw * sizeof(T); }
+    // dynamic shared memory of k_leaf_factor for an sz-column leaf (block + FP64 tile)
+    static constexpr size_t LEAF_SMEM_CAP = 220 * 1024;
+    static size_t leaf_smem(int sz) { return ((size_t)sizeof(T) * sz * (sz + 1) + 15) / 16 * 16 + 64 * 65 * 8; }
     template <int CW> static void hs_attr() {
         CK(cudaFuncSetAttribute(k_hsolve<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 256));
     }
@@ -1973,12 +1977,30 @@ struct EngineT final : EngineImpl {
                     LAUNCH_CHECK();
                 }
                 std::vector<DensePanel> dp;
+                std::vector<PotrfTask> lt;
+                size_t lsm = 0;
+                bool fused = true;   // every leaf fits one CTA's shared memory: one launch for all
                 for (int j : leaves) {
                     const BlockTree& t = S.tree[j];
                     const int sz = t.hi[s] - t.lo[s];
                     dp.push_back(DensePanel{arena + nd[j].leaf_off[s], sz, sz, sz, j});
+                    lt.push_back(PotrfTask{arena + nd[j].leaf_off[s], sz, sz, j});
+                    const size_t need = leaf_smem(sz);
+                    if (sz > LEAF_FUSED_MAX || need > LEAF_SMEM_CAP) fused = false;
+                    lsm = std::max(lsm, need);
                 }
-                factor_dense_batch(dp);
+                if (fused) {
+                    double fl = 0;
+                    for (auto& x : lt) fl += (double)x.nb * x.nb * x.nb / 3.0;
+                    flops += fl;
+                    PotrfTask* dl = (PotrfTask*)upload_tmp(sTask, lt);
+                    PROF(prof, "leaf_factor", stream, fl, 0,
+                         k_leaf_factor<T><<<(int)lt.size(), 256, lsm, stream>>>(dl, d_status));
+                    launches++;
+                    LAUNCH_CHECK();
+                } else {
+                    factor_dense_batch(dp);
+                }
                 std::vector<TrsvTask> tv;
                 for (int j : leaves) {
                     const BlockTree& t = S.tree[j];

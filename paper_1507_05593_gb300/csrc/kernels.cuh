@@ -139,6 +139,93 @@ __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict_
         for (int i = j + lane; i < nb; i += 32) a[i + (size_t)j * ld] = (T)s[i][j];
 }
 
+// ------------------------------------------------------------------ whole leaf block in one CTA
+// Cholesky of one sz x sz diagonal leaf (Alg. 6's leaf blocks, sz <= LEAF_FUSED_MAX) held in
+// shared memory: per 64-column panel, the diagonal tile in FP64 (as k_potrf_tile: pivot
+// 1/sqrt by rsqrt_newton, column scaled by multiplication, trailing tile update warps over
+// columns), then the rows below by a column sweep X <- X L^-T (one barrier per column) and the
+// trailing update of the rest of the leaf, both in the storage precision T.  Replaces the
+// POTRF / TRSM / GEMM launch chain of a leaf by one launch.  S: column-major, ld sz + 1.
+constexpr int LEAF_FUSED_MAX = 192;
+template <class T>
+__device__ void leaf_tile_chol(double* D, int nb, int* status, int node, double* rp) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < nb; ++k) {
+        if (threadIdx.x == 0) {
+            double d = D[k + k * 65];
+            if (!(d > 0.0)) {            // indefinite or NaN pivot: record, keep values finite
+                atomicCAS(status, 0, node + 1);
+                d = 1.0;
+            }
+            const double y = rsqrt_newton(d);
+            D[k + k * 65] = d * y;
+            *rp = y;
+        }
+        __syncthreads();
+        const double ri = *rp;
+        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i + k * 65] *= ri;
+        __syncthreads();
+        for (int j = k + 1 + warp; j < nb; j += 8) {
+            const double ljk = D[j + k * 65];
+            for (int i = j + lane; i < nb; i += 32) D[i + j * 65] = fma(-D[i + k * 65], ljk, D[i + j * 65]);
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_leaf_factor(const PotrfTask* __restrict__ tasks, int* status) {
+    extern __shared__ __align__(16) unsigned char lf_smem[];
+    __shared__ double rp;
+    __shared__ T dinv[NB];
+    const PotrfTask tk = tasks[blockIdx.x];
+    T* a = (T*)tk.a;
+    const int sz = tk.nb, ld = tk.ld, L = sz + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* S = (T*)lf_smem;
+    double* D = (double*)(lf_smem + (((size_t)sizeof(T) * sz * L + 15) / 16) * 16);   // 64 x 65 FP64 tile
+    for (int j = warp; j < sz; j += 8)
+        for (int i = j + lane; i < sz; i += 32) S[i + j * L] = a[i + (size_t)j * ld];
+    __syncthreads();
+    for (int t0 = 0; t0 < sz; t0 += NB) {
+        const int nb = min(NB, sz - t0);
+        T* Sd = S + t0 + (size_t)t0 * L;                 // diagonal tile
+        for (int j = warp; j < nb; j += 8)
+            for (int i = j + lane; i < nb; i += 32) D[i + j * 65] = (double)Sd[i + j * L];
+        __syncthreads();
+        leaf_tile_chol<T>(D, nb, status, tk.node, &rp);
+        for (int j = warp; j < nb; j += 8)
+            for (int i = j + lane; i < nb; i += 32) Sd[i + j * L] = (T)D[i + j * 65];
+        if (threadIdx.x < nb) dinv[threadIdx.x] = (T)(1.0 / D[threadIdx.x + threadIdx.x * 65]);
+        __syncthreads();
+        const int r0 = t0 + nb, m = sz - r0;             // rows below the tile
+        if (m <= 0) break;
+        // rows r0.. of columns t0..t0+nb: X <- X L_D^{-T}, column by column
+        for (int c = 0; c < nb; ++c) {
+            const T dc = dinv[c];
+            for (int i = threadIdx.x; i < m; i += blockDim.x) S[r0 + i + (size_t)(t0 + c) * L] *= dc;
+            __syncthreads();
+            for (int l = c + 1 + warp; l < nb; l += 8) {
+                const T llc = Sd[l + c * L];
+                for (int i = lane; i < m; i += 32)
+                    S[r0 + i + (size_t)(t0 + l) * L] -= S[r0 + i + (size_t)(t0 + c) * L] * llc;
+            }
+            __syncthreads();
+        }
+        // trailing update: S[i][j] -= sum_c S[i][t0 + c] S[j][t0 + c] for r0 <= j <= i < sz
+        for (int j = r0 + warp; j < sz; j += 8)
+            for (int i = j + lane; i < sz; i += 32) {
+                T acc = T(0);
+#pragma unroll 8
+                for (int c = 0; c < nb; ++c) acc = fma(S[i + (size_t)(t0 + c) * L], S[j + (size_t)(t0 + c) * L], acc);
+                S[i + (size_t)j * L] -= acc;
+            }
+        __syncthreads();
+    }
+    for (int j = warp; j < sz; j += 8)
+        for (int i = j + lane; i < sz; i += 32) a[i + (size_t)j * ld] = S[i + j * L];
+}
+
 // X L^T = B for a block of rows (nrows <= 64) below a factored diagonal tile (in place).
 // Thread (ty, tx) keeps rows ty + 16 p and columns tx + 16 q of X in registers; column j is
 // scaled by the reciprocal pivot by its owners and published to shared memory, then every
