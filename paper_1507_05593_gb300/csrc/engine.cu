@@ -703,6 +703,7 @@ struct EngineT final : EngineImpl {
         CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
         if (tc) CK(cudaFuncSetAttribute(k_push_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
         CK(cudaFuncSetAttribute(k_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM_CAP));
+        CK(cudaFuncSetAttribute(k_rf_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RFD_SMEM_CAP));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
         hs_attr<8>();
         hs_attr<4>();
@@ -716,6 +717,7 @@ struct EngineT final : EngineImpl {
         if (arena_base) cudaFree(arena_base);
         if (arena_host) cudaFreeHost(arena_host);
         if (rf_host) cudaFreeHost(rf_host);
+        if (rank_host) cudaFreeHost(rank_host);
         if (d_rfp_time) cudaFree(d_rfp_time);
         if (st_host) cudaFreeHost(st_host);
         if (stream) cudaStreamDestroy(stream);
@@ -1727,7 +1729,80 @@ struct EngineT final : EngineImpl {
     // implicit product; each pass is one cooperative launch of k_rf_pass, which keeps the
     // stopping decision and the rank on the device, so the host reads the state back
     // only when some block runs out of samples.
+    // Blocks small enough for one CTA (m, c <= rfd_max, no power iterations) go through the
+    // dense mode; the rest through the batched cooperative passes.
+    bool dense_ok(const RF& r) const {
+        const int mr = std::min(r.m, r.c);
+        return o.power_iters == 0 && mr > 0 && r.m <= rfd_max<T>() && r.c <= rfd_max<T>() &&
+               rfd_smem<T>(r.m, r.c, mr) <= RFD_SMEM_CAP;
+    }
     void range_finder_batch(std::vector<RF>& R) {
+        if (R.empty()) return;
+        std::vector<RF> D, B;
+        std::vector<int> wd, wb;
+        for (size_t i = 0; i < R.size(); ++i) {
+            if (dense_ok(R[i])) { D.push_back(R[i]); wd.push_back((int)i); }
+            else { B.push_back(R[i]); wb.push_back((int)i); }
+        }
+        if (!D.empty()) range_finder_dense(D);
+        if (!B.empty()) range_finder_batch_coop(B);
+        for (size_t i = 0; i < D.size(); ++i) R[wd[i]] = D[i];
+        for (size_t i = 0; i < B.size(); ++i) R[wb[i]] = B[i];
+    }
+    static constexpr size_t RFD_SMEM_CAP = 200 * 1024;
+    int* rank_host = nullptr;            // pinned: ranks found by the dense mode
+    size_t rank_host_cap = 0;
+    std::map<int, T*> ident;             // c x c identities of the current dense batch
+    void range_finder_dense(std::vector<RF>& R) {
+        ws.reset();
+        ident.clear();
+        if (R.size() > rank_host_cap) {
+            if (rank_host) CK(cudaFreeHost(rank_host));
+            rank_host_cap = std::max<size_t>(R.size(), 64);
+            CK(cudaMallocHost(&rank_host, sizeof(int) * (rank_host_cap + 2)));
+        }
+        const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        int* d_rank = (int*)ws.getb(sizeof(int) * R.size());
+        std::vector<Program> progs;
+        std::vector<RfDenseTask<T>> tasks;
+        size_t smem = 0;
+        for (size_t i = 0; i < R.size(); ++i) {
+            RF& r = R[i];
+            r.maxr = std::min(r.m, r.c);
+            T*& X = ident[r.c];
+            if (!X) {
+                X = wsT((size_t)r.c * r.c);
+                k_set_identity<T><<<std::min(cdiv(r.c * r.c, 256), 1024), 256, 0, stream>>>(X, r.c);
+                launches++;
+            }
+            T* Bm = wsT((size_t)r.m * r.c);     // the block, row-major (ld c): B = L X with X = I
+            progs.emplace_back();
+            mult_prog(progs.back(), r, X, r.c, Bm);
+            r.U = lr_alloc((long long)r.c * r.maxr);
+            r.V = lr_alloc((long long)r.m * r.maxr);
+            tasks.push_back(RfDenseTask<T>{Bm, r.U, r.V, r.m, r.c, r.maxr, 0, r.tol, u, r.block_id,
+                                           (uint32_t)restarts << 16, d_rank + i});
+            smem = std::max(smem, rfd_smem<T>(r.m, r.c, r.maxr));
+            flops += 2.0 * r.m * r.c * r.c;
+        }
+        run(progs);
+        RfDenseTask<T>* dt = (RfDenseTask<T>*)upload_tmp(sTask, tasks);
+        PROF(prof, "rf_dense", stream, 0, 0,
+             k_rf_dense<T><<<(int)tasks.size(), 512, smem, stream>>>(dt, o.seed, d_status + 2));
+        launches++;
+        LAUNCH_CHECK();
+        CK(cudaMemcpyAsync(rank_host, d_rank, sizeof(int) * R.size(), cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(rank_host + rank_host_cap, d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        sync_stream();
+        if (rank_host[rank_host_cap]) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
+        for (size_t i = 0; i < R.size(); ++i) {
+            RF& r = R[i];
+            r.rank = rank_host[i];
+            flops += (double)r.rank * 3.0 * 4.0 * r.c * r.rank + 2.0 * r.m * r.c * r.rank;
+        }
+    }
+
+    void range_finder_batch_coop(std::vector<RF>& R) {
         if (R.empty()) return;
         ws.reset();
         if (!coop_max) {

@@ -891,28 +891,35 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 
 // G (m x 16 at columns col0.., row-major, ld): entry (i, c) from counter (i, c/2, block_id, word3), key = seed;
 // Box-Muller on (w0, w1) for even c and (w2, w3) for odd c.  32 rows per CTA.
+// Two standard normal samples of row i, column pair cp of one sample block: Philox4x32-10 on
+// the counter (i, cp, block id, word3), key = seed, then Box-Muller on the two word pairs.
+template <class T>
+__device__ __forceinline__ void gauss_pair(uint32_t i, uint32_t cp, uint32_t block_id, uint32_t word3,
+                                           unsigned long long seed, T& z0, T& z1) {
+    uint32_t c[4] = {i, cp, block_id, word3};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+    if (sizeof(T) == 8) {
+        const double two32 = 2.3283064365386963e-10;   // 2^-32
+        const double twopi = 6.283185307179586;
+        z0 = (T)(sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32)));
+        z1 = (T)(sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32)));
+    } else {   // FP32 form: single-precision transforms of the same Philox words
+        const float f32 = 2.3283064365386963e-10f, tp = 6.2831853071795865f;
+        z0 = (T)(sqrtf(-2.0f * logf(((float)c[0] + 1.0f) * f32)) * cosf(tp * ((float)c[1] * f32)));
+        z1 = (T)(sqrtf(-2.0f * logf(((float)c[2] + 1.0f) * f32)) * cosf(tp * ((float)c[3] * f32)));
+    }
+}
+
 template <class T>
 __global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long seed) {
     const GaussTask tk = tasks[blockIdx.x];
     const int i = tk.row0 + (threadIdx.x >> 3), cp = threadIdx.x & 7;
     if (i >= tk.m) return;
-    uint32_t c[4] = {(uint32_t)i, (uint32_t)cp, tk.block_id, tk.word3};
-    philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
-    const double two32 = 2.3283064365386963e-10;   // 2^-32
-    const double twopi = 6.283185307179586;
+    T z0, z1;
+    gauss_pair<T>((uint32_t)i, (uint32_t)cp, tk.block_id, tk.word3, seed, z0, z1);
     T* G = (T*)tk.G;
-    if (sizeof(T) == 8) {
-        const double z0 = sqrt(-2.0 * log(((double)c[0] + 1.0) * two32)) * cos(twopi * ((double)c[1] * two32));
-        const double z1 = sqrt(-2.0 * log(((double)c[2] + 1.0) * two32)) * cos(twopi * ((double)c[3] * two32));
-        G[(size_t)i * tk.ld + tk.col0 + 2 * cp] = (T)z0;
-        G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = (T)z1;
-    } else {   // FP32 form: single-precision transforms of the same Philox words
-        const float f32 = 2.3283064365386963e-10f, tp = 6.2831853071795865f;
-        const float z0 = sqrtf(-2.0f * logf(((float)c[0] + 1.0f) * f32)) * cosf(tp * ((float)c[1] * f32));
-        const float z1 = sqrtf(-2.0f * logf(((float)c[2] + 1.0f) * f32)) * cosf(tp * ((float)c[3] * f32));
-        G[(size_t)i * tk.ld + tk.col0 + 2 * cp] = (T)z0;
-        G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = (T)z1;
-    }
+    G[(size_t)i * tk.ld + tk.col0 + 2 * cp] = z0;
+    G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = z1;
 }
 
 // dst[i*dsr + c*dsc] = src[i*ssr + c*ssc]; grid (tasks, 32).
@@ -951,6 +958,14 @@ template <class T>
 __global__ void k_perm_out(const T* __restrict__ y, const int32_t* __restrict__ perm, double* __restrict__ z, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         z[perm[i]] = (double)y[i];
+}
+
+// X (c x c, row-major) <- identity
+template <class T>
+__global__ void k_set_identity(T* __restrict__ X, int c) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)c * c;
+         e += (long long)gridDim.x * blockDim.x)
+        X[e] = (e / c == e % c) ? T(1) : T(0);
 }
 
 // N right-hand sides: column c of r / z at offset c n, y row-major (n x N)

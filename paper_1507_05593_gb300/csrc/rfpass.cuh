@@ -758,3 +758,212 @@ __global__ void __launch_bounds__(RFP_THREADS, 2) k_rf_pass(RfDev<T>* rf, const 
 }
 
 }  // namespace rsc
+
+namespace rsc {
+
+// ---------------------------------------------------------------- dense mode (small blocks)
+// The whole adaptive range finder (Alg. 3) of one block B (m x c, row-major, formed densely by
+// the implicit product of Alg. 5 applied to the identity) in one CTA: pass t draws the same
+// Philox samples G_t as the batched path (counter word3 = t | restarts << 16), Y = B^T G_t, two
+// projections against U, the stopping test ||Y||_F <= tol ||Y_1||_F, shifted CholeskyQR3 with
+// the dependent-column rule of rfp_chol, U appended; finally V = B U.  For blocks with
+// m, c <= RFD_MAX the passes then cost block barriers instead of grid barriers and host round
+// trips.  Shared memory: G (m x 16), Y, Z (c, maxr x 17), a 33-column tile of U.
+template <class T>
+struct RfDenseTask {
+    const T* B;             // m x c, row-major (ld c)
+    T* U;                   // c x maxr, column-major (ld c)
+    T* V;                   // m x maxr, column-major (ld m)
+    int m, c, maxr, pad;
+    double tol, u;
+    uint32_t block_id, word_hi;
+    int* rank;              // output: rank found
+};
+template <class T> constexpr int rfd_max() { return sizeof(T) == 8 ? 256 : 320; }
+template <class T> inline size_t rfd_smem(int m, int c, int maxr) {
+    return sizeof(T) * ((size_t)m * 16 + (size_t)c * 17 + (size_t)maxr * 17 + (size_t)c * 33);
+}
+
+template <class T>
+__global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restrict__ tasks, unsigned long long seed,
+                                                  int* err) {
+    extern __shared__ __align__(16) unsigned char rfd_smem_[];
+    __shared__ T Gs[16][17], Rl[272], rd[16];
+    __shared__ double red[16];
+    __shared__ int flag_s;
+    const RfDenseTask<T> tk = tasks[blockIdx.x];
+    const int m = tk.m, c = tk.c, maxr = tk.maxr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    T* G = (T*)rfd_smem_;                       // m x 16
+    T* Y = G + (size_t)m * 16;                  // c x 17
+    T* Z = Y + (size_t)c * 17;                  // maxr x 17
+    T* Ut = Z + (size_t)maxr * 17;              // c x 33 (tile of U for V = B U)
+    // ||Y||_F^2 (block reduction, fixed order)
+    auto frob2 = [&]() -> double {
+        double s = 0.0;
+        for (int e = tid; e < c * 16; e += nt) { const double v = (double)Y[(e >> 4) * 17 + (e & 15)]; s += v * v; }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        double t = 0.0;
+        for (int w = 0; w < (nt >> 5); ++w) t += red[w];
+        __syncthreads();
+        return t;
+    };
+    // Y -= U (U^T Y) with the current rank
+    auto project = [&](int rank) {
+        if (rank == 0) return;
+        for (int k = tid; k < rank; k += nt) {
+            T a[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) a[q] = T(0);
+            const T* uk = tk.U + (size_t)k * c;
+            for (int j = 0; j < c; ++j) {
+                const T uv = uk[j];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) a[q] = fma(uv, Y[j * 17 + q], a[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Z[k * 17 + q] = a[q];
+        }
+        __syncthreads();
+        for (int j = tid; j < c; j += nt) {
+            T a[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) a[q] = Y[j * 17 + q];
+            for (int k = 0; k < rank; ++k) {
+                const T uv = tk.U[j + (size_t)k * c];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) a[q] = fma(-uv, Z[k * 17 + q], a[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Y[j * 17 + q] = a[q];
+        }
+        __syncthreads();
+    };
+    // Gram matrix Y^T Y into Gs
+    auto gram = [&]() {
+        if (tid < 256) {
+            const int a = tid >> 4, b = tid & 15;
+            T s = T(0);
+            for (int j = 0; j < c; ++j) s = fma(Y[j * 17 + a], Y[j * 17 + b], s);
+            Gs[a][b] = s;
+        }
+        __syncthreads();
+    };
+    // Y[:, :b] <- Y[:, :b] R^{-1} (R, 1/diag in Rl / rd), forward substitution per row
+    auto rsolve = [&](int b) {
+        if (tid < 16) rd[tid] = Rl[256 + tid];
+        __syncthreads();
+        for (int j = tid; j < c; j += nt) {
+            T x[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (q < b) {
+                    T v = Y[j * 17 + q];
+#pragma unroll
+                    for (int k = 0; k < q; ++k) v = fma(-x[k], Rl[k * 16 + q], v);
+                    x[q] = v * rd[q];
+                    Y[j * 17 + q] = x[q];
+                } else {
+                    x[q] = T(0);
+                }
+            }
+        }
+        __syncthreads();
+    };
+    // warp 0 factors Gs (b x b) into Rl; returns the non-finite flag to every thread
+    auto chol = [&](int b, double coef) -> bool {
+        if (tid < 32) {
+            const bool bad = rfp_chol(Gs, b, coef, 4.0 * max(c, 16) * tk.u, Rl);
+            if (tid == 0) flag_s = bad ? 1 : 0;
+        }
+        __syncthreads();
+        return flag_s != 0;
+    };
+
+    int rank = 0;
+    double y1 = 0.0;
+    for (int t = 0; rank < maxr; ++t) {
+        // samples of pass t and Y = B^T G
+        for (int e = tid; e < m * 8; e += nt) {
+            const int i = e >> 3, cp = e & 7;
+            T z0, z1;
+            gauss_pair<T>((uint32_t)i, (uint32_t)cp, tk.block_id, (uint32_t)t | tk.word_hi, seed, z0, z1);
+            G[i * 16 + 2 * cp] = z0;
+            G[i * 16 + 2 * cp + 1] = z1;
+        }
+        __syncthreads();
+        for (int j = tid; j < c; j += nt) {
+            T a[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) a[q] = T(0);
+            for (int i = 0; i < m; ++i) {
+                const T bv = tk.B[(size_t)i * c + j];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) a[q] = fma(bv, G[i * 16 + q], a[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) Y[j * 17 + q] = a[q];
+        }
+        __syncthreads();
+        if (t == 0) y1 = sqrt(frob2());
+        project(rank);
+        project(rank);
+        const double nrm = sqrt(frob2());
+        if (!isfinite(nrm) || !isfinite(y1)) {
+            if (tid == 0) atomicCAS(err, 0, 1);
+            break;
+        }
+        if (nrm <= tk.tol * y1) break;
+        const int b = min(16, maxr - rank);
+        gram();
+        bool bad = chol(b, 11.0 * ((double)c * b + (double)b * (b + 1)) * tk.u);
+        rsolve(b);
+        project(rank);
+        gram();
+        bad |= chol(b, 0.0);
+        rsolve(b);
+        gram();
+        bad |= chol(b, 0.0);
+        rsolve(b);
+        if (bad) break;                         // non-finite pivot: drop the block's last pass
+        unsigned keep = 0;
+        for (int q = 0; q < b; ++q) keep |= (rd[q] != T(0) ? 1u : 0u) << q;
+        const int kept = __popc(keep);
+        for (int e = tid; e < c * b; e += nt) {
+            const int j = e % c, q = e / c;
+            if ((keep >> q) & 1u) tk.U[j + (size_t)(rank + __popc(keep & ((1u << q) - 1u))) * c] = Y[j * 17 + q];
+        }
+        __syncthreads();
+        if (kept == 0) break;
+        rank += kept;
+    }
+    // V = B U (m x rank, column-major), 32 columns of U staged at a time
+    for (int k0 = 0; k0 < rank; k0 += 32) {
+        const int kn = min(32, rank - k0);
+        for (int e = tid; e < c * 32; e += nt) {
+            const int j = e % c, kk = e / c;
+            Ut[j * 33 + kk] = kk < kn ? tk.U[j + (size_t)(k0 + kk) * c] : T(0);
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += nt) {
+            T a[32];
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk) a[kk] = T(0);
+            const T* bi = tk.B + (size_t)i * c;
+            for (int j = 0; j < c; ++j) {
+                const T bv = bi[j];
+#pragma unroll
+                for (int kk = 0; kk < 32; ++kk) a[kk] = fma(bv, Ut[j * 33 + kk], a[kk]);
+            }
+#pragma unroll
+            for (int kk = 0; kk < 32; ++kk)
+                if (kk < kn) tk.V[i + (size_t)(k0 + kk) * m] = a[kk];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *tk.rank = rank;
+}
+
+}  // namespace rsc
