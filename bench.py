@@ -150,6 +150,21 @@ def cpu_baseline(side, tol, rtol, crop=32):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def max_over_ranks(t_local, dist, device):
+    """Whole-job step time of N replicas: the slowest rank's time (every rank gets it)."""
+    import torch
+    if dist is None:
+        return t_local
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_seed(rank):
+    """Each replica factors and solves its own system: the conductivity field and b of rank r use seed r."""
+    return rank
+
+
 def reference_arm(a, rank, world):
     if rank != 0:
         return
@@ -267,7 +282,7 @@ def main():
         except Exception as e:  # reported, not fatal
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
 
-    p = W.diffusion_grf(a.side, 2.0, 8.0, seed=rank)
+    p = W.diffusion_grf(a.side, 2.0, 8.0, seed=replica_seed(rank))
     d_b = torch.tensor(p.b, device="cuda")
     d_x = torch.empty_like(d_b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -314,10 +329,7 @@ def main():
     kprof = R.rsc_get_kernel_profile(h) if dom else {}
     R.rsc_profile(h, False)
     t_step = sum(times) / len(times)
-    if dist:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(t_step, dist, "cuda")
     # end to end through the public host API: values and b copied in, x copied out
     t0 = time.perf_counter()
     R.rsc_factor(h, a.tol)
