@@ -150,6 +150,10 @@ def cpu_baseline(side, tol, rtol, crop=32):
 
 
 # ----------------------------------------------------------------------------- reference arm
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at 96^3 (FP32 form), by kernel class
+NCU_TRAFFIC = {"tn": 59.9e6}
+
+
 def max_over_ranks(t_local, dist, device):
     """Whole-job step time of N replicas: the slowest rank's time (every rank gets it)."""
     import torch
@@ -356,8 +360,11 @@ def main():
         hbm = peaks.get("hbm_gbs", 6800.0)
         per_launch_ms = k["ms"] / k["launches"]
         achieved = k["bytes"] / k["launches"] / (per_launch_ms * 1e-3) / 1e9
+        # DRAM bytes per launch measured by ncu for the same workload (profiles/k_tn_diffusion48_fp32.md);
+        # null for a kernel class without a capture of its current code
+        traffic = NCU_TRAFFIC.get(dom) if a.side == 96 else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "launches_timed": k["launches"],
+                "frac": achieved / hbm, "traffic": traffic, "launches_timed": k["launches"],
                 "avg_launch_us": per_launch_ms * 1e3,
                 "note": "algorithmic bytes per launch / CUDA-event launch time, peak of measured"}
     line = {
