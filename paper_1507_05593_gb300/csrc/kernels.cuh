@@ -407,6 +407,23 @@ __global__ void __launch_bounds__(256) k_push(const PushTask* __restrict__ tasks
 // line by line through L1) and every Y row is read once per 32 columns; the warps'
 // partial sums are reduced in shared memory in a fixed order.
 constexpr int TN_COLS = 32;
+// 16 consecutive elements from a 16-byte aligned address, as 16-byte vector loads
+__device__ __forceinline__ void load_row16(const float* y, float (&v)[16]) {
+    const float4* p = reinterpret_cast<const float4*>(y);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float4 f = p[h];
+        v[4 * h] = f.x; v[4 * h + 1] = f.y; v[4 * h + 2] = f.z; v[4 * h + 3] = f.w;
+    }
+}
+__device__ __forceinline__ void load_row16(const double* y, double (&v)[16]) {
+    const double2* p = reinterpret_cast<const double2*>(y);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+        const double2 f = p[h];
+        v[2 * h] = f.x; v[2 * h + 1] = f.y;
+    }
+}
 template <class T>
 __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     __shared__ T red[8][16][33];
@@ -427,6 +444,8 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
     for (int q = 0; q < 16; ++q) acc[q] = T(0);
     const int chunk = (re - rb + 7) >> 3;
     const int i0 = rb + warp * chunk, i1 = min(re, i0 + chunk);
+    // full 16-column rows of Y that start on a 16-byte boundary are read as 16-byte vectors
+    const bool vec = nc == 16 && (tk.ldy * (int)sizeof(T)) % 16 == 0 && ((uintptr_t)Y & 15) == 0;
     for (int ib = i0; ib < i1; ib += 32) {
       const int nb = min(32, i1 - ib);
       const int my = ib + lane;
@@ -438,7 +457,12 @@ __global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
         const int yr = __shfl_sync(0xffffffffu, yr_l, r);
         const T a = tok ? A[ar] : T(0);
         const T* y = Y + (size_t)yr * tk.ldy;
-        if (nc == 16) {
+        if (vec) {
+            T yv[16];
+            load_row16(y, yv);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = fma(a, yv[q], acc[q]);
+        } else if (nc == 16) {
 #pragma unroll
             for (int q = 0; q < 16; ++q) acc[q] = fma(a, y[q], acc[q]);
         } else if (nc == 1) {
