@@ -148,6 +148,31 @@ def test_poisson32_config_parity():
     assert rr <= 1e-8 and abs(it - it_ref) <= 2
 
 
+def test_poisson40_large_blocks_parity():
+    """40^3 Poisson, tol 1e-1: the top separator (1,600 columns) has internal blocks of 800
+    columns, compressed by the cooperative pass kernel's full 13-phase mode (more than 8
+    row chunks), the small blocks by the dense mode: ranks equal the oracle's, and the
+    preconditioner applications agree within 1e-8."""
+    p = W.poisson7(40)
+    o = _opts()
+    h = _gpu(p, o, 0.1)
+    an, f = _oracle(p, o, 0.1)
+    big = 0
+    for j in range(an.nsuper):
+        if not f.sn[j].compressed:
+            continue
+        info = R.rsc_get_supernode_info(h, j)
+        assert info["rank"] == f.sn[j].U.shape[1], j
+        big += info["c"] > 512
+    assert big >= 1
+    r = np.random.default_rng(7).standard_normal(p.n)
+    z_ref = F.apply_preconditioner(f, r)
+    d_r = torch.tensor(r, device="cuda")
+    d_z = torch.empty_like(d_r)
+    R.rsc_apply_preconditioner_device(h, d_r, d_z)
+    assert np.abs(d_z.cpu().numpy() - z_ref).max() <= 1e-8 * np.abs(z_ref).max()
+
+
 def test_poisson32_exact_sampled_blocks():
     """Exact 32^3 factor (dense 1024-column top separator): sampled supernodes vs oracle."""
     p = W.poisson7(32)
