@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
 constexpr int NN_ROWS = 128;
 template <class T>
 __global__ void __launch_bounds__(NN_ROWS) k_nn(const NnTask* __restrict__ tasks) {
-    __shared__ T Zs[64][17];
+    __shared__ __align__(16) T Zs[64][16];   // read by every thread (broadcast) as 16-byte vectors
     const NnTask tk = tasks[blockIdx.x];
     const int c0 = blockIdx.y * 16;
     const int nc = min(16, tk.N - c0);
@@ -601,8 +601,10 @@ __global__ void __launch_bounds__(NN_ROWS) k_nn(const NnTask* __restrict__ tasks
 #pragma unroll 4
                 for (int l = 0; l < lk; ++l) {
                     const T a = A[ar + (size_t)(l0 + l) * tk.lda];
+                    T zv[16];
+                    load_row16(&Zs[l][0], zv);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[q] = fma(a, Zs[l][q], acc[q]);
+                    for (int q = 0; q < 16; ++q) acc[q] = fma(a, zv[q], acc[q]);
                 }
             }
         }
