@@ -131,17 +131,25 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
     uint32_t phase = 0;
     int chunks = 0;
     for (int k0 = 0; k0 < op.K; k0 += TC_K) {
-        // stage the chunk: element (r, kk) of A rows / B rows, zero outside the task
-        for (int e = tid; e < TC_M * TC_K; e += blockDim.x) {
-            const int r = e % TC_M, kk = e / TC_M, kg = k0 + kk;
-            const float v = (r < m && kg < op.K) ? A[r + (size_t)kg * op.ld] : 0.f;
-            *(__nv_bfloat16*)(As + tc_off(r, kk)) = __float2bfloat16_rn(v);
-        }
-        for (int e = tid; e < TC_N * TC_K; e += blockDim.x) {
-            const int r = e % TC_N, kk = e / TC_N, kg = k0 + kk;
-            const float v = (r < n && kg < op.K) ? B[r + (size_t)kg * op.ld] : 0.f;
-            *(__nv_bfloat16*)(Bs + tc_off(r, kk)) = __float2bfloat16_rn(v);
-        }
+        // stage the chunk, zero outside the task: a thread converts 8 consecutive K values of one
+        // row and stores them as one 16-byte row of a core matrix (conflict-free 16-byte stores)
+        auto stage = [&](const float* src, int rows, int nr, unsigned char* dst) {
+            for (int e = tid; e < rows * 2; e += blockDim.x) {
+                const int r = e % rows, h = e / rows;     // h: K values 8h .. 8h + 7 of the chunk
+                uint32_t w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int kg0 = k0 + 8 * h + 2 * u, kg1 = kg0 + 1;
+                    const float v0 = (r < nr && kg0 < op.K) ? src[r + (size_t)kg0 * op.ld] : 0.f;
+                    const float v1 = (r < nr && kg1 < op.K) ? src[r + (size_t)kg1 * op.ld] : 0.f;
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                    w[u] = *reinterpret_cast<const uint32_t*>(&b2);
+                }
+                *reinterpret_cast<uint4*>(dst + tc_off(r, 8 * h)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        };
+        stage(A, TC_M, m, As);
+        stage(B, TC_N, n, Bs);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
