@@ -5,11 +5,12 @@ cell conductivity exp(g), g a seeded Gaussian random field (sigma 2, correlation
 length 8 cells); compression tolerance 1e-2, 16-column Gaussian samples, PCG to
 ||r||/||b|| <= 1e-8.  One step = rsc_factor + rsc_solve_device (b resident on the
 device); its time is the sum of the two calls' device times (CUDA events on the
-library's stream).  The best form (mixed FP32 factor, FP64 PCG) is timed for K
-steps; the plain FP64 form is timed once beside it.  L2 is flushed between steps
-(the factor storage is also larger than L2).
+library's stream).  The default form (BF16 Schur updates on tcgen05 tensor cores with
+FP32 accumulation, FP32 factor storage and sampling, FP64 diagonal Cholesky and PCG) is
+timed for K steps; the FP32 form and the plain FP64 form are timed once beside it.  L2
+is flushed between steps (the factor storage is also larger than L2).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64] [--side 96]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32|fp64] [--side 96]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 For N > 1 (torchrun) every rank solves its own replica (replicas only: the method
@@ -37,7 +38,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--prec", default="bf16")
     ap.add_argument("--side", type=int, default=96)
     ap.add_argument("--tol", type=float, default=1e-2)
     ap.add_argument("--rtol", type=float, default=1e-8)
@@ -150,6 +151,11 @@ def cpu_baseline(side, tol, rtol, crop=32):
 
 
 # ----------------------------------------------------------------------------- reference arm
+FORMS = {"bf16": "BF16 Schur updates on tcgen05 (FP32 accumulation), FP32 factor and sampling, FP64 diagonal "
+                 "Cholesky and PCG",
+         "fp32": "FP32 factor, Schur updates and sampling; FP64 diagonal Cholesky and PCG",
+         "fp64": "all FP64"}
+
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at 96^3 (FP32 form), by kernel class
 NCU_TRAFFIC = {"tn": 59.9e6}
 
@@ -244,10 +250,11 @@ def batch_workload(a):
     its, rr, st = res[-1][2], res[-1][3], res[-1][4]
     line = {"metric": "batched factor+PCG seconds (all systems x right-hand sides to rel. residual 1e-8)",
             "value": fs + ss, "unit": "s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
-            "higher_is_better": False, "dtype": "f32" if a.prec != "fp64" else "f64", "data": "synthetic",
+            "higher_is_better": False, "dtype": {"bf16": "bf16", "fp32": "f32"}.get(a.prec, "f64"),
+            "data": "synthetic",
             "config": {"workload": f"{a.systems} FV diffusion systems, sides U{{12..40}}, log-normal sigma 1, "
                                    f"{a.nrhs} right-hand sides each, tol {a.tol:g}", "unknowns": n,
-                       "form": f"{a.prec} factor, f64 PCG"},
+                       "form": FORMS.get(a.prec, a.prec)},
             "factor_s": fs, "solve_s": ss, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "relres_max": float(rr.max()), "analyze_s": t_an, "factor_bytes": st["factor_bytes"],
             "gpu_launches": st["gpu_launches"], "n_supernodes": st["n_supernodes"], "n_levels": st["n_levels"]}
@@ -340,15 +347,16 @@ def main():
     x, it_e2e, rr_e2e = R.rsc_solve(h, p.b, a.rtol, 2000)
     t_e2e = time.perf_counter() - t0
     res = np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
-    # plain FP64 form, once
-    fp64 = None
-    if not a.no_fp64 and a.prec != "fp64":
-        h64, _ = make("fp64")
-        t64, it64, rr64, st64 = step(h64)
-        fp64 = {"seconds": t64, "factor_s": st64["factor_seconds"], "solve_s": st64["solve_seconds"],
-                "iters": it64, "relres": rr64, "factor_bytes": st64["factor_bytes"],
-                "factor_tflops": st64["factor_flops"] / st64["factor_seconds"] / 1e12}
-        del h64
+    # the other forms, once each (after one untimed step)
+    def side_form(prec):
+        hs, _ = make(prec)
+        step(hs)
+        ts, its, rrs, sts = step(hs)
+        return {"seconds": ts, "factor_s": sts["factor_seconds"], "solve_s": sts["solve_seconds"],
+                "iters": its, "relres": rrs, "factor_bytes": sts["factor_bytes"],
+                "factor_tflops": sts["factor_flops"] / sts["factor_seconds"] / 1e12}
+    fp64 = side_form("fp64") if not a.no_fp64 and a.prec != "fp64" else None
+    fp32 = side_form("fp32") if not a.no_fp64 and a.prec == "bf16" else None
     roof = None
     if dom and dom in kprof and kprof[dom]["ms"] > 0:
         k = kprof[dom]
@@ -370,15 +378,16 @@ def main():
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if a.prec != "fp64" else "f64", "data": "synthetic",
-        "config": {"workload": _workload_name(a.side, a.tol), "form": f"{a.prec} factor, f64 PCG",
+        "dtype": {"bf16": "bf16", "fp32": "f32"}.get(a.prec, "f64"), "data": "synthetic",
+        "config": {"workload": _workload_name(a.side, a.tol), "form": FORMS.get(a.prec, a.prec),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "L2 flushed (256 MB write) before each step; factor storage larger than L2"},
         "iters": iters[-1], "relres": rrs[-1], "true_relres_check": res,
         "factor_s": st["factor_seconds"], "solve_s": st["solve_seconds"],
         "factor_tflops": st["factor_flops"] / st["factor_seconds"] / 1e12, "factor_gflop": st["factor_flops"] / 1e9,
         "factor_bytes": st["factor_bytes"], "analyze_s": t_an, "restarts": st["restarts"],
-        "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "roofline": roof, "kernel_profile_untimed": prof_all,
+        "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "fp32_form": fp32, "roofline": roof,
+        "kernel_profile_untimed": prof_all,
         "cpu_baseline": cpu, "clocks": clk,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(8 * (p.nnz + p.n)),
                 "d2h_bytes_per_step": int(8 * p.n)},
