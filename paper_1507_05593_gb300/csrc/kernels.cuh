@@ -90,12 +90,14 @@ __global__ void k_assemble(const double* __restrict__ val, const long long* __re
 // a few ulp).  On this part a dependent FP64 operation takes about 64 cycles, the library's
 // FP64 square root about 690 and division about 440, so the pivot's square root and
 // reciprocal come from these six operations.  Outside the float range the library is used.
+// STEPS = 1 leaves about 44 correct bits: enough where the factor is stored in FP32.
+template <int STEPS = 2>
 __device__ __forceinline__ double rsqrt_newton(double x) {
     if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
     double y = (double)rsqrtf((float)x);
     const double hx = 0.5 * x;
-    y = y * fma(-hx * y, y, 1.5);
-    y = y * fma(-hx * y, y, 1.5);
+#pragma unroll
+    for (int i = 0; i < STEPS; ++i) y = y * fma(-hx * y, y, 1.5);
     return y;
 }
 
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict_
                 atomicCAS(status, 0, tk.node + 1);
                 d = 1.0;
             }
-            const double y = rsqrt_newton(d);
+            const double y = rsqrt_newton<sizeof(T) == 8 ? 2 : 1>(d);
             s[k][k] = d * y;
             rpiv = y;
         }
@@ -157,7 +159,7 @@ __device__ void leaf_tile_chol(double* D, int nb, int* status, int node, double*
                 atomicCAS(status, 0, node + 1);
                 d = 1.0;
             }
-            const double y = rsqrt_newton(d);
+            const double y = rsqrt_newton<sizeof(T) == 8 ? 2 : 1>(d);
             D[k + k * 65] = d * y;
             *rp = y;
         }
