@@ -38,6 +38,17 @@ Algorithm by algorithm, in the paper's order and notation:
                                 tol_D <- tol_D / 1.25 per restart; after
                                 ``max_restarts`` restarts diagonal compression is
                                 switched off (Section 3.2 then guarantees success).
+* ``factor_fixed_rank``         Section 5.2's fixed-rank form of Alg. 3: block B
+                                (m x n) gets rank(B) = alpha sqrt(k) log2(k) + p,
+                                k = min(m, n) (Eq. rankFunction), alpha^O for
+                                off-diagonal and alpha^D for diagonal blocks.
+                                Reading: the rank is ceil(alpha sqrt(k) log2 k) + p,
+                                capped at k.  The samples are the same 16-column
+                                passes as the adaptive form with the stopping test
+                                off (tol = 0); in exact arithmetic span(U) equals
+                                span((B^T B)^q B^T G) for G the first rank(B) sampled
+                                columns, the one-shot form of Alg. 3.  Section 5.3's
+                                restart: alpha^D <- 1.25 alpha^D, starting from 0.5.
 
 Low-rank descendants keep U_prod = U_k^T U_k literally (Eq. "lowRankMult").
 Random test matrices come from ``oracle.philox.gaussian_block`` with block id
@@ -129,14 +140,28 @@ class SupernodeFactor:
         self.Uprod = None      # U_j^T U_j
 
 
+def rank_heuristic(m: int, n: int, alpha: float, p: int) -> int:
+    """Eq. rankFunction (Section 5.2): ceil(alpha sqrt(k) log2 k) + p with k = min(m, n),
+    capped at k (a block of k independent columns has no larger rank)."""
+    k = min(int(m), int(n))
+    if k <= 0:
+        return 0
+    return min(k, int(np.ceil(alpha * np.sqrt(k) * np.log2(k))) + int(p))
+
+
 class Factor:
     def __init__(self, an: Analysis):
         self.an = an
         self.sn = [SupernodeFactor() for _ in range(an.nsuper)]
         self.restarts = 0
+        self.compress = False
         self.tol = 0.0
         self.tol_D = 0.0
         self.diag_compress = False
+        self.fixed_rank = False    # Section 5.2 ranks instead of the adaptive stopping test
+        self.alpha_O = 0.0
+        self.alpha_D = 0.0
+        self.p = 0
 
     # ----------------------------------------------------------- descendant blocks
     def lo_rows(self, k, pos):
@@ -214,11 +239,12 @@ class Factor:
         return self.diagonal_solve(j, W, transpose=False)
 
     # ----------------------------------------------------------- adaptive range finder
-    def _range_finder(self, m, c, tol, block_id, mult, mult_T):
-        """Shared body of Alg. 3 and approximateDiagonalBlock: returns (V, U)."""
+    def _range_finder(self, m, c, tol, block_id, mult, mult_T, cap=None):
+        """Shared body of Alg. 3 and approximateDiagonalBlock: returns (V, U).
+        cap: largest rank (fixed-rank form, tol = 0); None: min(m, c)."""
         opts = self.an.opts
         b = opts.sample_block
-        maxr = min(m, c)
+        maxr = min(m, c) if cap is None else min(m, c, cap)
         U = np.zeros((c, 0))
         y1 = None
         t = 0
@@ -246,9 +272,10 @@ class Factor:
         an = self.an
         c0, c1 = an.cols(j)
         m = an.sym.rows[j].size
+        cap = rank_heuristic(m, c1 - c0, self.alpha_O, self.p) if self.fixed_rank else None
         V, U = self._range_finder(m, c1 - c0, self.tol, (j << 12) | 0,
                                   lambda G: self.offdiag_multiply(j, G),
-                                  lambda G: self.offdiag_multiply_T(j, G))
+                                  lambda G: self.offdiag_multiply_T(j, G), cap)
         s = self.sn[j]
         s.V, s.U, s.Uprod = V, U, U.T @ U
 
@@ -327,9 +354,10 @@ class Factor:
         t = D.tree
         r0, r1 = t.rows(s)
         q0, q1 = t.cols(s)
+        cap = rank_heuristic(r1 - r0, q1 - q0, self.alpha_D, self.p) if self.fixed_rank else None
         V, U = self._range_finder(r1 - r0, q1 - q0, self.tol_D, (j << 12) | s,
                                   lambda G: self.diagonal_multiply(j, s, G),
-                                  lambda G: self.diagonal_multiply_T(j, s, G))
+                                  lambda G: self.diagonal_multiply_T(j, s, G), cap)
         D.V[s], D.U[s] = V, U
 
     # ----------------------------------------------------------- Alg. 6
@@ -405,7 +433,7 @@ class Factor:
     def is_compressed(self, j):
         an = self.an
         c0, c1 = an.cols(j)
-        return self.tol > 0 and an.ordering.kinds[j] == "sep" and (c1 - c0) >= an.opts.tau_O
+        return self.compress and an.ordering.kinds[j] == "sep" and (c1 - c0) >= an.opts.tau_O
 
     def run(self):
         self.sn = [SupernodeFactor() for _ in range(self.an.nsuper)]
@@ -416,12 +444,9 @@ class Factor:
                 self.factor_supernode(j)
 
 
-def factor(an: Analysis, tol: float) -> Factor:
-    """Factor with the Section 5.3 restart loop (tolerance form)."""
-    f = Factor(an)
-    f.tol = tol
-    f.tol_D = tol
-    f.diag_compress = bool(an.opts.diag_compress and tol > 0)
+def _restart_loop(f: Factor, loosen) -> Factor:
+    """Section 5.3: on an indefinite diagonal block, make diagonal compression more
+    accurate (``loosen``) and factor again; after max_restarts restarts, switch it off."""
     attempt = 0
     while True:
         f.restarts = attempt
@@ -432,10 +457,39 @@ def factor(an: Analysis, tol: float) -> Factor:
             if not f.diag_compress:
                 raise
             attempt += 1
-            if attempt <= an.opts.max_restarts:
-                f.tol_D = f.tol_D / 1.25
+            if attempt <= f.an.opts.max_restarts:
+                loosen(f)
             else:
                 f.diag_compress = False
+
+
+def factor(an: Analysis, tol: float) -> Factor:
+    """Factor with the Section 5.3 restart loop (tolerance form: tol_D <- tol_D / 1.25)."""
+    f = Factor(an)
+    f.compress = tol > 0
+    f.tol = tol if tol > 0 else 0.0
+    f.tol_D = f.tol
+    f.diag_compress = bool(an.opts.diag_compress and f.compress)
+
+    def loosen(g):
+        g.tol_D = g.tol_D / 1.25
+    return _restart_loop(f, loosen)
+
+
+def factor_fixed_rank(an: Analysis, alpha_O: float, alpha_D: float = 0.5, p: int = 8) -> Factor:
+    """Factor with the ranks of Eq. rankFunction (Section 5.2) and the Section 5.3 restart
+    alpha^D <- 1.25 alpha^D."""
+    if not (alpha_O >= 0 and alpha_D >= 0 and p >= 0):
+        raise ValueError("alpha_O, alpha_D and p must be >= 0")
+    f = Factor(an)
+    f.compress = True
+    f.fixed_rank = True
+    f.alpha_O, f.alpha_D, f.p = float(alpha_O), float(alpha_D), int(p)
+    f.diag_compress = bool(an.opts.diag_compress)
+
+    def loosen(g):
+        g.alpha_D = g.alpha_D * 1.25
+    return _restart_loop(f, loosen)
 
 
 # ----------------------------------------------------------------------------- solve

@@ -404,3 +404,150 @@ def test_pcg_reaches_tolerance(tol):
     assert ok and rr <= 1e-8
     A = p.scipy()
     assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= 1e-8
+
+
+# --------------------------------------------------------------------------- fixed-rank form (Section 5.2)
+
+def test_rank_heuristic_closed_form():
+    """Eq. rankFunction with k = min(m, n): hand-computed values, the cap at k, and the
+    degenerate sizes."""
+    assert F.rank_heuristic(256, 300, 0.5, 8) == 72          # 0.5 * 16 * 8 + 8
+    assert F.rank_heuristic(5000, 1024, 1.0, 5) == 325       # 1 * 32 * 10 + 5
+    assert F.rank_heuristic(100, 100, 0.5, 0) == 34          # ceil(0.5 * 10 * 6.64386) = ceil(33.22)
+    assert F.rank_heuristic(20, 64, 2.0, 8) == 20            # 38.66 -> 39 + 8 = 47, capped at 20
+    assert F.rank_heuristic(1, 9, 3.0, 4) == 1               # log2(1) = 0: p, capped at 1
+    assert F.rank_heuristic(0, 9, 3.0, 4) == 0
+    assert F.rank_heuristic(64, 64, 0.0, 6) == 6
+
+
+def _spectrum_matrix(m, c, sv, seed):
+    rng = np.random.default_rng(seed)
+    Qa, _ = np.linalg.qr(rng.standard_normal((m, len(sv))))
+    Qb, _ = np.linalg.qr(rng.standard_normal((c, len(sv))))
+    return (Qa * sv) @ Qb.T
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+@pytest.mark.parametrize("r", [16, 40, 57])
+def test_fixed_rank_range_finder_is_one_shot_alg3(q, r):
+    """The blocked 16-column passes with the stopping test off span exactly what Alg. 3's
+    one-shot form spans: orth((B^T B)^q B^T G) for G the first r sampled columns, formed
+    here directly with numpy from the same Philox stream; V = B U, U orthonormal.  A
+    missing or extra power iteration, or a wrong sample column, moves the subspace by O(1)."""
+    p = W.poisson7(4)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(power_iters=q, seed=7))
+    f = F.Factor(an)
+    m, c = 150, 120
+    sv = 1.0 / (1.0 + np.arange(min(m, c)))
+    B = _spectrum_matrix(m, c, sv, 11)
+    bid = (5 << 12) | 3
+    V, U = f._range_finder(m, c, 0.0, bid, lambda X: B @ X, lambda G: B.T @ G, cap=r)
+    assert U.shape == (c, r) and V.shape == (m, r)
+    np.testing.assert_allclose(U.T @ U, np.eye(r), atol=1e-13)
+    np.testing.assert_allclose(V, B @ U, atol=1e-13)
+    G = np.hstack([gaussian_block(m, 16, 7, bid, t, 0) for t in range((r + 15) // 16)])[:, :r]
+    Y = B.T @ G
+    for _ in range(q):
+        Y = B.T @ (B @ Y)
+    Qref, _ = np.linalg.qr(Y)
+    # two backward-stable orthonormalisations of Y span subspaces within O(u cond(Y))
+    assert np.linalg.norm(U @ U.T - Qref @ Qref.T, 2) <= 20 * 1.1e-16 * np.linalg.cond(Y)
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_fixed_rank_error_within_randomized_bound(q):
+    """Halko, Martinsson and Tropp (2011), Thm. 10.5: with k = r - p and p >= 2 oversampling
+    columns, E||B - B U U^T||_F <= sqrt(1 + k/(p - 1)) (sum_{i>k} s_i^2)^{1/2}.  One seeded
+    draw is checked against 3x that expectation; power iterations may only help."""
+    p_ = W.poisson7(4)
+    an = F.analyze(p_.n, p_.row_ptr, p_.col_idx, p_.val, p_.coords, F.Options(power_iters=q, seed=3))
+    f = F.Factor(an)
+    m, c, r, ov = 200, 160, 48, 8
+    sv = np.exp(-np.arange(160) / 15.0)
+    B = _spectrum_matrix(m, c, sv, 4)
+    _, U = f._range_finder(m, c, 0.0, 9, lambda X: B @ X, lambda G: B.T @ G, cap=r)
+    err = np.linalg.norm(B - B @ U @ U.T)
+    k = r - ov
+    bound = np.sqrt(1 + k / (ov - 1)) * np.sqrt(np.sum(sv[k:] ** 2))
+    assert err <= 3 * bound
+    assert err >= np.sqrt(np.sum(sv[r:] ** 2)) * (1 - 1e-12)   # never better than the SVD
+
+
+@pytest.mark.parametrize("maker", [lambda: W.poisson7(8), lambda: W.diffusion_grf(8, 2.0, 3.0, 0),
+                                   lambda: W.elasticity_q1(4, incl=(1, 3))])
+def test_fixed_rank_full_rank_is_exact(maker):
+    """Ranks of Eq. rankFunction at or above min(m, n) for every block: nothing is dropped
+    and the compressed factor is the exact Cholesky factor (Alg. 1) to rounding."""
+    p = maker()
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=8, tau_O=16, tau_D=8, dof_per_node=p.dof_per_node))
+    f = F.factor_fixed_rank(an, 100.0, 100.0, 0)
+    assert any(s.compressed for s in f.sn) and any(s.compressed and s.D.hierarchical for s in f.sn)
+    L = _assemble_L(f)
+    Ap = an.Ap.toarray()
+    assert np.linalg.norm(L @ L.T - Ap) / np.linalg.norm(Ap) <= 1e-12
+    x, it, rr, ok = F.solve(an, f, p.b, 1e-8)
+    assert ok and it <= 2
+
+
+def test_fixed_rank_block_ranks_and_errors():
+    """Every compressed block gets exactly the rank of Eq. rankFunction (alpha^O for L^O_j,
+    alpha^D for internal diagonal blocks, k = min(m, n)), with an orthonormal U, and its
+    error is within the randomized bound of the explicit block's SVD tail; PCG converges."""
+    p = W.poisson7(10)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(leaf_size=8, tau_O=24, tau_D=16))
+    aO, aD, ov = 0.4, 0.7, 4
+    f = F.factor_fixed_rank(an, aO, aD, ov)
+    assert f.restarts == 0
+    n_off = n_diag = 0
+    for j in range(an.nsuper):
+        s = f.sn[j]
+        if not s.compressed:
+            continue
+        c0, c1 = an.cols(j)
+        m = an.sym.rows[j].size
+        if m:
+            n_off += 1
+            r = s.U.shape[1]
+            assert r == F.rank_heuristic(m, c1 - c0, aO, ov) < min(m, c1 - c0), j
+            np.testing.assert_allclose(s.U.T @ s.U, np.eye(r), atol=1e-13)
+            S = _prefix_schur(f, j)
+            LO = sla.solve_triangular(_assemble_LD(f, j), S[an.sym.rows[j]].T, lower=True).T
+            sv = np.linalg.svd(LO, compute_uv=False)
+            k = r - ov
+            bound = np.sqrt(1 + k / (ov - 1)) * np.sqrt(np.sum(sv[k:] ** 2))
+            assert np.linalg.norm(LO - s.V @ s.U.T) <= 3 * bound, j
+        if s.D.hierarchical:
+            t = s.D.tree
+            for b in range(1, t.nblocks + 1):
+                if not t.leaf[b]:
+                    n_diag += 1
+                    r0, r1 = t.rows(b)
+                    q0, q1 = t.cols(b)
+                    assert s.D.U[b].shape[1] == F.rank_heuristic(r1 - r0, q1 - q0, aD, ov), (j, b)
+    assert n_off and n_diag
+    x, it, rr, ok = F.solve(an, f, p.b, 1e-8)
+    assert ok and rr <= 1e-8
+    A = p.scipy()
+    assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= 1e-8
+
+
+def test_fixed_rank_restart_grows_alpha_D(monkeypatch):
+    """Section 5.3: an indefinite diagonal block restarts with alpha^D <- 1.25 alpha^D
+    (planted failure in the oracle, on the CPU)."""
+    p = W.poisson7(10)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(leaf_size=8, tau_O=24, tau_D=16))
+    calls = {"n": 0}
+    orig = F.Factor.factor_diagonal
+
+    def failing(self, j, s):
+        if self.restarts < 2 and calls["n"] < 2:
+            calls["n"] += 1
+            raise dense.NotPositiveDefinite("planted")
+        return orig(self, j, s)
+
+    monkeypatch.setattr(F.Factor, "factor_diagonal", failing)
+    f = F.factor_fixed_rank(an, 0.5, 0.5, 4)
+    assert f.restarts == 2 and abs(f.alpha_D - 0.5 * 1.25 ** 2) < 1e-15 and f.diag_compress
+    with pytest.raises(ValueError):
+        F.factor_fixed_rank(an, -1.0)
