@@ -298,15 +298,19 @@ def main():
     d_x = torch.empty_like(d_b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def make(prec):
+    def make(prec, power_iters=0):
         t = time.perf_counter()
-        h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, R.rsc_options_default(precision=prec))
+        o = R.rsc_options_default(precision=prec, power_iters=power_iters)
+        h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
         return h, time.perf_counter() - t
 
-    def step(h):
+    def step(h, fixed_rank=False):
         flush.fill_(1.0)
         torch.cuda.synchronize()
-        R.rsc_factor(h, a.tol)
+        if fixed_rank:   # Section 5.2 ranks: alpha^O = alpha^D = 0.5, p = 8
+            R.rsc_factor_fixed_rank(h, 0.5, 0.5, 8)
+        else:
+            R.rsc_factor(h, a.tol)
         it, rr = R.rsc_solve_device(h, d_b, d_x, a.rtol, 2000)
         st = R.rsc_get_stats(h)
         return st["factor_seconds"] + st["solve_seconds"], it, rr, st
@@ -348,15 +352,21 @@ def main():
     t_e2e = time.perf_counter() - t0
     res = np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
     # the other forms, once each (after one untimed step)
-    def side_form(prec):
-        hs, _ = make(prec)
-        step(hs)
-        ts, its, rrs, sts = step(hs)
+    def side_form(prec, power_iters=0, fixed_rank=False):
+        hs, _ = make(prec, power_iters)
+        step(hs, fixed_rank)
+        ts, its, rrs, sts = step(hs, fixed_rank)
         return {"seconds": ts, "factor_s": sts["factor_seconds"], "solve_s": sts["solve_seconds"],
                 "iters": its, "relres": rrs, "factor_bytes": sts["factor_bytes"],
                 "factor_tflops": sts["factor_flops"] / sts["factor_seconds"] / 1e12}
     fp64 = side_form("fp64") if not a.no_fp64 and a.prec != "fp64" else None
     fp32 = side_form("fp32") if not a.no_fp64 and a.prec == "bf16" else None
+    # the paper's own rank rule (Section 5.2) in the same form: RSC0 and RSC1 (one power iteration)
+    fixed = None
+    if not a.no_fp64:
+        fixed = {f"rsc{q}": side_form(a.prec, q, True) for q in (0, 1)}
+        for q, v in enumerate(fixed.values()):
+            v.update({"alpha_O": 0.5, "alpha_D": 0.5, "p": 8, "power_iters": q})
     roof = None
     if dom and dom in kprof and kprof[dom]["ms"] > 0:
         k = kprof[dom]
@@ -386,7 +396,8 @@ def main():
         "factor_s": st["factor_seconds"], "solve_s": st["solve_seconds"],
         "factor_tflops": st["factor_flops"] / st["factor_seconds"] / 1e12, "factor_gflop": st["factor_flops"] / 1e9,
         "factor_bytes": st["factor_bytes"], "analyze_s": t_an, "restarts": st["restarts"],
-        "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "fp32_form": fp32, "roofline": roof,
+        "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "fp32_form": fp32,
+        "fixed_rank_form": fixed, "roofline": roof,
         "kernel_profile_untimed": prof_all,
         "cpu_baseline": cpu, "clocks": clk,
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(8 * (p.nnz + p.n)),

@@ -125,6 +125,23 @@ rsc_status rsc_get_structure(const rsc_handle* h, int64_t* rows_ptr, int32_t* ro
  */
 rsc_status rsc_factor(rsc_handle* h, double tol);
 
+/*
+ * Numeric factorization in the fixed-rank form of Section 5.2: the same supernodes
+ * as rsc_factor with tol > 0 are compressed, but each block B (m x n) gets the rank
+ * of Eq. rankFunction, ceil(alpha sqrt(k) log2 k) + p with k = min(m, n), capped at
+ * k: alpha_O for off-diagonal blocks L^O_j (Alg. 3), alpha_D for the internal
+ * blocks of hierarchical diagonal blocks (Section 4.2).  The samples are drawn in
+ * 16-column passes from the same Philox stream as rsc_factor, with
+ * opts.power_iters power iterations (Alg. 3); the adaptive stopping test is off, so
+ * a block stops early only when its sampled columns are numerically dependent.
+ * On an indefinite diagonal block the factorization restarts with
+ * alpha_D <- 1.25 alpha_D (Section 5.3, which starts from alpha_D = 0.5); after
+ * max_restarts restarts diagonal compression is switched off.
+ * Errors: RSC_ERR_INVALID_ARG (alpha_O, alpha_D negative or not finite, p < 0), and
+ * those of rsc_factor.  Synchronous.
+ */
+rsc_status rsc_factor_fixed_rank(rsc_handle* h, double alpha_O, double alpha_D, int32_t p);
+
 /* New values for the same pattern (val[nnz] as in rsc_analyze); the next
  * rsc_factor uses them. */
 rsc_status rsc_refactor_values(rsc_handle* h, const double* val);

@@ -56,6 +56,7 @@ _SIGS = {
     "rsc_get_ordering": (C.c_int, [_P, _P, C.POINTER(C.c_int32), _P]),
     "rsc_get_structure": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "rsc_factor": (C.c_int, [_P, C.c_double]),
+    "rsc_factor_fixed_rank": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32]),
     "rsc_refactor_values": (C.c_int, [_P, _P]),
     "rsc_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "rsc_solve_device": (C.c_int, [_P, _P, _P, C.c_double, C.c_int32, C.POINTER(C.c_int32),
@@ -160,6 +161,11 @@ def rsc_get_structure(h: Handle):
 
 def rsc_factor(h: Handle, tol: float) -> None:
     _check(lib().rsc_factor(h.ptr, float(tol)), h.ptr)
+
+
+def rsc_factor_fixed_rank(h: Handle, alpha_O: float, alpha_D: float = 0.5, p: int = 8) -> None:
+    """Fixed-rank form (Section 5.2): ranks ceil(alpha sqrt(k) log2 k) + p, k = min(m, n)."""
+    _check(lib().rsc_factor_fixed_rank(h.ptr, float(alpha_O), float(alpha_D), int(p)), h.ptr)
 
 
 def rsc_refactor_values(h: Handle, val) -> None:

@@ -10,6 +10,7 @@
 #include "rsc_internal.h"
 
 using rsc::Engine;
+using rsc::FixedRank;
 
 struct rsc_handle {
     rsc::Symbolic sym;
@@ -121,6 +122,20 @@ rsc_status rsc_factor(rsc_handle* h, double tol) {
     return guarded(h, [&]() -> rsc_status {
         if (!h->eng) h->eng = new Engine(h->sym, h->opts);
         return h->eng->factor(h->val.data(), tol);
+    });
+}
+
+rsc_status rsc_factor_fixed_rank(rsc_handle* h, double alpha_O, double alpha_D, int32_t p) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    if (!(std::isfinite(alpha_O) && alpha_O >= 0) || !(std::isfinite(alpha_D) && alpha_D >= 0) || p < 0)
+        return fail(h, RSC_ERR_INVALID_ARG, "alpha_O, alpha_D and p must be finite and >= 0");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng) h->eng = new Engine(h->sym, h->opts);
+        FixedRank fr;
+        fr.alpha_O = alpha_O;
+        fr.alpha_D = alpha_D;
+        fr.p = p;
+        return h->eng->factor(h->val.data(), 0.0, &fr);
     });
 }
 

@@ -183,7 +183,7 @@ struct Profiler {
 struct EngineImpl {
     Profiler prof;
     virtual ~EngineImpl() = default;
-    virtual rsc_status factor(const double* val, double tol) = 0;
+    virtual rsc_status factor(const double* val, double tol, const FixedRank* fr) = 0;
     virtual bool factored() const = 0;
     virtual void apply(const double* d_r, double* d_z, cudaStream_t s) = 0;
     virtual void prepare_multi(int) {}
@@ -653,6 +653,8 @@ struct EngineT final : EngineImpl {
     bool plan_compress = false, plan_diag = false, have_plan = false;
     bool is_factored = false;
     double tol = 0.0, tol_D = 0.0;
+    bool fixed = false;          // Section 5.2 ranks instead of the adaptive stopping test
+    FixedRank fr_cur;            // alpha_D as grown by the restarts of this factorization
     int restarts = 0;
     bool diag_on = false;
     // device tables
@@ -1684,6 +1686,7 @@ struct EngineT final : EngineImpl {
     struct RF {                    // one block being compressed
         int j = 0, s = 0;          // s == 0: L^O_j; else internal block s of L^D_j
         int m = 0, c = 0, maxr = 0;
+        int cap = 1 << 30;         // largest rank: Eq. rankFunction in the fixed-rank form
         double tol = 0;
         uint32_t block_id = 0;
         T* U = nullptr; T* V = nullptr;
@@ -1732,7 +1735,7 @@ struct EngineT final : EngineImpl {
     // Blocks small enough for one CTA (m, c <= rfd_max, no power iterations) go through the
     // dense mode; the rest through the batched cooperative passes.
     bool dense_ok(const RF& r) const {
-        const int mr = std::min(r.m, r.c);
+        const int mr = std::min(std::min(r.m, r.c), r.cap);
         return o.power_iters == 0 && mr > 0 && r.m <= rfd_max<T>() && r.c <= rfd_max<T>() &&
                rfd_smem<T>(r.m, r.c, mr) <= RFD_SMEM_CAP;
     }
@@ -1768,7 +1771,7 @@ struct EngineT final : EngineImpl {
         size_t smem = 0;
         for (size_t i = 0; i < R.size(); ++i) {
             RF& r = R[i];
-            r.maxr = std::min(r.m, r.c);
+            r.maxr = std::min(std::min(r.m, r.c), r.cap);
             T*& X = ident[r.c];
             if (!X) {
                 X = wsT((size_t)r.c * r.c);
@@ -1826,7 +1829,7 @@ struct EngineT final : EngineImpl {
         const int halves = small ? 2 : 1;
         for (size_t i = 0; i < R.size(); ++i) {
             RF& r = R[i];
-            r.maxr = std::min(r.m, r.c);
+            r.maxr = std::min(std::min(r.m, r.c), r.cap);
             r.rank = 0;
             r.active = r.maxr > 0;
             r.passes = 0;
@@ -1874,7 +1877,10 @@ struct EngineT final : EngineImpl {
                 std::vector<RF*> owner;
                 for (RF& r : R) {
                     if (!r.active || t < r.pref_base + r.pref_n) continue;
-                    const int np_ = std::min(PREFETCH, std::max(1, cdiv(r.maxr - r.rank, 16) + 1));
+                    // one pass beyond the rank cap holds the adaptive stopping test; the
+                    // fixed-rank form (tol = 0) has none
+                    const int extra = r.tol > 0 ? 1 : 0;
+                    const int np_ = std::min(PREFETCH, std::max(1, cdiv(r.maxr - r.rank, 16) + extra));
                     const int N = 16 * np_;
                     progs.emplace_back();
                     owner.push_back(&r);
@@ -2093,7 +2099,8 @@ struct EngineT final : EngineImpl {
                     r.j = j; r.s = s;
                     r.m = t.hi[s] - t.mid[s];
                     r.c = t.mid[s] - t.lo[s];
-                    r.tol = tol_D;
+                    r.tol = fixed ? 0.0 : tol_D;
+                    if (fixed) r.cap = rank_heuristic(r.m, r.c, fr_cur.alpha_D, fr_cur.p);
                     r.block_id = ((uint32_t)j << 12) | (uint32_t)s;
                     R.push_back(r);
                 }
@@ -2113,7 +2120,8 @@ struct EngineT final : EngineImpl {
                 RF r;
                 r.j = j; r.s = 0;
                 r.m = nd[j].r; r.c = nd[j].c;
-                r.tol = tol;
+                r.tol = fixed ? 0.0 : tol;
+                if (fixed) r.cap = rank_heuristic(r.m, r.c, fr_cur.alpha_O, fr_cur.p);
                 r.block_id = (uint32_t)j << 12;
                 R.push_back(r);
             }
@@ -2235,11 +2243,13 @@ struct EngineT final : EngineImpl {
         check_status();
     }
 
-    rsc_status factor(const double* val, double tol_in) override {
+    rsc_status factor(const double* val, double tol_in, const FixedRank* fr) override {
         is_factored = false;
-        tol = tol_in > 0 ? tol_in : 0.0;
+        fixed = fr != nullptr;
+        if (fixed) fr_cur = *fr;
+        tol = fixed ? 0.0 : (tol_in > 0 ? tol_in : 0.0);
         tol_D = tol;
-        const bool compress = tol > 0;
+        const bool compress = fixed || tol > 0;
         diag_on = compress && o.diag_compress;
         restarts = 0;
         cudaEvent_t e0, e1;
@@ -2266,8 +2276,9 @@ struct EngineT final : EngineImpl {
                 sync_stream();
                 prof.flush();
                 ++restarts;
-                if (restarts <= o.max_restarts) tol_D /= 1.25;
-                else diag_on = false;
+                if (restarts > o.max_restarts) diag_on = false;
+                else if (fixed) fr_cur.alpha_D *= 1.25;   // Section 5.3
+                else tol_D /= 1.25;
                 continue;
             }
             break;
@@ -3022,7 +3033,14 @@ Engine::Engine(const Symbolic& S, const rsc_options& o) {
     impl_->uid = ++g_engine_uid;
 }
 Engine::~Engine() = default;
-rsc_status Engine::factor(const double* val, double tol) { return impl_->factor(val, tol); }
+rsc_status Engine::factor(const double* val, double tol, const FixedRank* fr) { return impl_->factor(val, tol, fr); }
+
+int rank_heuristic(int m, int n, double alpha, int p) {
+    const int k = std::min(m, n);
+    if (k <= 0) return 0;
+    const double r = std::ceil(alpha * std::sqrt((double)k) * std::log2((double)k));
+    return (int)std::min<double>(k, r + p);
+}
 bool Engine::factored() const { return impl_->factored(); }
 rsc_status Engine::solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                               const std::vector<double>& val, const double* b, double* x, double rtol,

@@ -19,11 +19,20 @@ struct Error : std::runtime_error {
 
 struct EngineImpl;
 
+// Section 5.2's fixed-rank form of Alg. 3: block B (m x n) gets the rank of Eq. rankFunction,
+// ceil(alpha sqrt(k) log2 k) + p with k = min(m, n), capped at k; alpha_O for off-diagonal
+// blocks, alpha_D (grown by 1.25 per indefinite restart, Section 5.3) for diagonal blocks.
+struct FixedRank {
+    double alpha_O = 0.0, alpha_D = 0.0;
+    int p = 0;
+};
+int rank_heuristic(int m, int n, double alpha, int p);
+
 class Engine {
 public:
     Engine(const Symbolic& S, const rsc_options& o);
     ~Engine();
-    rsc_status factor(const double* val, double tol);
+    rsc_status factor(const double* val, double tol, const FixedRank* fr = nullptr);
     bool factored() const;
     rsc_status solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                           const std::vector<double>& val, const double* b, double* x, double rtol,

@@ -140,3 +140,13 @@ def test_symbolic_properties_full_size():
         tail = Rk[Rk >= sp[pk + 1]]
         Rp = rows[rows_ptr[pk]:rows_ptr[pk + 1]]
         assert np.all(np.isin(tail, Rp))
+
+
+@pytest.mark.parametrize("args", [(-1.0, 0.5, 8), (1.0, float("nan"), 8), (1.0, 0.5, -1), (float("inf"), 0.5, 4)])
+def test_factor_fixed_rank_rejects_bad_parameters(args):
+    """rsc_factor_fixed_rank checks alpha_O, alpha_D and p on the host, before any GPU work."""
+    p = W.poisson7(4)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, R.rsc_options_default())
+    with pytest.raises(R.RscError) as e:
+        R.rsc_factor_fixed_rank(h, *args)
+    assert e.value.status == 1 and "alpha" in R.rsc_last_error(h)
