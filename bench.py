@@ -39,18 +39,32 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16")
-    ap.add_argument("--side", type=int, default=96)
+    ap.add_argument("--side", type=int, default=None,
+                    help="grid side: 96 (diffusion cells) or 40 (elasticity elements) by default")
     ap.add_argument("--tol", type=float, default=1e-2)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", default="diffusion", choices=["diffusion", "batch"])
+    ap.add_argument("--workload", default="diffusion", choices=["diffusion", "elasticity", "batch"])
     ap.add_argument("--systems", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.side is None:
+        a.side = 40 if a.workload == "elasticity" else 96
+    return a
 
 
-def _workload_name(side, tol):
+def _elasticity_incl(ne):
+    """The stiff inclusion of an ne^3-element block: the central (ne/4)^3 elements."""
+    return (3 * ne // 8, 3 * ne // 8 + ne // 4)
+
+
+def _workload_name(side, tol, workload="diffusion"):
+    if workload == "elasticity":
+        n = 3 * side * (side + 1) ** 2
+        return (f"q1_elasticity_{side}^3 elements ({n:,} unknowns, 3 DOF per node kept together), x = 0 face "
+                f"clamped, E = 1, nu = 0.3, stiff inclusion E = 1e3 on the central {side // 4}^3 elements, "
+                f"body force; compression tol {tol:g}, 16-col Gaussian samples, PCG rtol 1e-8")
     return (f"fv_diffusion_grf_{side}^3 ({side ** 3:,} unknowns), conductivity exp(GRF sigma 2, corr len 8), "
             f"compression tol {tol:g}, 16-col Gaussian samples, PCG rtol 1e-8")
 
@@ -116,11 +130,14 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import workloads as W
 from oracle import factor as F
-g = W.grf(({side}, {side}, {side}), 2.0, 8.0, 0)
 c = {crop}
-p = W.fv_diffusion(np.exp(g[:c, :c, :c]), 0)
+if {elastic}:
+    p = W.elasticity_q1(c, incl={incl})
+else:
+    g = W.grf(({side}, {side}, {side}), 2.0, 8.0, 0)
+    p = W.fv_diffusion(np.exp(g[:c, :c, :c]), 0)
 t0 = time.perf_counter()
-an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords)
+an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(dof_per_node=p.dof_per_node))
 t1 = time.perf_counter()
 f = F.factor(an, {tol})
 t2 = time.perf_counter()
@@ -130,28 +147,36 @@ print(json.dumps(dict(n=p.n, analyze=t1 - t0, factor=t2 - t1, solve=t3 - t2, ite
 """
 
 
-def run_oracle_sample(side, crop, tol, rtol):
-    """The oracle, as it stands, on a crop of the same conductivity field (single thread)."""
+def run_oracle_sample(side, crop, tol, rtol, workload="diffusion"):
+    """The oracle, as it stands, on a crop of the same conductivity field, or on a smaller
+    elasticity block of the same shape (single thread)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_CODE.format(root=ROOT, side=side, crop=crop, tol=tol, rtol=rtol)
+    code = _ORACLE_CODE.format(root=ROOT, side=side, crop=crop, tol=tol, rtol=rtol,
+                               elastic=workload == "elasticity", incl=_elasticity_incl(crop))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(side, tol, rtol, crop=32):
-    r = run_oracle_sample(side, crop, tol, rtol)
+def cpu_baseline(side, tol, rtol, crop=32, workload="diffusion", n_full=None):
+    if workload == "elasticity":
+        crop = 12
+    r = run_oracle_sample(side, crop, tol, rtol, workload)
     secs = r["factor"] + r["solve"]
-    scale = (side ** 3) / r["n"]
+    scale = (n_full or side ** 3) / r["n"]
+    what = (f"a {crop}^3-element block of the same elasticity problem" if workload == "elasticity"
+            else f"the {crop}^3 corner crop of the same conductivity field")
     return {"value": secs * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle factor+PCG on the {crop}^3 corner crop of the same conductivity field "
+            "sample": (f"oracle factor+PCG on {what} "
                        f"({r['n']:,} unknowns, tol {tol:g}, {r['iters']} iterations, measured {secs:.2f} s), "
                        f"scaled linearly by unknowns x{scale:.1f} (a lower bound: the method is superlinear)")}
 
 
 # ----------------------------------------------------------------------------- reference arm
 FORMS = {"bf16": "BF16 Schur updates on tcgen05 (FP32 accumulation), FP32 factor and sampling, FP64 diagonal "
+                 "Cholesky and PCG",
+         "tf32": "TF32 Schur updates on tcgen05 (FP32 accumulation), FP32 factor and sampling, FP64 diagonal "
                  "Cholesky and PCG",
          "fp32": "FP32 factor, Schur updates and sampling; FP64 diagonal Cholesky and PCG",
          "fp64": "all FP64"}
@@ -178,21 +203,25 @@ def replica_seed(rank):
 def reference_arm(a, rank, world):
     if rank != 0:
         return
+    elastic = a.workload == "elasticity"
+    n_full = 3 * a.side * (a.side + 1) ** 2 if elastic else a.side ** 3
     vals = []
     rec = None
     for i in range(a.warmup + a.steps):
-        crop = 24 if i < a.warmup else 32
-        r = run_oracle_sample(a.side, crop, a.tol, a.rtol)
+        crop = (10 if i < a.warmup else 12) if elastic else (24 if i < a.warmup else 32)
+        r = run_oracle_sample(a.side, crop, a.tol, a.rtol, a.workload)
         if i >= a.warmup:
-            vals.append((r["factor"] + r["solve"]) * (a.side ** 3) / r["n"])
+            vals.append((r["factor"] + r["solve"]) * n_full / r["n"])
             rec = r
     v = sum(vals) / len(vals)
-    sample = (f"oracle (numpy FP64, 1 thread) factor+PCG on the 32^3 corner crop of the same conductivity field "
-              f"({rec['n']:,} unknowns, {rec['iters']} iterations), scaled linearly by unknowns to the full grid")
+    what = ("a 12^3-element block of the same elasticity problem" if elastic
+            else "the 32^3 corner crop of the same conductivity field")
+    sample = (f"oracle (numpy FP64, 1 thread) factor+PCG on {what} "
+              f"({rec['n']:,} unknowns, {rec['iters']} iterations), scaled linearly by unknowns to the full problem")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": _workload_name(a.side, a.tol), "form": "cpu oracle"},
+            "config": {"workload": _workload_name(a.side, a.tol, a.workload), "form": "cpu oracle"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -286,21 +315,25 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     # cpu baseline first (host cores; a separate process) so it does not overlap the GPU timing
+    elastic = a.workload == "elasticity"
+    if elastic:
+        p = W.elasticity_q1(a.side, incl=_elasticity_incl(a.side))
+    else:
+        p = W.diffusion_grf(a.side, 2.0, 8.0, seed=replica_seed(rank))
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(a.side, a.tol, a.rtol)
+            cpu = cpu_baseline(a.side, a.tol, a.rtol, workload=a.workload, n_full=p.n)
         except Exception as e:  # reported, not fatal
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
 
-    p = W.diffusion_grf(a.side, 2.0, 8.0, seed=replica_seed(rank))
     d_b = torch.tensor(p.b, device="cuda")
     d_x = torch.empty_like(d_b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def make(prec, power_iters=0):
         t = time.perf_counter()
-        o = R.rsc_options_default(precision=prec, power_iters=power_iters)
+        o = R.rsc_options_default(precision=prec, power_iters=power_iters, dof_per_node=p.dof_per_node)
         h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
         return h, time.perf_counter() - t
 
@@ -360,10 +393,10 @@ def main():
                 "iters": its, "relres": rrs, "factor_bytes": sts["factor_bytes"],
                 "factor_tflops": sts["factor_flops"] / sts["factor_seconds"] / 1e12}
     fp64 = side_form("fp64") if not a.no_fp64 and a.prec != "fp64" else None
-    fp32 = side_form("fp32") if not a.no_fp64 and a.prec == "bf16" else None
+    fp32 = side_form("fp32") if not a.no_fp64 and a.prec in ("bf16", "tf32") else None
     # the paper's own rank rule (Section 5.2) in the same form: RSC0 and RSC1 (one power iteration)
     fixed = None
-    if not a.no_fp64:
+    if not a.no_fp64 and not elastic:
         fixed = {f"rsc{q}": side_form(a.prec, q, True) for q in (0, 1)}
         for q, v in enumerate(fixed.values()):
             v.update({"alpha_O": 0.5, "alpha_D": 0.5, "p": 8, "power_iters": q})
@@ -380,7 +413,7 @@ def main():
         achieved = k["bytes"] / k["launches"] / (per_launch_ms * 1e-3) / 1e9
         # DRAM bytes per launch measured by ncu for the same workload (profiles/k_tn_diffusion48_fp32.md);
         # null for a kernel class without a capture of its current code
-        traffic = NCU_TRAFFIC.get(dom) if a.side == 96 else None
+        traffic = NCU_TRAFFIC.get(dom) if a.side == 96 and not elastic else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "launches_timed": k["launches"],
                 "avg_launch_us": per_launch_ms * 1e3,
@@ -388,8 +421,8 @@ def main():
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16": "bf16", "fp32": "f32"}.get(a.prec, "f64"), "data": "synthetic",
-        "config": {"workload": _workload_name(a.side, a.tol), "form": FORMS.get(a.prec, a.prec),
+        "dtype": {"bf16": "bf16", "tf32": "tf32", "fp32": "f32"}.get(a.prec, "f64"), "data": "synthetic",
+        "config": {"workload": _workload_name(a.side, a.tol, a.workload), "form": FORMS.get(a.prec, a.prec),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "L2 flushed (256 MB write) before each step; factor storage larger than L2"},
         "iters": iters[-1], "relres": rrs[-1], "true_relres_check": res,

@@ -687,7 +687,8 @@ struct EngineT final : EngineImpl {
     std::vector<std::vector<PanelStep>> panel_steps;   // [level][step]
     std::vector<PushTask*> push_tasks;
     std::vector<int> push_count;
-    bool tc = false;                      // BF16 form: extend-add on tcgen05 tensor cores
+    bool tc = false;                      // BF16 / TF32 forms: extend-add on tcgen05 tensor cores
+    bool tc_tf32 = false;                 // TF32 operands (kind::tf32) instead of BF16
     std::vector<PushTask*> push_tasks_tc; // 128 x 64 tiles
     std::vector<int> push_count_tc;
     // sparse block values are gathered at factor time from these source indices
@@ -701,9 +702,13 @@ struct EngineT final : EngineImpl {
     Scratch sy, stmp;
 
     EngineT(const Symbolic& S_, const rsc_options& o_) : S(S_), o(o_) {
-        tc = sizeof(T) == 4 && o.precision == RSC_PREC_BF16;
+        tc = sizeof(T) == 4 && (o.precision == RSC_PREC_BF16 || o.precision == RSC_PREC_TF32);
+        tc_tf32 = tc && o.precision == RSC_PREC_TF32;
         CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-        if (tc) CK(cudaFuncSetAttribute(k_push_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
+        if (tc) {
+            CK(cudaFuncSetAttribute(k_push_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
+            CK(cudaFuncSetAttribute(k_push_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
+        }
         CK(cudaFuncSetAttribute(k_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM_CAP));
         CK(cudaFuncSetAttribute(k_rf_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RFD_SMEM_CAP));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
@@ -2216,8 +2221,9 @@ struct EngineT final : EngineImpl {
                     pb += sizeof(T) * ((double)e.rows * h_lo[e.k].K + 2.0 * e.elems);
                 }
                 if (tc && push_count_tc[l]) {
+                    auto kern = tc_tf32 ? k_push_tc<true> : k_push_tc<false>;
                     PROF(prof, "push_tc", stream, pf, pb,
-                         k_push_tc<<<push_count_tc[l], 128, TC_PAD_SMEM, stream>>>(
+                         kern<<<push_count_tc[l], 128, TC_PAD_SMEM, stream>>>(
                              push_tasks_tc[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf, (float*)arena, d_status + 1));
                 } else {
                     PROF(prof, "push", stream, pf, pb,

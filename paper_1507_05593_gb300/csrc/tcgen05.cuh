@@ -1,12 +1,14 @@
-// Tensor-core (tcgen05, sm_103a) extend-add for the BF16 form.
+// Tensor-core (tcgen05, sm_103a) extend-add for the BF16 and TF32 forms.
 //
 // One CTA (4 warps) computes a 128 x 64 tile S = A B^T of a push task, A = rows
 // pr0..pr1 of L^O_k (or V_k), B = rows pc0..pc1, K = the operand's columns:
-//  * each 16-wide K chunk of A and B is converted to BF16 and written to shared
-//    memory in the canonical K-major no-swizzle layout (8 x 16-byte core matrices;
-//    K-adjacent cores 128 B apart (LBO), 8-row groups 256 B apart (SBO));
-//  * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M 128, N 64, K 16) into an
-//    FP32 accumulator in tensor memory and commits it to an mbarrier;
+//  * each 16-wide K chunk of A and B is rounded to BF16 (or TF32) and written to
+//    shared memory in the canonical K-major no-swizzle layout (8 x 16-byte core
+//    matrices; K-adjacent cores 128 B apart (LBO), 8-row groups 256 B apart (SBO));
+//    a TF32 chunk is two slabs of 8 K values, one per MMA;
+//  * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M 128, N 64, K 16), or two
+//    kind::tf32 (K 8 each), into an FP32 accumulator in tensor memory and commits them
+//    to an mbarrier;
 //  * the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31
 //    = rows) and scatter-adds it into the ancestor's storage like k_push.
 // Every wait is bounded: on expiry the kernel records an error code and returns
@@ -40,13 +42,28 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
     return d;                           // base offset 0, lbo mode 0, layout type 0 (no swizzle)
 }
 
-// instruction descriptor: D F32, A/B BF16, both K-major, N = 64, M = 128
+// instruction descriptors: D F32, A/B BF16 (format 1 of kind::f16) or TF32 (format 2 of
+// kind::tf32), both K-major, N = 64, M = 128
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
+constexpr uint32_t TC_IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
 
-// byte offset of element (r, k) of a K-major tile with 16-element K chunks
+// byte offset of element (r, k) of a K-major BF16 tile with 16-element K chunks
 __device__ __forceinline__ uint32_t tc_off(int r, int k) {
     return (uint32_t)(((r >> 3) * 2 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// byte offset of the 16-byte core-matrix row holding K values 4h .. 4h + 3 of row r of a
+// TF32 tile of `rows` rows: slab h / 2 (8 K values, rows x 32 bytes), core h % 2 in it
+__device__ __forceinline__ uint32_t tc_off_tf32(int r, int h, int rows) {
+    return (uint32_t)((h >> 1) * rows * 32 + (r >> 3) * 256 + (h & 1) * 128 + (r & 7) * 16);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float v) {   // round to nearest, ties away
+    uint32_t o;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(o) : "f"(v));
+    return o;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
@@ -64,13 +81,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
+template <bool TF32>
 __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ tasks, const LoOp* __restrict__ lo,
                                                  const NodeTgt* __restrict__ tgts, const int32_t* __restrict__ rows,
                                                  const long long* __restrict__ rows_ptr,
                                                  const LeafMap* __restrict__ leafmap, float* __restrict__ arena,
                                                  int* err) {
-    __shared__ __align__(1024) unsigned char As[TC_M * TC_K * 2];
-    __shared__ __align__(1024) unsigned char Bs[TC_N * TC_K * 2];
+    constexpr int EB = TF32 ? 4 : 2;   // bytes per staged operand element
+    __shared__ __align__(1024) unsigned char As[TC_M * TC_K * EB];
+    __shared__ __align__(1024) unsigned char Bs[TC_N * TC_K * EB];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ long long rpart[TC_M], rleaf[TC_M], cpart[TC_N], cleaf[TC_N];
@@ -134,6 +153,19 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
         // stage the chunk, zero outside the task: a thread converts 8 consecutive K values of one
         // row and stores them as one 16-byte row of a core matrix (conflict-free 16-byte stores)
         auto stage = [&](const float* src, int rows, int nr, unsigned char* dst) {
+            if (TF32) {   // a thread rounds 4 consecutive K values of one row: one 16-byte core row
+                for (int e = tid; e < rows * 4; e += blockDim.x) {
+                    const int r = e % rows, h = e / rows;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int kg = k0 + 4 * h + u;
+                        w[u] = to_tf32((r < nr && kg < op.K) ? src[r + (size_t)kg * op.ld] : 0.f);
+                    }
+                    *reinterpret_cast<uint4*>(dst + tc_off_tf32(r, h, rows)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                return;
+            }
             for (int e = tid; e < rows * 2; e += blockDim.x) {
                 const int r = e % rows, h = e / rows;     // h: K values 8h .. 8h + 7 of the chunk
                 uint32_t w[4];
@@ -154,13 +186,27 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t da = tc_desc(sa, 128, 256), db = tc_desc(sb, 128, 256);
             const uint32_t acc = chunks > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                :: "r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc) : "memory");
+            if (TF32) {
+#pragma unroll
+                for (int sl = 0; sl < 2; ++sl) {   // slab sl: K values 8 sl .. 8 sl + 7 of the chunk
+                    const uint64_t da = tc_desc(sa + sl * TC_M * 32, 128, 256);
+                    const uint64_t db = tc_desc(sb + sl * TC_N * 32, 128, 256);
+                    const uint32_t acc_s = sl ? 1u : acc;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                        :: "r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC_TF32), "r"(acc_s) : "memory");
+                }
+            } else {
+                const uint64_t da = tc_desc(sa, 128, 256), db = tc_desc(sb, 128, 256);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                    :: "r"(tmem), "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc) : "memory");
+            }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(bar) : "memory");
             if (!mbar_wait(bar, phase)) {
