@@ -145,6 +145,7 @@ rsc_status rsc_refactor_values(rsc_handle* h, const double* val) {
     for (size_t e = 0; e < h->val.size(); ++e)
         if (!std::isfinite(val[e])) return fail(h, RSC_ERR_INVALID_ARG, "non-finite matrix value");
     std::memcpy(h->val.data(), val, sizeof(double) * h->val.size());
+    if (h->eng) h->eng->values_changed();
     return RSC_OK;
 }
 

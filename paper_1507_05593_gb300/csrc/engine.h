@@ -33,6 +33,7 @@ public:
     Engine(const Symbolic& S, const rsc_options& o);
     ~Engine();
     rsc_status factor(const double* val, double tol, const FixedRank* fr = nullptr);
+    void values_changed();   // new values of A: the SpMV copy is refreshed by the next solve
     bool factored() const;
     rsc_status solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                           const std::vector<double>& val, const double* b, double* x, double rtol,

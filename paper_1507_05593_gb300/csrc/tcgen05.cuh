@@ -2,13 +2,15 @@
 //
 // One CTA (4 warps) computes a 128 x 64 tile S = A B^T of a push task, A = rows
 // pr0..pr1 of L^O_k (or V_k), B = rows pc0..pc1, K = the operand's columns:
-//  * each 16-wide K chunk of A and B is rounded to BF16 (or TF32) and written to
-//    shared memory in the canonical K-major no-swizzle layout (8 x 16-byte core
-//    matrices; K-adjacent cores 128 B apart (LBO), 8-row groups 256 B apart (SBO));
-//    a TF32 chunk is two slabs of 8 K values, one per MMA;
-//  * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M 128, N 64, K 16), or two
-//    kind::tf32 (K 8 each), into an FP32 accumulator in tensor memory and commits them
-//    to an mbarrier;
+//  * each 16-wide K chunk of A and B is rounded to BF16 (or split into TF32 high and
+//    low parts) and written to shared memory in the canonical K-major no-swizzle
+//    layout (8 x 16-byte core matrices; K-adjacent cores 128 B apart (LBO), 8-row
+//    groups 256 B apart (SBO)); a TF32 chunk is two slabs of 8 K values;
+//  * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M 128, N 64, K 16), or per
+//    TF32 slab three kind::tf32 (K 8): A_hi B_hi + A_hi B_lo + A_lo B_hi, the
+//    error-compensated split of Ootomo and Yokota (2022) that keeps the product near
+//    FP32 accuracy (the A_lo B_lo term is below FP32 rounding), into an FP32
+//    accumulator in tensor memory, and commits them to an mbarrier;
 //  * the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31
 //    = rows) and scatter-adds it into the ancestor's storage like k_push.
 // Every wait is bounded: on expiry the kernel records an error code and returns
@@ -25,8 +27,10 @@ namespace rsc {
 constexpr int TC_M = 128, TC_N = 64, TC_K = 16;
 constexpr unsigned long long TC_SPIN_LIMIT = 1ull << 22;
 // Dynamic shared memory requested only to cap residency at 4 CTAs per SM (4 x 64 of the
-// 512 tensor-memory columns), so that no CTA ever waits in tcgen05.alloc.
+// 512 tensor-memory columns), so that no CTA ever waits in tcgen05.alloc: with the static
+// tiles (9.0 KB BF16, 27.0 KB split TF32) a CTA holds 50 / 57 KB of the SM's 228 KB.
 constexpr int TC_PAD_SMEM = 40 * 1024;
+constexpr int TC_PAD_SMEM_TF32 = 28 * 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
                                                  const long long* __restrict__ rows_ptr,
                                                  const LeafMap* __restrict__ leafmap, float* __restrict__ arena,
                                                  int* err) {
-    constexpr int EB = TF32 ? 4 : 2;   // bytes per staged operand element
+    constexpr int EB = TF32 ? 8 : 2;   // bytes per staged operand element (TF32: high and low parts)
     __shared__ __align__(1024) unsigned char As[TC_M * TC_K * EB];
     __shared__ __align__(1024) unsigned char Bs[TC_N * TC_K * EB];
     __shared__ __align__(8) uint64_t mbar;
@@ -153,16 +157,21 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
         // stage the chunk, zero outside the task: a thread converts 8 consecutive K values of one
         // row and stores them as one 16-byte row of a core matrix (conflict-free 16-byte stores)
         auto stage = [&](const float* src, int rows, int nr, unsigned char* dst) {
-            if (TF32) {   // a thread rounds 4 consecutive K values of one row: one 16-byte core row
+            if (TF32) {   // a thread splits 4 consecutive K values of one row: one 16-byte core row
+                          // of high parts, one of low parts (the low tile follows the high one)
                 for (int e = tid; e < rows * 4; e += blockDim.x) {
                     const int r = e % rows, h = e / rows;
-                    uint32_t w[4];
+                    uint32_t w[4], lo[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int kg = k0 + 4 * h + u;
-                        w[u] = to_tf32((r < nr && kg < op.K) ? src[r + (size_t)kg * op.ld] : 0.f);
+                        const float v = (r < nr && kg < op.K) ? src[r + (size_t)kg * op.ld] : 0.f;
+                        w[u] = to_tf32(v);
+                        lo[u] = to_tf32(v - __uint_as_float(w[u]));
                     }
-                    *reinterpret_cast<uint4*>(dst + tc_off_tf32(r, h, rows)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    const uint32_t o = tc_off_tf32(r, h, rows);
+                    *reinterpret_cast<uint4*>(dst + o) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4*>(dst + rows * TC_K * 4 + o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                 }
                 return;
             }
@@ -188,11 +197,14 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc = chunks > 0 ? 1u : 0u;
             if (TF32) {
+                // slab sl: K values 8 sl .. 8 sl + 7 of the chunk; term t: (hi, hi), (hi, lo), (lo, hi)
 #pragma unroll
-                for (int sl = 0; sl < 2; ++sl) {   // slab sl: K values 8 sl .. 8 sl + 7 of the chunk
-                    const uint64_t da = tc_desc(sa + sl * TC_M * 32, 128, 256);
-                    const uint64_t db = tc_desc(sb + sl * TC_N * 32, 128, 256);
-                    const uint32_t acc_s = sl ? 1u : acc;
+                for (int q = 0; q < 6; ++q) {
+                    const int sl = q / 3, t = q % 3;
+                    const uint32_t a_lo = t == 2 ? TC_M * TC_K * 4 : 0, b_lo = t == 1 ? TC_N * TC_K * 4 : 0;
+                    const uint64_t da = tc_desc(sa + a_lo + sl * TC_M * 32, 128, 256);
+                    const uint64_t db = tc_desc(sb + b_lo + sl * TC_N * 32, 128, 256);
+                    const uint32_t acc_s = q ? 1u : acc;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"

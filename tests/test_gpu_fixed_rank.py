@@ -182,14 +182,14 @@ def test_fixed_rank_poisson32_defaults():
 def test_fixed_rank_mixed_precision(prec):
     """FP32, TF32 and BF16 forms with fixed ranks: ranks equal the FP64 oracle's (the cap
     decides them, not a rounding-sensitive test), blocks within the forms' rounding (1e-4
-    FP32, 4e-3 TF32 and 3e-2 BF16 operands of the Schur updates), PCG to 1e-8."""
+    FP32 and split TF32, 3e-2 BF16 operands of the Schur updates), PCG to 1e-8."""
     p = W.diffusion_grf(12, 2.0, 3.0, 0)
     kw = dict(leaf_size=16, tau_O=40, tau_D=32)
     o = R.rsc_options_default(precision=prec, **kw)
     h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
     R.rsc_factor_fixed_rank(h, 0.5, 0.5, 8)
     an, f = _oracle_fixed(p, R.rsc_options_default(**kw), 0.5, 0.5, 8)
-    tol_blk = {"fp32": 1e-4, "tf32": 4e-3, "bf16": 3e-2}[prec]
+    tol_blk = {"fp32": 1e-4, "tf32": 1e-4, "bf16": 3e-2}[prec]
     for j in range(an.nsuper):
         if f.sn[j].compressed:
             assert R.rsc_get_supernode_info(h, j)["rank"] == f.sn[j].U.shape[1], j
@@ -198,4 +198,4 @@ def test_fixed_rank_mixed_precision(prec):
         assert np.abs(np.tril(LD) - np.tril(LDo)).max() <= tol_blk * max(1, np.abs(LDo).max()), j
     x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
     _, it_ref, _, _ = F.solve(an, f, p.b, 1e-8, 500)
-    assert rr <= 1e-8 and it <= it_ref + {"fp32": 3, "tf32": 5, "bf16": 10}[prec]
+    assert rr <= 1e-8 and it <= it_ref + {"fp32": 3, "tf32": 3, "bf16": 10}[prec]
