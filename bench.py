@@ -41,16 +41,19 @@ def _args():
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--side", type=int, default=None,
                     help="grid side: 96 (diffusion cells) or 40 (elasticity elements) by default")
-    ap.add_argument("--tol", type=float, default=1e-2)
+    ap.add_argument("--tol", type=float, default=None, help="compression tolerance: 0.1 (poisson) or 0.01")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", default="diffusion", choices=["diffusion", "elasticity", "batch"])
+    ap.add_argument("--workload", default="diffusion",
+                    choices=["diffusion", "elasticity", "poisson", "batch", "autograd"])
     ap.add_argument("--systems", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
     if a.side is None:
-        a.side = 40 if a.workload == "elasticity" else 96
+        a.side = {"elasticity": 40, "poisson": 32, "autograd": 64}.get(a.workload, 96)
+    if a.tol is None:
+        a.tol = 0.1 if a.workload == "poisson" else 1e-2
     return a
 
 
@@ -60,6 +63,9 @@ def _elasticity_incl(ne):
 
 
 def _workload_name(side, tol, workload="diffusion"):
+    if workload == "poisson":
+        return (f"poisson7_{side}^3 ({side ** 3:,} unknowns, Dirichlet), b ~ U[-1,1] seed 0, compression tol "
+                f"{tol:g}, 16-col Gaussian samples, PCG rtol 1e-8")
     if workload == "elasticity":
         n = 3 * side * (side + 1) ** 2
         return (f"q1_elasticity_{side}^3 elements ({n:,} unknowns, 3 DOF per node kept together), x = 0 face "
@@ -131,8 +137,10 @@ import numpy as np
 import workloads as W
 from oracle import factor as F
 c = {crop}
-if {elastic}:
+if {kind!r} == "elasticity":
     p = W.elasticity_q1(c, incl={incl})
+elif {kind!r} == "poisson":
+    p = W.poisson7(c)
 else:
     g = W.grf(({side}, {side}, {side}), 2.0, 8.0, 0)
     p = W.fv_diffusion(np.exp(g[:c, :c, :c]), 0)
@@ -151,8 +159,8 @@ def run_oracle_sample(side, crop, tol, rtol, workload="diffusion"):
     """The oracle, as it stands, on a crop of the same conductivity field, or on a smaller
     elasticity block of the same shape (single thread)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_CODE.format(root=ROOT, side=side, crop=crop, tol=tol, rtol=rtol,
-                               elastic=workload == "elasticity", incl=_elasticity_incl(crop))
+    code = _ORACLE_CODE.format(root=ROOT, side=side, crop=crop, tol=tol, rtol=rtol, kind=workload,
+                               incl=_elasticity_incl(crop))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -162,11 +170,13 @@ def run_oracle_sample(side, crop, tol, rtol, workload="diffusion"):
 def cpu_baseline(side, tol, rtol, crop=32, workload="diffusion", n_full=None):
     if workload == "elasticity":
         crop = 12
+    elif workload == "poisson":
+        crop = side          # the whole problem: seconds for the oracle
     r = run_oracle_sample(side, crop, tol, rtol, workload)
     secs = r["factor"] + r["solve"]
     scale = (n_full or side ** 3) / r["n"]
-    what = (f"a {crop}^3-element block of the same elasticity problem" if workload == "elasticity"
-            else f"the {crop}^3 corner crop of the same conductivity field")
+    what = {"elasticity": f"a {crop}^3-element block of the same elasticity problem",
+            "poisson": "the whole problem"}.get(workload, f"the {crop}^3 corner crop of the same conductivity field")
     return {"value": secs * scale, "unit": "s", "cores": 1, "kind": "oracle",
             "sample": (f"oracle factor+PCG on {what} "
                        f"({r['n']:,} unknowns, tol {tol:g}, {r['iters']} iterations, measured {secs:.2f} s), "
@@ -208,14 +218,19 @@ def reference_arm(a, rank, world):
     vals = []
     rec = None
     for i in range(a.warmup + a.steps):
-        crop = (10 if i < a.warmup else 12) if elastic else (24 if i < a.warmup else 32)
+        if elastic:
+            crop = 10 if i < a.warmup else 12
+        elif a.workload == "poisson":
+            crop = a.side
+        else:
+            crop = 24 if i < a.warmup else 32
         r = run_oracle_sample(a.side, crop, a.tol, a.rtol, a.workload)
         if i >= a.warmup:
             vals.append((r["factor"] + r["solve"]) * n_full / r["n"])
             rec = r
     v = sum(vals) / len(vals)
-    what = ("a 12^3-element block of the same elasticity problem" if elastic
-            else "the 32^3 corner crop of the same conductivity field")
+    what = {"elasticity": "a 12^3-element block of the same elasticity problem",
+            "poisson": "the whole problem"}.get(a.workload, "the 32^3 corner crop of the same conductivity field")
     sample = (f"oracle (numpy FP64, 1 thread) factor+PCG on {what} "
               f"({rec['n']:,} unknowns, {rec['iters']} iterations), scaled linearly by unknowns to the full problem")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
@@ -286,7 +301,63 @@ def batch_workload(a):
                        "form": FORMS.get(a.prec, a.prec)},
             "factor_s": fs, "solve_s": ss, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "relres_max": float(rr.max()), "analyze_s": t_an, "factor_bytes": st["factor_bytes"],
-            "gpu_launches": st["gpu_launches"], "n_supernodes": st["n_supernodes"], "n_levels": st["n_levels"]}
+            "gpu_launches": st["gpu_launches"], "n_supernodes": st["n_supernodes"], "n_levels": st["n_levels"],
+            "restarts": st["restarts"]}
+    print(json.dumps(line), flush=True)
+
+
+def autograd_workload(a):
+    """Differentiation form: loss 0.5 ||x(theta) - x*||^2 for the 7-point FV diffusion operator
+    on a side^3 grid with per-cell log-conductivity theta ~ N(0, 1) (seed 0), x* solved from
+    theta + 0.1 N(0, 1) (seed 1), b ~ U[-1, 1] (seed 2).  Forward = refactor with the new values
+    + PCG; backward = the adjoint PCG with the kept factor + the pattern contraction, then
+    autograd through the values to theta.  Timed with CUDA events around each, after warm-up."""
+    import numpy as np
+    import torch
+
+    import paper_1507_05593_gb300 as R
+    import workloads as W
+    from paper_1507_05593_gb300.autograd import sparse_spd_solve
+
+    torch.cuda.set_device(0)
+    shape = (a.side,) * 3
+    fv = W.FVValues(shape)
+    theta = np.random.default_rng(0).standard_normal(shape)
+    theta_star = theta + 0.1 * np.random.default_rng(1).standard_normal(shape)
+    b = torch.tensor(np.random.default_rng(2).uniform(-1, 1, fv.n), device="cuda")
+    h = R.rsc_analyze(fv.n, fv.row_ptr, fv.col_idx, fv(torch.tensor(theta)).numpy(), fv.coords,
+                      R.rsc_options_default(precision=a.prec))
+    with torch.no_grad():
+        xs = sparse_spd_solve(fv(torch.tensor(theta_star, device="cuda")), b, h, tol=a.tol, rtol=a.rtol)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw, bw = [], []
+    for i in range(a.warmup + a.steps):
+        flush.fill_(1.0)
+        th = torch.tensor(theta, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        ev[0].record()
+        x = sparse_spd_solve(fv(th), b, h, tol=a.tol, rtol=a.rtol)
+        loss = 0.5 * ((x - xs) ** 2).sum()
+        ev[1].record()
+        loss.backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        if i >= a.warmup:
+            fw.append(ev[0].elapsed_time(ev[1]) * 1e-3)
+            bw.append(ev[1].elapsed_time(ev[2]) * 1e-3)
+    st = R.rsc_get_stats(h)
+    f, g = sum(fw) / len(fw), sum(bw) / len(bw)
+    line = {"metric": "loss forward (factor + PCG) + backward (adjoint PCG, kept factor) seconds",
+            "value": f + g, "unit": "s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "higher_is_better": False, "dtype": {"bf16": "bf16", "tf32": "tf32", "fp32": "f32"}.get(a.prec, "f64"),
+            "data": "synthetic",
+            "config": {"workload": f"FV diffusion {a.side}^3, per-cell log-conductivity theta ~ N(0,1), "
+                                   f"loss 0.5||x(theta) - x*||^2, tol {a.tol:g}, PCG rtol {a.rtol:g}",
+                       "form": FORMS.get(a.prec, a.prec)},
+            "forward_s": f, "backward_s": g, "grad_norm": float(th.grad.norm()), "loss": float(loss),
+            "last_iters": st["last_iters"], "factor_bytes": st["factor_bytes"], "restarts": st["restarts"],
+            "gpu_launches": st["gpu_launches"]}
     print(json.dumps(line), flush=True)
 
 
@@ -301,6 +372,10 @@ def main():
     if a.workload == "batch":
         if rank == 0:
             batch_workload(a)
+        return
+    if a.workload == "autograd":
+        if rank == 0:
+            autograd_workload(a)
         return
     import numpy as np
     import torch
@@ -318,6 +393,8 @@ def main():
     elastic = a.workload == "elasticity"
     if elastic:
         p = W.elasticity_q1(a.side, incl=_elasticity_incl(a.side))
+    elif a.workload == "poisson":
+        p = W.poisson7(a.side)
     else:
         p = W.diffusion_grf(a.side, 2.0, 8.0, seed=replica_seed(rank))
     cpu = None
@@ -407,7 +484,7 @@ def main():
     fp32 = side_form("fp32") if not a.no_fp64 and a.prec in ("bf16", "tf32") else None
     # the paper's own rank rule (Section 5.2) in the same form: RSC0 and RSC1 (one power iteration)
     fixed = None
-    if not a.no_fp64 and not elastic:
+    if not a.no_fp64 and a.workload == "diffusion":
         fixed = {f"rsc{q}": side_form(a.prec, q, True) for q in (0, 1)}
         for q, v in enumerate(fixed.values()):
             v.update({"alpha_O": 0.5, "alpha_D": 0.5, "p": 8, "power_iters": q})
@@ -424,7 +501,7 @@ def main():
         achieved = k["bytes"] / k["launches"] / (per_launch_ms * 1e-3) / 1e9
         # DRAM bytes per launch measured by ncu for the same workload (profiles/k_tn_diffusion48_fp32.md);
         # null for a kernel class without a capture of its current code
-        traffic = NCU_TRAFFIC.get(dom) if a.side == 96 and not elastic else None
+        traffic = NCU_TRAFFIC.get(dom) if a.side == 96 and a.workload == "diffusion" else None
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "launches_timed": k["launches"],
                 "avg_launch_us": per_launch_ms * 1e3,

@@ -52,12 +52,40 @@ class DeviceMem {
 public:
     ~DeviceMem() { release(); }
     void* alloc(size_t bytes) {
-        void* p = nullptr;
         if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) / 256 * 256;
+        // a block kept by recycle() of the same size class (bytes .. 2 bytes), smallest first
+        int bi = -1;
+        for (int i = 0; i < (int)free_.size(); ++i)
+            if (free_[i].second >= bytes && free_[i].second <= 2 * bytes &&
+                (bi < 0 || free_[i].second < free_[bi].second))
+                bi = i;
+        if (bi >= 0) {
+            const auto b = free_[bi];
+            free_.erase(free_.begin() + bi);
+            ptrs_.push_back(b.first);
+            sizes_.push_back(b.second);
+            total_ += b.second;
+            return b.first;
+        }
+        void* p = nullptr;
         CK(cudaMalloc(&p, bytes));
         ptrs_.push_back(p);
+        sizes_.push_back(bytes);
         total_ += bytes;
         return p;
+    }
+    // keep every block for the next allocations of the same sizes (a launch list rebuilt
+    // after each factorization), instead of freeing and allocating them again
+    void recycle() {
+        for (size_t i = 0; i < ptrs_.size(); ++i) free_.emplace_back(ptrs_[i], sizes_[i]);
+        ptrs_.clear();
+        sizes_.clear();
+        total_ = 0;
+    }
+    void trim() {   // free the kept blocks that no allocation took
+        for (auto& b : free_) cudaFree(b.first);
+        free_.clear();
     }
     template <class X> X* upload(const std::vector<X>& v, cudaStream_t s) {
         X* p = (X*)alloc(sizeof(X) * std::max<size_t>(v.size(), 1));
@@ -67,12 +95,16 @@ public:
     void release() {
         for (void* p : ptrs_) cudaFree(p);
         ptrs_.clear();
+        sizes_.clear();
         total_ = 0;
+        trim();
     }
     size_t total() const { return total_; }
 
 private:
     std::vector<void*> ptrs_;
+    std::vector<size_t> sizes_;
+    std::vector<std::pair<void*, size_t>> free_;
     size_t total_ = 0;
 };
 
@@ -1803,10 +1835,21 @@ struct EngineT final : EngineImpl {
         CK(cudaMemcpyAsync(rank_host + rank_host_cap, d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, stream));
         sync_stream();
         if (rank_host[rank_host_cap]) throw Error(RSC_ERR_NOT_SPD, "non-finite sample");
+        // algorithmic work: the range finder on the dense block (three projections and Gram
+        // matrices per pass) and V = B U; bytes: the block read once, U and V written once
+        double pf = 0, pb = 0;
         for (size_t i = 0; i < R.size(); ++i) {
             RF& r = R[i];
             r.rank = rank_host[i];
-            flops += (double)r.rank * 3.0 * 4.0 * r.c * r.rank + 2.0 * r.m * r.c * r.rank;
+            const double f = (double)r.rank * 3.0 * 4.0 * r.c * r.rank + 2.0 * r.m * r.c * r.rank;
+            flops += f;
+            pf += f;
+            pb += sizeof(T) * ((double)r.m * r.c + (double)(r.m + r.c) * r.rank);
+        }
+        if (prof.enabled("rf_dense")) {
+            auto& a = prof.acc["rf_dense" + prof.tag];
+            a.flops += pf;
+            a.bytes += pb;
         }
     }
 
@@ -2252,6 +2295,8 @@ struct EngineT final : EngineImpl {
 
     rsc_status factor(const double* val, double tol_in, const FixedRank* fr) override {
         is_factored = false;
+        plan1.clear();   // launch lists of the previous factor: their memory is released now
+        planN.clear();
         fixed = fr != nullptr;
         if (fixed) fr_cur = *fr;
         tol = fixed ? 0.0 : (tol_in > 0 ? tol_in : 0.0);
@@ -2291,12 +2336,9 @@ struct EngineT final : EngineImpl {
             }
             break;
         }
-        // the preconditioner's launch list is part of building it
+        // the launch lists of the preconditioner apply are built at their first use (inside the
+        // solve's timed region): one column for rsc_solve, N columns for the batched solve
         ++factor_gen;
-        {
-            HostTimer ht_(this, "h_solve_plan");
-            build_solve_plan();
-        }
         CK(cudaEventRecord(e1, stream));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -2346,10 +2388,10 @@ struct EngineT final : EngineImpl {
         cudaGraphExec_t graph = nullptr;
         long long gen = -1;              // factorization the plan was built for
         double flops = 0, bytes = 0;
-        void clear() {
+        void clear() {   // the plan's device blocks are kept for its rebuild (DeviceMem::recycle)
             if (graph) cudaGraphExecDestroy(graph);
             graph = nullptr;
-            mem.release();
+            mem.recycle();
             seq.clear();
             flops = bytes = 0;
             gen = -1;
@@ -2658,6 +2700,7 @@ struct EngineT final : EngineImpl {
         CK(cudaStreamEndCapture(stream, &g));
         CK(cudaGraphInstantiate(&pl->graph, g, 0));
         CK(cudaGraphDestroy(g));
+        pl->mem.trim();
     }
 
     bool no_graph = std::getenv("RSC_NO_GRAPH") != nullptr;   // measurement aid: per-kernel apply profile
@@ -2716,11 +2759,18 @@ struct EngineT final : EngineImpl {
         launches += (long long)A.seq.size();
         if (d_z != A.gout) CK(cudaMemcpyAsync(d_z, A.gout, bytes, cudaMemcpyDeviceToDevice, s));
     }
-    void apply(const double* d_r, double* d_z, cudaStream_t s) override { run_plan(plan1, d_r, d_z, s); }
+    void apply(const double* d_r, double* d_z, cudaStream_t s) override {
+        if (plan1.gen != factor_gen || !plan1.graph) {
+            HostTimer ht_(this, "h_solve_plan");
+            build_solve_plan(1);
+        }
+        run_plan(plan1, d_r, d_z, s);
+    }
     long long n_of() const override { return S.n; }
     // nrhs right-hand sides at once (column c at d_r + c n): one pass over the factor for all
     void prepare_multi(int nrhs) override {
         if (nrhs > 1 && (planN.N != nrhs || planN.gen != factor_gen || !planN.graph)) {
+            HostTimer ht_(this, "h_solve_plan");
             build_solve_plan(nrhs);
             pl = &plan1;
         }
