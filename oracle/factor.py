@@ -64,6 +64,7 @@ from scipy.sparse import csgraph
 
 from . import dense
 from .dense import NotPositiveDefinite
+from .ordering import node_graph, spectral_coordinates
 from .ordering import order as nd_order
 from .philox import gaussian_block
 from .scatter import gather_rows, positions, scatter_rows
@@ -81,6 +82,7 @@ class Options:
     max_restarts: int = 8
     seed: int = 0
     diag_compress: bool = True
+    ordering: int = 0          # 0: lattice bisection; 1: graph nested dissection
 
 
 class Analysis:
@@ -95,8 +97,14 @@ class Analysis:
         Pn = sp.csr_matrix((np.ones(len(col_idx)), (np.repeat(np.arange(n), np.diff(row_ptr)) // dof,
                                                       np.asarray(col_idx) // dof)), shape=(n // dof, n // dof))
         ncomp, labels = csgraph.connected_components(Pn, directed=False)
-        self.ordering = nd_order(coords, dof, opts.leaf_size, opts.tau_O, opts.tau_D,
-                                 labels if ncomp > 1 else None)
+        comps = labels if ncomp > 1 else None
+        graph = None
+        if opts.ordering == 1 or coords is None:
+            graph = node_graph(n, row_ptr, col_idx, dof)
+            if coords is None:   # Section 4.3: positions from the graph Laplacian
+                coords = np.repeat(spectral_coordinates(graph[0], graph[1], comps), dof, axis=0)
+        self.coords = coords
+        self.ordering = nd_order(coords, dof, opts.leaf_size, opts.tau_O, opts.tau_D, comps, graph)
         p = self.ordering.perm
         self.A = A
         self.Ap = sp.csr_matrix(A[p][:, p])

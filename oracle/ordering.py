@@ -26,6 +26,27 @@
   paper's 7-block example names the root's children "3 and 6"; the block layout
   it draws makes them 2 and 6, which is what an in-order labelling gives.
 
+* Graph nested dissection (general sparsity; the paper's partitioner is unnamed, and
+  its non-grid examples need one that does not assume a lattice).  Reading: recursive
+  bisection of the node graph guided by real node positions X (given, or the spectral
+  coordinates below):
+
+  - a node set with at most ``leaf_size`` nodes is a leaf;
+  - otherwise take the axis of largest bounding-box extent of X (ties: lowest axis),
+    sort the nodes by (X[axis], node id) and cut at the median: L = the first
+    floor(size/2) nodes, R = the rest;
+  - the vertex separator is the boundary of the cut on one side: S_L = nodes of L
+    with a neighbour in R, S_R = nodes of R with a neighbour in L; S = S_L if
+    |S_L| <= |S_R| else S_R (removing S leaves no edge between the two halves);
+  - recurse on L minus S and R minus S, then the separator (postorder); inside a leaf or
+    separator, nodes are in ascending id order.
+
+* Spectral coordinates, Section 4.3: where no positions are given, node i sits at
+  (v1_i, v2_i, v3_i) for the three lowest eigenvectors of the node graph's Laplacian
+  (off-diagonal -1 per edge, diagonal = degree).  Reading: per connected component,
+  skipping that component's constant null vector (it carries no position); the
+  oracle solves the dense eigenproblem.
+
 Unknowns: with ``dof`` unknowns per node, node i owns unknowns dof*i .. dof*i+dof-1,
 which stay adjacent.  ``tau_D`` and supernode sizes count unknowns; the leaf
 rule counts nodes.
@@ -78,6 +99,109 @@ def nested_dissection(coords: np.ndarray, leaf_size: int = 64, dof: int = 1, com
             rec(np.nonzero(comp == c)[0].astype(np.int64))
     order = np.concatenate([p[1] for p in parts])
     return order, parts
+
+
+def _component_order(nnodes, components):
+    """Node id arrays of the connected components, in order of their smallest node."""
+    if components is None:
+        return [np.arange(nnodes, dtype=np.int64)]
+    comp = np.asarray(components)
+    first = {}
+    for i, c in enumerate(comp.tolist()):
+        first.setdefault(c, i)
+    return [np.nonzero(comp == c)[0].astype(np.int64) for c in sorted(first, key=first.get)]
+
+
+def graph_nested_dissection(adj_ptr, adj_idx, X, leaf_size: int = 64, components=None):
+    """Graph nested dissection of the node graph (CSR adjacency without self loops,
+    symmetric) guided by node positions X (nodes x 3, real).  Returns parts as
+    ``nested_dissection`` does."""
+    adj_ptr = np.asarray(adj_ptr)
+    adj_idx = np.asarray(adj_idx)
+    X = np.asarray(X, dtype=np.float64)
+    nnodes = X.shape[0]
+    parts: list[tuple[str, np.ndarray]] = []
+    side = np.zeros(nnodes, dtype=np.int8)      # scratch: 1 = in L, 2 = in R
+
+    def boundary(A, other):
+        """Nodes of A with a neighbour marked ``other``."""
+        out = []
+        for v in A.tolist():
+            nb = adj_idx[adj_ptr[v]:adj_ptr[v + 1]]
+            if np.any(side[nb] == other):
+                out.append(v)
+        return np.array(out, dtype=np.int64)
+
+    def rec(ids):
+        if ids.size == 0:
+            return
+        if ids.size <= leaf_size:
+            parts.append(("leaf", np.sort(ids)))
+            return
+        pts = X[ids]
+        ext = pts.max(axis=0) - pts.min(axis=0)
+        ax = int(np.argmax(ext))                    # first maximum = lowest axis on ties
+        srt = ids[np.lexsort((ids, pts[:, ax]))]    # by (X[ax], id)
+        h = ids.size // 2
+        L, R = srt[:h], srt[h:]
+        side[L] = 1
+        side[R] = 2
+        SL, SR = boundary(L, 2), boundary(R, 1)
+        side[ids] = 0
+        S = SL if SL.size <= SR.size else SR
+        inS = np.zeros(nnodes, dtype=bool)
+        inS[S] = True
+        rec(np.sort(L[~inS[L]]))
+        rec(np.sort(R[~inS[R]]))
+        if S.size:
+            parts.append(("sep", np.sort(S)))
+
+    for ids in _component_order(nnodes, components):
+        rec(ids)
+    order = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0, dtype=np.int64)
+    return order, parts
+
+
+def spectral_coordinates(adj_ptr, adj_idx, components=None) -> np.ndarray:
+    """Section 4.3: positions from the three lowest non-constant eigenvectors of the
+    graph Laplacian, per connected component (dense eigensolver: small graphs only).
+    Components with fewer than 4 nodes keep the missing coordinates at 0."""
+    adj_ptr = np.asarray(adj_ptr)
+    adj_idx = np.asarray(adj_idx)
+    nnodes = adj_ptr.size - 1
+    X = np.zeros((nnodes, 3))
+    for ids in _component_order(nnodes, components):
+        m = ids.size
+        if m < 2:
+            continue
+        if m > 6000:
+            raise NotImplementedError("the oracle's dense eigensolver is for small graphs")
+        loc = -np.ones(nnodes, dtype=np.int64)
+        loc[ids] = np.arange(m)
+        Lap = np.zeros((m, m))
+        for a, v in enumerate(ids.tolist()):
+            nb = loc[adj_idx[adj_ptr[v]:adj_ptr[v + 1]]]
+            Lap[a, nb] = -1.0
+            Lap[a, a] = nb.size
+        w, V = np.linalg.eigh(Lap)
+        k = min(3, m - 1)
+        X[ids, :k] = V[:, 1:1 + k]                 # column 0: the constant null vector
+    return X
+
+
+def node_graph(n, row_ptr, col_idx, dof: int = 1):
+    """CSR adjacency (sorted, no self loops) of the node graph: nodes u != v adjacent
+    when some unknown of u couples with some unknown of v in A's pattern."""
+    rp = np.asarray(row_ptr)
+    ci = np.asarray(col_idx)
+    rows = np.repeat(np.arange(n), np.diff(rp)) // dof
+    cols = ci // dof
+    keep = rows != cols
+    pairs = np.unique(np.stack([rows[keep], cols[keep]], axis=1), axis=0)
+    nn = n // dof
+    ptr = np.zeros(nn + 1, dtype=np.int64)
+    np.add.at(ptr, pairs[:, 0] + 1, 1)
+    return np.cumsum(ptr), pairs[:, 1].astype(np.int64)
 
 
 class BlockTree:
@@ -166,11 +290,19 @@ class Ordering:
 
 
 def order(coords: np.ndarray, dof: int = 1, leaf_size: int = 64, tau_O: int = 256,
-          tau_D: int = 256, components=None) -> Ordering:
+          tau_D: int = 256, components=None, graph=None) -> Ordering:
     """Nested dissection, then the Section 4.1 reorder of every separator that will
     be compressed (>= tau_O unknowns, Section 3.1: "at least tau_O") and whose
-    diagonal block is larger than tau_D."""
-    _, parts = nested_dissection(coords, leaf_size, dof, components)
+    diagonal block is larger than tau_D.
+
+    graph: None for the lattice bisection; (adj_ptr, adj_idx) of the node graph for
+    graph nested dissection guided by ``coords`` (one row per unknown, as for the
+    lattice form)."""
+    if graph is None:
+        _, parts = nested_dissection(coords, leaf_size, dof, components)
+    else:
+        _, parts = graph_nested_dissection(graph[0], graph[1], np.asarray(coords)[::dof], leaf_size,
+                                           components)
     node_blocks = []
     trees = []
     for kind, ids in parts:

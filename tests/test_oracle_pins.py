@@ -551,3 +551,146 @@ def test_fixed_rank_restart_grows_alpha_D(monkeypatch):
     assert f.restarts == 2 and abs(f.alpha_D - 0.5 * 1.25 ** 2) < 1e-15 and f.diag_compress
     with pytest.raises(ValueError):
         F.factor_fixed_rank(an, -1.0)
+
+
+# --------------------------------------------------------------------------- graph ordering, spectral coordinates
+
+from oracle.ordering import graph_nested_dissection, node_graph, spectral_coordinates  # noqa: E402
+
+
+def _path_graph(n):
+    ptr = [0]
+    idx = []
+    for v in range(n):
+        nb = [u for u in (v - 1, v + 1) if 0 <= u < n]
+        idx += nb
+        ptr.append(len(idx))
+    return np.array(ptr), np.array(idx)
+
+
+def test_graph_nd_path_worked_example():
+    """Hand-computed from the definition (path 0-1-...-9, X = index, leaf_size 2):
+    [0..9] -> L [0..4], R [5..9], S_L {4} (ties go to L);  [0..3] -> S {1}, leaves [0], [2,3];
+    [5..9] -> S {6}, leaf [5], [7..9] -> S {7}, leaf [8,9].  Postorder: 0 | 2 3 | 1 | 5 |
+    8 9 | 7 | 6 | 4."""
+    ptr, idx = _path_graph(10)
+    X = np.stack([np.arange(10.0), np.zeros(10), np.zeros(10)], axis=1)
+    order, parts = graph_nested_dissection(ptr, idx, X, leaf_size=2)
+    assert order.tolist() == [0, 2, 3, 1, 5, 8, 9, 7, 6, 4]
+    assert [k for k, _ in parts] == ["leaf", "leaf", "sep", "leaf", "leaf", "sep", "sep", "sep"]
+
+
+def test_graph_nd_grid_top_separator_is_a_grid_line():
+    """8 x 8 grid (5-point graph), X = lattice positions: the median cut along x puts
+    columns 0-3 in L; both boundaries are one column of 8 nodes, the tie goes to L, so the
+    last part is the column x = 3; every node appears once."""
+    p = W.poisson7(8, 8, 1)
+    ptr, idx = node_graph(p.n, p.row_ptr, p.col_idx)
+    order, parts = graph_nested_dissection(ptr, idx, p.coords, leaf_size=4)
+    assert sorted(order.tolist()) == list(range(64))
+    kind, top = parts[-1]
+    assert kind == "sep" and sorted(top.tolist()) == [3 + 8 * y for y in range(8)]
+
+
+@pytest.mark.parametrize("maker", [lambda: W.poisson7(6, 5, 4), lambda: W.diffusion_grf(7, 2.0, 3.0, 1),
+                                   lambda: W.elasticity_q1(3, incl=(1, 2))])
+def test_graph_nd_separators_separate(maker):
+    """Every separator the recursion emits cuts its node set in two: re-running the
+    definition's steps independently (component labelling of the set minus S by BFS), no
+    edge joins the two remaining halves; and the exact factor with this ordering is the
+    Cholesky factor of the permuted matrix."""
+    p = maker()
+    dof = p.dof_per_node
+    ptr, idx = node_graph(p.n, p.row_ptr, p.col_idx, dof)
+    X = p.coords[::dof]
+    order, parts = graph_nested_dissection(ptr, idx, X, leaf_size=6)
+    assert sorted(order.tolist()) == list(range(p.n // dof))
+    # reconstruct each call's node set: in postorder, a separator's set is itself plus the
+    # parts emitted since the call began; recompute the median halves and check the cut
+    pos = {}
+    for i, (_, ids) in enumerate(parts):
+        for v in ids.tolist():
+            pos[v] = i
+    seen = 0
+    for i, (kind, S) in enumerate(parts):
+        if kind != "sep":
+            continue
+        # the call that emitted S dissected S plus a contiguous run of earlier parts; find the
+        # largest run whose union with S is connected through edges touching S or each other
+        run = []
+        for j in range(i - 1, -1, -1):
+            run.append(parts[j][1])
+            allv = np.concatenate(run + [S])
+            pts = X[allv]
+            ext = pts.max(axis=0) - pts.min(axis=0)
+            ax = int(np.argmax(ext))
+            srt = allv[np.lexsort((allv, pts[:, ax]))]
+            h = allv.size // 2
+            L, R = set(srt[:h].tolist()), set(srt[h:].tolist())
+            sset = set(S.tolist())
+            SL = {v for v in L if any(u in R for u in idx[ptr[v]:ptr[v + 1]])}
+            SR = {v for v in R if any(u in L for u in idx[ptr[v]:ptr[v + 1]])}
+            if (SL if len(SL) <= len(SR) else SR) == sset:
+                Lr, Rr = L - sset, R - sset
+                for v in Lr:
+                    assert not any(u in Rr for u in idx[ptr[v]:ptr[v + 1]].tolist())
+                seen += 1
+                break
+    assert seen == sum(k == "sep" for k, _ in parts)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=6, tau_O=10 ** 9, dof_per_node=dof, ordering=1))
+    f = F.factor(an, 0.0)
+    L = _assemble_L(f)
+    Ap = an.Ap.toarray()
+    assert np.linalg.norm(L @ L.T - Ap) / np.linalg.norm(Ap) <= 1e-13
+
+
+def test_spectral_coordinates_path_closed_form():
+    """Path graph of n nodes: Laplacian eigenvectors cos(pi k (i + 1/2) / n), eigenvalues
+    2 - 2 cos(pi k / n); the coordinates are the modes k = 1, 2, 3 up to sign."""
+    n = 40
+    ptr, idx = _path_graph(n)
+    X = spectral_coordinates(ptr, idx)
+    i = np.arange(n)
+    for k in (1, 2, 3):
+        v = np.cos(np.pi * k * (i + 0.5) / n)
+        v /= np.linalg.norm(v)
+        assert abs(abs(X[:, k - 1] @ v) - 1.0) <= 1e-10
+
+
+def test_spectral_coordinates_box_grid_modes():
+    """9 x 7 x 5 grid graph: the Laplacian of a Cartesian product has the products of the
+    path modes c_m,k(t) = cos(pi k (t + 1/2) / m) as eigenvectors, eigenvalue the sum of
+    2 - 2 cos(pi k / m).  Lowest non-constant: c_9,1(x) (0.121), c_7,1(y) (0.198), then
+    c_9,1(x) c_7,1(y) (0.319) below c_5,1(z) (0.382): the three coordinates, up to sign."""
+    p = W.poisson7(9, 7, 5)
+    ptr, idx = node_graph(p.n, p.row_ptr, p.col_idx)
+    X = spectral_coordinates(ptr, idx)
+    x, y = p.coords[:, 0], p.coords[:, 1]
+    cx = np.cos(np.pi * (x + 0.5) / 9)
+    cy = np.cos(np.pi * (y + 0.5) / 7)
+    for c, v in enumerate((cx, cy, cx * cy)):
+        v = v / np.linalg.norm(v)
+        assert abs(abs(X[:, c] @ v) - 1.0) <= 1e-10
+
+
+def test_spectral_coordinates_components_and_end_to_end():
+    """Two disjoint grids: each component gets its own modes (no constant vector, zero mean
+    per component); analysis without coordinates uses them and PCG reaches 1e-8 with the
+    compressed factor."""
+    import scipy.sparse as sp
+    a, b = W.poisson7(6), W.poisson7(5, 4, 3)
+    A = sp.block_diag([a.scipy(), b.scipy()]).tocsr()
+    A.sort_indices()
+    ptr, idx = node_graph(A.shape[0], A.indptr, A.indices)
+    comp = np.r_[np.zeros(a.n, int), np.ones(b.n, int)]
+    X = spectral_coordinates(ptr, idx, comp)
+    for c in (0, 1):
+        assert np.abs(X[comp == c].mean(axis=0)).max() <= 1e-12
+        assert np.abs(np.linalg.norm(X[comp == c], axis=0) - 1.0).max() <= 1e-12
+    p = W.diffusion_grf(12, 2.0, 3.0, 0)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, None, F.Options(leaf_size=16, tau_O=40, tau_D=32))
+    f = F.factor(an, 0.05)
+    assert any(s.compressed for s in f.sn)
+    x, it, rr, ok = F.solve(an, f, p.b, 1e-8)
+    assert ok and rr <= 1e-8
