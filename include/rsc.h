@@ -62,7 +62,10 @@ typedef struct {
     int32_t max_restarts;  /* indefinite restarts before diagonal compression is switched off; 8 */
     int32_t precision;     /* rsc_precision; RSC_PREC_FP64 */
     int32_t diag_compress; /* 1: compress diagonal blocks hierarchically (Section 4); 1 */
-    int32_t reserved;      /* must be 0 */
+    int32_t ordering;      /* 0: nested dissection by lattice bisection (coords = integer lattice
+                              positions); 1: graph nested dissection for general sparsity, guided by
+                              coords (any real positions).  coords == NULL selects 1 with spectral
+                              positions (Section 4.3); 0 */
     uint64_t seed;         /* key of the Philox4x32-10 stream of the random test matrices; 0 */
 } rsc_options;
 
@@ -92,12 +95,15 @@ rsc_status rsc_options_default(rsc_options* opts);
  * geometric ordering and block tree of every separator with more than tau_D
  * unknowns that is large enough to be compressed.
  *   n        unknowns; row_ptr[n+1] (int64), col_idx[nnz] (int32), val[nnz] (FP64);
- *   coords   n x 3 row-major lattice coordinates of each unknown (unknowns of one
- *            node repeat the node's coordinates); required;
+ *   coords   n x 3 row-major positions of each unknown (unknowns of one node repeat
+ *            the node's position): integer lattice positions for opts->ordering = 0,
+ *            any real positions for 1; NULL: positions from the three lowest
+ *            non-constant eigenvectors of the node graph's Laplacian (Section 4.3,
+ *            Lanczos on the host) and the graph ordering;
  *   opts     NULL for defaults.
  * The values are copied and used by rsc_factor.  No GPU work is done here.
  * Errors: RSC_ERR_INVALID_ARG (pattern not symmetric, unsorted, missing
- * diagonal, non-finite value, n not a multiple of dof_per_node, NULL coords).
+ * diagonal, non-finite value, n not a multiple of dof_per_node, ordering not 0 or 1).
  */
 rsc_status rsc_analyze(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
                        const double* coords, const rsc_options* opts, rsc_handle** out);
@@ -105,6 +111,11 @@ rsc_status rsc_analyze(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
 /* perm[n]: perm[new] = old unknown; *n_snodes = M; snode_ptr[M+1] column boundaries
  * (each output may be NULL). */
 rsc_status rsc_get_ordering(const rsc_handle* h, int32_t* perm, int32_t* n_snodes, int64_t* snode_ptr);
+
+/* Node positions the ordering used (Section 4.3): pos[3 * node + axis] for the n / dof_per_node
+ * nodes, the given coordinates or the spectral ones (rounded lattice positions for
+ * ordering 0).  Errors: RSC_ERR_INVALID_ARG (NULL). */
+rsc_status rsc_get_coordinates(const rsc_handle* h, double* pos);
 
 /* Supernodal structure: rows_ptr[M+1] and rows[rows_ptr[M]] hold R_j (sorted
  * permuted row indices after C_j); parent[M] (-1 for roots); level[M]; kind[M]

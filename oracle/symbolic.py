@@ -6,8 +6,15 @@ Follows the paper's definitions literally:
   rows i > p of A(:,p) united with struct(L(:,c)) \\ {p} over the tree children c
   of p; the tree parent of p is the smallest row of struct(L(:,p));
 * R_j (Eq. before "descendents"): rows after supernode j's columns with a
-  nonzero in some column of C_j, i.e. the union of the column structures over
-  p in C_j restricted to rows after C_j;
+  nonzero in some column of C_j.  Reading: the paper also states (below Eq.
+  "schurOffDiag") that a descendant k of j has R_k meeting the rows after C_j only
+  inside R_j; when a supernode's columns are not one chain of the elimination tree
+  (the graph ordering's separators and leaves may be disconnected), the union of
+  the column structures can break that, so R_j is the smallest set that keeps it:
+  the rows after C_j of A(:, C_j) united with R_k restricted to rows after C_j
+  over every k in D_j (computed in supernode order).  It contains the union of the
+  column structures and equals it whenever every supernode is an elimination-tree
+  chain (every lattice ordering); the extra rows hold exact zeros;
 * D_j (Eq. "descendents"): supernodes k < j with R_k meeting C_j;
 * R^D_{k->j}, R^O_{k->j} (Eqs. "rowsDiagKtoJ", "rowsOffKtoJ"): positions in R_k of
   the rows that fall in C_j, resp. in R_j.
@@ -47,10 +54,12 @@ def symbolic(Ap: sp.csr_matrix, snode_ptr: np.ndarray) -> Symbolic:
     children: list[list[int]] = [[] for _ in range(n)]
     struct: dict[int, np.ndarray] = {}
     R = []
+    meets: list[list[int]] = [[] for _ in range(M)]   # k with R_k meeting C_j (D_j), filled as R_k is known
     for j in range(M):
         c0, c1 = int(snode_ptr[j]), int(snode_ptr[j + 1])
         acc = []
         for p in range(c0, c1):
+            # column elimination tree (the column structures of L)
             col = csc.indices[csc.indptr[p]:csc.indptr[p + 1]]
             pieces = [col[col > p]]
             for c in children[p]:
@@ -62,8 +71,13 @@ def symbolic(Ap: sp.csr_matrix, snode_ptr: np.ndarray) -> Symbolic:
                 etree[p] = s[0]
                 children[s[0]].append(p)
                 struct[p] = s
-            acc.append(s[s >= c1])
-        R.append(np.unique(np.concatenate(acc)).astype(np.int64) if acc else np.zeros(0, np.int64))
+            acc.append(col[col >= c1].astype(np.int64))   # rows after C_j of A(:, C_j)
+        for k in meets[j]:                                   # R_k beyond C_j, k in D_j
+            acc.append(R[k][R[k] >= c1])
+        Rj = np.unique(np.concatenate(acc)).astype(np.int64) if acc else np.zeros(0, np.int64)
+        R.append(Rj)
+        for i in np.unique(snode_of[Rj]).tolist():
+            meets[i].append(j)
     sym = Symbolic()
     sym.n = n
     sym.snode_ptr = np.asarray(snode_ptr, dtype=np.int64)

@@ -28,7 +28,7 @@ class rsc_options(C.Structure):
     _fields_ = [("tau_O", C.c_int32), ("tau_D", C.c_int32), ("leaf_size", C.c_int32),
                 ("sample_block", C.c_int32), ("power_iters", C.c_int32), ("dof_per_node", C.c_int32),
                 ("max_restarts", C.c_int32), ("precision", C.c_int32), ("diag_compress", C.c_int32),
-                ("reserved", C.c_int32), ("seed", C.c_uint64)]
+                ("ordering", C.c_int32), ("seed", C.c_uint64)]
 
 
 class rsc_stats_t(C.Structure):
@@ -55,6 +55,7 @@ _SIGS = {
     "rsc_analyze": (C.c_int, [C.c_int64, _P, _P, _P, _P, C.POINTER(rsc_options), C.POINTER(_P)]),
     "rsc_get_ordering": (C.c_int, [_P, _P, C.POINTER(C.c_int32), _P]),
     "rsc_get_structure": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "rsc_get_coordinates": (C.c_int, [_P, _P]),
     "rsc_factor": (C.c_int, [_P, C.c_double]),
     "rsc_factor_fixed_rank": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32]),
     "rsc_refactor_values": (C.c_int, [_P, _P]),
@@ -133,7 +134,9 @@ def rsc_analyze(n, row_ptr, col_idx, val, coords, opts: rsc_options | None = Non
     st = lib().rsc_analyze(int(n), _ptr(rp), _ptr(ci), _ptr(v), _ptr(xyz),
                            C.byref(opts) if opts is not None else None, C.byref(out))
     _check(st)
-    return Handle(out.value, int(n))
+    h = Handle(out.value, int(n))
+    h.dof = int(opts.dof_per_node) if opts is not None else 1
+    return h
 
 
 def rsc_get_ordering(h: Handle):
@@ -143,6 +146,13 @@ def rsc_get_ordering(h: Handle):
     sp = np.empty(m.value + 1, np.int64)
     _check(lib().rsc_get_ordering(h.ptr, None, None, _ptr(sp)), h.ptr)
     return perm, sp
+
+
+def rsc_get_coordinates(h: Handle) -> np.ndarray:
+    """Node positions the ordering used, (n / dof_per_node) x 3."""
+    pos = np.empty((h.n // getattr(h, "dof", 1), 3), np.float64)
+    _check(lib().rsc_get_coordinates(h.ptr, _ptr(pos)), h.ptr)
+    return pos
 
 
 def rsc_get_structure(h: Handle):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librsc.so")
-SOURCES = ["symbolic.cpp", "capi.cpp", "engine.cu"]
+SOURCES = ["symbolic.cpp", "graph_order.cpp", "capi.cpp", "engine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -104,6 +104,12 @@ rsc_status rsc_get_ordering(const rsc_handle* h, int32_t* perm, int32_t* n_snode
     return RSC_OK;
 }
 
+rsc_status rsc_get_coordinates(const rsc_handle* h, double* pos) {
+    if (!h || !pos) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle or pos");
+    std::memcpy(pos, h->sym.node_pos.data(), sizeof(double) * h->sym.node_pos.size());
+    return RSC_OK;
+}
+
 rsc_status rsc_get_structure(const rsc_handle* h, int64_t* rows_ptr, int32_t* rows, int32_t* parent,
                              int32_t* level, int32_t* kind) {
     if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");

@@ -27,6 +27,8 @@ struct Symbolic {
     int M = 0;                              // supernodes
     std::vector<int32_t> perm, iperm;       // perm[new] = old
     int ncomp = 1;                          // connected components of the node graph
+    bool graph_ordering = false;            // graph nested dissection (else lattice bisection)
+    std::vector<double> node_pos;           // [n / dof * 3] positions the ordering used
     std::vector<int32_t> comp_of;           // [n / dof] component of each node (original order)
     std::vector<int64_t> sn_ptr;            // [M+1] column boundaries
     std::vector<int32_t> snode_of;          // [n] supernode of each (new) column
@@ -51,6 +53,17 @@ struct Symbolic {
     int nrows(int j) const { return (int)(rows_ptr[j + 1] - rows_ptr[j]); }
     const int32_t* R(int j) const { return rows.data() + rows_ptr[j]; }
 };
+
+// Graph ordering (graph_order.cpp): node graph of A's pattern (CSR, sorted, no self
+// loops), spectral positions per component (nodes x 3), graph nested dissection of one
+// component (parts: 0 leaf / 1 separator, in postorder).
+void node_graph(int64_t n, const int64_t* rp, const int32_t* ci, int dof, std::vector<int64_t>& ptr,
+                std::vector<int32_t>& idx);
+void spectral_positions(const std::vector<int64_t>& ptr, const std::vector<int32_t>& idx,
+                        const std::vector<std::vector<int32_t>>& comps, std::vector<double>& X);
+void graph_nested_dissection(const std::vector<int64_t>& ptr, const std::vector<int32_t>& idx, const double* X,
+                             int leaf_size, std::vector<int32_t>& ids,
+                             std::vector<std::pair<uint8_t, std::vector<int32_t>>>& parts);
 
 // Ordering + symbolic analysis; returns an empty string on success, else the reason.
 std::string analyze_symbolic(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,

@@ -11,10 +11,13 @@
 //    longest bounding-box axis (Section 4.1) and gets an in-order labelled block tree.
 //  * R_j (Section 2.1) is built per supernode from the rows below C_j of A's
 //    columns in C_j and the rows of R_k below C_j for every supernode k whose
-//    first row of R_k lies in C_j (its supernodal tree children).  This supernode-
-//    level union is a different computation from the per-column elimination-tree
-//    definition the paper states; the two are checked to agree bit for bit.
+//    first row of R_k lies in C_j (its supernodal tree children).  This is the
+//    smallest row set with the property the paper states for descendants (R_k
+//    meets the rows after C_j only inside R_j); it equals the union of the column
+//    structures whenever every supernode is an elimination-tree chain (lattice
+//    orderings) and adds rows of exact zeros otherwise (the graph ordering).
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <functional>
 #include <numeric>
@@ -78,7 +81,8 @@ void nd_recurse(std::vector<int32_t>& ids, const int64_t* P, int leaf_size,
 
 // Section 4.1: recursive halving along the longest bounding-box axis; returns the
 // new node order and fills the in-order labelled tree (ranges in unknowns).
-void geometric_split(const std::vector<int32_t>& ids_in, const int64_t* P, int dof, int tau_D,
+template <class C>
+void geometric_split(const std::vector<int32_t>& ids_in, const C* P, int dof, int tau_D,
                      std::vector<int32_t>& out, BlockTree& t) {
     struct Rec { int label; int hi; };
     int counter = 0;
@@ -103,19 +107,19 @@ void geometric_split(const std::vector<int32_t>& ids_in, const int64_t* P, int d
             out.insert(out.end(), ids.begin(), ids.end());
             return {s, t.hi[s]};
         }
-        int64_t mn[3], mx[3];
-        for (int a = 0; a < 3; ++a) { mn[a] = INT64_MAX; mx[a] = INT64_MIN; }
+        C mn[3], mx[3];
+        for (int a = 0; a < 3; ++a) { mn[a] = std::numeric_limits<C>::max(); mx[a] = std::numeric_limits<C>::lowest(); }
         for (int32_t i : ids)
             for (int a = 0; a < 3; ++a) {
-                mn[a] = std::min(mn[a], P[3 * i + a]);
-                mx[a] = std::max(mx[a], P[3 * i + a]);
+                mn[a] = std::min(mn[a], P[3 * (int64_t)i + a]);
+                mx[a] = std::max(mx[a], P[3 * (int64_t)i + a]);
             }
         int ax = 0;
-        int64_t best = -1;
+        C best = -1;
         for (int a = 0; a < 3; ++a)
             if (mx[a] - mn[a] > best) { best = mx[a] - mn[a]; ax = a; }
         std::stable_sort(ids.begin(), ids.end(), [P, ax](int32_t a, int32_t b) {
-            return P[3 * a + ax] < P[3 * b + ax];
+            return P[3 * (int64_t)a + ax] < P[3 * (int64_t)b + ax];
         });
         size_t h = ids.size() / 2;
         std::vector<int32_t> l(ids.begin(), ids.begin() + h), r(ids.begin() + h, ids.end());
@@ -144,7 +148,9 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
                              const double* coords, const rsc_options& o, Symbolic& S) {
     if (n <= 0) return "n must be positive";
     if (!rp || !ci || !val) return "row_ptr, col_idx and val are required";
-    if (!coords) return "node coordinates are required for the nested-dissection ordering";
+    if (o.ordering != 0 && o.ordering != 1) return "ordering must be 0 (lattice) or 1 (graph)";
+    // no positions: spectral positions (Section 4.3) and the graph ordering
+    const bool graph = o.ordering == 1 || !coords;
     if (o.dof_per_node < 1 || n % o.dof_per_node) return "n must be a multiple of dof_per_node";
     if (o.leaf_size < 1 || o.tau_D < 1 || o.tau_O < 1) return "leaf_size, tau_O and tau_D must be positive";
     if (o.sample_block != 16) return "sample_block must be 16";
@@ -172,16 +178,22 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
                 ++pos[j];
             }
     }
-    for (int64_t i = 0; i < 3 * n; ++i) {
-        if (!std::isfinite(coords[i])) return "non-finite coordinate";
-        if (std::fabs(coords[i]) >= 2147483648.0) return "coordinates must be lattice positions below 2^31 in magnitude";
-    }
+    if (coords)
+        for (int64_t i = 0; i < 3 * n; ++i) {
+            if (!std::isfinite(coords[i])) return "non-finite coordinate";
+            if (!graph && std::fabs(coords[i]) >= 2147483648.0)
+                return "coordinates must be lattice positions below 2^31 in magnitude";
+        }
 
     const int dof = o.dof_per_node;
     const int64_t nodes = n / dof;
-    std::vector<int64_t> P(3 * nodes);
-    for (int64_t v = 0; v < nodes; ++v)
-        for (int a = 0; a < 3; ++a) P[3 * v + a] = (int64_t)std::llround(coords[3 * (v * dof) + a]);
+    std::vector<int64_t> P;
+    std::vector<double> X;   // real node positions (graph ordering)
+    if (!graph) {
+        P.resize(3 * nodes);
+        for (int64_t v = 0; v < nodes; ++v)
+            for (int a = 0; a < 3; ++a) P[3 * v + a] = (int64_t)std::llround(coords[3 * (v * dof) + a]);
+    }
 
     // connected components of the node graph: each is dissected on its own, in order of
     // its smallest node (independent systems stacked block-diagonally become a forest)
@@ -211,14 +223,32 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
         }
     }
     std::vector<std::pair<uint8_t, std::vector<int32_t>>> parts;
-    for (auto& cnodes : comps) nd_recurse(cnodes, P.data(), o.leaf_size, parts);
-    S.ncomp = (int)comps.size();
-    S.comp_of = std::move(comp);
-    const int ncomp_saved = S.ncomp;
-    std::vector<int32_t> comp_saved = std::move(S.comp_of);
+    if (graph) {
+        std::vector<int64_t> gptr;
+        std::vector<int32_t> gidx;
+        node_graph(n, rp, ci, dof, gptr, gidx);
+        if (coords) {
+            X.resize(3 * nodes);
+            for (int64_t v = 0; v < nodes; ++v)
+                for (int a = 0; a < 3; ++a) X[3 * v + a] = coords[3 * (v * dof) + a];
+        } else {
+            spectral_positions(gptr, gidx, comps, X);
+        }
+        for (auto& cnodes : comps) {
+            std::vector<int32_t> ids = cnodes;
+            graph_nested_dissection(gptr, gidx, X.data(), o.leaf_size, ids, parts);
+        }
+    } else {
+        for (auto& cnodes : comps) nd_recurse(cnodes, P.data(), o.leaf_size, parts);
+    }
+    const int ncomp_saved = (int)comps.size();
+    std::vector<int32_t> comp_saved = std::move(comp);
     S = Symbolic();
     S.ncomp = ncomp_saved;
     S.comp_of = std::move(comp_saved);
+    S.graph_ordering = graph;
+    if (graph) S.node_pos = X;
+    else S.node_pos.assign(P.begin(), P.end());
     S.n = n;
     S.dof = dof;
     S.M = (int)parts.size();
@@ -232,7 +262,8 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
         int64_t nc = (int64_t)part.second.size() * dof;
         std::vector<int32_t> ids;
         if (part.first == 1 && nc >= o.tau_O && nc > o.tau_D) {
-            geometric_split(part.second, P.data(), dof, o.tau_D, ids, S.tree[j]);
+            if (graph) geometric_split(part.second, X.data(), dof, o.tau_D, ids, S.tree[j]);
+            else geometric_split(part.second, P.data(), dof, o.tau_D, ids, S.tree[j]);
         } else {
             ids = std::move(part.second);
         }

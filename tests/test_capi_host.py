@@ -41,7 +41,7 @@ def _bad(p, **changes):
     return loc
 
 
-@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "nocoords", "dof", "range", "hugecoord"])
+@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "badordering", "dof", "range", "hugecoord"])
 def test_analyze_rejects_bad_input(what):
     p = W.poisson7(4)
     rp, ci, v, xyz = p.row_ptr.copy(), p.col_idx.copy(), p.val.copy(), p.coords.copy()
@@ -61,8 +61,8 @@ def test_analyze_rejects_bad_input(what):
         ci[d] = 63
     elif what == "nan":
         v[5] = np.nan
-    elif what == "nocoords":
-        xyz = None
+    elif what == "badordering":
+        opts.ordering = 2
     elif what == "dof":
         opts.dof_per_node = 5
     elif what == "range":
@@ -76,7 +76,8 @@ def test_analyze_rejects_bad_input(what):
 
 
 def _oracle_opts(o):
-    return F.Options(tau_O=o.tau_O, tau_D=o.tau_D, leaf_size=o.leaf_size, dof_per_node=o.dof_per_node)
+    return F.Options(tau_O=o.tau_O, tau_D=o.tau_D, leaf_size=o.leaf_size, dof_per_node=o.dof_per_node,
+                     ordering=o.ordering)
 
 
 @pytest.mark.parametrize("maker,kw", [
@@ -150,3 +151,88 @@ def test_factor_fixed_rank_rejects_bad_parameters(args):
     with pytest.raises(R.RscError) as e:
         R.rsc_factor_fixed_rank(h, *args)
     assert e.value.status == 1 and "alpha" in R.rsc_last_error(h)
+
+
+# ----------------------------------------------------------------------------- graph ordering
+
+def _jittered(p, seed=3):
+    X = p.coords + 0.3 * np.random.default_rng(seed).uniform(-1, 1, p.coords.shape)
+    return X if p.dof_per_node == 1 else np.repeat(X[::p.dof_per_node], p.dof_per_node, axis=0)
+
+
+@pytest.mark.parametrize("maker,kw,pos", [
+    (lambda: W.poisson7(8), dict(leaf_size=8, tau_O=24, tau_D=16), "lattice"),
+    (lambda: W.poisson7(12), dict(leaf_size=16, tau_O=40, tau_D=32), "jitter"),
+    (lambda: W.elasticity_q1(4, incl=(1, 3)), dict(leaf_size=8, tau_O=48, tau_D=24, dof_per_node=3), "jitter"),
+    (lambda: W.random_geometric(1500, 0.12, seed=2), dict(leaf_size=24, tau_O=60, tau_D=40), "points"),
+    (lambda: W.diffusion_grf(20, 2.0, 4.0, 1), dict(leaf_size=32, tau_O=64, tau_D=64), "jitter"),
+])
+def test_graph_ordering_bit_exact_vs_oracle(maker, kw, pos):
+    """Graph nested dissection (ordering 1) with the same real positions on both sides:
+    permutation, supernodes, row structures, tree and kinds equal the oracle's bit for bit,
+    block trees included."""
+    p = maker()
+    X = _jittered(p) if pos == "jitter" else p.coords
+    o = R.rsc_options_default(ordering=1, **kw)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, X, o)
+    perm, sp = R.rsc_get_ordering(h)
+    rows_ptr, rows, parent, level, kind = R.rsc_get_structure(h)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, X, _oracle_opts(o))
+    np.testing.assert_array_equal(perm, an.ordering.perm)
+    np.testing.assert_array_equal(sp, an.ordering.snode_ptr)
+    for j in range(an.nsuper):
+        np.testing.assert_array_equal(rows[rows_ptr[j]:rows_ptr[j + 1]], an.sym.rows[j])
+    np.testing.assert_array_equal(parent, an.sym.parent)
+    assert [int(k) for k in kind] == [1 if x == "sep" else 0 for x in an.ordering.kinds]
+    np.testing.assert_array_equal(R.rsc_get_coordinates(h), X[::p.dof_per_node])
+    assert any(t is not None for t in an.ordering.trees)
+
+
+def _proj(V):
+    Q, _ = np.linalg.qr(V)
+    return Q @ Q.T
+
+
+def test_spectral_positions_small_graph_equal_oracle():
+    """No coordinates, 6 x 5 x 4 grid (120 nodes, so the Lanczos run spans the whole space
+    orthogonal to the constant vector): the three positions span the oracle's eigenvectors of
+    the Laplacian (eigenvalues 0.268, 0.382, 0.586 against 0.650 next, non-degenerate) to
+    rounding, each column orthogonal to the constant vector."""
+    from oracle.ordering import node_graph, spectral_coordinates
+    p = W.poisson7(6, 5, 4)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, None, R.rsc_options_default(leaf_size=8))
+    X = R.rsc_get_coordinates(h)
+    ptr, idx = node_graph(p.n, p.row_ptr, p.col_idx)
+    Xo = spectral_coordinates(ptr, idx)
+    for c in range(3):
+        assert abs(abs(X[:, c] @ Xo[:, c]) / np.linalg.norm(X[:, c]) - 1.0) <= 1e-9
+    assert np.abs(X.sum(axis=0)).max() <= 1e-10
+    perm, _ = R.rsc_get_ordering(h)
+    assert np.array_equal(np.sort(perm), np.arange(p.n))
+
+
+@pytest.mark.parametrize("maker", [lambda: W.poisson7(14, 12, 10), lambda: W.random_geometric(2500, 0.1, seed=5)])
+def test_spectral_positions_larger_graph_are_low_modes(maker):
+    """Larger graphs (the Lanczos run stops at 160 steps): the positions are orthonormal,
+    orthogonal to the constant vector, and their Rayleigh quotients lie within 5% of the
+    three lowest non-zero Laplacian eigenvalues (dense reference); the ordering they guide
+    is a valid permutation whose separators the analysis accepts."""
+    from oracle.ordering import node_graph
+    p = maker()
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, None, R.rsc_options_default(leaf_size=16))
+    X = R.rsc_get_coordinates(h)
+    ptr, idx = node_graph(p.n, p.row_ptr, p.col_idx)
+    n = p.n
+    import scipy.sparse as sp_
+    Adj = sp_.csr_matrix((np.ones(idx.size), idx, ptr), shape=(n, n))
+    Lap = sp_.diags(np.asarray(Adj.sum(axis=1)).ravel()) - Adj
+    comps = sp_.csgraph.connected_components(Adj, directed=False)[0]
+    w = np.linalg.eigvalsh(Lap.toarray())
+    lam = w[comps:comps + 3]
+    np.testing.assert_allclose(X.T @ X, np.eye(3), atol=1e-8)
+    if comps == 1:
+        assert np.abs(X.sum(axis=0)).max() <= 1e-8
+        rq = np.sort(np.einsum("ic,ic->c", X, Lap @ X))
+        assert np.all(np.abs(rq - lam) <= 0.05 * lam), (rq, lam)
+    perm, _ = R.rsc_get_ordering(h)
+    assert np.array_equal(np.sort(perm), np.arange(n))

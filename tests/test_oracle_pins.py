@@ -694,3 +694,40 @@ def test_spectral_coordinates_components_and_end_to_end():
     assert any(s.compressed for s in f.sn)
     x, it, rr, ok = F.solve(an, f, p.b, 1e-8)
     assert ok and rr <= 1e-8
+
+
+@pytest.mark.parametrize("maker", [lambda: W.random_geometric(400, 0.16, seed=1), lambda: W.poisson7(7, 6, 5)])
+def test_symbolic_closed_rows_graph_ordering(maker):
+    """Graph ordering, whose separators and leaves need not be elimination-tree chains:
+    R_j contains the brute-force union of the column structures, keeps the Section 2.1
+    property (R_k after C_j inside R_j for every k in D_j), and is the smallest such set:
+    every extra row comes from a descendant's R_k.  The exact factor with this structure is
+    the Cholesky factor (the extra rows are zeros)."""
+    p = maker()
+    X = p.coords + (0.0 if p.shape == () else 0.3 * np.random.default_rng(4).uniform(-1, 1, p.coords.shape))
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, X, F.Options(leaf_size=6, tau_O=10 ** 9, ordering=1))
+    L = _brute_structure(an.Ap.toarray() != 0)
+    sym = an.sym
+    Ap = an.Ap.tocsc()
+    strict = 0
+    for j in range(an.nsuper):
+        c0, c1 = an.cols(j)
+        brute = set((np.nonzero(L[c1:, c0:c1].any(axis=1))[0] + c1).tolist())
+        Rj = set(sym.rows[j].tolist())
+        assert brute <= Rj
+        strict += len(Rj - brute)
+        a_part = set(r for p_ in range(c0, c1) for r in Ap.indices[Ap.indptr[p_]:Ap.indptr[p_ + 1]].tolist()
+                     if r >= c1)
+        from_desc = set()
+        for k, pD, pO in sym.desc[j]:
+            Rk = sym.rows[k]
+            tail = set(Rk[Rk >= c1].tolist())
+            assert tail <= Rj
+            from_desc |= tail
+        assert Rj == a_part | from_desc
+    f = F.factor(an, 0.0)
+    Lf = _assemble_L(f)
+    Apd = an.Ap.toarray()
+    assert np.linalg.norm(Lf @ Lf.T - Apd) / np.linalg.norm(Apd) <= 1e-13
+    if p.shape == ():
+        assert strict > 0        # this graph has non-chain supernodes: the closure adds rows

@@ -24,6 +24,10 @@ examples, Section 6):
 * ``elasticity_q1`` trilinear hexahedral linear elasticity, 2x2x2 Gauss rule,
                     the x = 0 face clamped, a stiff central inclusion and a
                     uniform body force; three unknowns per node kept adjacent.
+* ``random_geometric`` a non-grid sparsity pattern: points uniform in the unit
+                    cube joined when closer than a radius; the matrix is the
+                    graph Laplacian plus a diagonal shift; coordinates are the
+                    points' real positions (for the graph ordering).
 """
 from __future__ import annotations
 
@@ -293,3 +297,18 @@ class FVValues:
         off = -t[torch.as_tensor(self.face, device=dev)]
         on = diag[torch.as_tensor(self.rows, device=dev)]
         return torch.where(is_diag, on, off)
+
+
+def random_geometric(npts: int, radius: float, shift: float = 0.1, seed: int = 0) -> Problem:
+    """Graph Laplacian + shift I of the random geometric graph on ``npts`` points uniform
+    in [0,1]^3 (numpy Philox, ``seed``), edge between points closer than ``radius``;
+    b ~ U[-1, 1] (seed ``seed``).  Coordinates are the points themselves (real)."""
+    X = _rng(seed).uniform(0.0, 1.0, (npts, 3))
+    d2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(axis=2)
+    a, b = np.nonzero(np.triu(d2 < radius * radius, 1))
+    deg = np.bincount(np.r_[a, b], minlength=npts).astype(np.float64)
+    rows = np.concatenate([a, b, np.arange(npts)])
+    cols = np.concatenate([b, a, np.arange(npts)])
+    vals = np.concatenate([-np.ones(2 * a.size), deg + shift])
+    rp, ci, v = _csr_from_coo(npts, rows, cols, vals)
+    return Problem(f"random_geometric_{npts}_{radius:g}", npts, rp, ci, v, X, rhs_uniform(npts, seed), 1, ())
