@@ -50,6 +50,16 @@ Algorithm by algorithm, in the paper's order and notation:
                                 columns, the one-shot form of Alg. 3.  Section 5.3's
                                 restart: alpha^D <- 1.25 alpha^D, starting from 0.5.
 
+* Interior blocks (Section 5.1, ``Options.interior_blocks``): every maximal subtree
+  of the supernodal tree without a compressed supernode is one interior block B,
+  contiguous in the ordering; only L_B = chol(A(C_B, C_B)) is kept (Eq.
+  "interiorDiagonalDef", a dense Cholesky here) and L(R_B, C_B) is never stored.
+  Where the factorization needs rows X of it, they are L(X, C_B) = A(X, C_B) L_B^{-T}
+  (Eq. "interiorBlockClosedForm"), formed for the small Schur complements and
+  dropped; products L(X, C_B) L(Y, C_B)^T G go through Eq. "interiorBlockMult":
+  A(Y, C_B)^T G, two triangular solves with L_B, then A(X, C_B).  The preconditioner
+  apply solves with L_B and uses the same closed form for the block's off-diagonal.
+
 Low-rank descendants keep U_prod = U_k^T U_k literally (Eq. "lowRankMult").
 Random test matrices come from ``oracle.philox.gaussian_block`` with block id
 (j << 12) | s (s = 0 for the off-diagonal block, s = label for diagonal blocks).
@@ -83,6 +93,7 @@ class Options:
     seed: int = 0
     diag_compress: bool = True
     ordering: int = 0          # 0: lattice bisection; 1: graph nested dissection
+    interior_blocks: bool = False   # Section 5.1: L(R_B, C_B) of interior blocks not stored
 
 
 class Analysis:
@@ -170,6 +181,64 @@ class Factor:
         self.alpha_O = 0.0
         self.alpha_D = 0.0
         self.p = 0
+        self.iblock_of = None      # Section 5.1: interior block of each supernode (-1: none)
+        self.iblocks = []          # per block: dict(first, last, c0, c1, RB, L)
+
+    # ----------------------------------------------------------- Section 5.1
+    def _find_interior_blocks(self):
+        """Maximal subtrees of the supernodal tree with no compressed supernode; each is
+        a contiguous run of supernodes first..last (postorder) ending at its root."""
+        an = self.an
+        M = an.nsuper
+        parent = an.sym.parent
+        self.iblock_of = -np.ones(M, dtype=np.int64)
+        self.iblocks = []
+        if not an.opts.interior_blocks:
+            return
+        bad = [self.is_compressed(j) for j in range(M)]
+        first = list(range(M))
+        for j in range(M):                       # children precede parents
+            pj = int(parent[j])
+            if pj >= 0:
+                bad[pj] = bad[pj] or bad[j]
+                first[pj] = min(first[pj], first[j])
+        for j in range(M):
+            pj = int(parent[j])
+            if bad[j] or (pj >= 0 and not bad[pj]):
+                continue                         # not the root of a maximal clean subtree
+            f0 = first[j]
+            assert all(not bad[k] for k in range(f0, j + 1)), "interior block not contiguous"
+            c0, _ = an.cols(f0)
+            _, c1 = an.cols(j)
+            rows = [an.sym.rows[k] for k in range(f0, j + 1)]
+            RB = np.unique(np.concatenate(rows)) if rows else np.zeros(0, np.int64)
+            RB = RB[RB >= c1]
+            self.iblock_of[f0:j + 1] = len(self.iblocks)
+            self.iblocks.append(dict(first=f0, last=j, c0=c0, c1=c1, RB=RB, L=None))
+
+    def _ib_L(self, b, rows):
+        """Rows ``rows`` of L(:, C_B): A(rows, C_B) L_B^{-T} (Eq. interiorBlockClosedForm)."""
+        B = self.iblocks[b]
+        Arc = self.an.A_block(rows, np.arange(B["c0"], B["c1"]))
+        return dense.solve_lower(B["L"], Arc.T).T
+
+    def _ib_mult(self, b, rows_out, rows_in, G):
+        """L(rows_out, C_B) L(rows_in, C_B)^T G by Eq. interiorBlockMult."""
+        B = self.iblocks[b]
+        CB = np.arange(B["c0"], B["c1"])
+        T = self.an.A_block(rows_in, CB).T @ G
+        T = dense.solve_lower(B["L"], T)
+        T = dense.solve_lower_T(B["L"], T)
+        return self.an.A_block(rows_out, CB) @ T
+
+    def _split_desc(self, j):
+        """D_j without interior supernodes, and the interior blocks that meet D_j."""
+        if self.iblock_of is None or not self.iblocks:
+            return self.an.sym.desc[j], []
+        ib = self.iblock_of
+        normal = [d for d in self.an.sym.desc[j] if ib[d[0]] < 0]
+        blocks = sorted({int(ib[d[0]]) for d in self.an.sym.desc[j] if ib[d[0]] >= 0})
+        return normal, blocks
 
     # ----------------------------------------------------------- descendant blocks
     def lo_rows(self, k, pos):
@@ -225,11 +294,14 @@ class Factor:
         Cj = np.arange(c0, c1)
         G = self.diagonal_solve(j, G, transpose=True)
         W = an.A_block(Rj, Cj) @ G
-        for k, pD, pO in an.sym.desc[j]:
+        normal, blocks = self._split_desc(j)
+        for k, pD, pO in normal:
             Rk = an.sym.rows[k]
             G_sub = gather_rows(G, Cj, Rk[pD])
             T = self.lo_apply(k, pO, pD, G_sub)
             W -= scatter_rows(T, Rk[pO], Rj)
+        for b in blocks:
+            W -= self._ib_mult(b, Rj, Cj, G)
         return W
 
     def offdiag_multiply_T(self, j, G):
@@ -239,11 +311,14 @@ class Factor:
         Rj = an.sym.rows[j]
         Cj = np.arange(c0, c1)
         W = an.A_block(Rj, Cj).T @ G
-        for k, pD, pO in an.sym.desc[j]:
+        normal, blocks = self._split_desc(j)
+        for k, pD, pO in normal:
             Rk = an.sym.rows[k]
             G_sub = gather_rows(G, Rj, Rk[pO])
             T = self.lo_apply(k, pD, pO, G_sub)
             W -= scatter_rows(T, Rk[pD], Cj)
+        for b in blocks:
+            W -= self._ib_mult(b, Cj, Rj, G)
         return self.diagonal_solve(j, W, transpose=False)
 
     # ----------------------------------------------------------- adaptive range finder
@@ -314,7 +389,10 @@ class Factor:
         q0, q1 = t.cols(s)
         G = self.diagonal_solve(j, G, True, t.left[s])
         W = an.A_block(np.arange(c0 + r0, c0 + r1), np.arange(c0 + q0, c0 + q1)) @ G
-        for k, _, _ in an.sym.desc[j]:
+        normal, blocks = self._split_desc(j)
+        for b in blocks:
+            W -= self._ib_mult(b, np.arange(c0 + r0, c0 + r1), np.arange(c0 + q0, c0 + q1), G)
+        for k, _, _ in normal:
             Rk = an.sym.rows[k]
             pr = self._desc_rows_in(j, k, c0 + r0, c0 + r1)
             pc = self._desc_rows_in(j, k, c0 + q0, c0 + q1)
@@ -340,7 +418,10 @@ class Factor:
         r0, r1 = t.rows(s)
         q0, q1 = t.cols(s)
         W = an.A_block(np.arange(c0 + r0, c0 + r1), np.arange(c0 + q0, c0 + q1)).T @ G
-        for k, _, _ in an.sym.desc[j]:
+        normal, blocks = self._split_desc(j)
+        for b in blocks:
+            W -= self._ib_mult(b, np.arange(c0 + q0, c0 + q1), np.arange(c0 + r0, c0 + r1), G)
+        for k, _, _ in normal:
             Rk = an.sym.rows[k]
             pr = self._desc_rows_in(j, k, c0 + r0, c0 + r1)
             pc = self._desc_rows_in(j, k, c0 + q0, c0 + q1)
@@ -377,7 +458,11 @@ class Factor:
         r0, r1 = t.rows(s)
         gl = np.arange(c0 + r0, c0 + r1)
         S = an.A_block(gl, gl)
-        for k, _, _ in an.sym.desc[j]:
+        normal, blocks = self._split_desc(j)
+        for b in blocks:                                     # a sub-block of L(R_B, C_B), dropped after
+            Lr = self._ib_L(b, gl)
+            S -= Lr @ Lr.T
+        for k, _, _ in normal:
             Rk = an.sym.rows[k]
             pr = self._desc_rows_in(j, k, c0 + r0, c0 + r1)
             if pr.size:
@@ -399,7 +484,13 @@ class Factor:
         Rj = an.sym.rows[j]
         UD = an.A_block(Cj, Cj)
         UO = an.A_block(Rj, Cj) if with_offdiag else None
-        for k, pD, pO in an.sym.desc[j]:
+        normal, blocks = self._split_desc(j)
+        for b in blocks:                                     # sub-blocks of L(R_B, C_B), dropped after
+            Lc = self._ib_L(b, Cj)
+            UD -= Lc @ Lc.T
+            if with_offdiag and Rj.size:
+                UO -= self._ib_L(b, Rj) @ Lc.T
+        for k, pD, pO in normal:
             Rk = an.sym.rows[k]
             dloc = positions(Rk[pD], Cj)                         # scatter(., R^D_glob, C_j, R^D_glob, C_j)
             UD[np.ix_(dloc, dloc)] -= self.lo_pair_product(k, pD, pD)
@@ -445,7 +536,15 @@ class Factor:
 
     def run(self):
         self.sn = [SupernodeFactor() for _ in range(self.an.nsuper)]
+        self._find_interior_blocks()
         for j in range(self.an.nsuper):
+            b = int(self.iblock_of[j])
+            if b >= 0:
+                B = self.iblocks[b]
+                if j == B["last"]:                           # Eq. interiorDiagonalDef
+                    CB = np.arange(B["c0"], B["c1"])
+                    B["L"] = dense.cholesky(self.an.A_block(CB, CB))
+                continue
             if self.is_compressed(j):
                 self.factor_compressed(j)
             else:
@@ -509,9 +608,19 @@ def apply_preconditioner(f: Factor, r: np.ndarray) -> np.ndarray:
     perm = an.ordering.perm
     y = np.array(r[perm], dtype=np.float64)
     M = an.nsuper
+    ib = f.iblock_of if f.iblock_of is not None else -np.ones(M, dtype=np.int64)
     for j in range(M):
         c0, c1 = an.cols(j)
         Rj = an.sym.rows[j]
+        if ib[j] >= 0:                                       # interior block, once at its first supernode
+            B = f.iblocks[int(ib[j])]
+            if j == B["first"]:
+                b0, b1 = B["c0"], B["c1"]
+                y[b0:b1] = dense.solve_lower(B["L"], y[b0:b1, None])[:, 0]
+                if B["RB"].size:
+                    t = dense.solve_lower_T(B["L"], y[b0:b1, None])
+                    y[B["RB"]] -= (an.A_block(B["RB"], np.arange(b0, b1)) @ t)[:, 0]
+            continue
         y[c0:c1] = f.diagonal_solve(j, y[c0:c1, None], transpose=False)[:, 0]
         if Rj.size:
             s = f.sn[j]
@@ -522,6 +631,15 @@ def apply_preconditioner(f: Factor, r: np.ndarray) -> np.ndarray:
     for j in range(M - 1, -1, -1):
         c0, c1 = an.cols(j)
         Rj = an.sym.rows[j]
+        if ib[j] >= 0:                                       # interior block, once at its root
+            B = f.iblocks[int(ib[j])]
+            if j == B["last"]:
+                b0, b1 = B["c0"], B["c1"]
+                if B["RB"].size:
+                    t = an.A_block(B["RB"], np.arange(b0, b1)).T @ y[B["RB"], None]
+                    y[b0:b1] -= dense.solve_lower(B["L"], t)[:, 0]
+                y[b0:b1] = dense.solve_lower_T(B["L"], y[b0:b1, None])[:, 0]
+            continue
         if Rj.size:
             s = f.sn[j]
             if s.compressed:
@@ -574,7 +692,15 @@ def solve(an: Analysis, f: Factor, b: np.ndarray, rtol=1e-8, max_iter=1000):
 def factor_bytes(f: Factor) -> int:
     """Bytes of the stored factor in FP64 (dense blocks, V and U factors)."""
     tot = 0
-    for s in f.sn:
+    an = f.an
+    for j, s in enumerate(f.sn):
+        if f.iblock_of is not None and f.iblock_of[j] >= 0:
+            # Section 5.1: only the in-block part of the supernodal panel is stored
+            B = f.iblocks[int(f.iblock_of[j])]
+            c0, c1 = an.cols(j)
+            Rj = an.sym.rows[j]
+            tot += (c1 - c0) * (c1 - c0 + 1) // 2 + (c1 - c0) * int(np.sum(Rj < B["c1"]))
+            continue
         D = s.D
         if D.hierarchical:
             tot += sum(L.size for L in D.leafL.values())

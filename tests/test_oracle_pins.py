@@ -731,3 +731,61 @@ def test_symbolic_closed_rows_graph_ordering(maker):
     assert np.linalg.norm(Lf @ Lf.T - Apd) / np.linalg.norm(Apd) <= 1e-13
     if p.shape == ():
         assert strict > 0        # this graph has non-chain supernodes: the closure adds rows
+
+
+# --------------------------------------------------------------------------- interior blocks (Section 5.1)
+
+@pytest.mark.parametrize("maker,kw", [
+    (lambda: W.poisson7(10), dict(leaf_size=8, tau_O=24, tau_D=16)),
+    (lambda: W.diffusion_grf(12, 2.0, 3.0, 0), dict(leaf_size=16, tau_O=40, tau_D=32)),
+    (lambda: W.elasticity_q1(4, incl=(1, 3)), dict(leaf_size=8, tau_O=48, tau_D=24, dof_per_node=3)),
+])
+def test_interior_blocks_closed_form_and_apply(maker, kw):
+    """Eq. interiorBlockClosedForm: an interior block's columns of the factor are untouched
+    by compression, so A(X, C_B) L_B^{-T} equals the library Cholesky factor of the permuted
+    matrix in those columns; the preconditioner with interior blocks equals the one that
+    stores every block (ranks equal, apply within 1e-12, same PCG iterations), and it stores
+    exactly the off-block entries c_j |R_j after C_B| fewer."""
+    p = maker()
+    an_s = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(**kw))
+    an_i = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(interior_blocks=True, **kw))
+    fs, fi = F.factor(an_s, 0.05), F.factor(an_i, 0.05)
+    assert len(fi.iblocks) >= 2 and any(B["RB"].size for B in fi.iblocks)
+    Lx = np.linalg.cholesky(an_i.Ap.toarray())
+    saved = 0
+    for b, B in enumerate(fi.iblocks):
+        c0, c1 = B["c0"], B["c1"]
+        rows = np.arange(c0, p.n)
+        np.testing.assert_allclose(fi._ib_L(b, rows), Lx[c0:, c0:c1], atol=1e-12 * np.abs(Lx).max())
+        for j in range(B["first"], B["last"] + 1):
+            jc0, jc1 = an_i.cols(j)
+            saved += (jc1 - jc0) * int(np.sum(an_i.sym.rows[j] >= c1))
+    for j in range(an_s.nsuper):
+        if fs.sn[j].compressed:
+            assert fi.sn[j].compressed and fi.sn[j].U.shape[1] == fs.sn[j].U.shape[1], j
+    r = np.random.default_rng(3).standard_normal(p.n)
+    zs, zi = F.apply_preconditioner(fs, r), F.apply_preconditioner(fi, r)
+    assert np.abs(zs - zi).max() <= 1e-12 * np.abs(zs).max()
+    _, its, _, ok_s = F.solve(an_s, fs, p.b, 1e-8)
+    _, iti, rr, ok_i = F.solve(an_i, fi, p.b, 1e-8)
+    assert ok_s and ok_i and its == iti and rr <= 1e-8
+    assert F.factor_bytes(fs) - F.factor_bytes(fi) == 8 * saved > 0
+
+
+def test_interior_blocks_cover_the_uncompressed_subtrees():
+    """Blocks are the maximal subtrees without a compressed supernode: contiguous, disjoint,
+    every supernode outside them is compressed or has a compressed descendant."""
+    p = W.poisson7(12)
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(leaf_size=16, tau_O=40, tau_D=32, interior_blocks=True))
+    f = F.factor(an, 0.1)
+    parent = an.sym.parent
+    ib = f.iblock_of
+    for b, B in enumerate(f.iblocks):
+        assert np.all(ib[B["first"]:B["last"] + 1] == b)
+        assert parent[B["last"]] < 0 or ib[parent[B["last"]]] < 0
+    comp_desc = np.array([f.is_compressed(j) for j in range(an.nsuper)])
+    for j in range(an.nsuper):
+        if parent[j] >= 0:
+            comp_desc[parent[j]] |= comp_desc[j]
+    assert np.array_equal(ib < 0, comp_desc)
