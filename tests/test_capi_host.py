@@ -236,3 +236,36 @@ def test_spectral_positions_larger_graph_are_low_modes(maker):
         assert np.all(np.abs(rq - lam) <= 0.05 * lam), (rq, lam)
     perm, _ = R.rsc_get_ordering(h)
     assert np.array_equal(np.sort(perm), np.arange(n))
+
+
+def test_graph_ordering_disconnected_and_tiny_components():
+    """A stack of two grids, an isolated node and 2- and 3-node paths: with shared positions
+    the graph ordering is bit-exact vs the oracle; without positions every component gets
+    its own spectral positions (a single node at 0, a 2-node path +-1/sqrt 2 on one axis),
+    equal to the oracle's up to sign per column."""
+    import scipy.sparse as sp_
+    from oracle.ordering import node_graph, spectral_coordinates
+    a, b = W.poisson7(5), W.poisson7(4, 3, 2)
+    blocks = [a.scipy(), sp_.csr_matrix(np.array([[2.0]])), b.scipy(),
+              sp_.csr_matrix(np.array([[2.0, -1.0], [-1.0, 2.0]])),
+              sp_.csr_matrix(np.array([[2.0, -1.0, 0.0], [-1.0, 2.0, -1.0], [0.0, -1.0, 2.0]]))]
+    A = sp_.block_diag(blocks).tocsr()
+    A.sort_indices()
+    n = A.shape[0]
+    Xg = np.random.default_rng(0).uniform(size=(n, 3))
+    h = R.rsc_analyze(n, A.indptr, A.indices, A.data, Xg, R.rsc_options_default(leaf_size=4, ordering=1))
+    an = F.analyze(n, A.indptr, A.indices, A.data, Xg, F.Options(leaf_size=4, ordering=1))
+    np.testing.assert_array_equal(R.rsc_get_ordering(h)[0], an.ordering.perm)
+    h = R.rsc_analyze(n, A.indptr, A.indices, A.data, None, R.rsc_options_default(leaf_size=4))
+    X = R.rsc_get_coordinates(h)
+    ptr, idx = node_graph(n, A.indptr, A.indices)
+    comp = np.repeat(np.arange(5), [m.shape[0] for m in blocks])
+    Xo = spectral_coordinates(ptr, idx, comp)
+    for c in range(5):
+        sel = comp == c
+        for k in range(3):
+            u, v = X[sel, k], Xo[sel, k]
+            assert min(np.abs(u - v).max(), np.abs(u + v).max()) <= 1e-9, (c, k)
+    assert X[a.n, :].tolist() == [0.0, 0.0, 0.0]
+    perm, _ = R.rsc_get_ordering(h)
+    assert np.array_equal(np.sort(perm), np.arange(n))
