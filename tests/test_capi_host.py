@@ -261,11 +261,12 @@ def test_graph_ordering_disconnected_and_tiny_components():
     ptr, idx = node_graph(n, A.indptr, A.indices)
     comp = np.repeat(np.arange(5), [m.shape[0] for m in blocks])
     Xo = spectral_coordinates(ptr, idx, comp)
-    for c in range(5):
+    for c in range(5):            # the subspace is unique (the 5^3 cube's 3 modes share one eigenvalue)
         sel = comp == c
-        for k in range(3):
-            u, v = X[sel, k], Xo[sel, k]
-            assert min(np.abs(u - v).max(), np.abs(u + v).max()) <= 1e-9, (c, k)
+        k = min(3, int(sel.sum()) - 1)
+        if k <= 0:
+            continue
+        assert np.abs(_proj(X[sel, :k]) - _proj(Xo[sel, :k])).max() <= 1e-9, c
     assert X[a.n, :].tolist() == [0.0, 0.0, 0.0]
     perm, _ = R.rsc_get_ordering(h)
     assert np.array_equal(np.sort(perm), np.arange(n))
