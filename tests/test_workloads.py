@@ -74,3 +74,21 @@ def test_grf_moments_and_correlation_length():
     for lag in (3, 6, 9):
         c = np.mean(g * np.roll(g, lag, axis=0)) / sigma ** 2
         assert abs(c - np.exp(-lag ** 2 / (2 * L ** 2))) <= 0.12, (lag, c)
+
+
+def test_fv_values_torch_function_matches_generator_and_differentiates():
+    """FVValues(shape)(theta) is fv_diffusion(exp(theta)) entry for entry in CSR order, and
+    its derivative in theta passes torch's finite-difference gradcheck (FP64, CPU)."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    shape = (3, 4, 5)
+    theta = np.random.default_rng(7).standard_normal(shape)
+    fv = W.FVValues(shape)
+    ref = W.fv_diffusion(np.exp(theta), 0)
+    np.testing.assert_array_equal(fv.row_ptr, ref.row_ptr)
+    np.testing.assert_array_equal(fv.col_idx, ref.col_idx)
+    vals = fv(torch.tensor(theta)).numpy()
+    np.testing.assert_allclose(vals, ref.val, rtol=1e-13, atol=1e-13)
+    small = W.FVValues((2, 2, 3))
+    th = torch.tensor(np.random.default_rng(8).standard_normal((2, 2, 3)), requires_grad=True)
+    assert torch.autograd.gradcheck(small, (th,), eps=1e-6, atol=1e-7)
