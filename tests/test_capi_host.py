@@ -270,3 +270,20 @@ def test_graph_ordering_disconnected_and_tiny_components():
     assert X[a.n, :].tolist() == [0.0, 0.0, 0.0]
     perm, _ = R.rsc_get_ordering(h)
     assert np.array_equal(np.sort(perm), np.arange(n))
+
+
+def test_no_gpu_fails_loudly():
+    """Without a usable GPU the numeric calls return RSC_ERR_CUDA with a message and leave
+    the handle unfactored (a later solve is RSC_ERR_STATE): there is no CPU fallback."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = W.poisson7(4)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, R.rsc_options_default())
+    for call in (lambda: R.rsc_factor(h, 0.1), lambda: R.rsc_factor_fixed_rank(h, 0.5)):
+        with pytest.raises(R.RscError) as e:
+            call()
+        assert e.value.status == 5 and "CUDA" in str(e.value)
+    with pytest.raises(R.RscError) as e:
+        R.rsc_solve(h, p.b)
+    assert e.value.status == 7
