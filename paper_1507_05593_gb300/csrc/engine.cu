@@ -244,7 +244,6 @@ struct EngineImpl {
                    cudaStream_t s);
     cudaStream_t stream = nullptr;
     DeviceMem amem;   // matrix for SpMV
-    int* d_rp32 = nullptr;   // unused placeholder
     long long* d_rp = nullptr;
     int32_t* d_ci = nullptr;
     double* d_val = nullptr;
