@@ -221,12 +221,15 @@ rsc_status rsc_pattern_outer_device(rsc_handle* h, const double* d_u, const doub
  *    with that device current); the first call after each rsc_factor (or with
  *    another handle) copies its task records into the array on cuda_stream.  Make
  *    such a first call before any stream capture.
+ *  - Every call synchronises cuda_stream before it returns: d_z holds the result and
+ *    a failure of the call's kernels is reported by the call itself.
  *  - Every call, from every handle, shares the one array and it keeps the last
  *    call's contents; calls whose GPU work overlaps (other streams, other host
- *    threads) race with each other.  The call synchronises cuda_stream on return.
+ *    threads) race with each other.
  *  - Returns RSC_ERR_INVALID_ARG when the problem needs more than the 64 MiB
  *    (about n * sizeof(factor element) plus the task records), RSC_ERR_STATE
- *    before rsc_factor.
+ *    before rsc_factor or when the current CUDA device is not the one the handle
+ *    was factored on.
  */
 rsc_status rsc_apply_preconditioner_device_noalloc(rsc_handle* h, const double* d_r, double* d_z, void* cuda_stream);
 
