@@ -228,6 +228,7 @@ struct EngineImpl {
     virtual void stats(rsc_stats_t* out) const = 0;
     virtual long long generation() const = 0;
     long long uid = 0;    // unique per engine (never reused, unlike its address)
+    int device = 0;       // the CUDA device the engine's memory and stream belong to
     virtual rsc_status apply_noalloc(const double* d_r, double* d_z, cudaStream_t s, char* base, size_t cap,
                                      bool load) = 0;
     virtual bool noalloc_ready() const = 0;
@@ -741,6 +742,9 @@ struct EngineT final : EngineImpl {
             CK(cudaFuncSetAttribute(k_push_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM_TF32));
         }
         CK(cudaFuncSetAttribute(k_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM_CAP));
+        CK(cudaFuncSetAttribute(k_tn_s<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_bytes<T>(16)));
+        CK(cudaFuncSetAttribute(k_tn_s<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_bytes<T>(32)));
+        CK(cudaFuncSetAttribute(k_tn_s<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_bytes<T>(64)));
         CK(cudaFuncSetAttribute(k_rf_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RFD_SMEM_CAP));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
         hs_attr<8>();
@@ -1272,7 +1276,7 @@ struct EngineT final : EngineImpl {
     }
     void add_tn(Stage& s, const TnTask& t) {
         if (t.K == 0 || t.nrow == 0 || t.N == 0) return;
-        for (int t0 = 0; t0 < t.K; t0 += TN_COLS) { TnTask c = t; c.t0 = t0; s.tn.push_back(c); }
+        for (int t0 = 0; t0 < t.K; t0 += TS_COLS) { TnTask c = t; c.t0 = t0; s.tn.push_back(c); }
         flops += 2.0 * t.nrow * t.K * t.N;
     }
     void add_nn(Stage& s, const NnTask& t) {
@@ -1294,13 +1298,16 @@ struct EngineT final : EngineImpl {
     }
     static Stage& next(Program& P) { P.emplace_back(); return P.back(); }
 
-    static double task_flops(const TnTask& t) { return 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0) * t.N; }
+    static double task_flops(const TnTask& t) { return 2.0 * t.nrow * std::min(TS_COLS, t.K - t.t0) * t.N; }
     static double task_flops(const NnTask& t) { return 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K * t.N; }
     static double task_flops(const TrsvTask& t) { return (double)t.c * t.c * t.N; }
     template <class X> static double task_flops(const X&) { return 0.0; }
+    // algorithmic bytes of a TN product: A's rows once, Y's gathered rows once per task (counted
+    // with its first 64-column tile), Z written once (and read when beta != 0)
     static double task_bytes(const TnTask& t) {
-        const double cols = std::min(TN_COLS, t.K - t.t0);
-        return sizeof(T) * (t.nrow * cols + t.nrow * (double)t.N + cols * t.N);
+        const double cols = std::min(TS_COLS, t.K - t.t0);
+        return sizeof(T) * (t.nrow * cols + (t.t0 == 0 ? t.nrow * (double)t.N : 0.0) +
+                            cols * t.N * (t.beta != 0.0 ? 2.0 : 1.0));
     }
     static double task_bytes(const NnTask& t) {
         const double rows = std::min(NN_ROWS, t.nrow - t.row0);
@@ -1325,7 +1332,7 @@ struct EngineT final : EngineImpl {
         for (auto& p : progs) len = std::max(len, p.size());
         for (size_t i = 0; i < len; ++i) {
             Stage st;
-            int yn_tn = 1, yn_nn = 1, yn_csr = 1, yn_tr = 1;
+            int yn_nn = 1, yn_csr = 1, yn_tr = 1;
             for (auto& p : progs) {
                 if (i >= p.size()) continue;
                 Stage& s = p[i];
@@ -1339,7 +1346,6 @@ struct EngineT final : EngineImpl {
                 st.tn.insert(st.tn.end(), s.tn.begin(), s.tn.end());
                 st.nn.insert(st.nn.end(), s.nn.begin(), s.nn.end());
             }
-            for (auto& t : st.tn) yn_tn = std::max(yn_tn, cdiv(t.N, 16));
             for (auto& t : st.nn) yn_nn = std::max(yn_nn, cdiv(t.N, 16));
             for (auto& t : st.csr) yn_csr = std::max(yn_csr, cdiv(t.N, 16));
             for (auto& t : st.trsv) yn_tr = std::max(yn_tr, cdiv(t.N, TRSV_CW));
@@ -1355,22 +1361,28 @@ struct EngineT final : EngineImpl {
             launch_kind("csr", st.csr, yn_csr, [&](CsrTask* d, int n, int y) { k_csr_mm<T><<<dim3(n, y), 256, 0, s>>>(d); });
             launch_kind("trsv", st.trsv, yn_tr,
                         [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
-            int zs_tn = 1;
+            int zs_tn = 1, yc_tn = 1, np_tn = 16;
             {   // long row ranges: split the rows over CTAs (deterministic fixed-order reduction)
                 int coff = 0;
                 for (auto& t : st.tn) {
-                    const int ych = cdiv(t.N, 16);
+                    const int ych = cdiv(t.N, 64);
+                    yc_tn = std::max(yc_tn, ych);
+                    np_tn = std::max(np_tn, std::min(t.N, 64) <= 16 ? 16 : std::min(t.N, 64) <= 32 ? 32 : 64);
                     if (t.nrow < TN_SPLIT_MIN || coff + ych > TN_CNT_CAP) continue;
                     t.nsplit = std::min(cdiv(t.nrow, TN_SPLIT_ROWS), TN_SPLIT_MAX);
                     t.rps = cdiv(t.nrow, t.nsplit);
-                    t.part = wsT((size_t)t.nsplit * 32 * t.N);
+                    t.part = wsT((size_t)t.nsplit * TS_COLS * t.N);
                     t.cnt = d_tncnt + coff;
                     coff += ych;
                     zs_tn = std::max(zs_tn, t.nsplit);
                 }
             }
-            launch_kind("tn", st.tn, yn_tn,
-                        [&](TnTask* d, int n, int y) { k_tn<T><<<dim3(n, y, zs_tn), 256, 0, s>>>(d); });
+            launch_kind("tn", st.tn, yc_tn, [&](TnTask* d, int n, int y) {
+                const dim3 g((unsigned)n, (unsigned)y, (unsigned)zs_tn);
+                if (np_tn == 16) k_tn_s<T, 16><<<g, 256, ts_smem_bytes<T>(16), s>>>(d);
+                else if (np_tn == 32) k_tn_s<T, 32><<<g, 256, ts_smem_bytes<T>(32), s>>>(d);
+                else k_tn_s<T, 64><<<g, 256, ts_smem_bytes<T>(64), s>>>(d);
+            });
             launch_kind("nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) { k_nn<T><<<dim3(n, y), NN_ROWS, 0, s>>>(d); });
         }
         progs.clear();
@@ -2294,6 +2306,9 @@ struct EngineT final : EngineImpl {
 
     rsc_status factor(const double* val, double tol_in, const FixedRank* fr) override {
         is_factored = false;
+        // the records of the allocation-free apply point into the factor being replaced
+        na_y = nullptr;
+        na_loaded_gen = -1;
         plan1.clear();   // launch lists of the previous factor: their memory is released now
         planN.clear();
         fixed = fr != nullptr;
@@ -3092,6 +3107,7 @@ Engine::Engine(const Symbolic& S, const rsc_options& o) {
     if (o.precision == RSC_PREC_FP64) impl_.reset(new EngineT<double>(S, o));
     else impl_.reset(new EngineT<float>(S, o));
     impl_->uid = ++g_engine_uid;
+    CK(cudaGetDevice(&impl_->device));
 }
 Engine::~Engine() = default;
 rsc_status Engine::factor(const double* val, double tol, const FixedRank* fr) { return impl_->factor(val, tol, fr); }
@@ -3153,8 +3169,14 @@ rsc_status Engine::pattern_outer(const std::vector<int64_t>& rp, const std::vect
 
 rsc_status Engine::apply_precond_noalloc(const double* d_r, double* d_z, void* stream) {
     cudaStream_t s = stream ? (cudaStream_t)stream : impl_->stream;
+    // the records hold device addresses of the engine's device: the static region of another
+    // device must never be paired with them
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    if (dev != impl_->device)
+        throw Error(RSC_ERR_STATE, "the current CUDA device (" + std::to_string(dev) +
+                                       ") is not the device the handle was factored on (" +
+                                       std::to_string(impl_->device) + ")");
     std::lock_guard<std::mutex> lock(g_na_mu);
     auto it = g_na_addr.find(dev);
     if (it == g_na_addr.end()) {
@@ -3163,13 +3185,14 @@ rsc_status Engine::apply_precond_noalloc(const double* d_r, double* d_z, void* s
         if (e != cudaSuccess) throw Error(RSC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         it = g_na_addr.emplace(dev, p).first;
     }
+    // reload when the region holds another engine's records or those of an earlier factor
     const std::pair<long long, long long> mine{impl_->uid, impl_->generation()};
     auto ld = g_na_loaded.find(dev);
     const bool load = ld == g_na_loaded.end() || ld->second != mine || !impl_->noalloc_ready();
     if (load) g_na_loaded.erase(dev);
     rsc_status st = impl_->apply_noalloc(d_r, d_z, s, it->second, NOALLOC_SCRATCH_BYTES, load);
     if (load) g_na_loaded[dev] = mine;
-    CK(cudaStreamSynchronize(s));
+    CK(cudaStreamSynchronize(s));   // every call returns with its result in d_z
     return st;
 }
 

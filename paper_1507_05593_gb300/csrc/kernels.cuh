@@ -569,6 +569,175 @@ __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
     if (threadIdx.x == 0) *tk.cnt = 0u;
 }
 
+// ------------------------------------------------------------------ staged TN product (factorization)
+// Z[t, :] = beta Z[t, :] + alpha sum_i A[arow_i, t] Y[yrow_i, :] for one 64-column tile of A
+// (t0 .. t0 + 63) and all N <= 64 columns of Y in one CTA, so every element of A is read
+// from memory once.  Rows stream through shared memory in chunks of 32 with cp.async double
+// buffering: the A chunk is read down its columns (a warp reads 32 consecutive rows of one
+// column, 128 contiguous bytes for FP32), the Y chunk row by row (the gathered rows are
+// contiguous N-vectors, copied 16 bytes at a time when aligned).  Thread (tg, cg) owns TT
+// columns of A and 4 columns of Y (NP = N padded to 16, 32 or 64; TT = NP / 16) and
+// accumulates over the chunk's rows from shared memory, so no cross-thread reduction is
+// needed.  With tk.nsplit > 1 CTA z takes rows [z rps, (z + 1) rps) and writes its partial
+// sums to part[z][64][N]; the last CTA to arrive (counter cnt[0]) adds them in ascending z
+// (deterministic), writes Z and resets the counter.
+constexpr int TS_COLS = 64;
+constexpr int TS_ROWS = 32;
+template <class T>
+__host__ __device__ constexpr size_t ts_smem_bytes(int np) {
+    return sizeof(T) * ((size_t)2 * TS_COLS * (TS_ROWS + 1) + (size_t)2 * TS_ROWS * (np + 4));
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+template <class T, int NP>
+__global__ void __launch_bounds__(256) k_tn_s(const TnTask* __restrict__ tasks) {
+    extern __shared__ __align__(16) unsigned char ts_smem[];
+    constexpr int AST = TS_ROWS + 1;       // As[t][r]: a column of the chunk per row of As
+    constexpr int YST = NP + 4;            // Ys[r][c]: 16-byte aligned rows
+    constexpr int CG = NP / 4;             // column groups of 4
+    constexpr int TT = TS_COLS * CG / 256; // columns of A per thread
+    T* As = (T*)ts_smem;
+    T* Ys = As + 2 * TS_COLS * AST;
+    __shared__ int last;
+    const TnTask tk = tasks[blockIdx.x];
+    const int cb = blockIdx.y * 64;                     // 64-column chunk of Y and Z
+    const int nc = min(64, tk.N - cb);
+    if (nc <= 0 || (int)blockIdx.z >= tk.nsplit) return;
+    const int tid = threadIdx.x;
+    const int rb = (int)blockIdx.z * tk.rps;
+    const int re = tk.nsplit > 1 ? min(tk.nrow, rb + tk.rps) : tk.nrow;
+    const int kc = min(TS_COLS, tk.K - tk.t0);          // valid columns of this tile
+    const T* A = (const T*)tk.A + (size_t)tk.t0 * tk.lda;
+    const T* Y = (const T*)tk.Y + cb;
+    constexpr int VW = 16 / (int)sizeof(T);             // elements per 16-byte copy
+    const bool yvec = (nc % VW) == 0 && (tk.ldy % VW) == 0 && (((uintptr_t)Y) & 15) == 0;
+    auto issue = [&](int r0, int buf) {
+        const int rc = min(TS_ROWS, re - r0);
+        T* as = As + buf * TS_COLS * AST;
+        T* ys = Ys + buf * TS_ROWS * YST;
+        for (int e = tid; e < TS_COLS * TS_ROWS; e += 256) {
+            const int t = e / TS_ROWS, r = e % TS_ROWS;
+            if (t < kc && r < rc) {
+                const int i = r0 + r;
+                const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
+                const T* src = A + (size_t)t * tk.lda + ar;
+                if (sizeof(T) == 8) cp_async8(as + t * AST + r, src);
+                else cp_async4(as + t * AST + r, src);
+            }
+        }
+        if (yvec) {
+            const int per = nc / VW;
+            for (int e = tid; e < TS_ROWS * per; e += 256) {
+                const int r = e / per, q = e % per;
+                if (r < rc) {
+                    const int i = r0 + r;
+                    const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+                    cp_async16(ys + r * YST + q * VW, Y + (size_t)yr * tk.ldy + q * VW);
+                }
+            }
+        } else {
+            for (int e = tid; e < TS_ROWS * nc; e += 256) {
+                const int r = e / nc, c = e % nc;
+                if (r < rc) {
+                    const int i = r0 + r;
+                    const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
+                    if (sizeof(T) == 8) cp_async8(ys + r * YST + c, Y + (size_t)yr * tk.ldy + c);
+                    else cp_async4(ys + r * YST + c, Y + (size_t)yr * tk.ldy + c);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    const int cg = tid % CG, tg = tid / CG;
+    T acc[TT][4];
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[u][q] = T(0);
+    const int nch = (re - rb + TS_ROWS - 1) / TS_ROWS;
+    if (nch > 0) issue(rb, 0);
+    for (int ci = 0; ci < nch; ++ci) {
+        const int buf = ci & 1;
+        if (ci + 1 < nch) { issue(rb + (ci + 1) * TS_ROWS, buf ^ 1); cp_async_wait<1>(); }
+        else cp_async_wait<0>();
+        __syncthreads();
+        const int rc = min(TS_ROWS, re - rb - ci * TS_ROWS);
+        const T* as = As + buf * TS_COLS * AST + (tg * TT) * AST;
+        const T* ys = Ys + buf * TS_ROWS * YST + cg * 4;
+#pragma unroll 4
+        for (int r = 0; r < rc; ++r) {
+            T yv[4];
+            if (sizeof(T) == 4) {
+                const float4 f = *reinterpret_cast<const float4*>(ys + r * YST);
+                yv[0] = f.x; yv[1] = f.y; yv[2] = f.z; yv[3] = f.w;
+            } else {
+                const double2 f0 = *reinterpret_cast<const double2*>(ys + r * YST);
+                const double2 f1 = *reinterpret_cast<const double2*>(ys + r * YST + 2);
+                yv[0] = f0.x; yv[1] = f0.y; yv[2] = f1.x; yv[3] = f1.y;
+            }
+#pragma unroll
+            for (int u = 0; u < TT; ++u) {
+                const T a = as[u * AST + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[u][q] = fma(a, yv[q], acc[u][q]);
+            }
+        }
+        __syncthreads();
+    }
+    const int c0 = cg * 4;
+    if (tk.nsplit == 1) {
+#pragma unroll
+        for (int u = 0; u < TT; ++u) {
+            const int t = tg * TT + u;
+            if (t >= kc) continue;
+            T* z = (T*)tk.Z + (size_t)(tk.t0 + t) * tk.ldz + cb;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c0 + q;
+                if (c >= nc) break;
+                z[c] = tk.beta != 0.0 ? (T)tk.beta * z[c] + (T)tk.alpha * acc[u][q] : (T)tk.alpha * acc[u][q];
+            }
+        }
+        return;
+    }
+    // partial sums of this row range: part[z][t][cb + c], row length N
+    T* part = (T*)tk.part;
+#pragma unroll
+    for (int u = 0; u < TT; ++u) {
+        const int t = tg * TT + u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = c0 + q;
+            if (c < nc) part[((size_t)blockIdx.z * TS_COLS + t) * tk.N + cb + c] = acc[u][q];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(tk.cnt + blockIdx.y, 1u) == (unsigned)(tk.nsplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int e = tid; e < kc * nc; e += 256) {
+        const int t = e / nc, c = e % nc;
+        T s = T(0);
+        for (int zz = 0; zz < tk.nsplit; ++zz) s += __ldcg(part + ((size_t)zz * TS_COLS + t) * tk.N + cb + c);
+        T* z = (T*)tk.Z + (size_t)(tk.t0 + t) * tk.ldz + cb + c;
+        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * s : (T)tk.alpha * s;
+    }
+    if (tid == 0) tk.cnt[blockIdx.y] = 0u;
+}
+
 // One CTA of 128 threads per (task, 128-row chunk, 16-column chunk); a thread owns one
 // row and its 16 outputs, so each element of A is loaded once.
 constexpr int NN_ROWS = 128;
