@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--systems", type=int, default=256)
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the compact runs of the other configurations (C1, C3, C4, C5)")
     a = ap.parse_args()
     if a.side is None:
         a.side = {"elasticity": 40, "poisson": 32, "autograd": 64}.get(a.workload, 96)
@@ -155,10 +157,11 @@ print(json.dumps(dict(n=p.n, analyze=t1 - t0, factor=t2 - t1, solve=t3 - t2, ite
 """
 
 
-def run_oracle_sample(side, crop, tol, rtol, workload="diffusion"):
+def run_oracle_sample(side, crop, tol, rtol, workload="diffusion", threads=1):
     """The oracle, as it stands, on a crop of the same conductivity field, or on a smaller
-    elasticity block of the same shape (single thread)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    elasticity block of the same shape (numpy with `threads` BLAS threads)."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = _ORACLE_CODE.format(root=ROOT, side=side, crop=crop, tol=tol, rtol=rtol, kind=workload,
                                incl=_elasticity_incl(crop))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
@@ -167,20 +170,115 @@ def run_oracle_sample(side, crop, tol, rtol, workload="diffusion"):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(side, tol, rtol, crop=32, workload="diffusion", n_full=None):
+def cpu_baseline(side, tol, rtol, crop=32, workload="diffusion", n_full=None, threads=1):
     if workload == "elasticity":
         crop = 12
     elif workload == "poisson":
         crop = side          # the whole problem: seconds for the oracle
-    r = run_oracle_sample(side, crop, tol, rtol, workload)
+    r = run_oracle_sample(side, crop, tol, rtol, workload, threads)
     secs = r["factor"] + r["solve"]
     scale = (n_full or side ** 3) / r["n"]
     what = {"elasticity": f"a {crop}^3-element block of the same elasticity problem",
             "poisson": "the whole problem"}.get(workload, f"the {crop}^3 corner crop of the same conductivity field")
-    return {"value": secs * scale, "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": secs * scale, "unit": "s", "cores": threads, "kind": "oracle",
             "sample": (f"oracle factor+PCG on {what} "
-                       f"({r['n']:,} unknowns, tol {tol:g}, {r['iters']} iterations, measured {secs:.2f} s), "
+                       f"({r['n']:,} unknowns, tol {tol:g}, {r['iters']} iterations, measured {secs:.2f} s, "
+                       f"{threads} BLAS thread{'s' if threads > 1 else ''} of nproc = {os.cpu_count()}), "
                        f"scaled linearly by unknowns x{scale:.1f} (a lower bound: the method is superlinear)")}
+
+
+def _oracle_code(code, threads=1, timeout=900):
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+_ORACLE_BATCH = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import factor as F
+p = W.diffusion_lognormal({side}, 1.0, seed=0)
+t0 = time.perf_counter()
+an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options())
+f = F.factor(an, {tol})
+t1 = time.perf_counter()
+its = [F.solve(an, f, W.rhs_uniform(p.n, seed=c), {rtol}, 2000)[1] for c in range({nrhs})]
+t2 = time.perf_counter()
+print(json.dumps(dict(n=p.n, factor=t1 - t0, solve=t2 - t1, iters=max(its))))
+"""
+
+_ORACLE_ADJOINT = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import factor as F
+c = {crop}
+theta = np.random.default_rng(0).standard_normal(({side}, {side}, {side}))[:c, :c, :c]
+p = W.fv_diffusion(np.exp(theta), 2)
+t0 = time.perf_counter()
+an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options())
+f = F.factor(an, {tol})
+x, it, rr, ok = F.solve(an, f, p.b, {rtol}, 2000)
+t1 = time.perf_counter()
+lam, it2, rr2, ok2 = F.solve(an, f, x, {rtol}, 2000)
+t2 = time.perf_counter()
+print(json.dumps(dict(n=p.n, forward=t1 - t0, backward=t2 - t1, iters=it)))
+"""
+
+
+def _sub_bench(args, timeout=900):
+    """One compact run of bench.py for another configuration; its JSON line, or the failure."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--no-others"] + args
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+        for ln in reversed(out.stdout.strip().splitlines()):
+            if ln.startswith("{"):
+                return json.loads(ln)
+        return {"failed": (out.stderr or out.stdout)[-400:]}
+    except Exception as e:
+        return {"failed": str(e)[:400]}
+
+
+def _compact(d, keys):
+    if not d or "failed" in d:
+        return d
+    return {k: d.get(k) for k in keys if k in d}
+
+
+def other_configs(a):
+    """C1 (Poisson 32^3, all FP64), C3 (elasticity 40^3, TF32 Schur updates), C4 (256 systems x 8
+    right-hand sides, BF16), C5 (differentiation 64^3, FP32 factor): value, iterations, the plain
+    FP64 GPU path beside and the oracle baseline, 3 timed steps each."""
+    base = ["--steps", "3", "--warmup", "1"]
+    keys = ["value", "factor_s", "solve_s", "iters", "relres", "factor_bytes", "restarts", "factor_tflops",
+            "cpu_baseline", "plain_fp64", "fp32_form", "roofline", "dtype", "config", "form", "e2e", "gpu_launches"]
+    out = {}
+    c1 = _sub_bench(["--workload", "poisson", "--prec", "fp64"] + base)
+    c1_32 = _sub_bench(["--workload", "poisson", "--prec", "fp32", "--no-cpu-baseline"] + base)
+    out["C1_poisson32_fp64"] = _compact(c1, keys)
+    if c1_32 and "failed" not in c1_32:
+        out["C1_poisson32_fp64"]["fp32_form"] = _compact(c1_32, ["value", "factor_s", "solve_s", "iters"])
+    out["C3_elasticity40_tf32"] = _compact(_sub_bench(["--workload", "elasticity", "--prec", "tf32"] + base), keys)
+    bkeys = ["value", "factor_s", "solve_s", "iters_max", "iters_mean", "relres_max", "factor_bytes", "restarts",
+             "config", "dtype", "cpu_baseline", "gpu_launches"]
+    c4 = _compact(_sub_bench(["--workload", "batch"] + base), bkeys)
+    c4_64 = _sub_bench(["--workload", "batch", "--prec", "fp64", "--no-cpu-baseline", "--steps", "1", "--warmup", "1"])
+    if c4 and "failed" not in c4:
+        c4["plain_fp64"] = _compact(c4_64, ["value", "factor_s", "solve_s", "iters_max", "factor_bytes"])
+    out["C4_batch256x8_bf16"] = c4
+    akeys = ["value", "forward_s", "backward_s", "last_iters", "factor_bytes", "restarts", "config", "dtype",
+             "cpu_baseline", "gpu_launches"]
+    c5 = _compact(_sub_bench(["--workload", "autograd", "--prec", "fp32"] + base), akeys)
+    c5_64 = _sub_bench(["--workload", "autograd", "--prec", "fp64", "--no-cpu-baseline"] + base)
+    if c5 and "failed" not in c5:
+        c5["plain_fp64"] = _compact(c5_64, ["value", "forward_s", "backward_s", "last_iters"])
+    out["C5_autograd64_fp32"] = c5
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -191,8 +289,60 @@ FORMS = {"bf16": "BF16 Schur updates on tcgen05 (FP32 accumulation), FP32 factor
          "fp32": "FP32 factor, Schur updates and sampling; FP64 diagonal Cholesky and PCG",
          "fp64": "all FP64"}
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at 96^3 (FP32 form), by kernel class
-NCU_TRAFFIC = {"tn": 59.9e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at 96^3, by kernel class, for the
+# code as it stands (profiles/); a class whose kernel changed after its capture has none
+NCU_TRAFFIC = {}
+
+# SIMT peaks measured on this machine's GB300 with an FMA loop; the HBM and
+# BF16 tensor peaks come from MEASURED_PEAKS.json.  TF32 tensor: the BF16 peak times the nominal
+# TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s dense).
+FP64_SIMT_TFLOPS = 1.00
+FP32_SIMT_TFLOPS = 67.7
+
+
+def _peaks():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"hbm": pk.get("hbm_gbs", 6766.4), "bf16": pk.get("bf16_tflops", 1884.3), "src": "of measured"}
+    except Exception:
+        return {"hbm": 6800.0, "bf16": 1900.0, "src": "of fallback"}
+
+
+# which compute roof bounds a kernel class: tensor-core classes against the tensor peak of their
+# operand type, the FP64 Cholesky tiles against FP64 SIMT, the rest against SIMT of the storage type
+TENSOR_CLASSES = {"push_tc"}
+FP64_CLASSES = {"potrf"}
+
+
+def roofline_entry(name, k, prec, source):
+    """Roofline of one kernel class from its launches: achieved algorithmic bytes and flops per
+    launch / average launch time; the bound is the roof the class's arithmetic intensity reaches
+    first (ridge = compute peak / HBM peak)."""
+    pk = _peaks()
+    if not k or k.get("launches", 0) == 0 or k.get("ms", 0) <= 0:
+        return None
+    sec = k["ms"] * 1e-3
+    gbs = k["bytes"] / sec / 1e9 if k.get("bytes") else 0.0
+    tfs = k["flops"] / sec / 1e12 if k.get("flops") else 0.0
+    if name in TENSOR_CLASSES:
+        cpk = pk["bf16"] * (1.1 / 2.25 if prec == "tf32" else 1.0)
+        cunit, csrc = f"{'TF32' if prec == 'tf32' else 'BF16'} tensor", pk["src"]
+    elif name in FP64_CLASSES or prec == "fp64":
+        cpk, cunit, csrc = FP64_SIMT_TFLOPS, "FP64 SIMT", "of builder-measured (DFMA loop)"
+    else:
+        cpk, cunit, csrc = FP32_SIMT_TFLOPS, "FP32 SIMT", "of builder-measured (FFMA loop)"
+    ridge = cpk * 1e12 / (pk["hbm"] * 1e9)
+    ai = (k["flops"] / k["bytes"]) if k.get("bytes") else float("inf")
+    if k.get("bytes") and ai < ridge:
+        ent = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm"], "unit": "GB/s", "frac": gbs / pk["hbm"],
+               "peak_src": pk["src"]}
+    else:
+        ent = {"bound": "tensor" if name in TENSOR_CLASSES else "alu", "achieved": tfs, "peak": cpk,
+               "unit": "TFLOP/s", "frac": tfs / cpk, "peak_src": f"{cunit} {csrc}"}
+    ent.update({"kernel": name, "launches": k["launches"], "avg_launch_us": k["ms"] / k["launches"] * 1e3,
+                "achieved_gbs": gbs, "achieved_tflops": tfs, "intensity_flop_per_byte": None if ai == float("inf")
+                else ai, "source": source})
+    return ent
 
 
 def max_over_ranks(t_local, dist, device):
@@ -215,7 +365,7 @@ def reference_arm(a, rank, world):
         return
     elastic = a.workload == "elasticity"
     n_full = 3 * a.side * (a.side + 1) ** 2 if elastic else a.side ** 3
-    vals = []
+    vals, secs = [], []
     rec = None
     for i in range(a.warmup + a.steps):
         if elastic:
@@ -227,16 +377,21 @@ def reference_arm(a, rank, world):
         r = run_oracle_sample(a.side, crop, a.tol, a.rtol, a.workload)
         if i >= a.warmup:
             vals.append((r["factor"] + r["solve"]) * n_full / r["n"])
+            secs.append(r["factor"] + r["solve"])
             rec = r
     v = sum(vals) / len(vals)
+    t_sample = sum(secs) / len(secs)
     what = {"elasticity": "a 12^3-element block of the same elasticity problem",
             "poisson": "the whole problem"}.get(a.workload, "the 32^3 corner crop of the same conductivity field")
     sample = (f"oracle (numpy FP64, 1 thread) factor+PCG on {what} "
               f"({rec['n']:,} unknowns, {rec['iters']} iterations), scaled linearly by unknowns to the full problem")
+    # value: the sample's time scaled to the whole workload (the metric); ms_per_step: the time a
+    # timed step took (one bounded sample)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "warmup": a.warmup, "ms_per_step": t_sample * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": _workload_name(a.side, a.tol, a.workload), "form": "cpu oracle"},
+            "config": {"workload": _workload_name(a.side, a.tol, a.workload)}, "form": "cpu oracle (FP64)",
+            "value_basis": f"sample time x {n_full / rec['n']:.1f} (unknowns of the workload / of the sample)",
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -292,6 +447,17 @@ def batch_workload(a):
     fs = sum(r[0] for r in res) / len(res)
     ss = sum(r[1] for r in res) / len(res)
     its, rr, st = res[-1][2], res[-1][3], res[-1][4]
+    cpu = None
+    if not a.no_cpu_baseline:
+        try:   # the oracle on system 0 (all its right-hand sides), scaled by unknowns
+            r = _oracle_code(_ORACLE_BATCH.format(root=ROOT, side=int(sides[0]), tol=a.tol, rtol=a.rtol,
+                                                  nrhs=a.nrhs))
+            secs = r["factor"] + r["solve"]
+            cpu = {"value": secs * n / r["n"], "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": (f"oracle factor + {a.nrhs} PCG solves of system 0 ({r['n']:,} unknowns, side "
+                              f"{int(sides[0])}, measured {secs:.2f} s), scaled linearly by unknowns x{n / r['n']:.1f}")}
+        except Exception as e:
+            cpu = {"value": None, "sample": f"failed: {e}"[:300]}
     line = {"metric": "batched factor+PCG seconds (all systems x right-hand sides to rel. residual 1e-8)",
             "value": fs + ss, "unit": "s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "higher_is_better": False, "dtype": {"bf16": "bf16", "fp32": "f32"}.get(a.prec, "f64"),
@@ -302,7 +468,7 @@ def batch_workload(a):
             "factor_s": fs, "solve_s": ss, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "relres_max": float(rr.max()), "analyze_s": t_an, "factor_bytes": st["factor_bytes"],
             "gpu_launches": st["gpu_launches"], "n_supernodes": st["n_supernodes"], "n_levels": st["n_levels"],
-            "restarts": st["restarts"]}
+            "restarts": st["restarts"], "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -348,6 +514,17 @@ def autograd_workload(a):
             bw.append(ev[1].elapsed_time(ev[2]) * 1e-3)
     st = R.rsc_get_stats(h)
     f, g = sum(fw) / len(fw), sum(bw) / len(bw)
+    cpu = None
+    if not a.no_cpu_baseline:
+        try:   # the oracle's factor + forward PCG and adjoint PCG on a 24^3 corner of theta, scaled
+            crop = min(24, a.side)
+            r = _oracle_code(_ORACLE_ADJOINT.format(root=ROOT, side=a.side, crop=crop, tol=a.tol, rtol=a.rtol))
+            secs = r["forward"] + r["backward"]
+            cpu = {"value": secs * fv.n / r["n"], "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": (f"oracle factor + PCG + adjoint PCG on the {crop}^3 corner of theta ({r['n']:,} "
+                              f"unknowns, measured {secs:.2f} s), scaled linearly by unknowns x{fv.n / r['n']:.1f}")}
+        except Exception as e:
+            cpu = {"value": None, "sample": f"failed: {e}"[:300]}
     line = {"metric": "loss forward (factor + PCG) + backward (adjoint PCG, kept factor) seconds",
             "value": f + g, "unit": "s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "higher_is_better": False, "dtype": {"bf16": "bf16", "tf32": "tf32", "fp32": "f32"}.get(a.prec, "f64"),
@@ -357,7 +534,7 @@ def autograd_workload(a):
                        "form": FORMS.get(a.prec, a.prec)},
             "forward_s": f, "backward_s": g, "grad_norm": float(th.grad.norm()), "loss": float(loss),
             "last_iters": st["last_iters"], "factor_bytes": st["factor_bytes"], "restarts": st["restarts"],
-            "gpu_launches": st["gpu_launches"]}
+            "gpu_launches": st["gpu_launches"], "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -472,55 +649,67 @@ def main():
     t_f = sum(r[1] for r in e2e_runs) / len(e2e_runs)
     x = e2e_runs[-1][2]
     res = np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
-    # the other forms, once each (after one untimed step)
-    def side_form(prec, power_iters=0, fixed_rank=False):
+    # the other forms over the same number of timed steps (after one untimed step); the paper's
+    # own rank rule over min(steps, 3)
+    def side_form(prec, power_iters=0, fixed_rank=False, nsteps=None):
         hs, _ = make(prec, power_iters)
         step(hs, fixed_rank)
-        ts, its, rrs, sts = step(hs, fixed_rank)
-        return {"seconds": ts, "factor_s": sts["factor_seconds"], "solve_s": sts["solve_seconds"],
-                "iters": its, "relres": rrs, "factor_bytes": sts["factor_bytes"], "restarts": sts["restarts"],
-                "factor_tflops": sts["factor_flops"] / sts["factor_seconds"] / 1e12}
+        runs = [step(hs, fixed_rank) for _ in range(nsteps or a.steps)]
+        sts = runs[-1][3]
+        secs = sum(r[0] for r in runs) / len(runs)
+        fsec = sum(r[3]["factor_seconds"] for r in runs) / len(runs)
+        return {"seconds": secs, "steps": len(runs), "factor_s": fsec, "solve_s": secs - fsec,
+                "iters": runs[-1][1], "relres": runs[-1][2], "factor_bytes": sts["factor_bytes"],
+                "restarts": sts["restarts"], "factor_tflops": sts["factor_flops"] / fsec / 1e12}
     fp64 = side_form("fp64") if not a.no_fp64 and a.prec != "fp64" else None
     fp32 = side_form("fp32") if not a.no_fp64 and a.prec in ("bf16", "tf32") else None
     # the paper's own rank rule (Section 5.2) in the same form: RSC0 and RSC1 (one power iteration)
     fixed = None
     if not a.no_fp64 and a.workload == "diffusion":
-        fixed = {f"rsc{q}": side_form(a.prec, q, True) for q in (0, 1)}
+        fixed = {f"rsc{q}": side_form(a.prec, q, True, min(a.steps, 3)) for q in (0, 1)}
         for q, v in enumerate(fixed.values()):
             v.update({"alpha_O": 0.5, "alpha_D": 0.5, "p": 8, "power_iters": q})
+    # roofline of the dominant class, timed live over the K timed steps
     roof = None
     if dom and dom in kprof and kprof[dom]["ms"] > 0:
-        k = kprof[dom]
-        peaks = {}
+        roof = roofline_entry(dom, kprof[dom], a.prec, "CUDA events on the library's stream around every launch "
+                                                        "of the class during the timed steps")
+        if roof:
+            roof["traffic"] = NCU_TRAFFIC.get(dom) if a.side == 96 and a.workload == "diffusion" else None
+            roof["launches_timed"] = roof.pop("launches")
+            roof["note"] = "algorithmic bytes (flops) per launch / CUDA-event launch time"
+    # every hot class and the preconditioner apply, from the untimed profiled step
+    top = sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:8]
+    rooflines = [e for e in (roofline_entry(n, v, a.prec, "untimed profiled step (CUDA events per launch)")
+                             for n, v in top) if e]
+    if "apply" in kern and all(e["kernel"] != "apply" for e in rooflines):
+        e = roofline_entry("apply", kern["apply"], a.prec, "untimed profiled step (one graph launch per apply)")
+        if e:
+            rooflines.append(e)
+    others = None
+    if rank == 0 and not a.no_others and a.workload == "diffusion" and a.side == 96:
+        others = other_configs(a)
+    cpu_all = None
+    if rank == 0 and cpu is not None and not a.no_cpu_baseline:
         try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except Exception:
-            pass
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        per_launch_ms = k["ms"] / k["launches"]
-        achieved = k["bytes"] / k["launches"] / (per_launch_ms * 1e-3) / 1e9
-        # DRAM bytes per launch measured by ncu for the same workload (profiles/k_tn_diffusion48_fp32.md);
-        # null for a kernel class without a capture of its current code
-        traffic = NCU_TRAFFIC.get(dom) if a.side == 96 and a.workload == "diffusion" else None
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "launches_timed": k["launches"],
-                "avg_launch_us": per_launch_ms * 1e3,
-                "note": "algorithmic bytes per launch / CUDA-event launch time, peak of measured"}
+            cpu_all = cpu_baseline(a.side, a.tol, a.rtol, workload=a.workload, n_full=p.n, threads=os.cpu_count())
+        except Exception as e:
+            cpu_all = {"value": None, "sample": f"failed: {e}"[:300]}
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "tf32": "tf32", "fp32": "f32"}.get(a.prec, "f64"), "data": "synthetic",
-        "config": {"workload": _workload_name(a.side, a.tol, a.workload), "form": FORMS.get(a.prec, a.prec),
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "l2": "L2 flushed (256 MB write) before each step; factor storage larger than L2"},
+        "config": {"workload": _workload_name(a.side, a.tol, a.workload)},
+        "form": FORMS.get(a.prec, a.prec), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+        "l2": "L2 flushed (256 MB write) before each step; factor storage larger than L2",
         "iters": iters[-1], "relres": rrs[-1], "true_relres_check": res,
         "factor_s": st["factor_seconds"], "solve_s": st["solve_seconds"],
         "factor_tflops": st["factor_flops"] / st["factor_seconds"] / 1e12, "factor_gflop": st["factor_flops"] / 1e9,
         "factor_bytes": st["factor_bytes"], "analyze_s": t_an, "restarts": st["restarts"],
         "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "fp32_form": fp32,
-        "fixed_rank_form": fixed, "roofline": roof,
+        "fixed_rank_form": fixed, "roofline": roof, "rooflines": rooflines,
         "kernel_profile_untimed": prof_all,
-        "cpu_baseline": cpu, "clocks": clk,
+        "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "clocks": clk, "other_configs": others,
         "step_wall_s": sum(walls) / len(walls),
         "e2e": {"value": t_e2e, "unit": "s", "factor_wall_s": t_f, "solve_wall_s": t_e2e - t_f,
                 "h2d_bytes_per_step": int(8 * (p.nnz + p.n)),

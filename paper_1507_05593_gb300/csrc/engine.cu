@@ -1472,7 +1472,7 @@ struct EngineT final : EngineImpl {
     static size_t hs_smem(int c, int cw) { return (size_t)(c + HS_ZROWS) * cw * sizeof(T); }
     // dynamic shared memory of k_leaf_factor for an sz-column leaf (block + FP64 tile)
     static constexpr size_t LEAF_SMEM_CAP = 220 * 1024;
-    static size_t leaf_smem(int sz) { return ((size_t)sizeof(T) * sz * (sz + 1) + 15) / 16 * 16 + 64 * 65 * 8; }
+    static size_t leaf_smem(int sz) { return ((size_t)sizeof(T) * sz * leaf_ld(sz) + 15) / 16 * 16 + LP * LEAF_DT * 8; }
     template <int CW> static void hs_attr() {
         CK(cudaFuncSetAttribute(k_hsolve<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 256));
     }
@@ -2088,6 +2088,7 @@ struct EngineT final : EngineImpl {
                 for (int depth = 0;; ++depth) {
                     std::vector<GemmTask> gt;
                     bool any = false;
+                    double gfl = 0, gby = 0;
                     for (int j : leaves) {
                         NodeRT& n = nd[j];
                         const BlockTree& t = S.tree[j];
@@ -2109,10 +2110,12 @@ struct EngineT final : EngineImpl {
                                 gt.push_back(g);
                             }
                         flops += (double)sz * (sz + 1) * n.brank[p];
+                        gfl += (double)sz * (sz + 1) * n.brank[p];
+                        gby += sizeof(T) * ((double)sz * n.brank[p] + (double)sz * (sz + 1));
                     }
                     if (!any) break;
                     GemmTask* dg = (GemmTask*)upload_tmp(sT2, gt);
-                    PROF(prof, "leaf_gemm", stream, 0, 0, k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg));
+                    PROF(prof, "leaf_gemm", stream, gfl, gby, k_gemm_tile<T><<<(int)gt.size(), 256, 0, stream>>>(dg));
                     launches++;
                     LAUNCH_CHECK();
                 }
@@ -2130,11 +2133,14 @@ struct EngineT final : EngineImpl {
                     lsm = std::max(lsm, need);
                 }
                 if (fused) {
-                    double fl = 0;
-                    for (auto& x : lt) fl += (double)x.nb * x.nb * x.nb / 3.0;
+                    double fl = 0, by = 0;
+                    for (auto& x : lt) {
+                        fl += (double)x.nb * x.nb * x.nb / 3.0;
+                        by += sizeof(T) * (double)x.nb * (x.nb + 1);   // lower triangle read and written
+                    }
                     flops += fl;
                     PotrfTask* dl = (PotrfTask*)upload_tmp(sTask, lt);
-                    PROF(prof, "leaf_factor", stream, fl, 0,
+                    PROF(prof, "leaf_factor", stream, fl, by,
                          k_leaf_factor<T><<<(int)lt.size(), 256, lsm, stream>>>(dl, d_status));
                     launches++;
                     LAUNCH_CHECK();

@@ -143,85 +143,134 @@ __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict_
 
 // ------------------------------------------------------------------ whole leaf block in one CTA
 // Cholesky of one sz x sz diagonal leaf (Alg. 6's leaf blocks, sz <= LEAF_FUSED_MAX) held in
-// shared memory: per 64-column panel, the diagonal tile in FP64 (as k_potrf_tile: pivot
-// 1/sqrt by rsqrt_newton, column scaled by multiplication, trailing tile update warps over
-// columns), then the rows below by a column sweep X <- X L^-T (one barrier per column) and the
-// trailing update of the rest of the leaf, both in the storage precision T.  Replaces the
-// POTRF / TRSM / GEMM launch chain of a leaf by one launch.  S: column-major, ld sz + 1.
+// shared memory, by 32-column panels:
+//  * the 32 x 32 diagonal tile in FP64 by four warps, one per SM sub-partition, so that the
+//    FP64 units of all four take part: per pivot every lane forms 1/sqrt by rsqrt_newton, holds
+//    l(i, k) of its row, and warp w updates the tile columns j = k + 1 + w (mod 4) with l(j, k)
+//    taken from lane j by a shuffle; a 128-thread barrier separates the pivots;
+//  * the rows below, X <- X L_D^{-T}, one thread per row by forward substitution (the tile
+//    is read by broadcast from shared memory);
+//  * the trailing update of the rest of the leaf in 4 x 4 register blocks with 16-byte loads;
+// the last two in the storage precision T.  S: column-major, ld L = a multiple of 4 above sz.
 constexpr int LEAF_FUSED_MAX = 192;
+constexpr int LP = 32;   // panel width of the leaf factorization
+__host__ __device__ constexpr int leaf_ld(int sz) { return (sz + 4) / 4 * 4; }
+constexpr int LEAF_DT = LP + 1;          // column stride of the FP64 tile
+
 template <class T>
-__device__ void leaf_tile_chol(double* D, int nb, int* status, int node, double* rp) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void leaf_tile_chol4(T* S, int L, int t0, int nb, double* D, T* dinv, int* status,
+                                                int node) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // w < 4
     for (int k = 0; k < nb; ++k) {
-        if (threadIdx.x == 0) {
-            double d = D[k + k * 65];
-            if (!(d > 0.0)) {            // indefinite or NaN pivot: record, keep values finite
-                atomicCAS(status, 0, node + 1);
-                d = 1.0;
-            }
-            const double y = rsqrt_newton<sizeof(T) == 8 ? 2 : 1>(d);
-            D[k + k * 65] = d * y;
-            *rp = y;
+        double piv = D[k * LEAF_DT + k];
+        if (!(piv > 0.0)) {          // indefinite or NaN pivot: record, keep values finite
+            if (threadIdx.x == 0) atomicCAS(status, 0, node + 1);
+            piv = 1.0;
         }
-        __syncthreads();
-        const double ri = *rp;
-        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) D[i + k * 65] *= ri;
-        __syncthreads();
-        for (int j = k + 1 + warp; j < nb; j += 8) {
-            const double ljk = D[j + k * 65];
-            for (int i = j + lane; i < nb; i += 32) D[i + j * 65] = fma(-D[i + k * 65], ljk, D[i + j * 65]);
+        const double y = rsqrt_newton<sizeof(T) == 8 ? 2 : 1>(piv);
+        const double lik = (lane > k && lane < nb) ? D[k * LEAF_DT + lane] * y : 0.0;
+        for (int j = k + 1 + w; j < nb; j += 4) {
+            const double ljk = __shfl_sync(0xffffffffu, lik, j);
+            if (lane >= j && lane < nb) D[j * LEAF_DT + lane] = fma(-lik, ljk, D[j * LEAF_DT + lane]);
         }
-        __syncthreads();
+        if (w == 0) {
+            if (lane == k) { S[t0 + k + (size_t)(t0 + k) * L] = (T)(piv * y); dinv[k] = (T)y; }
+            else if (lane > k && lane < nb) S[t0 + lane + (size_t)(t0 + k) * L] = (T)lik;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
     }
 }
 
 template <class T>
 __global__ void __launch_bounds__(256) k_leaf_factor(const PotrfTask* __restrict__ tasks, int* status) {
     extern __shared__ __align__(16) unsigned char lf_smem[];
-    __shared__ double rp;
-    __shared__ T dinv[NB];
+    __shared__ T dinv[LP];
     const PotrfTask tk = tasks[blockIdx.x];
     T* a = (T*)tk.a;
-    const int sz = tk.nb, ld = tk.ld, L = sz + 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sz = tk.nb, ld = tk.ld, L = leaf_ld(sz);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     T* S = (T*)lf_smem;
-    double* D = (double*)(lf_smem + (((size_t)sizeof(T) * sz * L + 15) / 16) * 16);   // 64 x 65 FP64 tile
+    double* D = (double*)(lf_smem + ((size_t)sizeof(T) * sz * L + 15) / 16 * 16);   // 32 x 33 FP64 tile
     for (int j = warp; j < sz; j += 8)
         for (int i = j + lane; i < sz; i += 32) S[i + j * L] = a[i + (size_t)j * ld];
     __syncthreads();
-    for (int t0 = 0; t0 < sz; t0 += NB) {
-        const int nb = min(NB, sz - t0);
-        T* Sd = S + t0 + (size_t)t0 * L;                 // diagonal tile
-        for (int j = warp; j < nb; j += 8)
-            for (int i = j + lane; i < nb; i += 32) D[i + j * 65] = (double)Sd[i + j * L];
+    for (int t0 = 0; t0 < sz; t0 += LP) {
+        const int nb = min(LP, sz - t0);
+        for (int e = tid; e < LP * LP; e += blockDim.x) {
+            const int i = e & 31, j = e >> 5;
+            D[j * LEAF_DT + i] = (i < nb && j < nb && i >= j) ? (double)S[t0 + i + (size_t)(t0 + j) * L] : 0.0;
+        }
         __syncthreads();
-        leaf_tile_chol<T>(D, nb, status, tk.node, &rp);
-        for (int j = warp; j < nb; j += 8)
-            for (int i = j + lane; i < nb; i += 32) Sd[i + j * L] = (T)D[i + j * 65];
-        if (threadIdx.x < nb) dinv[threadIdx.x] = (T)(1.0 / D[threadIdx.x + threadIdx.x * 65]);
+        if (warp < 4) leaf_tile_chol4<T>(S, L, t0, nb, D, dinv, status, tk.node);
         __syncthreads();
         const int r0 = t0 + nb, m = sz - r0;             // rows below the tile
         if (m <= 0) break;
-        // rows r0.. of columns t0..t0+nb: X <- X L_D^{-T}, column by column
-        for (int c = 0; c < nb; ++c) {
-            const T dc = dinv[c];
-            for (int i = threadIdx.x; i < m; i += blockDim.x) S[r0 + i + (size_t)(t0 + c) * L] *= dc;
-            __syncthreads();
-            for (int l = c + 1 + warp; l < nb; l += 8) {
-                const T llc = Sd[l + c * L];
-                for (int i = lane; i < m; i += 32)
-                    S[r0 + i + (size_t)(t0 + l) * L] -= S[r0 + i + (size_t)(t0 + c) * L] * llc;
+        // X <- X L_D^{-T}: row i of X solves x L_D^T = b by forward substitution
+        const T* Ld = S + t0 + (size_t)t0 * L;
+        for (int i = tid; i < m; i += blockDim.x) {
+            T* row = S + r0 + i + (size_t)t0 * L;
+            T x[LP];
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+                if (c >= nb) break;
+                T sacc = row[(size_t)c * L];
+#pragma unroll
+                for (int l = 0; l < c; ++l) sacc = fma(-x[l], Ld[c + (size_t)l * L], sacc);
+                x[c] = sacc * dinv[c];
             }
-            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < LP; ++c) {
+                if (c >= nb) break;
+                row[(size_t)c * L] = x[c];
+            }
         }
-        // trailing update: S[i][j] -= sum_c S[i][t0 + c] S[j][t0 + c] for r0 <= j <= i < sz
-        for (int j = r0 + warp; j < sz; j += 8)
-            for (int i = j + lane; i < sz; i += 32) {
-                T acc = T(0);
-#pragma unroll 8
-                for (int c = 0; c < nb; ++c) acc = fma(S[i + (size_t)(t0 + c) * L], S[j + (size_t)(t0 + c) * L], acc);
-                S[i + (size_t)j * L] -= acc;
+        __syncthreads();
+        // trailing update: S[i][j] -= sum_c X[i][c] X[j][c] for r0 <= j <= i < sz, 4 x 4 blocks
+        // (r0 and L are multiples of 4: a block's four rows of a column are one 16-byte load;
+        // rows past sz read the column's padding and are never written)
+        const int mb = (m + 3) >> 2;                     // 4-row blocks
+        const int nblk = mb * (mb + 1) / 2;              // lower-triangular block pairs (bi >= bj)
+        for (int e = tid; e < nblk; e += blockDim.x) {
+            int bi = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while ((bi + 1) * (bi + 2) / 2 <= e) ++bi;
+            while (bi * (bi + 1) / 2 > e) --bi;
+            const int bj = e - bi * (bi + 1) / 2;
+            const int i0 = r0 + 4 * bi, j0 = r0 + 4 * bj;
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+            for (int c = 0; c < nb; ++c) {
+                const T* col = S + (size_t)(t0 + c) * L;
+                T xi[4], xj[4];
+                if (sizeof(T) == 4) {
+                    const float4 fi = *reinterpret_cast<const float4*>(col + i0);
+                    const float4 fj = *reinterpret_cast<const float4*>(col + j0);
+                    xi[0] = fi.x; xi[1] = fi.y; xi[2] = fi.z; xi[3] = fi.w;
+                    xj[0] = fj.x; xj[1] = fj.y; xj[2] = fj.z; xj[3] = fj.w;
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const double2 fi = *reinterpret_cast<const double2*>(col + i0 + 2 * h);
+                        const double2 fj = *reinterpret_cast<const double2*>(col + j0 + 2 * h);
+                        xi[2 * h] = fi.x; xi[2 * h + 1] = fi.y;
+                        xj[2 * h] = fj.x; xj[2 * h + 1] = fj.y;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(xi[u], xj[v], acc[u][v]);
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int i = i0 + u, j = j0 + v;
+                    if (i < sz && j <= i) S[i + (size_t)j * L] -= acc[u][v];
+                }
+        }
         __syncthreads();
     }
     for (int j = warp; j < sz; j += 8)
@@ -571,21 +620,23 @@ __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
 
 // ------------------------------------------------------------------ staged TN product (factorization)
 // Z[t, :] = beta Z[t, :] + alpha sum_i A[arow_i, t] Y[yrow_i, :] for one 64-column tile of A
-// (t0 .. t0 + 63) and all N <= 64 columns of Y in one CTA, so every element of A is read
-// from memory once.  Rows stream through shared memory in chunks of 32 with cp.async double
+// (t0 .. t0 + 63) and up to 64 columns of Y in one CTA, so every element of A is read from
+// memory once.  Rows stream through shared memory in chunks of 32 with cp.async double
 // buffering: the A chunk is read down its columns (a warp reads 32 consecutive rows of one
-// column, 128 contiguous bytes for FP32), the Y chunk row by row (the gathered rows are
-// contiguous N-vectors, copied 16 bytes at a time when aligned).  Thread (tg, cg) owns TT
-// columns of A and 4 columns of Y (NP = N padded to 16, 32 or 64; TT = NP / 16) and
-// accumulates over the chunk's rows from shared memory, so no cross-thread reduction is
-// needed.  With tk.nsplit > 1 CTA z takes rows [z rps, (z + 1) rps) and writes its partial
-// sums to part[z][64][N]; the last CTA to arrive (counter cnt[0]) adds them in ascending z
+// column, 128 contiguous bytes for FP32) into As[t][r], the Y chunk row by row (the gathered
+// rows are contiguous N-vectors, copied 16 bytes at a time when aligned) into Ys[r][c].
+// Thread (tg, cg) owns TT columns of A and 4 columns of Y (NP = N padded to 16, 32 or 64;
+// TT = NP / 16) and accumulates over the chunk's rows from shared memory, RV rows per step
+// (one 16-byte load of As per column and of Ys per row: 64 multiply-adds per 8 loads in
+// FP32), so no cross-thread reduction is needed; rows past the chunk's end are zero-filled.
+// With tk.nsplit > 1 CTA z takes rows [z rps, (z + 1) rps) and writes its partial sums to
+// part[z][64][N]; the last CTA to arrive (counter cnt[y]) adds them in ascending z
 // (deterministic), writes Z and resets the counter.
 constexpr int TS_COLS = 64;
 constexpr int TS_ROWS = 32;
 template <class T>
 __host__ __device__ constexpr size_t ts_smem_bytes(int np) {
-    return sizeof(T) * ((size_t)2 * TS_COLS * (TS_ROWS + 1) + (size_t)2 * TS_ROWS * (np + 4));
+    return sizeof(T) * ((size_t)2 * TS_COLS * (TS_ROWS + 4) + (size_t)2 * TS_ROWS * (np + 4));
 }
 __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc) : "memory");
@@ -603,10 +654,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <class T, int NP>
 __global__ void __launch_bounds__(256) k_tn_s(const TnTask* __restrict__ tasks) {
     extern __shared__ __align__(16) unsigned char ts_smem[];
-    constexpr int AST = TS_ROWS + 1;       // As[t][r]: a column of the chunk per row of As
+    constexpr int AST = TS_ROWS + 4;       // As[t][r]: a column of the chunk per row of As (16-byte rows)
     constexpr int YST = NP + 4;            // Ys[r][c]: 16-byte aligned rows
     constexpr int CG = NP / 4;             // column groups of 4
     constexpr int TT = TS_COLS * CG / 256; // columns of A per thread
+    constexpr int RV = 16 / (int)sizeof(T);   // rows per step (one 16-byte load)
     T* As = (T*)ts_smem;
     T* Ys = As + 2 * TS_COLS * AST;
     __shared__ int last;
@@ -624,6 +676,7 @@ __global__ void __launch_bounds__(256) k_tn_s(const TnTask* __restrict__ tasks) 
     const bool yvec = (nc % VW) == 0 && (tk.ldy % VW) == 0 && (((uintptr_t)Y) & 15) == 0;
     auto issue = [&](int r0, int buf) {
         const int rc = min(TS_ROWS, re - r0);
+        const int rc4 = (rc + RV - 1) / RV * RV;
         T* as = As + buf * TS_COLS * AST;
         T* ys = Ys + buf * TS_ROWS * YST;
         for (int e = tid; e < TS_COLS * TS_ROWS; e += 256) {
@@ -634,8 +687,12 @@ __global__ void __launch_bounds__(256) k_tn_s(const TnTask* __restrict__ tasks) 
                 const T* src = A + (size_t)t * tk.lda + ar;
                 if (sizeof(T) == 8) cp_async8(as + t * AST + r, src);
                 else cp_async4(as + t * AST + r, src);
+            } else if (r >= rc && r < rc4) {
+                as[t * AST + r] = T(0);
             }
         }
+        if (rc4 > rc)
+            for (int e = tid; e < (rc4 - rc) * NP; e += 256) ys[(rc + e / NP) * YST + e % NP] = T(0);
         if (yvec) {
             const int per = nc / VW;
             for (int e = tid; e < TS_ROWS * per; e += 256) {
@@ -675,23 +732,35 @@ __global__ void __launch_bounds__(256) k_tn_s(const TnTask* __restrict__ tasks) 
         const int rc = min(TS_ROWS, re - rb - ci * TS_ROWS);
         const T* as = As + buf * TS_COLS * AST + (tg * TT) * AST;
         const T* ys = Ys + buf * TS_ROWS * YST + cg * 4;
-#pragma unroll 4
-        for (int r = 0; r < rc; ++r) {
-            T yv[4];
-            if (sizeof(T) == 4) {
-                const float4 f = *reinterpret_cast<const float4*>(ys + r * YST);
-                yv[0] = f.x; yv[1] = f.y; yv[2] = f.z; yv[3] = f.w;
-            } else {
-                const double2 f0 = *reinterpret_cast<const double2*>(ys + r * YST);
-                const double2 f1 = *reinterpret_cast<const double2*>(ys + r * YST + 2);
-                yv[0] = f0.x; yv[1] = f0.y; yv[2] = f1.x; yv[3] = f1.y;
+        for (int r = 0; r < rc; r += RV) {
+            T yv[RV][4], av[TT][RV];
+#pragma unroll
+            for (int h = 0; h < RV; ++h) {
+                if (sizeof(T) == 4) {
+                    const float4 f = *reinterpret_cast<const float4*>(ys + (r + h) * YST);
+                    yv[h][0] = f.x; yv[h][1] = f.y; yv[h][2] = f.z; yv[h][3] = f.w;
+                } else {
+                    const double2 f0 = *reinterpret_cast<const double2*>(ys + (r + h) * YST);
+                    const double2 f1 = *reinterpret_cast<const double2*>(ys + (r + h) * YST + 2);
+                    yv[h][0] = f0.x; yv[h][1] = f0.y; yv[h][2] = f1.x; yv[h][3] = f1.y;
+                }
             }
 #pragma unroll
             for (int u = 0; u < TT; ++u) {
-                const T a = as[u * AST + r];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[u][q] = fma(a, yv[q], acc[u][q]);
+                if (sizeof(T) == 4) {
+                    const float4 f = *reinterpret_cast<const float4*>(as + u * AST + r);
+                    av[u][0] = f.x; av[u][1] = f.y; av[u][2] = f.z; av[u][3] = f.w;
+                } else {
+                    const double2 f = *reinterpret_cast<const double2*>(as + u * AST + r);
+                    av[u][0] = f.x; av[u][1] = f.y;
+                }
             }
+#pragma unroll
+            for (int h = 0; h < RV; ++h)
+#pragma unroll
+                for (int u = 0; u < TT; ++u)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[u][q] = fma(av[u][h], yv[h][q], acc[u][q]);
         }
         __syncthreads();
     }
