@@ -256,6 +256,16 @@ rsc_status rsc_profile(rsc_handle* h, int32_t enable, const char* kernels);
  * the last rsc_profile call (algorithmic flops and bytes).  json[len] host buffer. */
 rsc_status rsc_get_kernel_profile(rsc_handle* h, char* json, int64_t len);
 
+/* Kernel-variant tuning of the BF16 / TF32 forms (the paper has no counterpart): the thin
+ * products of the implicit sampling (Alg. 2, Alg. 5 and their transposes) have a SIMT kernel
+ * and a tcgen05 tensor-core kernel with different tiles.  During a handle's first rsc_factor
+ * in those forms the launches alternate between the two, timed with CUDA events, per (product
+ * class, sample-column width, log2 of the launch's flops); later factorizations use the faster
+ * one per key.  json[len] receives {key: {choice (0 SIMT, 1 tensor cores), simt_ns_per_mflop,
+ * tensor_ns_per_mflop, launches: [simt, tensor]}}; {} before the first factorization.
+ * Errors: RSC_ERR_INVALID_ARG (NULL, or len too small). */
+rsc_status rsc_get_autotune(const rsc_handle* h, char* json, int64_t len);
+
 /* Message of the last error on h (or of the last failed rsc_analyze if h is NULL). */
 const char* rsc_last_error(const rsc_handle* h);
 

@@ -72,6 +72,7 @@ _SIGS = {
     "rsc_get_stats": (C.c_int, [_P, C.POINTER(rsc_stats_t)]),
     "rsc_profile": (C.c_int, [_P, C.c_int32, C.c_char_p]),
     "rsc_get_kernel_profile": (C.c_int, [_P, C.c_char_p, C.c_int64]),
+    "rsc_get_autotune": (C.c_int, [_P, C.c_char_p, C.c_int64]),
     "rsc_last_error": (C.c_char_p, [_P]),
     "rsc_destroy": (None, [_P]),
 }
@@ -286,6 +287,14 @@ def rsc_get_kernel_profile(h: Handle) -> dict:
     import json
     buf = C.create_string_buffer(1 << 16)
     _check(lib().rsc_get_kernel_profile(h.ptr, buf, len(buf)), h.ptr)
+    return json.loads(buf.value.decode())
+
+
+def rsc_get_autotune(h: Handle) -> dict:
+    """The kernel-variant choices of the BF16 / TF32 forms (see include/rsc.h)."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().rsc_get_autotune(h.ptr, buf, len(buf)), h.ptr)
     return json.loads(buf.value.decode())
 
 

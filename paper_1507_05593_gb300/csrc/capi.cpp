@@ -302,6 +302,17 @@ rsc_status rsc_get_kernel_profile(rsc_handle* h, char* json, int64_t len) {
     });
 }
 
+rsc_status rsc_get_autotune(const rsc_handle* h, char* json, int64_t len) {
+    rsc_handle* hh = const_cast<rsc_handle*>(h);
+    if (!h || !json || len <= 0) return fail(hh, RSC_ERR_INVALID_ARG, "NULL argument");
+    return guarded(hh, [&]() -> rsc_status {
+        std::string s = h->eng ? h->eng->tuning_json() : std::string("{}");
+        if ((int64_t)s.size() + 1 > len) return fail(hh, RSC_ERR_INVALID_ARG, "buffer too small");
+        std::memcpy(json, s.c_str(), s.size() + 1);
+        return RSC_OK;
+    });
+}
+
 const char* rsc_last_error(const rsc_handle* h) {
     if (h) return h->err.c_str();
     return g_last_error.c_str();

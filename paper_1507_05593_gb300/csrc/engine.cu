@@ -32,6 +32,7 @@
 #include "kernels.cuh"
 #include "tcgen05.cuh"
 #include "rfpass.cuh"
+#include "tcprod.cuh"
 
 namespace rsc {
 
@@ -211,8 +212,105 @@ struct Profiler {
         }                                                                      \
     } while (0)
 
+// ------------------------------------------------------------------ kernel-variant tuner
+// Autotuning of the thin products' kernel (SIMT or tensor cores, which differ in tile shape:
+// 64 or 128 columns of A per CTA, 16 or 64 sample columns per CTA) per (class, padded sample
+// width, log2 of the launch's flops).  During a handle's first factorization in a form that has
+// both kernels, the launches of each key alternate between the variants and are timed with CUDA
+// events; after that factorization every key takes the variant with the smaller time per flop
+// (keys seen with one variant only, or never, take the default).  Every launch runs exactly one
+// variant, so the tuned factorization computes the same factor as any other.
+struct Tuner {
+    bool tuning = false;
+    struct Stat { double sec[2] = {0, 0}, flops[2] = {0, 0}; int n[2] = {0, 0}; int choice = -1; };
+    std::map<std::string, Stat> tab;
+    struct Pend { std::string key; int var; double flops; cudaEvent_t a, b; };
+    std::vector<Pend> pend;
+    std::vector<cudaEvent_t> pool;
+    ~Tuner() {
+        for (auto& p : pend) { pool.push_back(p.a); pool.push_back(p.b); }
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+    static std::string key(const char* cls, int np, double flops) {
+        const int b = flops > 1.0 ? (int)std::floor(std::log2(flops)) : 0;
+        return std::string(cls) + "/n" + std::to_string(np) + "/2^" + std::to_string(b);
+    }
+    int pick(const std::string& k, int dflt) {
+        if (tuning) {
+            const Stat& st = tab[k];
+            return st.n[1] < st.n[0] ? 1 : 0;
+        }
+        auto it = tab.find(k);
+        return (it != tab.end() && it->second.choice >= 0) ? it->second.choice : dflt;
+    }
+    cudaEvent_t ev() {
+        if (pool.empty()) { cudaEvent_t e; CK(cudaEventCreate(&e)); return e; }
+        cudaEvent_t e = pool.back(); pool.pop_back(); return e;
+    }
+    struct Timed {   // events around one launch while tuning (empty key: not a tuned launch)
+        Tuner& t; bool on; cudaStream_t s; Pend p{};
+        Timed(Tuner& t_, const std::string& k, int var, double fl, cudaStream_t s_)
+            : t(t_), on(t_.tuning && !k.empty()), s(s_) {
+            if (!on) return;
+            p.key = k; p.var = var; p.flops = fl; p.a = t.ev(); p.b = t.ev();
+            t.tab[k].n[var]++;
+            CK(cudaEventRecord(p.a, s));
+        }
+        ~Timed() {
+            if (!on) return;
+            if (cudaEventRecord(p.b, s) == cudaSuccess) t.pend.push_back(p);
+        }
+    };
+    // after the tuning factorization (stream idle): collect the times, choose per key
+    void finish() {
+        for (auto& p : pend) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                Stat& st = tab[p.key];
+                st.sec[p.var] += ms * 1e-3;
+                st.flops[p.var] += p.flops;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pend.clear();
+        for (auto& kv : tab) {
+            Stat& st = kv.second;
+            if (st.flops[0] > 0 && st.flops[1] > 0)
+                st.choice = st.sec[1] / st.flops[1] < st.sec[0] / st.flops[0] ? 1 : 0;
+        }
+        tuning = false;
+    }
+    // a factorization that failed: drop its timings (tuning resumes with the next one)
+    void abandon() {
+        for (auto& p : pend) { pool.push_back(p.a); pool.push_back(p.b); }
+        pend.clear();
+        for (auto& kv : tab) kv.second.n[0] = kv.second.n[1] = 0;
+        tuning = false;
+    }
+    std::string json() const {
+        std::string out = "{";
+        char buf[320];
+        bool first = true;
+        for (auto& kv : tab) {
+            const Stat& st = kv.second;
+            std::snprintf(buf, sizeof(buf),
+                          "%s\"%s\": {\"choice\": %d, \"simt_ns_per_mflop\": %.3f, \"tensor_ns_per_mflop\": %.3f, "
+                          "\"launches\": [%d, %d]}",
+                          first ? "" : ", ", kv.first.c_str(), st.choice,
+                          st.flops[0] > 0 ? st.sec[0] / st.flops[0] * 1e15 : -1.0,
+                          st.flops[1] > 0 ? st.sec[1] / st.flops[1] * 1e15 : -1.0, st.n[0], st.n[1]);
+            out += buf;
+            first = false;
+        }
+        return out + "}";
+    }
+};
+
 // ------------------------------------------------------------------ engine base
 struct EngineImpl {
+    Tuner tuner;
+    bool tuned_once = false;
     Profiler prof;
     virtual ~EngineImpl() = default;
     virtual rsc_status factor(const double* val, double tol, const FixedRank* fr) = 0;
@@ -740,6 +838,7 @@ struct EngineT final : EngineImpl {
         if (tc) {
             CK(cudaFuncSetAttribute(k_push_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM));
             CK(cudaFuncSetAttribute(k_push_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PAD_SMEM_TF32));
+            if (tc_tf32) tc_attrs<true>(); else tc_attrs<false>();
         }
         CK(cudaFuncSetAttribute(k_leaf_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM_CAP));
         CK(cudaFuncSetAttribute(k_tn_s<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_bytes<T>(16)));
@@ -1274,9 +1373,13 @@ struct EngineT final : EngineImpl {
         t.Z = Z; t.ldz = ldz; t.row0 = 0; t.Y = Y; t.ldy = ldy; t.N = N; t.alpha = alpha; t.atomic = atomic ? 1 : 0;
         return t;
     }
+    // columns of A per launched TN task: 128 for the tensor-core kernel, 64 for the SIMT one (the
+    // stage keeps whole tasks; run() cuts them for the kernel variant it launches)
+    int cur_tn_cols = TS_COLS;
+    int tn_cols() const { return cur_tn_cols; }
     void add_tn(Stage& s, const TnTask& t) {
         if (t.K == 0 || t.nrow == 0 || t.N == 0) return;
-        for (int t0 = 0; t0 < t.K; t0 += TS_COLS) { TnTask c = t; c.t0 = t0; s.tn.push_back(c); }
+        s.tn.push_back(t);
         flops += 2.0 * t.nrow * t.K * t.N;
     }
     void add_nn(Stage& s, const NnTask& t) {
@@ -1298,14 +1401,14 @@ struct EngineT final : EngineImpl {
     }
     static Stage& next(Program& P) { P.emplace_back(); return P.back(); }
 
-    static double task_flops(const TnTask& t) { return 2.0 * t.nrow * std::min(TS_COLS, t.K - t.t0) * t.N; }
+    double task_flops(const TnTask& t) const { return 2.0 * t.nrow * std::min(tn_cols(), t.K - t.t0) * t.N; }
     static double task_flops(const NnTask& t) { return 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K * t.N; }
     static double task_flops(const TrsvTask& t) { return (double)t.c * t.c * t.N; }
     template <class X> static double task_flops(const X&) { return 0.0; }
     // algorithmic bytes of a TN product: A's rows once, Y's gathered rows once per task (counted
     // with its first 64-column tile), Z written once (and read when beta != 0)
-    static double task_bytes(const TnTask& t) {
-        const double cols = std::min(TS_COLS, t.K - t.t0);
+    double task_bytes(const TnTask& t) const {
+        const double cols = std::min(tn_cols(), t.K - t.t0);
         return sizeof(T) * (t.nrow * cols + (t.t0 == 0 ? t.nrow * (double)t.N : 0.0) +
                             cols * t.N * (t.beta != 0.0 ? 2.0 : 1.0));
     }
@@ -1324,6 +1427,37 @@ struct EngineT final : EngineImpl {
         PROF(prof, name, stream, fl, by, launch(d, (int)all.size(), ychunks));
         launches++;
         LAUNCH_CHECK();
+    }
+
+    // tensor-core thin products of the BF16 / TF32 forms (FP32 storage only)
+    template <bool TF> static void tn_tc_np(const TnTask* d, dim3 g, int np, cudaStream_t s, int* err) {
+        if (np == 16) k_tn_tc<TF, 16><<<g, 128, tp_smem_bytes<TF>(16), s>>>(d, err);
+        else if (np == 32) k_tn_tc<TF, 32><<<g, 128, tp_smem_bytes<TF>(32), s>>>(d, err);
+        else k_tn_tc<TF, 64><<<g, 128, tp_smem_bytes<TF>(64), s>>>(d, err);
+    }
+    template <bool TF> static void nn_tc_np(const NnTask* d, dim3 g, int np, cudaStream_t s, int* err) {
+        if (np == 16) k_nn_tc<TF, 16><<<g, 128, tp_smem_bytes<TF>(16), s>>>(d, err);
+        else if (np == 32) k_nn_tc<TF, 32><<<g, 128, tp_smem_bytes<TF>(32), s>>>(d, err);
+        else k_nn_tc<TF, 64><<<g, 128, tp_smem_bytes<TF>(64), s>>>(d, err);
+    }
+    void launch_tn_tc(const TnTask* d, dim3 g, int np, cudaStream_t s) {
+        if (tc_tf32) tn_tc_np<true>(d, g, np, s, d_status + 1);
+        else tn_tc_np<false>(d, g, np, s, d_status + 1);
+    }
+    void launch_nn_tc(const NnTask* d, dim3 g, int np, cudaStream_t s) {
+        if (tc_tf32) nn_tc_np<true>(d, g, np, s, d_status + 1);
+        else nn_tc_np<false>(d, g, np, s, d_status + 1);
+    }
+    template <bool TF> static void tc_attrs() {
+        for (int np : {16, 32, 64}) {
+            const int b = tp_smem_bytes<TF>(np);
+            if (np == 16) { CK(cudaFuncSetAttribute(k_tn_tc<TF, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+                            CK(cudaFuncSetAttribute(k_nn_tc<TF, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)); }
+            if (np == 32) { CK(cudaFuncSetAttribute(k_tn_tc<TF, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+                            CK(cudaFuncSetAttribute(k_nn_tc<TF, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)); }
+            if (np == 64) { CK(cudaFuncSetAttribute(k_tn_tc<TF, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+                            CK(cudaFuncSetAttribute(k_nn_tc<TF, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)); }
+        }
     }
 
     void run(std::vector<Program>& progs) {
@@ -1346,7 +1480,17 @@ struct EngineT final : EngineImpl {
                 st.tn.insert(st.tn.end(), s.tn.begin(), s.tn.end());
                 st.nn.insert(st.nn.end(), s.nn.begin(), s.nn.end());
             }
-            for (auto& t : st.nn) yn_nn = std::max(yn_nn, cdiv(t.N, 16));
+            int np_nn = 16;
+            double fl_nn = 0;
+            for (auto& t : st.nn) {
+                np_nn = std::max(np_nn, std::min(t.N, 64) <= 16 ? 16 : std::min(t.N, 64) <= 32 ? 32 : 64);
+                fl_nn += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * (double)t.K * t.N;
+            }
+            // kernel variants of the thin products (BF16 / TF32 forms: SIMT or tensor cores), chosen
+            // per (class, sample-column width, size) by the tuner
+            const std::string knn = Tuner::key("nn", np_nn, fl_nn);
+            const int vnn = (tc && !st.nn.empty()) ? tuner.pick(knn, 1) : 0;
+            for (auto& t : st.nn) yn_nn = std::max(yn_nn, cdiv(t.N, vnn ? 64 : 16));
             for (auto& t : st.csr) yn_csr = std::max(yn_csr, cdiv(t.N, 16));
             for (auto& t : st.trsv) yn_tr = std::max(yn_tr, cdiv(t.N, TRSV_CW));
             const unsigned long long seed = o.seed;
@@ -1362,28 +1506,48 @@ struct EngineT final : EngineImpl {
             launch_kind("trsv", st.trsv, yn_tr,
                         [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
             int zs_tn = 1, yc_tn = 1, np_tn = 16;
+            double fl_tn = 0;
+            for (auto& t : st.tn) {
+                np_tn = std::max(np_tn, std::min(t.N, 64) <= 16 ? 16 : std::min(t.N, 64) <= 32 ? 32 : 64);
+                fl_tn += 2.0 * t.nrow * (double)t.K * t.N;
+            }
+            const std::string ktn = Tuner::key("tn", np_tn, fl_tn);
+            const int vtn = (tc && !st.tn.empty()) ? tuner.pick(ktn, 0) : 0;
+            cur_tn_cols = vtn ? TP_M : TS_COLS;
+            {   // whole tasks -> column tiles of the chosen kernel
+                std::vector<TnTask> cut;
+                cut.reserve(st.tn.size() * 2);
+                for (const TnTask& t : st.tn)
+                    for (int t0 = 0; t0 < t.K; t0 += cur_tn_cols) { TnTask c = t; c.t0 = t0; cut.push_back(c); }
+                st.tn.swap(cut);
+            }
             {   // long row ranges: split the rows over CTAs (deterministic fixed-order reduction)
                 int coff = 0;
                 for (auto& t : st.tn) {
                     const int ych = cdiv(t.N, 64);
                     yc_tn = std::max(yc_tn, ych);
-                    np_tn = std::max(np_tn, std::min(t.N, 64) <= 16 ? 16 : std::min(t.N, 64) <= 32 ? 32 : 64);
                     if (t.nrow < TN_SPLIT_MIN || coff + ych > TN_CNT_CAP) continue;
                     t.nsplit = std::min(cdiv(t.nrow, TN_SPLIT_ROWS), TN_SPLIT_MAX);
                     t.rps = cdiv(t.nrow, t.nsplit);
-                    t.part = wsT((size_t)t.nsplit * TS_COLS * t.N);
+                    t.part = wsT((size_t)t.nsplit * tn_cols() * t.N);
                     t.cnt = d_tncnt + coff;
                     coff += ych;
                     zs_tn = std::max(zs_tn, t.nsplit);
                 }
             }
-            launch_kind("tn", st.tn, yc_tn, [&](TnTask* d, int n, int y) {
+            launch_kind(vtn ? "tn_tc" : "tn", st.tn, yc_tn, [&](TnTask* d, int n, int y) {
                 const dim3 g((unsigned)n, (unsigned)y, (unsigned)zs_tn);
-                if (np_tn == 16) k_tn_s<T, 16><<<g, 256, ts_smem_bytes<T>(16), s>>>(d);
+                Tuner::Timed tt(tuner, tc ? ktn : std::string(), vtn, fl_tn, s);
+                if (vtn) launch_tn_tc(d, g, np_tn, s);
+                else if (np_tn == 16) k_tn_s<T, 16><<<g, 256, ts_smem_bytes<T>(16), s>>>(d);
                 else if (np_tn == 32) k_tn_s<T, 32><<<g, 256, ts_smem_bytes<T>(32), s>>>(d);
                 else k_tn_s<T, 64><<<g, 256, ts_smem_bytes<T>(64), s>>>(d);
             });
-            launch_kind("nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) { k_nn<T><<<dim3(n, y), NN_ROWS, 0, s>>>(d); });
+            launch_kind(vnn ? "nn_tc" : "nn", st.nn, yn_nn, [&](NnTask* d, int n, int y) {
+                Tuner::Timed tt(tuner, tc ? knn : std::string(), vnn, fl_nn, s);
+                if (vnn) launch_nn_tc(d, dim3((unsigned)n, (unsigned)y), np_nn, s);
+                else k_nn<T><<<dim3(n, y), NN_ROWS, 0, s>>>(d);
+            });
         }
         progs.clear();
     }
@@ -2334,6 +2498,8 @@ struct EngineT final : EngineImpl {
             if (!d_rfp_time) CK(cudaMalloc(&d_rfp_time, sizeof(unsigned long long) * 16));
             CK(cudaMemsetAsync(d_rfp_time, 0, sizeof(unsigned long long) * 16, stream));
         }
+        // the first factorization of a BF16 / TF32 handle tunes the thin products' kernel variants
+        tuner.tuning = tc && !tuned_once;
         // the timed region covers every attempt: a restart (Section 5.3) repeats the factorization
         CK(cudaEventRecord(e0, stream));
         for (;;) {
@@ -2344,6 +2510,7 @@ struct EngineT final : EngineImpl {
                 if (e.status != RSC_ERR_NOT_SPD || !diag_on) {
                     cudaEventDestroy(e0);
                     cudaEventDestroy(e1);
+                    tuner.abandon();
                     throw;
                 }
                 sync_stream();
@@ -2366,6 +2533,7 @@ struct EngineT final : EngineImpl {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         factor_seconds = ms * 1e-3;
+        if (tuner.tuning) { tuner.finish(); tuned_once = true; }
         prof.flush();
         if (prof.on && d_rfp_time) {
             unsigned long long tp[16];
@@ -3218,5 +3386,6 @@ void Engine::profile(int enable, const char* only) {
     impl_->prof.only = only ? only : "";
 }
 std::string Engine::profile_json() { return impl_->prof.json(); }
+std::string Engine::tuning_json() const { return impl_->tuner.json(); }
 
 }  // namespace rsc

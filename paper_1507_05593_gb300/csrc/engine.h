@@ -55,6 +55,7 @@ public:
     void stats(rsc_stats_t* out) const;
     void profile(int enable, const char* only);
     std::string profile_json();
+    std::string tuning_json() const;
 
 private:
     std::unique_ptr<EngineImpl> impl_;

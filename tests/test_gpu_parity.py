@@ -326,3 +326,30 @@ def test_diffusion96_full_size_properties():
         assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= 1e-8
         st = R.rsc_get_stats(h)
         assert st["n_compressed"] == 165 and st["factor_bytes"] > 0
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_autotuned_products_agree(prec):
+    """The first factorization of a BF16 / TF32 handle alternates the SIMT and tensor-core thin
+    products to time them; the second uses the faster one per key.  Both factorizations give the
+    oracle's ranks and blocks within the form's tolerance, and PCG reaches 1e-8."""
+    p = W.diffusion_grf(24, 2.0, 4.0, 0)
+    kw = dict(leaf_size=32, tau_O=64, tau_D=64)
+    h = _gpu(p, _opts(precision=prec, **kw), 0.01)
+    tab = R.rsc_get_autotune(h)
+    assert any(v["launches"][0] > 0 and v["launches"][1] > 0 for v in tab.values()), tab
+    assert all(v["choice"] in (-1, 0, 1) for v in tab.values())
+    an, f = _oracle(p, R.rsc_options_default(**kw), 0.01)
+    for rep in range(2):
+        if rep:
+            R.rsc_factor(h, 0.01)
+        for j in range(an.nsuper):
+            if f.sn[j].compressed:
+                assert R.rsc_get_supernode_info(h, j)["rank"] == f.sn[j].U.shape[1], (rep, j)
+            LD, LO = R.rsc_get_supernode_blocks(h, j)
+            LDo, LOo = _oracle_blocks(f, j)
+            assert np.abs(np.tril(LD) - np.tril(LDo)).max() <= MIXED_TOL[prec] * max(1, np.abs(LDo).max()), (rep, j)
+            if LOo.size:
+                assert np.abs(LO - LOo).max() <= MIXED_TOL[prec] * max(1, np.abs(LOo).max()), (rep, j)
+        x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
+        assert rr <= 1e-8
