@@ -157,6 +157,13 @@ rsc_status rsc_factor_fixed_rank(rsc_handle* h, double alpha_O, double alpha_D, 
  * rsc_factor uses them. */
 rsc_status rsc_refactor_values(rsc_handle* h, const double* val);
 
+/* As rsc_refactor_values with the values on the device: d_val[nnz] (FP64, the order of the CSR
+ * given to rsc_analyze), read on cuda_stream (a cudaStream_t, NULL = the handle's stream); the
+ * call returns after the library holds its own copy.  Until the next rsc_refactor_values the
+ * factorization and the SpMV of the solves use these values (no host copy is made).  Errors:
+ * RSC_ERR_INVALID_ARG (NULL, a non-finite value). */
+rsc_status rsc_refactor_values_device(rsc_handle* h, const double* d_val, void* cuda_stream);
+
 /*
  * PCG from x0 = 0 on the original (unpermuted) system, preconditioned by
  * M^{-1} = P (L L^T)^{-1} P^T, until ||r||/||b|| <= rtol (recursive residual,
@@ -255,6 +262,15 @@ rsc_status rsc_profile(rsc_handle* h, int32_t enable, const char* kernels);
 /* JSON object {class: {launches, ms, flops, bytes}} of the profiled launches since
  * the last rsc_profile call (algorithmic flops and bytes).  json[len] host buffer. */
 rsc_status rsc_get_kernel_profile(rsc_handle* h, char* json, int64_t len);
+
+/* Failure detection (the paper has no counterpart).  The cooperative kernel of the range finder
+ * (Alg. 3, one launch per sampling pass) separates its phases by grid barriers whose waits are
+ * bounded: after `polls` polls (about 64 ns apart) a waiting block gives up, the kernel records
+ * the expiry and returns, the following passes of that factorization do no work, and rsc_factor
+ * returns RSC_ERR_TIMEOUT; the handle stays usable (rsc_refactor_values, rsc_factor).
+ * polls = 0 restores the default (2^22 polls, about a quarter of a second).  Errors:
+ * RSC_ERR_INVALID_ARG (polls < 0). */
+rsc_status rsc_set_wait_limit(rsc_handle* h, int64_t polls);
 
 /* Kernel-variant tuning of the BF16 / TF32 forms (the paper has no counterpart): the thin
  * products of the implicit sampling (Alg. 2, Alg. 5 and their transposes) have a SIMT kernel

@@ -73,6 +73,8 @@ _SIGS = {
     "rsc_profile": (C.c_int, [_P, C.c_int32, C.c_char_p]),
     "rsc_get_kernel_profile": (C.c_int, [_P, C.c_char_p, C.c_int64]),
     "rsc_get_autotune": (C.c_int, [_P, C.c_char_p, C.c_int64]),
+    "rsc_set_wait_limit": (C.c_int, [_P, C.c_int64]),
+    "rsc_refactor_values_device": (C.c_int, [_P, _P, _P]),
     "rsc_last_error": (C.c_char_p, [_P]),
     "rsc_destroy": (None, [_P]),
 }
@@ -184,6 +186,13 @@ def rsc_refactor_values(h: Handle, val) -> None:
     _check(lib().rsc_refactor_values(h.ptr, _ptr(v)), h.ptr)
 
 
+def rsc_refactor_values_device(h: Handle, d_val, stream=None) -> None:
+    """d_val: CUDA float64 tensor of the nnz values (or a raw device pointer as an int)."""
+    pv = d_val.data_ptr() if hasattr(d_val, "data_ptr") else int(d_val)
+    s = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().rsc_refactor_values_device(h.ptr, C.c_void_p(pv), s), h.ptr)
+
+
 def rsc_solve(h: Handle, b, rtol: float = 1e-8, max_iter: int = 1000, raise_on_no_convergence: bool = True):
     """Returns (x, iters, final_relres)."""
     bb = np.ascontiguousarray(b, dtype=np.float64)
@@ -288,6 +297,10 @@ def rsc_get_kernel_profile(h: Handle) -> dict:
     buf = C.create_string_buffer(1 << 16)
     _check(lib().rsc_get_kernel_profile(h.ptr, buf, len(buf)), h.ptr)
     return json.loads(buf.value.decode())
+
+
+def rsc_set_wait_limit(h: Handle, polls: int) -> None:
+    _check(lib().rsc_set_wait_limit(h.ptr, int(polls)), h.ptr)
 
 
 def rsc_get_autotune(h: Handle) -> dict:

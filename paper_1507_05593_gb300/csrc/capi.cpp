@@ -155,6 +155,15 @@ rsc_status rsc_refactor_values(rsc_handle* h, const double* val) {
     return RSC_OK;
 }
 
+rsc_status rsc_refactor_values_device(rsc_handle* h, const double* d_val, void* stream) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    if (!d_val) return fail(h, RSC_ERR_INVALID_ARG, "d_val is NULL");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng) h->eng = new Engine(h->sym, h->opts);
+        return h->eng->values_device(d_val, (long long)h->val.size(), stream);
+    });
+}
+
 rsc_status rsc_solve(rsc_handle* h, const double* b, double* x, double rtol, int32_t max_iter, int32_t* iters,
                      double* final_relres) {
     if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
@@ -298,6 +307,16 @@ rsc_status rsc_get_kernel_profile(rsc_handle* h, char* json, int64_t len) {
         std::string s = h->eng ? h->eng->profile_json() : std::string("{}");
         if ((int64_t)s.size() + 1 > len) return fail(h, RSC_ERR_INVALID_ARG, "buffer too small");
         std::memcpy(json, s.c_str(), s.size() + 1);
+        return RSC_OK;
+    });
+}
+
+rsc_status rsc_set_wait_limit(rsc_handle* h, int64_t polls) {
+    if (!h) return fail(nullptr, RSC_ERR_INVALID_ARG, "NULL handle");
+    if (polls < 0) return fail(h, RSC_ERR_INVALID_ARG, "polls must be >= 0");
+    return guarded(h, [&]() -> rsc_status {
+        if (!h->eng) h->eng = new Engine(h->sym, h->opts);
+        h->eng->set_wait_limit(polls);
         return RSC_OK;
     });
 }

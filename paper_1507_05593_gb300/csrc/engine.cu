@@ -311,6 +311,15 @@ struct Tuner {
 struct EngineImpl {
     Tuner tuner;
     bool tuned_once = false;
+    // polls of a grid-barrier wait of the cooperative range-finder kernel before it gives up
+    unsigned long long rf_spin_limit = RFP_SPIN_LIMIT;
+    // values given on the device (rsc_refactor_values_device): the caller's order, nnz entries;
+    // while vals_dev is set they, not the host copy, feed the factorization and the SpMV
+    DeviceMem umem;
+    double* d_uval = nullptr;
+    long long n_uval = 0;
+    bool vals_dev = false;
+    void set_values_device(const double* d_val, long long nnz, cudaStream_t s);
     Profiler prof;
     virtual ~EngineImpl() = default;
     virtual rsc_status factor(const double* val, double tol, const FixedRank* fr) = 0;
@@ -584,6 +593,13 @@ rsc_status EngineImpl::pcg_batch(const std::vector<int64_t>& rp, const std::vect
     return st;
 }
 
+// out[e] = v[src[e]]
+__global__ void k_gather_vals(const double* __restrict__ v, const long long* __restrict__ src, long long cnt,
+                              double* __restrict__ out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+        out[e] = v[src[e]];
+}
+
 // out[e] = alpha * u[i] * v[j] for every stored entry e = (i, j) of the CSR pattern
 __global__ void k_pattern_outer(long long n, const long long* __restrict__ rp, const int32_t* __restrict__ ci,
                                 const double* __restrict__ u, const double* __restrict__ v, double alpha,
@@ -606,9 +622,39 @@ void EngineImpl::ensure_matrix(const std::vector<int64_t>& rp, const std::vector
         d_ci = (int32_t*)amem.alloc(sizeof(int32_t) * ci.size());
         CK(cudaMemcpyAsync(d_ci, ci.data(), sizeof(int32_t) * ci.size(), cudaMemcpyHostToDevice, s));
         d_val = (double*)amem.alloc(sizeof(double) * val.size());
-        CK(cudaMemcpyAsync(d_val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, s));
+        if (vals_dev) CK(cudaMemcpyAsync(d_val, d_uval, sizeof(double) * val.size(), cudaMemcpyDeviceToDevice, s));
+        else CK(cudaMemcpyAsync(d_val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, s));
         a_uploaded = true;
     }
+}
+
+// number of non-finite entries of v[0..n) (atomic count)
+__global__ void k_count_nonfinite(const double* __restrict__ v, long long n, int* __restrict__ cnt) {
+    int c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c += !isfinite(v[i]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+void EngineImpl::set_values_device(const double* d_in, long long nnz, cudaStream_t s) {
+    if (!d_uval || n_uval != nnz) {
+        umem.release();
+        d_uval = (double*)umem.alloc(sizeof(double) * (nnz + 2));
+        n_uval = nnz;
+    }
+    int* d_cnt = (int*)(d_uval + nnz);   // 8 bytes past the values
+    CK(cudaMemsetAsync(d_cnt, 0, sizeof(int), s));
+    k_count_nonfinite<<<std::max(1, std::min(cdiv(nnz, 256), 1024)), 256, 0, s>>>(d_in, nnz, d_cnt);
+    launches++;
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) throw Error(RSC_ERR_INVALID_ARG, "non-finite matrix value");
+    CK(cudaMemcpyAsync(d_uval, d_in, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));   // the caller may reuse d_in on return; the engine's stream sees the copy
+    vals_dev = true;
+    a_uploaded = false;
 }
 
 void EngineImpl::pattern_outer(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
@@ -824,6 +870,7 @@ struct EngineT final : EngineImpl {
     // sparse block values are gathered at factor time from these source indices
     std::vector<long long> sp_src;     // concatenated value sources of all CsrBlocks
     double* d_spval = nullptr;
+    long long* d_spsrc = nullptr;
     // scratch
     Scratch sG, sY, sUr, sVr, sX, sZ, sT, sTv, sTask, sTask2, sT2;
     double flops = 0.0;
@@ -1092,6 +1139,7 @@ struct EngineT final : EngineImpl {
         int32_t* d_sprp = pmem.upload(sp_rp, stream);
         int32_t* d_spci = pmem.upload(sp_ci, stream);
         d_spval = (double*)pmem.alloc(sizeof(double) * std::max<size_t>(sp_src.size(), 1));
+        d_spsrc = pmem.upload(sp_src, stream);   // for values given on the device
         for (auto& pb : pend) {
             CsrBlock b{d_sprp + pb.rp_off, d_spci + pb.ci_off, d_spval + pb.v_off, pb.nrows, 0};
             NodeRT& n = nd[pb.node];
@@ -2150,7 +2198,8 @@ struct EngineT final : EngineImpl {
             int nrf_ = nrf, nch_ = nch;
             unsigned long long* ptime = prof.on ? d_rfp_time : nullptr;
             int small_ = small ? 1 : 0;
-            void* args[] = {&d_rfd, &d_pp, &nrf_, &d_chunks, &nch_, &bar, &err, &ptime, &small_};
+            unsigned long long lim = rf_spin_limit;
+            void* args[] = {&d_rfd, &d_pp, &nrf_, &d_chunks, &nch_, &bar, &err, &ptime, &small_, &lim};
             PROF(prof, "rf_pass", stream, 0, 0,
                  CK(cudaLaunchCooperativeKernel((const void*)k_rf_pass<T>, dim3(grid), dim3(RFP_THREADS), args, 0,
                                                 stream)));
@@ -2379,13 +2428,20 @@ struct EngineT final : EngineImpl {
         CK(cudaMemsetAsync(d_status, 0, sizeof(int) * 3, stream));
         CK(cudaMemsetAsync(arena, 0, sizeof(T) * std::max<long long>(arena_elems, 1), stream));
         const size_t nval = (size_t)(S.lsrc.empty() ? 0 : *std::max_element(S.lsrc.begin(), S.lsrc.end()) + 1);
-        CK(cudaMemcpyAsync(d_valbuf, val, sizeof(double) * nval, cudaMemcpyHostToDevice, stream));
+        if (vals_dev) CK(cudaMemcpyAsync(d_valbuf, d_uval, sizeof(double) * nval, cudaMemcpyDeviceToDevice, stream));
+        else CK(cudaMemcpyAsync(d_valbuf, val, sizeof(double) * nval, cudaMemcpyHostToDevice, stream));
         if (asm_cnt) {
             k_assemble<T><<<std::min(cdiv(asm_cnt, 256), 8192), 256, 0, stream>>>(d_valbuf, d_asm_src, d_asm_dst, asm_cnt,
                                                                                    arena);
             launches++;
         }
-        {
+        if (vals_dev) {   // sparse-block values gathered on the device
+            if (!sp_src.empty()) {
+                k_gather_vals<<<std::min(cdiv((long long)sp_src.size(), 256), 4096), 256, 0, stream>>>(
+                    d_uval, d_spsrc, (long long)sp_src.size(), d_spval);
+                launches++;
+            }
+        } else {
             std::vector<double> spv(sp_src.size());
             for (size_t e = 0; e < sp_src.size(); ++e) spv[e] = val[sp_src[e]];
             if (!spv.empty())
@@ -3292,7 +3348,14 @@ int rank_heuristic(int m, int n, double alpha, int p) {
     const double r = std::ceil(alpha * std::sqrt((double)k) * std::log2((double)k));
     return (int)std::min<double>(k, r + p);
 }
-void Engine::values_changed() { impl_->a_uploaded = false; }
+void Engine::values_changed() {
+    impl_->a_uploaded = false;
+    impl_->vals_dev = false;   // the host copy holds the values again
+}
+rsc_status Engine::values_device(const double* d_val, long long nnz, void* stream) {
+    impl_->set_values_device(d_val, nnz, stream ? (cudaStream_t)stream : impl_->stream);
+    return RSC_OK;
+}
 bool Engine::factored() const { return impl_->factored(); }
 rsc_status Engine::solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                               const std::vector<double>& val, const double* b, double* x, double rtol,
@@ -3387,5 +3450,6 @@ void Engine::profile(int enable, const char* only) {
 }
 std::string Engine::profile_json() { return impl_->prof.json(); }
 std::string Engine::tuning_json() const { return impl_->tuner.json(); }
+void Engine::set_wait_limit(long long polls) { impl_->rf_spin_limit = polls > 0 ? (unsigned long long)polls : RFP_SPIN_LIMIT; }
 
 }  // namespace rsc

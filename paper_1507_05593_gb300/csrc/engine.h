@@ -34,6 +34,7 @@ public:
     ~Engine();
     rsc_status factor(const double* val, double tol, const FixedRank* fr = nullptr);
     void values_changed();   // new values of A: the SpMV copy is refreshed by the next solve
+    rsc_status values_device(const double* d_val, long long nnz, void* stream);   // new values, on the device
     bool factored() const;
     rsc_status solve_host(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                           const std::vector<double>& val, const double* b, double* x, double rtol,
@@ -56,6 +57,7 @@ public:
     void profile(int enable, const char* only);
     std::string profile_json();
     std::string tuning_json() const;
+    void set_wait_limit(long long polls);
 
 private:
     std::unique_ptr<EngineImpl> impl_;

@@ -29,7 +29,7 @@ namespace rsc {
 
 constexpr int RFP_ROWS = 64;             // rows per chunk
 constexpr int RFP_THREADS = 256;
-constexpr unsigned long long RFP_SPIN_LIMIT = 1ull << 22;
+constexpr unsigned long long RFP_SPIN_LIMIT = 1ull << 22;   // default polls of a barrier wait (64 ns apart)
 constexpr int RFP_SMALL = 8;             // blocks of at most this many chunks: small-block mode
 
 template <class T>
@@ -55,7 +55,8 @@ struct RfBarrier { unsigned count, gen; };
 
 // Grid barrier for a cooperative launch (all CTAs resident).  Returns false when the
 // wait ran out; the caller then returns.
-__device__ __forceinline__ bool rfp_grid_sync(RfBarrier* bar, unsigned& gen, int* err, int& ok_s) {
+__device__ __forceinline__ bool rfp_grid_sync(RfBarrier* bar, unsigned& gen, int* err, int& ok_s,
+                                              unsigned long long limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -67,7 +68,7 @@ __device__ __forceinline__ bool rfp_grid_sync(RfBarrier* bar, unsigned& gen, int
             atomicAdd(&bar->gen, 1u);
         } else {
             ok = 0;
-            for (unsigned long long it = 0; it < RFP_SPIN_LIMIT; ++it) {
+            for (unsigned long long it = 0; it < limit; ++it) {
                 if (*(volatile unsigned*)&bar->gen != gen) { ok = 1; break; }
                 __nanosleep(64);
             }
@@ -262,7 +263,8 @@ __device__ bool rfp_chol(T (*G)[17], int b, double coef, double delta, T* out) {
 template <class T>
 __global__ void __launch_bounds__(RFP_THREADS, 2) k_rf_pass(RfDev<T>* rf, const RfPass<T>* __restrict__ ps, int nrf,
                                                          const int2* __restrict__ chunks, int nchunks, RfBarrier* bar,
-                                                         int* err, unsigned long long* ptime, int small) {
+                                                         int* err, unsigned long long* ptime, int small,
+                                                         unsigned long long spin_limit) {
     __shared__ T Ys[RFP_ROWS][17];
     __shared__ T Us[RFP_ROWS][33];
     __shared__ T Zs[32][17];
@@ -272,6 +274,9 @@ __global__ void __launch_bounds__(RFP_THREADS, 2) k_rf_pass(RfDev<T>* rf, const 
     __shared__ int ok_s;
     __shared__ int nz_s[RFP_THREADS];
     const int tid = threadIdx.x;
+    // a wait of an earlier pass ran out: the barrier count may be stale, so no pass runs until
+    // the host has seen the error
+    if (*(volatile int*)err) return;
     if (tid == 0) gen_s = *(volatile unsigned*)&bar->gen;   // cannot change before every CTA has arrived once
     int any = 0;
     for (int r = tid; r < nrf; r += RFP_THREADS) any |= (ps[r].Yb != nullptr && rfp_ld(&rf[r].active));
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(RFP_THREADS, 2) k_rf_pass(RfDev<T>* rf, const 
     const bool timed = ptime != nullptr && blockIdx.x == 0 && tid == 0;
     if (timed) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     auto sync = [&](int ph) {
-        const bool ok = rfp_grid_sync(bar, gen, err, ok_s);
+        const bool ok = rfp_grid_sync(bar, gen, err, ok_s, spin_limit);
         if (timed) {
             unsigned long long t;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -13,8 +13,8 @@
 //    accumulator in tensor memory, and commits them to an mbarrier;
 //  * the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31
 //    = rows) and scatter-adds it into the ancestor's storage like k_push.
-// Every wait is bounded: on expiry the kernel records an error code and returns
-// after freeing its tensor memory.
+// Every wait is bounded: on expiry the kernel records an error code, waits (bounded) for the
+// MMA in flight and returns after freeing its tensor memory.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -224,7 +224,11 @@ __global__ void __launch_bounds__(128) k_push_tc(const PushTask* __restrict__ ta
             if (!mbar_wait(bar, phase)) {
                 abort_flag = 1;
                 atomicCAS(err, 0, 1);
-                mbar_wait(bar, phase);   // one more bounded wait for an MMA in flight
+                // keep waiting (bounded) for the MMA in flight before the tensor memory is freed;
+                // a CTA may not exit holding tensor memory (a later tcgen05.alloc on this SM,
+                // which cannot be bounded, would wait for it), so it is freed even if completion
+                // is never observed, and the factorization reports RSC_ERR_TIMEOUT
+                for (int k = 0; k < 4 && !mbar_wait(bar, phase); ++k) {}
             }
         }
         __syncthreads();

@@ -353,3 +353,60 @@ def test_autotuned_products_agree(prec):
                 assert np.abs(LO - LOo).max() <= MIXED_TOL[prec] * max(1, np.abs(LOo).max()), (rep, j)
         x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
         assert rr <= 1e-8
+
+
+def test_expired_barrier_wait_reports_timeout_and_handle_recovers():
+    """A grid-barrier wait of the cooperative range-finder kernel that runs out (wait limit set
+    to one poll, so a block that reaches a barrier before the others gives up) ends the
+    factorization with RSC_ERR_TIMEOUT instead of hanging or faulting; with the default limit
+    restored and the values set again the handle factors and solves as before."""
+    p = W.poisson7(32)
+    h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, _opts())
+    R.rsc_set_wait_limit(h, 1)
+    with pytest.raises(R.RscError) as e:
+        R.rsc_factor(h, 0.1)
+    assert e.value.status == 6, e.value
+    with pytest.raises(R.RscError) as e:
+        R.rsc_solve(h, p.b)
+    assert e.value.status == 7
+    R.rsc_set_wait_limit(h, 0)
+    R.rsc_refactor_values(h, p.val)
+    R.rsc_factor(h, 0.1)
+    x, it, rr = R.rsc_solve(h, p.b, 1e-8, 200)
+    an, f = _oracle(p, _opts(), 0.1)
+    _, it_ref, _, _ = F.solve(an, f, p.b, 1e-8, 200)
+    assert rr <= 1e-8 and abs(it - it_ref) <= 2
+    with pytest.raises(R.RscError):
+        R.rsc_set_wait_limit(h, -1)
+
+
+def test_refactor_values_device_matches_host_values():
+    """New values given on the device (no host copy) factor and solve like the same values given
+    on the host; a non-finite device value is rejected; host values take over again afterwards."""
+    p = W.diffusion_grf(12, 1.0, 3.0, 0)
+    q = W.diffusion_grf(12, 1.0, 3.0, 1)
+    kw = dict(leaf_size=16, tau_O=40, tau_D=32)
+    h_host = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, _opts(**kw))
+    h_dev = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, _opts(**kw))
+    R.rsc_refactor_values(h_host, q.val)
+    R.rsc_refactor_values_device(h_dev, torch.tensor(q.val, device="cuda"))
+    for h in (h_host, h_dev):
+        R.rsc_factor(h, 0.1)
+    for j in range(R.rsc_get_stats(h_host)["n_supernodes"]):
+        a, ao = R.rsc_get_supernode_blocks(h_host, j)
+        b, bo = R.rsc_get_supernode_blocks(h_dev, j)
+        assert np.abs(a - b).max() <= 1e-12 * max(1, np.abs(a).max()), j
+        if ao.size:
+            assert np.abs(ao - bo).max() <= 1e-12 * max(1, np.abs(ao).max()), j
+    x, it, rr = R.rsc_solve(h_dev, q.b, 1e-8, 200)     # the SpMV uses the device values too
+    assert rr <= 1e-8
+    assert np.linalg.norm(q.b - q.scipy() @ x) / np.linalg.norm(q.b) <= 1e-8
+    bad = torch.tensor(q.val, device="cuda")
+    bad[5] = float("nan")
+    with pytest.raises(R.RscError) as e:
+        R.rsc_refactor_values_device(h_dev, bad)
+    assert e.value.status == 1
+    R.rsc_refactor_values(h_dev, p.val)                 # host values again
+    R.rsc_factor(h_dev, 0.1)
+    x, it, rr = R.rsc_solve(h_dev, p.b, 1e-8, 200)
+    assert np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b) <= 1e-8
