@@ -67,6 +67,11 @@ typedef struct {
                               coords (any real positions).  coords == NULL selects 1 with spectral
                               positions (Section 4.3); 0 */
     uint64_t seed;         /* key of the Philox4x32-10 stream of the random test matrices; 0 */
+    int32_t amalgamate;    /* 1: relaxed amalgamation of small supernodes (Section 3.1's grouping "as in
+                              CHOLMOD"): a supernode's last child merges into it while the merged
+                              block has at most 4 columns, or at most 16 / 48 columns with at most
+                              80% / 10% entries new to both blocks, or at most 5% new entries at any
+                              size; compressed separators (>= tau_O columns) are never merged; 0 */
 } rsc_options;
 
 typedef struct {

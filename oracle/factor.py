@@ -75,10 +75,12 @@ from scipy.sparse import csgraph
 from . import dense
 from .dense import NotPositiveDefinite
 from .ordering import node_graph, spectral_coordinates
+from .ordering import Ordering
 from .ordering import order as nd_order
 from .philox import gaussian_block
 from .scatter import gather_rows, positions, scatter_rows
 from .symbolic import symbolic
+from .amalgamate import amalgamate
 
 
 @dataclasses.dataclass
@@ -94,6 +96,7 @@ class Options:
     diag_compress: bool = True
     ordering: int = 0          # 0: lattice bisection; 1: graph nested dissection
     interior_blocks: bool = False   # Section 5.1: L(R_B, C_B) of interior blocks not stored
+    amalgamate: bool = False   # Section 3.1: relaxed amalgamation of small supernodes (amalgamate.py)
 
 
 class Analysis:
@@ -121,6 +124,13 @@ class Analysis:
         self.Ap = sp.csr_matrix(A[p][:, p])
         self.Ap.sort_indices()
         self.sym = symbolic(self.Ap, self.ordering.snode_ptr)
+        if opts.amalgamate:
+            od = self.ordering
+            kint = [1 if k == "sep" else 0 for k in od.kinds]
+            ptr, kinds, members = amalgamate(od.snode_ptr, kint, self.sym.rows, opts.tau_O)
+            trees = [od.trees[m[0]] if len(m) == 1 else None for m in members]
+            self.ordering = Ordering(od.perm, ptr, ["sep" if k == 1 else "leaf" for k in kinds], trees)
+            self.sym = symbolic(self.Ap, ptr)
 
     @property
     def nsuper(self):

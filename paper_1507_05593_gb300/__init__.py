@@ -28,7 +28,7 @@ class rsc_options(C.Structure):
     _fields_ = [("tau_O", C.c_int32), ("tau_D", C.c_int32), ("leaf_size", C.c_int32),
                 ("sample_block", C.c_int32), ("power_iters", C.c_int32), ("dof_per_node", C.c_int32),
                 ("max_restarts", C.c_int32), ("precision", C.c_int32), ("diag_compress", C.c_int32),
-                ("ordering", C.c_int32), ("seed", C.c_uint64)]
+                ("ordering", C.c_int32), ("seed", C.c_uint64), ("amalgamate", C.c_int32)]
 
 
 class rsc_stats_t(C.Structure):
@@ -111,6 +111,8 @@ def rsc_options_default(**kw) -> rsc_options:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PREC[v]
+        if not any(f == k for f, _ in rsc_options._fields_):
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, int(v))
     return o
 

@@ -62,6 +62,7 @@ rsc_status rsc_options_default(rsc_options* o) {
     o->precision = RSC_PREC_FP64;
     o->diag_compress = 1;
     o->seed = 0;
+    o->amalgamate = 0;
     return RSC_OK;
 }
 
@@ -77,6 +78,8 @@ rsc_status rsc_analyze(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
             return fail(nullptr, RSC_ERR_INVALID_ARG, "unknown precision");
         if (o.power_iters < 0 || o.max_restarts < 0)
             return fail(nullptr, RSC_ERR_INVALID_ARG, "power_iters and max_restarts must be >= 0");
+        if (o.amalgamate != 0 && o.amalgamate != 1)
+            return fail(nullptr, RSC_ERR_INVALID_ARG, "amalgamate must be 0 or 1");
         h = new rsc_handle();
         h->opts = o;
         std::string why = rsc::analyze_symbolic(n, row_ptr, col_idx, val, coords, o, h->sym);

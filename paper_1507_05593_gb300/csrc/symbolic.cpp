@@ -17,6 +17,7 @@
 //    structures whenever every supernode is an elimination-tree chain (lattice
 //    orderings) and adds rows of exact zeros otherwise (the graph ordering).
 #include <algorithm>
+#include <iterator>
 #include <limits>
 #include <cmath>
 #include <functional>
@@ -143,6 +144,135 @@ void geometric_split(const std::vector<int32_t>& ids_in, const C* P, int dof, in
 }
 
 }  // namespace
+
+// Supernodal row structures R_j, parents, levels and descendants of the partition S.sn_ptr.
+static void build_structure(Symbolic& S) {
+    const int64_t n = S.n;
+    S.rows.clear();
+    S.desc_k.clear();
+    S.desc_p0.clear();
+    S.desc_p1.clear();
+    // supernodal row structures by union through the supernodal tree
+    S.rows_ptr.assign(S.M + 1, 0);
+    S.parent.assign(S.M, -1);
+    S.level.assign(S.M, 0);
+    std::vector<std::vector<int32_t>> children(S.M);
+    std::vector<int32_t> mark(n, -1);
+    std::vector<int32_t> acc;
+    for (int j = 0; j < S.M; ++j) {
+        int64_t c0 = S.sn_ptr[j], c1 = S.sn_ptr[j + 1];
+        acc.clear();
+        for (int64_t c = c0; c < c1; ++c)
+            for (int64_t e = S.lp[c]; e < S.lp[c + 1]; ++e) {
+                int32_t r = S.li[e];
+                if (r >= c1 && mark[r] != j) { mark[r] = j; acc.push_back(r); }
+            }
+        int lev = 0;
+        for (int32_t k : children[j]) {
+            lev = std::max(lev, S.level[k] + 1);
+            for (int64_t e = S.rows_ptr[k]; e < S.rows_ptr[k + 1]; ++e) {
+                int32_t r = S.rows[e];
+                if (r >= c1 && mark[r] != j) { mark[r] = j; acc.push_back(r); }
+            }
+        }
+        S.level[j] = lev;
+        std::sort(acc.begin(), acc.end());
+        S.rows.insert(S.rows.end(), acc.begin(), acc.end());
+        S.rows_ptr[j + 1] = (int64_t)S.rows.size();
+        if (!acc.empty()) {
+            S.parent[j] = S.snode_of[acc[0]];
+            children[S.parent[j]].push_back(j);
+        }
+    }
+    S.nlevels = 0;
+    for (int j = 0; j < S.M; ++j) S.nlevels = std::max(S.nlevels, S.level[j] + 1);
+    S.level_nodes.assign(S.nlevels, {});
+    for (int j = 0; j < S.M; ++j) S.level_nodes[S.level[j]].push_back(j);
+
+    // descendants: runs of R_k per supernode
+    std::vector<std::vector<int32_t>> dk(S.M), d0(S.M), d1(S.M);
+    for (int k = 0; k < S.M; ++k) {
+        const int32_t* Rk = S.R(k);
+        int r = S.nrows(k);
+        int p = 0;
+        while (p < r) {
+            int j = S.snode_of[Rk[p]];
+            int q = p;
+            while (q < r && Rk[q] < S.sn_ptr[j + 1]) ++q;
+            dk[j].push_back(k);
+            d0[j].push_back(p);
+            d1[j].push_back(q);
+            p = q;
+        }
+    }
+    S.desc_ptr.assign(S.M + 1, 0);
+    for (int j = 0; j < S.M; ++j) {
+        S.desc_ptr[j + 1] = S.desc_ptr[j] + (int64_t)dk[j].size();
+        S.desc_k.insert(S.desc_k.end(), dk[j].begin(), dk[j].end());
+        S.desc_p0.insert(S.desc_p0.end(), d0[j].begin(), d0[j].end());
+        S.desc_p1.insert(S.desc_p1.end(), d1[j].begin(), d1[j].end());
+    }
+}
+
+// Section 3.1 groups small supernodes "as in CHOLMOD": relaxed amalgamation.  Supernodes are
+// visited in order (a postorder of the supernodal tree); group G absorbs the group L before it
+// while L's parent lies in G (the first row of R_L is a column of G), neither is a compressed
+// separator (>= tau_O columns) nor would the merged separator be one, and, with ns = c_L + c_G,
+// R_M = R_G united with the rows of R_L after G, s(c, r) = c (c + 1) / 2 + c r stored entries
+// and z = 1 - (s(L) + s(G)) / s(M): ns <= 4, or ns <= 16 and z <= 0.8, or ns <= 48 and z <= 0.1,
+// or z <= 0.05 (CHOLMOD's default relaxation).  The merged group keeps G's kind; the structure
+// is then rebuilt for the merged partition.  Columns keep their order.
+static bool merge_ok(int64_t cL, int64_t rL, int64_t cG, int64_t rG, int64_t rM) {
+    auto st = [](int64_t c, int64_t r) { return (double)(c * (c + 1) / 2 + c * r); };
+    const int64_t ns = cL + cG;
+    const double z = 1.0 - (st(cL, rL) + st(cG, rG)) / st(ns, rM);
+    return ns <= 4 || (ns <= 16 && z <= 0.8) || (ns <= 48 && z <= 0.1) || z <= 0.05;
+}
+
+static void amalgamate_supernodes(Symbolic& S, int tau_O) {
+    struct Grp { int64_t c0, c1; std::vector<int32_t> R; uint8_t kind; int first; int count; };
+    std::vector<Grp> st;
+    auto compressed = [&](uint8_t kind, int64_t c) { return kind == 1 && c >= tau_O; };
+    for (int s = 0; s < S.M; ++s) {
+        Grp G{S.sn_ptr[s], S.sn_ptr[s + 1], std::vector<int32_t>(S.R(s), S.R(s) + S.nrows(s)), S.kind[s], s, 1};
+        while (!st.empty()) {
+            const Grp& L = st.back();
+            const int64_t cL = L.c1 - L.c0, cG = G.c1 - G.c0;
+            if (L.R.empty() || L.R[0] < G.c0 || L.R[0] >= G.c1) break;
+            if (compressed(L.kind, cL) || compressed(G.kind, cG) || compressed(G.kind, cL + cG)) break;
+            std::vector<int32_t> RM;
+            {
+                std::vector<int32_t> tail;
+                for (int32_t r : L.R)
+                    if (r >= G.c1) tail.push_back(r);
+                std::set_union(G.R.begin(), G.R.end(), tail.begin(), tail.end(), std::back_inserter(RM));
+            }
+            if (!merge_ok(cL, (int64_t)L.R.size(), cG, (int64_t)G.R.size(), (int64_t)RM.size())) break;
+            G.c0 = L.c0;
+            G.first = L.first;
+            G.count += L.count;
+            G.R.swap(RM);
+            st.pop_back();
+        }
+        st.push_back(std::move(G));
+    }
+    if ((int)st.size() == S.M) return;
+    std::vector<int64_t> ptr(1, 0);
+    std::vector<uint8_t> kind;
+    std::vector<BlockTree> tree;
+    for (const Grp& g : st) {
+        ptr.push_back(g.c1);
+        kind.push_back(g.kind);
+        tree.push_back(g.count == 1 ? S.tree[g.first] : BlockTree());
+    }
+    S.M = (int)st.size();
+    S.sn_ptr.swap(ptr);
+    S.kind.swap(kind);
+    S.tree.swap(tree);
+    for (int j = 0; j < S.M; ++j)
+        for (int64_t c = S.sn_ptr[j]; c < S.sn_ptr[j + 1]; ++c) S.snode_of[c] = j;
+    build_structure(S);
+}
 
 std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, const double* val,
                              const double* coords, const rsc_options& o, Symbolic& S) {
@@ -304,66 +434,8 @@ std::string analyze_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, co
         }
     }
 
-    // supernodal row structures by union through the supernodal tree
-    S.rows_ptr.assign(S.M + 1, 0);
-    S.parent.assign(S.M, -1);
-    S.level.assign(S.M, 0);
-    std::vector<std::vector<int32_t>> children(S.M);
-    std::vector<int32_t> mark(n, -1);
-    std::vector<int32_t> acc;
-    for (int j = 0; j < S.M; ++j) {
-        int64_t c0 = S.sn_ptr[j], c1 = S.sn_ptr[j + 1];
-        acc.clear();
-        for (int64_t c = c0; c < c1; ++c)
-            for (int64_t e = S.lp[c]; e < S.lp[c + 1]; ++e) {
-                int32_t r = S.li[e];
-                if (r >= c1 && mark[r] != j) { mark[r] = j; acc.push_back(r); }
-            }
-        int lev = 0;
-        for (int32_t k : children[j]) {
-            lev = std::max(lev, S.level[k] + 1);
-            for (int64_t e = S.rows_ptr[k]; e < S.rows_ptr[k + 1]; ++e) {
-                int32_t r = S.rows[e];
-                if (r >= c1 && mark[r] != j) { mark[r] = j; acc.push_back(r); }
-            }
-        }
-        S.level[j] = lev;
-        std::sort(acc.begin(), acc.end());
-        S.rows.insert(S.rows.end(), acc.begin(), acc.end());
-        S.rows_ptr[j + 1] = (int64_t)S.rows.size();
-        if (!acc.empty()) {
-            S.parent[j] = S.snode_of[acc[0]];
-            children[S.parent[j]].push_back(j);
-        }
-    }
-    S.nlevels = 0;
-    for (int j = 0; j < S.M; ++j) S.nlevels = std::max(S.nlevels, S.level[j] + 1);
-    S.level_nodes.assign(S.nlevels, {});
-    for (int j = 0; j < S.M; ++j) S.level_nodes[S.level[j]].push_back(j);
-
-    // descendants: runs of R_k per supernode
-    std::vector<std::vector<int32_t>> dk(S.M), d0(S.M), d1(S.M);
-    for (int k = 0; k < S.M; ++k) {
-        const int32_t* Rk = S.R(k);
-        int r = S.nrows(k);
-        int p = 0;
-        while (p < r) {
-            int j = S.snode_of[Rk[p]];
-            int q = p;
-            while (q < r && Rk[q] < S.sn_ptr[j + 1]) ++q;
-            dk[j].push_back(k);
-            d0[j].push_back(p);
-            d1[j].push_back(q);
-            p = q;
-        }
-    }
-    S.desc_ptr.assign(S.M + 1, 0);
-    for (int j = 0; j < S.M; ++j) {
-        S.desc_ptr[j + 1] = S.desc_ptr[j] + (int64_t)dk[j].size();
-        S.desc_k.insert(S.desc_k.end(), dk[j].begin(), dk[j].end());
-        S.desc_p0.insert(S.desc_p0.end(), d0[j].begin(), d0[j].end());
-        S.desc_p1.insert(S.desc_p1.end(), d1[j].begin(), d1[j].end());
-    }
+    build_structure(S);
+    if (o.amalgamate) amalgamate_supernodes(S, o.tau_O);
     return "";
 }
 

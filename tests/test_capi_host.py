@@ -77,7 +77,7 @@ def test_analyze_rejects_bad_input(what):
 
 def _oracle_opts(o):
     return F.Options(tau_O=o.tau_O, tau_D=o.tau_D, leaf_size=o.leaf_size, dof_per_node=o.dof_per_node,
-                     ordering=o.ordering)
+                     ordering=o.ordering, amalgamate=bool(o.amalgamate))
 
 
 @pytest.mark.parametrize("maker,kw", [
@@ -88,6 +88,13 @@ def _oracle_opts(o):
     (lambda: W.elasticity_q1(3, incl=(1, 2)), dict(leaf_size=8, dof_per_node=3)),
     (lambda: W.elasticity_q1(8), dict(dof_per_node=3)),
     (lambda: W.diffusion_grf(20, 2.0, 4.0, 1), dict(leaf_size=32, tau_O=64, tau_D=64)),
+    # relaxed amalgamation (Section 3.1) on lattice and graph orderings, scalar and 3-DOF nodes
+    (lambda: W.poisson7(12), dict(leaf_size=8, tau_O=40, tau_D=32, amalgamate=1)),
+    (lambda: W.poisson7(7, 5, 6), dict(leaf_size=4, tau_O=12, tau_D=8, amalgamate=1)),
+    (lambda: W.poisson7(32), dict(amalgamate=1)),
+    (lambda: W.elasticity_q1(4, incl=(1, 3)), dict(leaf_size=4, tau_O=48, tau_D=24, dof_per_node=3, amalgamate=1)),
+    (lambda: W.random_geometric(1500, 0.12, seed=0), dict(leaf_size=16, tau_O=40, tau_D=32, ordering=1,
+                                                          amalgamate=1)),
 ])
 def test_symbolic_bit_exact_vs_oracle(maker, kw):
     p = maker()
@@ -102,6 +109,9 @@ def test_symbolic_bit_exact_vs_oracle(maker, kw):
         np.testing.assert_array_equal(rows[rows_ptr[j]:rows_ptr[j + 1]], an.sym.rows[j])
     np.testing.assert_array_equal(parent, an.sym.parent)
     assert [int(k) for k in kind] == [1 if x == "sep" else 0 for x in an.ordering.kinds]
+    if kw.get("amalgamate"):   # never more supernodes than without (fewer where small ones exist)
+        assert an.nsuper <= F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                                     _oracle_opts(R.rsc_options_default(**dict(kw, amalgamate=0)))).nsuper
     # levels: children strictly below parents, leaves at 0
     for j in range(an.nsuper):
         if parent[j] >= 0:
@@ -184,6 +194,9 @@ def test_graph_ordering_bit_exact_vs_oracle(maker, kw, pos):
         np.testing.assert_array_equal(rows[rows_ptr[j]:rows_ptr[j + 1]], an.sym.rows[j])
     np.testing.assert_array_equal(parent, an.sym.parent)
     assert [int(k) for k in kind] == [1 if x == "sep" else 0 for x in an.ordering.kinds]
+    if kw.get("amalgamate"):   # never more supernodes than without (fewer where small ones exist)
+        assert an.nsuper <= F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                                     _oracle_opts(R.rsc_options_default(**dict(kw, amalgamate=0)))).nsuper
     np.testing.assert_array_equal(R.rsc_get_coordinates(h), X[::p.dof_per_node])
     assert any(t is not None for t in an.ordering.trees)
 

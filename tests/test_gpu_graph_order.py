@@ -20,15 +20,27 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_graph_ordering_random_geometric_parity():
-    p = W.random_geometric(1500, 0.12, seed=2)
-    kw = dict(leaf_size=24, tau_O=60, tau_D=40, ordering=1)
+AMALG = [("graph", lambda: W.random_geometric(1500, 0.12, seed=2), dict(leaf_size=24, tau_O=60, tau_D=40, ordering=1)),
+         ("graph_amalgamated", lambda: W.random_geometric(1500, 0.12, seed=2),
+          dict(leaf_size=24, tau_O=60, tau_D=40, ordering=1, amalgamate=1)),
+         ("lattice_amalgamated", lambda: W.diffusion_grf(14, 2.0, 3.0, 0),
+          dict(leaf_size=8, tau_O=40, tau_D=32, amalgamate=1))]
+
+
+@pytest.mark.parametrize("name,maker,kw", AMALG, ids=[a[0] for a in AMALG])
+def test_graph_ordering_random_geometric_parity(name, maker, kw):
+    """Graph ordering, and relaxed amalgamation of small supernodes (Section 3.1) on the graph
+    and the lattice orderings: the merged partition (bit-exact on the host) factors with the
+    oracle's ranks, one apply within 1e-8, PCG iterations within +-2."""
+    p = maker()
     o = R.rsc_options_default(**kw)
     h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
     R.rsc_factor(h, 0.1)
-    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(**kw))
+    an = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords,
+                   F.Options(**{k: (bool(v) if k == "amalgamate" else v) for k, v in kw.items()}))
     f = F.factor(an, 0.1)
     assert sum(s.compressed for s in f.sn) >= 1
+    assert R.rsc_get_stats(h)["n_supernodes"] == an.nsuper
     for j in range(an.nsuper):
         info = R.rsc_get_supernode_info(h, j)
         assert info["compressed"] == int(f.sn[j].compressed), j

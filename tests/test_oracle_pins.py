@@ -789,3 +789,69 @@ def test_interior_blocks_cover_the_uncompressed_subtrees():
         if parent[j] >= 0:
             comp_desc[parent[j]] |= comp_desc[j]
     assert np.array_equal(ib < 0, comp_desc)
+
+
+# ----------------------------------------------------------------------------- relaxed amalgamation (Section 3.1)
+
+from oracle.amalgamate import merge_ok  # noqa: E402
+
+AMALG_CASES = [
+    ("poisson10", lambda: W.poisson7(10), dict(leaf_size=8, tau_O=40, tau_D=32)),
+    ("poisson_7x5x6", lambda: W.poisson7(7, 5, 6), dict(leaf_size=4, tau_O=12, tau_D=8)),
+    ("rgg600", lambda: W.random_geometric(600, 0.16, seed=2), dict(leaf_size=12, tau_O=30, tau_D=16, ordering=1)),
+]
+
+
+def test_merge_rule_closed_form():
+    """The relaxation thresholds (CHOLMOD's defaults): blocks of at most 4 columns always merge;
+    up to 16 columns at most 80% new entries, up to 48 at most 10%, any size at most 5%."""
+    assert merge_ok(2, 3, 2, 9, 9)                     # 4 columns, whatever the fill
+    # 8 + 8 columns, rows 8 -> 8: s(L) = 36 + 64, s(G) = 36 + 64, s(M) = 136 + 128, z = 0.24
+    assert merge_ok(8, 8, 8, 8, 8)
+    # 24 + 24 columns into 30 rows: s(M) = 1176 + 1440 = 2616, s(L) + s(G) = 2 (300 + 720), z = 0.22
+    assert not merge_ok(24, 30, 24, 30, 30)
+    # 40 + 8 columns: s(L) = 820 + 40 * 48 = 2740, s(G) = 36 + 8 * 40 = 356, s(M) = 1176 + 48 * 40 = 3096
+    assert merge_ok(40, 48, 8, 40, 40)                 # z = 0.0 <= 0.1 at 48 columns
+    assert not merge_ok(40, 8, 9, 40, 40)              # 49 columns, z = 0.51
+
+
+@pytest.mark.parametrize("name,maker,kw", AMALG_CASES, ids=[c[0] for c in AMALG_CASES])
+def test_amalgamation_against_brute_force(name, maker, kw):
+    """Merged supernodes: contiguous groups of the unmerged ones in which every member but the
+    last has its supernodal parent inside the group; no compressed separator merged; fewer
+    supernodes; every nonzero of the exact factor (dense Cholesky of P A P^T, brute force)
+    inside the merged partition's stored blocks; the exact factor computed blockwise with the
+    merged partition equals the dense factor (the Cholesky factor is unique)."""
+    p = maker()
+    a0 = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(**kw))
+    a1 = F.analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, F.Options(amalgamate=True, **kw))
+    assert np.array_equal(a0.ordering.perm, a1.ordering.perm)
+    p0, p1 = a0.sym.snode_ptr, a1.sym.snode_ptr
+    assert a1.nsuper < a0.nsuper and set(p1.tolist()) <= set(p0.tolist())
+    for g in range(a1.nsuper):
+        c0, c1 = int(p1[g]), int(p1[g + 1])
+        members = [j for j in range(a0.nsuper) if c0 <= p0[j] < c1]
+        for j in members[:-1]:
+            assert a0.sym.parent[j] in members, (g, j)
+        if len(members) > 1:
+            assert not (a1.ordering.kinds[g] == "sep" and c1 - c0 >= kw["tau_O"])
+            assert all(not (a0.ordering.kinds[j] == "sep" and p0[j + 1] - p0[j] >= kw["tau_O"]) for j in members)
+    Ad = a1.Ap.toarray()
+    Ld = np.linalg.cholesky(Ad)
+    nz = np.abs(Ld) > 1e-14 * np.abs(Ld).max()
+    for g in range(a1.nsuper):
+        c0, c1 = int(p1[g]), int(p1[g + 1])
+        allowed = np.zeros(p.n, bool)
+        allowed[c0:c1] = True
+        allowed[a1.sym.rows[g]] = True
+        for c in range(c0, c1):
+            rows = np.nonzero(nz[c:, c])[0] + c
+            assert allowed[rows].all(), (g, c)
+    f = F.factor(a1, 0.0)
+    L = np.zeros_like(Ad)
+    for g in range(a1.nsuper):
+        c0, c1 = a1.cols(g)
+        L[c0:c1, c0:c1] = f.sn[g].D.L
+        if a1.sym.rows[g].size:
+            L[np.ix_(a1.sym.rows[g], np.arange(c0, c1))] = f.sn[g].LO
+    assert np.abs(L - Ld).max() <= 1e-12 * np.abs(Ld).max()
