@@ -900,6 +900,7 @@ struct EngineT final : EngineImpl {
         nd.resize(S.M);
     }
     ~EngineT() override {
+        if (dense_graph) cudaGraphExecDestroy(dense_graph);
         plan1.clear();
         planN.clear();
         if (arena_base) cudaFree(arena_base);
@@ -1257,6 +1258,14 @@ struct EngineT final : EngineImpl {
                     push_count_tc[l] = (int)bt[l].size();
                 }
             }
+        }
+        if (dense_graph) { cudaGraphExecDestroy(dense_graph); dense_graph = nullptr; }
+        dense_prefix = 0;
+        for (int l = 0; l < S.nlevels; ++l) {
+            bool any = false;
+            for (int j : S.level_nodes[l]) any |= nd[j].compressed;
+            if (any) break;
+            dense_prefix = l + 1;
         }
         CK(cudaStreamSynchronize(stream));
         plan_compress = compress;
@@ -2422,6 +2431,58 @@ struct EngineT final : EngineImpl {
     }
 
     // ---------------------------------------------------------------- factor
+    // ---------------------------------------------------------------- per-level launches
+    // dense panel factorization steps of the level and the inverses of its dense diagonal blocks
+    void issue_panels_and_inverses(int l) {
+        run_panel_steps(panel_steps[l]);
+        if (inv_count[l]) {
+            double fl = 0;
+            for (int j : S.level_nodes[l])
+                if (!nd[j].hier) fl += (double)nd[j].c * std::min(nd[j].c, SOLVE_MAX) * std::min(nd[j].c, SOLVE_MAX) / 3.0;
+            const dim3 grid((unsigned)inv_count[l], (unsigned)cdiv(inv_maxc[l], TRSV_CW));
+            PROF(prof, "trinv", stream, fl, 0, k_trsv_subst<T, TRSV_CW><<<grid, 256, 0, stream>>>(inv_tasks[l]));
+            launches++;
+            LAUNCH_CHECK();
+        }
+    }
+    // algorithmic flops of the level's dense work (counted whether launched or replayed)
+    void count_level_flops(int l) {
+        for (int j : S.level_nodes[l]) {
+            const NodeRT& n = nd[j];
+            if (!n.hier) flops += (double)n.c * std::min(n.c, SOLVE_MAX) * std::min(n.c, SOLVE_MAX) / 3.0;
+            if (!n.compressed) {
+                const double c = n.c, r = n.r;
+                flops += c * c * c / 3.0 + r * c * c;
+            }
+        }
+    }
+    // the level's extend-add into its ancestors (d_lo holds the sources' L^O_k or V_k)
+    void issue_push(int l) {
+        if (!push_count[l]) return;
+        double pf = 0, pb = 0;
+        if (prof.on)
+            for (auto& e : push_elems[l]) {
+                pf += 2.0 * e.elems * h_lo[e.k].K;
+                pb += sizeof(T) * ((double)e.rows * h_lo[e.k].K + 2.0 * e.elems);
+            }
+        if (tc && push_count_tc[l]) {
+            auto kern = tc_tf32 ? k_push_tc<true> : k_push_tc<false>;
+            const int pad = tc_tf32 ? TC_PAD_SMEM_TF32 : TC_PAD_SMEM;
+            PROF(prof, "push_tc", stream, pf, pb,
+                 kern<<<push_count_tc[l], 128, pad, stream>>>(
+                     push_tasks_tc[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf, (float*)arena, d_status + 1));
+        } else {
+            PROF(prof, "push", stream, pf, pb,
+                 k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf,
+                                                             arena));
+        }
+        launches++;
+        LAUNCH_CHECK();
+    }
+    int dense_prefix = 0;                       // levels before the first compressed supernode
+    cudaGraphExec_t dense_graph = nullptr;      // their launches, captured once per plan
+    long long dense_graph_launches = 0;
+
     void run_once(const double* val) {
         lr_used = 0;
         flops = 0.0;
@@ -2460,31 +2521,39 @@ struct EngineT final : EngineImpl {
             }
             if (n.compressed) h_lo[j] = LoOp{nullptr, 1, 0};
         }
-        for (int l = 0; l < S.nlevels; ++l) {
+        // levels before the first compressed supernode have a launch list fixed by the plan: one
+        // CUDA graph (captured at the first factorization with this plan) replays them
+        int l_start = 0;
+        if (dense_prefix > 0 && !prof.on && !no_graph) {
+            CK(cudaMemcpyAsync(d_lo, h_lo.data(), sizeof(LoOp) * S.M, cudaMemcpyHostToDevice, stream));
+            if (!dense_graph) {
+                const long long before = launches;
+                CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+                for (int l = 0; l < dense_prefix; ++l) {
+                    issue_panels_and_inverses(l);
+                    issue_push(l);
+                }
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamEndCapture(stream, &g));
+                CK(cudaGraphInstantiate(&dense_graph, g, 0));
+                CK(cudaGraphDestroy(g));
+                dense_graph_launches = launches - before;
+                launches = before;
+            }
+            CK(cudaGraphLaunch(dense_graph, stream));
+            launches += dense_graph_launches;
+            for (int l = 0; l < dense_prefix; ++l) count_level_flops(l);
+            l_start = dense_prefix;
+        }
+        for (int l = l_start; l < S.nlevels; ++l) {
             const double t_l0 = now_ms();
             if (std::getenv("RSC_PROFILE_BY_LEVEL")) {
                 char tg[16];
                 std::snprintf(tg, sizeof(tg), "@%02d", l);
                 prof.tag = tg;
             }
-            run_panel_steps(panel_steps[l]);
-            if (inv_count[l]) {
-                double fl = 0;
-                for (int j : S.level_nodes[l])
-                    if (!nd[j].hier) fl += (double)nd[j].c * std::min(nd[j].c, SOLVE_MAX) * std::min(nd[j].c, SOLVE_MAX) / 3.0;
-                flops += fl;
-                const dim3 grid((unsigned)inv_count[l], (unsigned)cdiv(inv_maxc[l], TRSV_CW));
-                PROF(prof, "trinv", stream, fl, 0, k_trsv_subst<T, TRSV_CW><<<grid, 256, 0, stream>>>(inv_tasks[l]));
-                launches++;
-                LAUNCH_CHECK();
-            }
-            for (int j : S.level_nodes[l]) {
-                const NodeRT& n = nd[j];
-                if (!n.compressed) {
-                    const double c = n.c, r = n.r;
-                    flops += c * c * c / 3.0 + r * c * c;
-                }
-            }
+            issue_panels_and_inverses(l);
+            count_level_flops(l);
             std::vector<int> comp;
             for (int j : S.level_nodes[l])
                 if (nd[j].compressed) comp.push_back(j);
@@ -2494,26 +2563,7 @@ struct EngineT final : EngineImpl {
             }
             // extend-add of the level into its ancestors
             CK(cudaMemcpyAsync(d_lo, h_lo.data(), sizeof(LoOp) * S.M, cudaMemcpyHostToDevice, stream));
-            if (push_count[l]) {
-                double pf = 0, pb = 0;
-                for (auto& e : push_elems[l]) {
-                    pf += 2.0 * e.elems * h_lo[e.k].K;
-                    pb += sizeof(T) * ((double)e.rows * h_lo[e.k].K + 2.0 * e.elems);
-                }
-                if (tc && push_count_tc[l]) {
-                    auto kern = tc_tf32 ? k_push_tc<true> : k_push_tc<false>;
-                    const int pad = tc_tf32 ? TC_PAD_SMEM_TF32 : TC_PAD_SMEM;
-                    PROF(prof, "push_tc", stream, pf, pb,
-                         kern<<<push_count_tc[l], 128, pad, stream>>>(
-                             push_tasks_tc[l], d_lo, d_tgt, d_rows, d_rows_ptr, d_leaf, (float*)arena, d_status + 1));
-                } else {
-                    PROF(prof, "push", stream, pf, pb,
-                         k_push<T><<<push_count[l], 256, 0, stream>>>(push_tasks[l], d_lo, d_tgt, d_rows, d_rows_ptr,
-                                                                     d_leaf, arena));
-                }
-                launches++;
-                LAUNCH_CHECK();
-            }
+            issue_push(l);
             sync_stream();   // h_lo is rewritten by the next level
             if (prof.on) {
                 char nm[32];
