@@ -2704,8 +2704,11 @@ struct EngineT final : EngineImpl {
     static void push_nn_chunks(std::vector<NnTask>& v, NnTask t) {
         for (int r0 = 0; r0 < t.nrow; r0 += NN_ROWS) { NnTask c = t; c.row0 = r0; v.push_back(c); }
     }
-    static void push_tn_chunks(std::vector<TnTask>& v, const TnTask& t) {
-        for (int t0 = 0; t0 < t.K; t0 += TN_COLS) { TnTask c = t; c.t0 = t0; v.push_back(c); }
+    // columns of A per apply TN task: the vector kernel k_tn1 takes 32, the staged k_tn_s (several
+    // right-hand sides) 64
+    int ap_tn_cols() const { return pl->N == 1 ? TN_COLS : TS_COLS; }
+    void push_tn_chunks(std::vector<TnTask>& v, const TnTask& t) const {
+        for (int t0 = 0; t0 < t.K; t0 += ap_tn_cols()) { TnTask c = t; c.t0 = t0; v.push_back(c); }
     }
     // vector forms on y (ld 1, one column); yoff / ymap index rows of y
     TnTask vtn(const void* A, int lda, int K, int nrow, const int32_t* ymap, int yoff, T* Z, double alpha = 1.0,
@@ -2956,7 +2959,7 @@ struct EngineT final : EngineImpl {
         pl->trsv = pl->mem.upload(B.trsv, stream);
         {   // long TN tasks: rows split over CTAs with per-task partial sums and arrival counters
             // (kept in the plan; each counter is back at zero when its launch ends)
-            const int ych = cdiv(N, 16);
+            const int ych = N == 1 ? 1 : cdiv(N, 64), wcols = ap_tn_cols();
             auto split_of = [&](const TnTask& t) {
                 if (N == 1) return t.nrow > TN1_SPLIT_ROWS ? cdiv(t.nrow, TN1_SPLIT_ROWS) : 1;
                 return t.nrow >= TN_SPLIT_MIN ? std::min(cdiv(t.nrow, TN_SPLIT_ROWS), TN_SPLIT_MAX) : 1;
@@ -2964,7 +2967,7 @@ struct EngineT final : EngineImpl {
             long long npart = 0, ncnt = 0;
             for (auto& t : B.tn) {
                 const int ns = split_of(t);
-                if (ns > 1) { npart += (long long)ns * TN_COLS * N; ncnt += ych; }
+                if (ns > 1) { npart += (long long)ns * wcols * N; ncnt += ych; }
             }
             T* part = npart ? (T*)pl->mem.alloc(sizeof(T) * npart) : nullptr;
             unsigned* cnt = ncnt ? (unsigned*)pl->mem.alloc(sizeof(unsigned) * ncnt) : nullptr;
@@ -2974,7 +2977,7 @@ struct EngineT final : EngineImpl {
                 if (ns == 1) continue;
                 t.nsplit = ns;
                 t.rps = cdiv(t.nrow, ns);
-                t.part = part; part += (size_t)ns * TN_COLS * N;
+                t.part = part; part += (size_t)ns * wcols * N;
                 t.cnt = cnt; cnt += ych;
             }
             for (Launch& L : pl->seq)
@@ -2983,8 +2986,8 @@ struct EngineT final : EngineImpl {
         }
         pl->tn = pl->mem.upload(B.tn, stream);
         pl->nn = pl->mem.upload(B.nn, stream);
-        for (auto& t : B.tn) pl->flops += 2.0 * t.nrow * std::min(TN_COLS, t.K - t.t0);
-        for (auto& t : B.nn) pl->flops += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K;
+        for (auto& t : B.tn) pl->flops += 2.0 * t.nrow * std::min(ap_tn_cols(), t.K - t.t0) * N;
+        for (auto& t : B.nn) pl->flops += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K * N;
         pl->bytes += (4.0 * sizeof(T) * n + 16.0 * n) * N;
         sync_stream();
         // capture the launch list once
@@ -3022,9 +3025,13 @@ struct EngineT final : EngineImpl {
                 case L_TN:
                     if (N == 1)
                         PROF(P, "ap_tn", s, 0, 0, k_tn1<T><<<dim3(L.count, 1, std::max(L.flag, 1)), 256, 0, s>>>(A.tn + L.off));
-                    else
-                        PROF(P, "ap_tn", s, 0, 0,
-                             k_tn<T><<<dim3(L.count, cdiv(N, 16), std::max(L.flag, 1)), 256, 0, s>>>(A.tn + L.off));
+                    else {   // several right-hand sides: the staged kernel, 64 columns of A per CTA
+                        const dim3 g((unsigned)L.count, (unsigned)cdiv(N, 64), (unsigned)std::max(L.flag, 1));
+                        const int np = std::min(N, 64) <= 16 ? 16 : std::min(N, 64) <= 32 ? 32 : 64;
+                        if (np == 16) PROF(P, "ap_tn", s, 0, 0, k_tn_s<T, 16><<<g, 256, ts_smem_bytes<T>(16), s>>>(A.tn + L.off));
+                        else if (np == 32) PROF(P, "ap_tn", s, 0, 0, k_tn_s<T, 32><<<g, 256, ts_smem_bytes<T>(32), s>>>(A.tn + L.off));
+                        else PROF(P, "ap_tn", s, 0, 0, k_tn_s<T, 64><<<g, 256, ts_smem_bytes<T>(64), s>>>(A.tn + L.off));
+                    }
                     break;
                 case L_NN:
                     PROF(P, "ap_nn", s, 0, 0, k_nn<T><<<dim3(L.count, cdiv(N, 16)), NN_ROWS, 0, s>>>(A.nn + L.off));

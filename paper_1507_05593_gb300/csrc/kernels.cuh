@@ -452,11 +452,9 @@ __global__ void __launch_bounds__(256) k_push(const PushTask* __restrict__ tasks
         }
 }
 
-// ------------------------------------------------------------------ thin products (N columns, chunks of 16)
-// One CTA per (task, 32-column tile of A, 16-column chunk of Y).  Lane l owns column
-// t0 + l; the 8 warps take contiguous row ranges (so each lane's column of A is read
-// line by line through L1) and every Y row is read once per 32 columns; the warps'
-// partial sums are reduced in shared memory in a fixed order.
+// ------------------------------------------------------------------ thin products
+// TN products Z = A^T Y: k_tn1 (one right-hand side, the preconditioner apply) below, k_tn_s
+// (up to 64 columns, staged through shared memory) further down; NN products Y += A Z: k_nn.
 constexpr int TN_COLS = 32;
 // 16 consecutive elements from a 16-byte aligned address, as 16-byte vector loads
 __device__ __forceinline__ void load_row16(const float* y, float (&v)[16]) {
@@ -475,103 +473,16 @@ __device__ __forceinline__ void load_row16(const double* y, double (&v)[16]) {
         v[2 * h] = f.x; v[2 * h + 1] = f.y;
     }
 }
-template <class T>
-__global__ void __launch_bounds__(256) k_tn(const TnTask* __restrict__ tasks) {
-    __shared__ T red[8][16][33];
-    __shared__ int last;
-    const TnTask tk = tasks[blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.y * 16;
-    const int nc = min(16, tk.N - c0);
-    if (nc <= 0 || (int)blockIdx.z >= tk.nsplit) return;
-    const int rb = (int)blockIdx.z * tk.rps;
-    const int re = tk.nsplit > 1 ? min(tk.nrow, rb + tk.rps) : tk.nrow;
-    const int t = tk.t0 + lane;
-    const bool tok = t < tk.K;
-    const T* A = (const T*)tk.A + (size_t)(tok ? t : 0) * tk.lda;
-    const T* Y = (const T*)tk.Y + c0;
-    T acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = T(0);
-    const int chunk = (re - rb + 7) >> 3;
-    const int i0 = rb + warp * chunk, i1 = min(re, i0 + chunk);
-    // full 16-column rows of Y that start on a 16-byte boundary are read as 16-byte vectors
-    const bool vec = nc == 16 && (tk.ldy * (int)sizeof(T)) % 16 == 0 && ((uintptr_t)Y & 15) == 0;
-    for (int ib = i0; ib < i1; ib += 32) {
-      const int nb = min(32, i1 - ib);
-      const int my = ib + lane;
-      const int ar_l = my < i1 ? (tk.amap ? tk.amap[my] : my) + tk.aoff : 0;
-      const int yr_l = my < i1 ? (tk.ymap ? tk.ymap[my] : my) + tk.yoff : 0;
-#pragma unroll 4
-      for (int r = 0; r < nb; ++r) {
-        const int ar = __shfl_sync(0xffffffffu, ar_l, r);
-        const int yr = __shfl_sync(0xffffffffu, yr_l, r);
-        const T a = tok ? A[ar] : T(0);
-        const T* y = Y + (size_t)yr * tk.ldy;
-        if (vec) {
-            T yv[16];
-            load_row16(y, yv);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = fma(a, yv[q], acc[q]);
-        } else if (nc == 16) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc[q] = fma(a, y[q], acc[q]);
-        } else if (nc == 1) {
-            acc[0] = fma(a, y[0], acc[0]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q)
-                if (q < nc) acc[q] = fma(a, y[q], acc[q]);
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q) red[warp][q][lane] = acc[q];
-    __syncthreads();
-    if (tk.nsplit == 1) {
-        for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
-            const int q = e >> 5, l = e & 31;
-            if (q >= nc || tk.t0 + l >= tk.K) continue;
-            T s = T(0);
-#pragma unroll
-            for (int w = 0; w < 8; ++w) s += red[w][q][l];
-            T* z = (T*)tk.Z + (size_t)(tk.t0 + l) * tk.ldz + c0 + q;
-            *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * s : (T)tk.alpha * s;
-        }
-        return;
-    }
-    T* part = (T*)tk.part;
-    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
-        const int q = e >> 5, l = e & 31;
-        if (q >= nc) continue;
-        T s = T(0);
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += red[w][q][l];
-        part[((size_t)blockIdx.z * 32 + l) * tk.N + c0 + q] = s;
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(tk.cnt + blockIdx.y, 1u) == (unsigned)(tk.nsplit - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
-        const int q = e >> 5, l = e & 31;
-        if (q >= nc || tk.t0 + l >= tk.K) continue;
-        T s = T(0);
-        for (int zz = 0; zz < tk.nsplit; ++zz) s += __ldcg(part + ((size_t)zz * 32 + l) * tk.N + c0 + q);
-        T* z = (T*)tk.Z + (size_t)(tk.t0 + l) * tk.ldz + c0 + q;
-        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * s : (T)tk.alpha * s;
-    }
-    if (threadIdx.x == 0) tk.cnt[blockIdx.y] = 0u;
-}
-
-// Vector form of k_tn (N = 1): one CTA per (task, 32-column tile, row split), a warp per
-// column, lanes down the rows (coalesced column reads).  With tk.nsplit > 1, CTA z sums rows
-// [z rps, (z + 1) rps) into part[z][32] and the last CTA to arrive adds the partial sums in
-// ascending z (deterministic) and resets its counter.
+// TN product for one right-hand side (N = 1, the preconditioner apply): one CTA per (task, 32-
+// column tile, row split).  The gathered y values of a 512-row chunk are staged in shared memory
+// once for the CTA; warp w then takes columns 4w .. 4w + 3 together (four independent
+// accumulators, lanes down the rows: coalesced reads of A) and reduces them with shuffles.
+// With tk.nsplit > 1, CTA z sums rows [z rps, (z + 1) rps) into part[z][32] and the last CTA to
+// arrive adds the partial sums in ascending z (deterministic) and resets its counter.
+constexpr int TN1_CHUNK = 512;
 template <class T>
 __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
+    __shared__ T ys[TN1_CHUNK];
     __shared__ int last;
     const TnTask tk = tasks[blockIdx.x];
     if ((int)blockIdx.z >= tk.nsplit) return;
@@ -580,25 +491,45 @@ __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
     const int re = tk.nsplit > 1 ? min(tk.nrow, rb + tk.rps) : tk.nrow;
     const T* Y = (const T*)tk.Y;
     T* part = (T*)tk.part;
-    for (int tt = warp; tt < TN_COLS; tt += 8) {
-        const int t = tk.t0 + tt;
-        if (t >= tk.K) break;
-        const T* A = (const T*)tk.A + (size_t)t * tk.lda;
-        T acc = T(0);
-#pragma unroll 4
-        for (int i = rb + lane; i < re; i += 32) {
-            const int ar = (tk.amap ? tk.amap[i] : i) + tk.aoff;
-            const int yr = (tk.ymap ? tk.ymap[i] : i) + tk.yoff;
-            acc = fma(A[ar], Y[(size_t)yr * tk.ldy], acc);
-        }
+    const int tt0 = 4 * warp;                          // this warp's first column of the tile
+    const T* A = (const T*)tk.A + (size_t)(tk.t0 + tt0) * tk.lda;
+    bool ok[4];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
+    for (int u = 0; u < 4; ++u) ok[u] = tk.t0 + tt0 + u < tk.K;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int c0 = rb; c0 < re; c0 += TN1_CHUNK) {
+        const int cn = min(TN1_CHUNK, re - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+            const int yr = (tk.ymap ? tk.ymap[c0 + i] : c0 + i) + tk.yoff;
+            ys[i] = Y[(size_t)yr * tk.ldy];
+        }
+        __syncthreads();
+        if (ok[0]) {
+#pragma unroll 2
+            for (int i = lane; i < cn; i += 32) {
+                const int ar = (tk.amap ? tk.amap[c0 + i] : c0 + i) + tk.aoff;
+                const T yv = ys[i];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (ok[u]) acc[u] = fma(A[(size_t)u * tk.lda + ar], yv, acc[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!ok[u]) continue;
+            const int tt = tt0 + u;
             if (tk.nsplit == 1) {
-                T* z = (T*)tk.Z + (size_t)t * tk.ldz;
-                *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc : (T)tk.alpha * acc;
+                T* z = (T*)tk.Z + (size_t)(tk.t0 + tt) * tk.ldz;
+                *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc[u] : (T)tk.alpha * acc[u];
             } else {
-                part[(size_t)blockIdx.z * TN_COLS + tt] = acc;
+                part[(size_t)blockIdx.z * TN_COLS + tt] = acc[u];
             }
         }
     }
@@ -610,10 +541,10 @@ __global__ void __launch_bounds__(256) k_tn1(const TnTask* __restrict__ tasks) {
     if (!last) return;
     __threadfence();
     if (threadIdx.x < TN_COLS && tk.t0 + (int)threadIdx.x < tk.K) {
-        T acc = T(0);
-        for (int zz = 0; zz < tk.nsplit; ++zz) acc += __ldcg(part + (size_t)zz * TN_COLS + threadIdx.x);
+        T a = T(0);
+        for (int zz = 0; zz < tk.nsplit; ++zz) a += __ldcg(part + (size_t)zz * TN_COLS + threadIdx.x);
         T* z = (T*)tk.Z + (size_t)(tk.t0 + threadIdx.x) * tk.ldz;
-        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * acc : (T)tk.alpha * acc;
+        *z = tk.beta != 0.0 ? (T)tk.beta * *z + (T)tk.alpha * a : (T)tk.alpha * a;
     }
     if (threadIdx.x == 0) *tk.cnt = 0u;
 }
