@@ -72,6 +72,11 @@ typedef struct {
                               block has at most 4 columns, or at most 16 / 48 columns with at most
                               80% / 10% entries new to both blocks, or at most 5% new entries at any
                               size; compressed separators (>= tau_O columns) are never merged; 0 */
+    int32_t interior_blocks; /* 1: interior blocks (Section 5.1): for every maximal subtree B of the
+                              supernodal tree without a compressed supernode, L(R_B, C_B) is not kept
+                              after the factorization; the solves use A(R_B, C_B) L_B^{-T} instead
+                              (Eq. interiorBlockClosedForm).  The allocation-free apply does not
+                              support it (RSC_ERR_INVALID_ARG); 0 */
 } rsc_options;
 
 typedef struct {
@@ -252,7 +257,8 @@ rsc_status rsc_get_supernode_info(const rsc_handle* h, int32_t j, int32_t* info)
 
 /* Dense blocks of supernode j (FP64, column-major): LD[c*c] the diagonal block
  * (hierarchical blocks expanded, V_s U_s^T in the off-diagonal blocks), LO[r*c]
- * L^O_j or V_j U_j^T (either may be NULL). */
+ * L^O_j or V_j U_j^T (either may be NULL), r = |R_j|.  With interior_blocks = 1 the
+ * rows of R_j after an interior block's columns are not stored and come back as NaN. */
 rsc_status rsc_get_supernode_blocks(const rsc_handle* h, int32_t j, double* LD, double* LO);
 
 rsc_status rsc_get_stats(const rsc_handle* h, rsc_stats_t* out);

@@ -28,7 +28,8 @@ class rsc_options(C.Structure):
     _fields_ = [("tau_O", C.c_int32), ("tau_D", C.c_int32), ("leaf_size", C.c_int32),
                 ("sample_block", C.c_int32), ("power_iters", C.c_int32), ("dof_per_node", C.c_int32),
                 ("max_restarts", C.c_int32), ("precision", C.c_int32), ("diag_compress", C.c_int32),
-                ("ordering", C.c_int32), ("seed", C.c_uint64), ("amalgamate", C.c_int32)]
+                ("ordering", C.c_int32), ("seed", C.c_uint64), ("amalgamate", C.c_int32),
+                ("interior_blocks", C.c_int32)]
 
 
 class rsc_stats_t(C.Structure):

@@ -63,6 +63,7 @@ rsc_status rsc_options_default(rsc_options* o) {
     o->diag_compress = 1;
     o->seed = 0;
     o->amalgamate = 0;
+    o->interior_blocks = 0;
     return RSC_OK;
 }
 
@@ -80,6 +81,8 @@ rsc_status rsc_analyze(int64_t n, const int64_t* row_ptr, const int32_t* col_idx
             return fail(nullptr, RSC_ERR_INVALID_ARG, "power_iters and max_restarts must be >= 0");
         if (o.amalgamate != 0 && o.amalgamate != 1)
             return fail(nullptr, RSC_ERR_INVALID_ARG, "amalgamate must be 0 or 1");
+        if (o.interior_blocks != 0 && o.interior_blocks != 1)
+            return fail(nullptr, RSC_ERR_INVALID_ARG, "interior_blocks must be 0 or 1");
         h = new rsc_handle();
         h->opts = o;
         std::string why = rsc::analyze_symbolic(n, row_ptr, col_idx, val, coords, o, h->sym);

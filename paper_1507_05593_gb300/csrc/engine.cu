@@ -21,6 +21,7 @@
 #include <cstring>
 #include <cstdio>
 #include <map>
+#include <tuple>
 #include <atomic>
 #include <mutex>
 #include <functional>
@@ -757,6 +758,14 @@ rsc_status EngineImpl::pcg(const std::vector<int64_t>& rp, const std::vector<int
 }
 
 // ------------------------------------------------------------------ typed engine
+// Section 5.1: one sparse factor of the interior-block products, A restricted to a row set
+// (CSR rows listed compactly; CSR row i is row rmap[i] of the product's output).
+struct IbCsr { CsrBlock blk{}; const int32_t* rmap = nullptr; int pend = -1; long long moff = 0; };   // pend, moff: plan-time bookkeeping
+// The Eq. interiorBlockMult term of interior block b in the products with a block of L:
+// f (L X): t = A(C_B, cols) X, W(rows) -= A(rows, C_B) L_B^{-T} L_B^{-1} t; t (L^T G) the same with
+// rows and columns exchanged.
+struct IbTerm { int b = 0; IbCsr in_f, out_f, in_t, out_t; };
+
 template <class T>
 struct EngineT final : EngineImpl {
     struct NodeRT {
@@ -782,6 +791,8 @@ struct EngineT final : EngineImpl {
         std::vector<CsrBlock> bR, bC;      // per internal block: A(rows_s, cols_s) by rows / by cols
         int32_t* tailpos = nullptr;        // per descendant: positions of R_k's tail rows inside R_j
         std::vector<long long> tail_off;   // offset of descendant d's tail map inside tailpos
+        int ib = -1;                       // interior block holding this supernode (Section 5.1), -1: none
+        std::vector<std::vector<IbTerm>> ibt;   // by label (0: L^O_j): interior-block terms
     };
 
     const Symbolic& S;
@@ -826,6 +837,73 @@ struct EngineT final : EngineImpl {
     T* lr_base = nullptr;
     long long lr_cap = 0, lr_used = 0;
     std::vector<NodeRT> nd;
+
+    // ---------------------------------------------------------------- interior blocks (Section 5.1)
+    // A maximal subtree of the supernodal tree without a compressed supernode; its supernodes are
+    // the contiguous run first..last (postorder) and its columns C_B = [c0, c1).  Their panels keep
+    // the rows inside C_B only: those rows are the sparse factor L_B = chol(A(C_B, C_B)) (Eq.
+    // interiorDiagonalDef); L(R_B, C_B) is never formed, its uses go through A(., C_B) L_B^{-T}
+    // (Eqs. interiorBlockClosedForm, interiorBlockMult).
+    struct IbEntry { int32_t x, y; long long src; };   // A(x, c0 + y), x outside C_B (x >= c1)
+    struct IBlock {
+        int first = 0, last = 0, root_level = 0;
+        long long c0 = 0, c1 = 0;
+        std::vector<std::vector<int>> lvl;   // the block's supernodes by level (0 .. root_level)
+        std::vector<IbEntry> adj;            // sorted by (x, y)
+        IbCsr fwd, bwd;                      // apply: A(R_B, C_B) by rows x, A(C_B, R_B) by rows y (global)
+    };
+    // A dense target region (a dense diagonal, a diagonal leaf or an uncompressed panel outside
+    // every block) receiving block b's Schur complement C(P, Q) = A(P, C_B) A_BB^{-1} A(C_B, Q):
+    // in = A(C_B, P) (CSR columns index P), out = A(Q, C_B) with rmap = column positions of Q in the
+    // region, cmap = row positions of P; the region is column-major at base with leading dim ld.
+    struct IbDense { int b = 0; T* base = nullptr; int ld = 0; int nP = 0; IbCsr in, out; const int32_t* cmap = nullptr; long long cmoff = 0; };
+    std::vector<IBlock> iblocks;
+    std::vector<std::vector<int>> ib_root;          // by level: blocks whose root is at that level
+    std::vector<std::vector<IbDense>> ib_dense;     // by level of the block root
+    bool ib_on = false;
+    int ib_maxP = 0;
+    T* ib_win = nullptr;     // (2 ib_maxP + 64) x 64, rows ib_maxP .. ib_maxP + 63 the identity
+    T* d_zero = nullptr;     // one zero (source of zero fills)
+
+    // blocks of the current plan; truncates the rows of their supernodes to those inside C_B
+    void find_interior_blocks() {
+        iblocks.clear();
+        ib_root.assign(S.nlevels, {});
+        ib_on = o.interior_blocks != 0;
+        if (!ib_on) return;
+        const int M = S.M;
+        std::vector<char> bad(M);
+        std::vector<int> first(M);
+        for (int j = 0; j < M; ++j) { bad[j] = nd[j].compressed; first[j] = j; }
+        for (int j = 0; j < M; ++j) {   // children precede their parents
+            const int p = S.parent[j];
+            if (p >= 0) {
+                if (p <= j) throw Error(RSC_ERR_INVALID_ARG, "supernodes not in postorder");
+                bad[p] = bad[p] || bad[j];
+                first[p] = std::min(first[p], first[j]);
+            }
+        }
+        for (int j = 0; j < M; ++j) {
+            const int p = S.parent[j];
+            if (bad[j] || (p >= 0 && !bad[p])) continue;   // not the root of a maximal clean subtree
+            IBlock B;
+            B.first = first[j];
+            B.last = j;
+            B.c0 = S.sn_ptr[first[j]];
+            B.c1 = S.sn_ptr[j + 1];
+            B.root_level = S.level[j];
+            B.lvl.assign(B.root_level + 1, {});
+            for (int k = B.first; k <= j; ++k) {
+                if (bad[k] || S.level[k] > B.root_level) throw Error(RSC_ERR_INVALID_ARG, "interior block not contiguous");
+                nd[k].ib = (int)iblocks.size();
+                B.lvl[S.level[k]].push_back(k);
+                const int32_t* Rk = S.R(k);
+                nd[k].r = (int)(std::lower_bound(Rk, Rk + S.nrows(k), (int32_t)B.c1) - Rk);
+            }
+            ib_root[B.root_level].push_back((int)iblocks.size());
+            iblocks.push_back(std::move(B));
+        }
+    }
     bool plan_compress = false, plan_diag = false, have_plan = false;
     bool is_factored = false;
     double tol = 0.0, tol_D = 0.0;
@@ -929,6 +1007,10 @@ struct EngineT final : EngineImpl {
             n.c0 = S.sn_ptr[j];
             n.compressed = compress && S.kind[j] == 1 && n.c >= o.tau_O;
             n.hier = n.compressed && diag && S.tree[j].nblocks > 0;
+        }
+        find_interior_blocks();
+        for (int j = 0; j < M; ++j) {
+            NodeRT& n = nd[j];
             if (!n.compressed) {
                 n.off = off;
                 n.ld = n.c + n.r;
@@ -1056,8 +1138,14 @@ struct EngineT final : EngineImpl {
             const NodeRT& n = nd[j];
             const int lc = (int)(c - n.c0);
             const int32_t* Rj = S.R(j);
+            const long long bc1 = n.ib >= 0 ? iblocks[n.ib].c1 : S.n;
             for (long long e = S.lp[c]; e < S.lp[c + 1]; ++e) {
                 const long long g = S.li[e];
+                if (g >= bc1) {   // A(R_B, C_B): kept sparse for the closed forms
+                    IBlock& B = iblocks[n.ib];
+                    B.adj.push_back(IbEntry{(int32_t)g, (int32_t)(c - B.c0), S.lsrc[e]});
+                    continue;
+                }
                 const bool inC = g < n.c0 + n.c;
                 const int lr = inC ? (int)(g - n.c0) : (int)(std::lower_bound(Rj, Rj + n.r, (int32_t)g) - Rj);
                 if (!n.compressed) {
@@ -1137,11 +1225,204 @@ struct EngineT final : EngineImpl {
                     }
             }
         }
+        // interior blocks (Section 5.1): sparse factors of the closed forms, rows listed compactly
+        std::vector<int32_t> ibmap;
+        ib_dense.assign(S.nlevels, {});
+        ib_maxP = 0;
+        if (ib_on) {
+            struct Ent { long long key; int col; long long src; };
+            // CSR over the distinct keys (ascending); CSR row i is output row keymap(key_i)
+            auto ib_build = [&](std::vector<Ent>& ent, auto keymap, IbCsr& dst) {
+                std::sort(ent.begin(), ent.end(), [](const Ent& a, const Ent& b) {
+                    return a.key != b.key ? a.key < b.key : a.col < b.col;
+                });
+                std::vector<Coo> coo;
+                std::vector<int32_t> rm;
+                long long last = -1;
+                for (const Ent& e : ent) {
+                    if (rm.empty() || e.key != last) { rm.push_back((int32_t)keymap(e.key)); last = e.key; }
+                    coo.push_back(Coo{(int)rm.size() - 1, e.col, e.src});
+                }
+                dst.pend = (int)pend.size();
+                add_csr(coo, (int)rm.size(), true, -1, 0);
+                dst.moff = (long long)ibmap.size();
+                ibmap.insert(ibmap.end(), rm.begin(), rm.end());
+            };
+            auto ident = [](long long k) { return k; };
+            for (IBlock& B : iblocks) {
+                std::sort(B.adj.begin(), B.adj.end(), [](const IbEntry& a, const IbEntry& b) {
+                    return a.x != b.x ? a.x < b.x : a.y < b.y;
+                });
+                std::vector<Ent> f, bw;
+                for (const IbEntry& e : B.adj) {
+                    f.push_back(Ent{e.x, (int)(B.c0 + e.y), e.src});
+                    bw.push_back(Ent{e.y, e.x, e.src});
+                }
+                const long long c0 = B.c0;
+                ib_build(f, ident, B.fwd);
+                ib_build(bw, [c0](long long k) { return c0 + k; }, B.bwd);
+            }
+            // entries of block B with x in the global range [g0, g1)
+            auto in_range = [](const IBlock& B, long long g0, long long g1) {
+                auto lo = std::lower_bound(B.adj.begin(), B.adj.end(), g0,
+                                           [](const IbEntry& e, long long g) { return (long long)e.x < g; });
+                auto hi = std::lower_bound(lo, B.adj.end(), g1,
+                                           [](const IbEntry& e, long long g) { return (long long)e.x < g; });
+                return std::make_pair(lo, hi);
+            };
+            // Eq. interiorBlockMult terms of the compressed supernodes
+            for (int j = 0; j < M; ++j) {
+                NodeRT& n = nd[j];
+                if (!n.compressed) continue;
+                std::vector<int> bl;
+                for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d)
+                    if (nd[S.desc_k[d]].ib >= 0) bl.push_back(nd[S.desc_k[d]].ib);
+                std::sort(bl.begin(), bl.end());
+                bl.erase(std::unique(bl.begin(), bl.end()), bl.end());
+                if (bl.empty()) continue;
+                const BlockTree& bt = S.tree[j];
+                const int nlab = n.hier ? bt.nblocks : 0;
+                n.ibt.assign(nlab + 1, {});
+                const int32_t* Rj = S.R(j);
+                for (int b : bl) {
+                    const IBlock& B = iblocks[b];
+                    auto rc = in_range(B, n.c0, n.c0 + n.c);
+                    std::vector<IbEntry> inC(rc.first, rc.second), inR;
+                    for (const IbEntry& e : B.adj) {
+                        if (e.x < n.c0 + n.c) continue;
+                        const int pos = (int)(std::lower_bound(Rj, Rj + n.r, e.x) - Rj);
+                        if (pos < n.r && Rj[pos] == e.x) inR.push_back(IbEntry{pos, e.y, e.src});
+                    }
+                    for (IbEntry& e : inC) e.x -= (int32_t)n.c0;   // local to C_j
+                    // rows / columns of the block of L the product is taken with: (X in ro, C_B), (X in co, C_B)
+                    auto term = [&](const std::vector<IbEntry>& ro, const std::vector<IbEntry>& co, int rbase, int cbase,
+                                    std::vector<IbTerm>& dst) {
+                        if (ro.empty() || co.empty()) return;
+                        IbTerm tm;
+                        tm.b = b;
+                        std::vector<Ent> e1, e2, e3, e4;
+                        for (const IbEntry& e : co) {
+                            e1.push_back(Ent{e.y, e.x - cbase, e.src});    // in_f: t = A(C_B, cols) X
+                            e4.push_back(Ent{e.x - cbase, e.y, e.src});    // out_t: W(cols) -= A(cols, C_B) t
+                        }
+                        for (const IbEntry& e : ro) {
+                            e2.push_back(Ent{e.x - rbase, e.y, e.src});    // out_f: W(rows) -= A(rows, C_B) t
+                            e3.push_back(Ent{e.y, e.x - rbase, e.src});    // in_t: t = A(C_B, rows) G
+                        }
+                        ib_build(e1, ident, tm.in_f);
+                        ib_build(e2, ident, tm.out_f);
+                        ib_build(e3, ident, tm.in_t);
+                        ib_build(e4, ident, tm.out_t);
+                        dst.push_back(tm);
+                    };
+                    term(inR, inC, 0, 0, n.ibt[0]);   // L^O_j: rows R_j, columns C_j
+                    for (int sl = 1; sl <= nlab; ++sl) {
+                        if (bt.leaf[sl]) continue;
+                        std::vector<IbEntry> ro, co;
+                        for (const IbEntry& e : inC) {
+                            if (e.x >= bt.mid[sl] && e.x < bt.hi[sl]) ro.push_back(e);
+                            if (e.x >= bt.lo[sl] && e.x < bt.mid[sl]) co.push_back(e);
+                        }
+                        term(ro, co, bt.mid[sl], bt.lo[sl], n.ibt[sl]);
+                    }
+                }
+            }
+            // dense targets of each block's Schur complement
+            for (int b = 0; b < (int)iblocks.size(); ++b) {
+                const IBlock& B = iblocks[b];
+                std::vector<int> tj;
+                for (const IbEntry& e : B.adj) tj.push_back(S.snode_of[e.x]);
+                std::sort(tj.begin(), tj.end());
+                tj.erase(std::unique(tj.begin(), tj.end()), tj.end());
+                // P: (storage row position, entry), Q: (storage column position, entry)
+                auto region = [&](std::vector<std::pair<int, IbEntry>>& P, std::vector<std::pair<int, IbEntry>>& Q, T* base,
+                                  int ld) {
+                    if (P.empty() || Q.empty()) return;
+                    IbDense dn;
+                    dn.b = b;
+                    dn.base = base;
+                    dn.ld = ld;
+                    std::vector<int32_t> pkeys;   // distinct x of P in order, and their row positions
+                    std::vector<int32_t> prow;
+                    std::vector<Ent> ein, eout;
+                    for (auto& pe : P) {
+                        if (pkeys.empty() || pkeys.back() != pe.second.x) { pkeys.push_back(pe.second.x); prow.push_back(pe.first); }
+                        ein.push_back(Ent{pe.second.y, (int)pkeys.size() - 1, pe.second.src});
+                    }
+                    std::map<long long, int> pcol;
+                    for (auto& qe : Q) {
+                        pcol[qe.second.x] = qe.first;
+                        eout.push_back(Ent{qe.second.x, qe.second.y, qe.second.src});
+                    }
+                    dn.nP = (int)pkeys.size();
+                    ib_build(ein, ident, dn.in);
+                    ib_build(eout, [&](long long x) { return (long long)pcol[x]; }, dn.out);
+                    dn.cmoff = (long long)ibmap.size();
+                    ibmap.insert(ibmap.end(), prow.begin(), prow.end());
+                    ib_maxP = std::max(ib_maxP, dn.nP);
+                    ib_dense[B.root_level].push_back(dn);
+                };
+                for (int j : tj) {
+                    const NodeRT& n = nd[j];
+                    auto rc = in_range(B, n.c0, n.c0 + n.c);
+                    if (rc.first == rc.second) continue;
+                    if (!n.compressed) {   // an uncompressed panel outside every block: rows C_j and R_j
+                        const int32_t* Rj = S.R(j);
+                        std::vector<std::pair<int, IbEntry>> P, Q;
+                        for (auto it = rc.first; it != rc.second; ++it) {
+                            P.push_back({(int)(it->x - n.c0), *it});
+                            Q.push_back({(int)(it->x - n.c0), *it});
+                        }
+                        for (auto it = rc.second; it != B.adj.end(); ++it) {
+                            const int pos = (int)(std::lower_bound(Rj, Rj + n.r, it->x) - Rj);
+                            if (pos < n.r && Rj[pos] == it->x) P.push_back({n.c + pos, *it});
+                        }
+                        region(P, Q, arena + n.off, n.ld);
+                    } else if (!n.hier) {
+                        std::vector<std::pair<int, IbEntry>> P;
+                        for (auto it = rc.first; it != rc.second; ++it) P.push_back({(int)(it->x - n.c0), *it});
+                        region(P, P, arena + n.off, n.c);
+                    } else {
+                        const BlockTree& bt = S.tree[j];
+                        for (int sl = 1; sl <= bt.nblocks; ++sl) {
+                            if (!bt.leaf[sl]) continue;
+                            auto lr = in_range(B, n.c0 + bt.lo[sl], n.c0 + bt.hi[sl]);
+                            std::vector<std::pair<int, IbEntry>> P;
+                            for (auto it = lr.first; it != lr.second; ++it) P.push_back({(int)(it->x - n.c0 - bt.lo[sl]), *it});
+                            region(P, P, arena + n.leaf_off[sl], bt.hi[sl] - bt.lo[sl]);
+                        }
+                    }
+                }
+            }
+        }
         int32_t* d_sprp = pmem.upload(sp_rp, stream);
         int32_t* d_spci = pmem.upload(sp_ci, stream);
         d_spval = (double*)pmem.alloc(sizeof(double) * std::max<size_t>(sp_src.size(), 1));
         d_spsrc = pmem.upload(sp_src, stream);   // for values given on the device
+        if (ib_on) {
+            int32_t* d_ibmap = pmem.upload(ibmap, stream);
+            auto resolve = [&](IbCsr& c) {
+                if (c.pend < 0) return;
+                const PendingBlk& pb = pend[c.pend];
+                c.blk = CsrBlock{d_sprp + pb.rp_off, d_spci + pb.ci_off, d_spval + pb.v_off, pb.nrows, 0};
+                c.rmap = d_ibmap + c.moff;
+            };
+            for (IBlock& B : iblocks) { resolve(B.fwd); resolve(B.bwd); }
+            for (NodeRT& n : nd)
+                for (auto& v : n.ibt)
+                    for (IbTerm& t : v) { resolve(t.in_f); resolve(t.out_f); resolve(t.in_t); resolve(t.out_t); }
+            for (auto& v : ib_dense)
+                for (IbDense& d : v) { resolve(d.in); resolve(d.out); d.cmap = d_ibmap + d.cmoff; }
+            if (ib_maxP > 0) {
+                std::vector<T> win((size_t)(2 * ib_maxP + 64) * 64, T(0));
+                for (int i = 0; i < 64; ++i) win[(size_t)(ib_maxP + i) * 64 + i] = T(1);
+                ib_win = pmem.upload(win, stream);
+            }
+            d_zero = (T*)pmem.alloc(256);
+            CK(cudaMemsetAsync(d_zero, 0, 256, stream));
+        }
         for (auto& pb : pend) {
+            if (pb.node < 0) continue;   // interior-block factors, resolved above
             CsrBlock b{d_sprp + pb.rp_off, d_spci + pb.ci_off, d_spval + pb.v_off, pb.nrows, 0};
             NodeRT& n = nd[pb.node];
             if (pb.label == 0) (pb.orient == 0 ? n.aR : n.aC) = b;
@@ -1222,7 +1503,8 @@ struct EngineT final : EngineImpl {
             for (int j = 0; j < M; ++j)
                 for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
                     const int k = S.desc_k[d];
-                    const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+                    if (nd[k].ib >= 0 && nd[j].ib != nd[k].ib) continue;   // Section 5.1: the closed forms
+                    const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = nd[k].r;
                     const int rend = nd[j].compressed ? p1 : rk;
                     const double w = p1 - p0, h = rend - p0;
                     elems[k] += w * (w + 1) / 2 + (h - w) * w;
@@ -1246,7 +1528,8 @@ struct EngineT final : EngineImpl {
                 for (int j = 0; j < M; ++j)
                     for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
                         const int k = S.desc_k[d];
-                        const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
+                        if (nd[k].ib >= 0 && nd[j].ib != nd[k].ib) continue;
+                        const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = nd[k].r;
                         const int rend = nd[j].compressed ? p1 : rk;
                         for (int pc = p0; pc < p1; pc += TC_N)
                             for (int pr = pc; pr < rend; pr += TC_M)
@@ -1262,7 +1545,7 @@ struct EngineT final : EngineImpl {
         if (dense_graph) { cudaGraphExecDestroy(dense_graph); dense_graph = nullptr; }
         dense_prefix = 0;
         for (int l = 0; l < S.nlevels; ++l) {
-            bool any = false;
+            bool any = !ib_dense[l].empty();   // interior-block Schur complements run as programs
             for (int j : S.level_nodes[l]) any |= nd[j].compressed;
             if (any) break;
             dense_prefix = l + 1;
@@ -1638,6 +1921,131 @@ struct EngineT final : EngineImpl {
     };
     Workspace ws;
     T* wsT(size_t n) { return (T*)ws.getb(sizeof(T) * n); }
+    // t buffers of the interior-block terms, kept for the products that write the same output
+    // (the passes of one range finder reuse theirs; the workspace reset drops them)
+    std::map<std::tuple<const void*, int, int, int>, T*> ib_tcache;
+    void ws_reset() { ws.reset(); ib_tcache.clear(); }
+
+    // ---------------------------------------------------------------- interior blocks (programs)
+    // Stage i of sub joins stage at + i of P.
+    static void merge_into(Program& P, size_t at, Program& sub) {
+        if (P.size() < at + sub.size()) P.resize(at + sub.size());
+        for (size_t i = 0; i < sub.size(); ++i) {
+            Stage& d = P[at + i];
+            Stage& s = sub[i];
+            const long long hb = (long long)d.hacts.size();
+            d.hacts.insert(d.hacts.end(), s.hacts.begin(), s.hacts.end());
+            for (HTask h : s.hs) { h.acts = (const HAct*)(intptr_t)((intptr_t)h.acts + hb); d.hs.push_back(h); }
+            d.gauss.insert(d.gauss.end(), s.gauss.begin(), s.gauss.end());
+            d.copy.insert(d.copy.end(), s.copy.begin(), s.copy.end());
+            d.csr.insert(d.csr.end(), s.csr.begin(), s.csr.end());
+            d.trsv.insert(d.trsv.end(), s.trsv.begin(), s.trsv.end());
+            d.tn.insert(d.tn.end(), s.tn.begin(), s.tn.end());
+            d.nn.insert(d.nn.end(), s.nn.begin(), s.nn.end());
+        }
+    }
+    static void add_csr_map(Stage& s, const IbCsr& b, const T* X, int ldx, T* Y, int ldy, int N, double alpha,
+                            const int32_t* cmap, int mode, int lower) {
+        for (int r0 = 0; r0 < b.blk.nrows; r0 += 16) {
+            CsrTask t{b.blk, X, ldx, Y, ldy, N, r0, alpha};
+            t.rmap = b.rmap;
+            t.cmap = cmap;
+            t.mode = mode;
+            t.lower = lower;
+            s.csr.push_back(t);
+        }
+    }
+    // t (|C_B| x N, row-major, rows local to C_B) <- L_B^{-1} t or L_B^{-T} t: the block's
+    // supernodes level by level, each with its diagonal solve and its panel rows inside C_B.
+    void prog_block_solve(Program& P, int b, T* t, int N, bool transpose) {
+        const IBlock& B = iblocks[b];
+        const int nl = (int)B.lvl.size();
+        for (int li = 0; li < nl; ++li) {
+            const int lv = transpose ? nl - 1 - li : li;
+            const std::vector<int>& nodes = B.lvl[lv];
+            if (nodes.empty()) continue;
+            if (transpose) {   // t[C_k] -= L(R_k in C_B, C_k)^T t[R_k in C_B]
+                Stage st;
+                for (int k : nodes) {
+                    const NodeRT& n = nd[k];
+                    add_tn(st, tn_task(arena + n.off + n.c, n.ld, n.c, n.r, nullptr, 0, d_rows + S.rows_ptr[k], (int)-B.c0,
+                                       t, N, t + (size_t)(n.c0 - B.c0) * N, N, N, -1.0, 1.0));
+                }
+                if (!st.tn.empty()) P.push_back(std::move(st));
+            }
+            const size_t base = P.size();
+            for (int k : nodes) {
+                Program sub;
+                prog_diag_solve(sub, k, 0, t + (size_t)(nd[k].c0 - B.c0) * N, N, N, transpose);
+                merge_into(P, base, sub);
+            }
+            if (!transpose) {   // t[R_k in C_B] -= L(R_k in C_B, C_k) t[C_k]; after the level's solves
+                Stage& st = P.back();
+                for (int k : nodes) {
+                    const NodeRT& n = nd[k];
+                    add_nn(st, nn_task(arena + n.off + n.c, n.ld, n.c, n.r, nullptr, 0, d_rows + S.rows_ptr[k], (int)-B.c0,
+                                       t + (size_t)(n.c0 - B.c0) * N, N, t, N, N, -1.0, true));
+                }
+            }
+        }
+    }
+    // Eq. interiorBlockMult for every interior block meeting label s of supernode j: stage `at` of
+    // P starts W(out) -= A(out, C_B) L_B^{-T} L_B^{-1} A(C_B, in) X (in / out: columns / rows of the
+    // block of L, exchanged for the transpose); the terms end before the stages appended after.
+    void ib_chains(Program& P, size_t at, int j, int s, bool transpose, const T* X, int ldx, T* W, int ldw, int N) {
+        const NodeRT& n = nd[j];
+        if ((int)n.ibt.size() <= s) return;
+        for (size_t i = 0; i < n.ibt[s].size(); ++i) {
+            const IbTerm& tm = n.ibt[s][i];
+            const IBlock& B = iblocks[tm.b];
+            const IbCsr& in = transpose ? tm.in_t : tm.in_f;
+            const IbCsr& out = transpose ? tm.out_t : tm.out_f;
+            const int nb = (int)(B.c1 - B.c0);
+            T*& t = ib_tcache[std::make_tuple((const void*)W, s, (int)i, N)];
+            if (!t) t = wsT((size_t)nb * N);
+            Program sub;
+            add_copy(next(sub), d_zero, 0, 0, t, N, 1, nb, N);   // t = 0, then the listed rows
+            add_csr_map(sub.back(), in, X, ldx, t, N, N, 1.0, nullptr, 0, 0);
+            prog_block_solve(sub, tm.b, t, N, false);
+            prog_block_solve(sub, tm.b, t, N, true);
+            add_csr_map(next(sub), out, t, N, W, ldw, N, -1.0, nullptr, 2, 0);
+            merge_into(P, at, sub);
+        }
+    }
+    // Schur complements of the blocks whose root is at level l into their dense targets,
+    // C(P, Q) = A(P, C_B) L_B^{-T} L_B^{-1} A(C_B, Q) for 64 columns of P per program, the
+    // lower triangle subtracted in place (Section 5.1: the needed sub-blocks of L(R_B, C_B)
+    // appear only through the closed form).
+    static constexpr size_t IB_WS_CAP = (size_t)512 << 20;
+    void ib_dense_level(int l) {
+        if (!ib_on || ib_dense[l].empty()) return;
+        const std::vector<IbDense>& v = ib_dense[l];
+        size_t i = 0;
+        while (i < v.size()) {
+            ws_reset();
+            std::vector<Program> progs;
+            size_t bytes = 0;
+            for (; i < v.size() && bytes < IB_WS_CAP; ++i) {
+                const IbDense& d = v[i];
+                const IBlock& B = iblocks[d.b];
+                const int nb = (int)(B.c1 - B.c0);
+                for (int p0 = 0; p0 < d.nP; p0 += 64) {
+                    const int N = std::min(64, d.nP - p0);
+                    T* t = wsT((size_t)nb * N);
+                    bytes += sizeof(T) * (size_t)nb * N;
+                    progs.emplace_back();
+                    Program& P = progs.back();
+                    add_copy(next(P), d_zero, 0, 0, t, N, 1, nb, N);
+                    // columns p0 .. p0 + N - 1 of the identity over P: the window's rows ib_maxP ..
+                    add_csr_map(P.back(), d.in, ib_win + (size_t)(ib_maxP - p0) * 64, 64, t, N, N, 1.0, nullptr, 0, 0);
+                    prog_block_solve(P, d.b, t, N, false);
+                    prog_block_solve(P, d.b, t, N, true);
+                    add_csr_map(next(P), d.out, t, N, d.base, d.ld, N, -1.0, d.cmap + p0, 2, 1);
+                }
+            }
+            run(progs);
+        }
+    }
 
     // ---------------------------------------------------------------- dense / hierarchical triangular solves (programs)
     // Action list of the solve with the subtree of L^D_j rooted at s (0: whole block),
@@ -1837,11 +2245,13 @@ struct EngineT final : EngineImpl {
 
     void prog_offdiag_T(Program& P, int j, const T* G, int N, T* W) {
         const NodeRT& n = nd[j];
+        const size_t base = P.size();
         Stage& st = next(P);
         add_csr(st, n.aC, G, N, W, N, N);
         int di = 0;
         for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
             const int k = S.desc_k[d];
+            if (nd[k].ib >= 0) continue;   // interior blocks: the Eq. interiorBlockMult terms
             const LoOp& op = lo(k);
             const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
             if (op.K == 0 || rk == p1) continue;          // empty R^O: no contribution
@@ -1851,6 +2261,7 @@ struct EngineT final : EngineImpl {
             add_nn(st, nn_task(op.base, op.ld, op.K, p1 - p0, nullptr, p0, d_rows + S.rows_ptr[k] + p0, (int)-n.c0, Z, N,
                                W, N, N, -1.0, true));
         }
+        ib_chains(P, base, j, 0, true, G, N, W, N, N);
         if (inverse_ready(j)) prog_diag_solve_inv(P, j, W, N, N, false);
         else prog_diag_solve(P, j, 0, W, N, N, false);
     }
@@ -1861,11 +2272,13 @@ struct EngineT final : EngineImpl {
         add_copy(next(P), X, N, 1, Xp, N, 1, n.c, N);
         if (inverse_ready(j)) prog_diag_solve_inv(P, j, Xp, N, N, true);
         else prog_diag_solve(P, j, 0, Xp, N, N, true);
+        const size_t base = P.size();
         Stage& st = next(P);
         add_csr(st, n.aR, Xp, N, W, N, N);
         int di = 0;
         for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d, ++di) {
             const int k = S.desc_k[d];
+            if (nd[k].ib >= 0) continue;   // interior blocks: the Eq. interiorBlockMult terms
             const LoOp& op = lo(k);
             const int p0 = S.desc_p0[d], p1 = S.desc_p1[d], rk = S.nrows(k);
             if (op.K == 0 || rk == p1) continue;
@@ -1876,6 +2289,7 @@ struct EngineT final : EngineImpl {
             add_nn(st, nn_task(op.base, op.ld, op.K, rk - p1, nullptr, p1, n.tailpos + n.tail_off[di], 0, Z, N, W, N, N,
                                -1.0, true));
         }
+        ib_chains(P, base, j, 0, false, Xp, N, W, N, N);
     }
 
     // positions of R_k inside the global range [g0, g1) (a sub-run of the C_j run)
@@ -1896,6 +2310,7 @@ struct EngineT final : EngineImpl {
         const long long gin = n.c0 + (transpose ? r0 : q0), gout = n.c0 + (transpose ? q0 : r0);
         for (long long d = S.desc_ptr[j]; d < S.desc_ptr[j + 1]; ++d) {
             const int k = S.desc_k[d];
+            if (nd[k].ib >= 0) continue;   // interior blocks: the Eq. interiorBlockMult terms
             const LoOp& op = lo(k);
             if (op.K == 0) continue;
             int a0, a1, b0, b1;
@@ -1929,18 +2344,22 @@ struct EngineT final : EngineImpl {
         const int cs = t.mid[s] - t.lo[s];
         add_copy(next(P), X, N, 1, Xp, N, 1, cs, N);
         prog_diag_solve(P, j, t.left[s], Xp, N, N, true);
+        const size_t base = P.size();
         Stage& st = next(P);
         add_csr(st, n.bR[s], Xp, N, W, N, N);
         diag_terms(st, j, s, Xp, N, W, false);
+        ib_chains(P, base, j, s, false, Xp, N, W, N, N);
     }
 
     // Alg. 5 transposed: W (|cols_s| x N) = (L^D_{j,s})^T G, G (|rows_s| x N).
     void prog_diag_mult_T(Program& P, int j, int s, const T* G, int N, T* W) {
         const NodeRT& n = nd[j];
         const BlockTree& t = S.tree[j];
+        const size_t base = P.size();
         Stage& st = next(P);
         add_csr(st, n.bC[s], G, N, W, N, N);
         diag_terms(st, j, s, G, N, W, true);
+        ib_chains(P, base, j, s, true, G, N, W, N, N);
         prog_diag_solve(P, j, t.left[s], W, N, N, false);
     }
 
@@ -2026,7 +2445,7 @@ struct EngineT final : EngineImpl {
     size_t rank_host_cap = 0;
     std::map<int, T*> ident;             // c x c identities of the current dense batch
     void range_finder_dense(std::vector<RF>& R) {
-        ws.reset();
+        ws_reset();
         ident.clear();
         if (R.size() > rank_host_cap) {
             if (rank_host) CK(cudaFreeHost(rank_host));
@@ -2087,7 +2506,7 @@ struct EngineT final : EngineImpl {
 
     void range_finder_batch_coop(std::vector<RF>& R) {
         if (R.empty()) return;
-        ws.reset();
+        ws_reset();
         if (!coop_max) {
             int dev = 0, nsm = 0, per_sm = 0;
             CK(cudaGetDevice(&dev));
@@ -2259,7 +2678,7 @@ struct EngineT final : EngineImpl {
     // with D the block diagonal of the leaves: every term reads x, so the preconditioner
     // applies the diagonal solve as three parallel launches instead of the in-order chain.
     void inverse_factors(const std::vector<int>& hier) {
-        ws.reset();
+        ws_reset();
         std::vector<Program> progs;
         for (int j : hier) {
             NodeRT& n = nd[j];
@@ -2564,6 +2983,7 @@ struct EngineT final : EngineImpl {
             // extend-add of the level into its ancestors
             CK(cudaMemcpyAsync(d_lo, h_lo.data(), sizeof(LoOp) * S.M, cudaMemcpyHostToDevice, stream));
             issue_push(l);
+            ib_dense_level(l);
             sync_stream();   // h_lo is rewritten by the next level
             if (prof.on) {
                 char nm[32];
@@ -2573,7 +2993,7 @@ struct EngineT final : EngineImpl {
         }
         // push flops: lower half of L^O_k L^O_k^T per source
         for (int k = 0; k < S.M; ++k) {
-            const double rk = S.nrows(k), K = h_lo[k].K;
+            const double rk = nd[k].r, K = h_lo[k].K;
             flops += rk * (rk + 1) * K;
         }
         prof.tag.clear();
@@ -2662,7 +3082,7 @@ struct EngineT final : EngineImpl {
     //   backward, levels in reverse: y_C -= L^O^T y_R (or U (V^T y_R)), the actions
     //   in reverse order, the transposed small dense solves.
     // It is captured once into a CUDA graph reading g_in and writing g_out.
-    enum LKind { L_PERM_IN, L_PERM_OUT, L_TRSV, L_TN, L_NN, L_HSOLVE };
+    enum LKind { L_PERM_IN, L_PERM_OUT, L_TRSV, L_TN, L_NN, L_HSOLVE, L_COPY, L_CSR };
     struct Launch { int kind; int count; size_t off; int flag; };
     // one launch list (and its CUDA graph) per number of right-hand sides: plan1 for the PCG of
     // one system, planN for the batched PCG (N columns of y, row-major)
@@ -2679,6 +3099,9 @@ struct EngineT final : EngineImpl {
         TrsvTask* trsv = nullptr;
         TnTask* tn = nullptr;
         NnTask* nn = nullptr;
+        CopyTask* copy = nullptr;        // interior blocks (Section 5.1)
+        CsrTask* csr = nullptr;
+        T* y2 = nullptr;                 // second work vector: the interior blocks' solves
         cudaGraphExec_t graph = nullptr;
         long long gen = -1;              // factorization the plan was built for
         double flops = 0, bytes = 0;
@@ -2698,6 +3121,8 @@ struct EngineT final : EngineImpl {
         std::vector<TrsvTask> trsv;
         std::vector<TnTask> tn;
         std::vector<NnTask> nn;
+        std::vector<CopyTask> copy;
+        std::vector<CsrTask> csr;
     };
     struct Act { std::vector<TrsvTask> trsv; std::vector<TnTask> tn; std::vector<NnTask> nn; };
 
@@ -2831,6 +3256,103 @@ struct EngineT final : EngineImpl {
             }
             if (HT.size() > o) pl->seq.push_back(Launch{L_HSOLVE, (int)(HT.size() - o), o, maxc});
         };
+        // Section 5.1: an interior block's part of the forward substitution ends with
+        // y[R_B] -= A(R_B, C_B) L_B^{-T} y[C_B]; the backward one starts with
+        // y[C_B] -= L_B^{-1} A(C_B, R_B) y[R_B]; both solves with L_B run on the second vector y2
+        // (rows C_B), the block's supernodes level by level as in the main sweep.
+        if (ib_on) pl->y2 = (T*)pl->mem.alloc(sizeof(T) * n * N);
+        auto ib_solve = [&](const std::vector<int>& bl, int top, bool transpose) {
+            T* keep = pl->y;
+            pl->y = pl->y2;
+            for (int li = 0; li <= top; ++li) {
+                const int lv = transpose ? top - li : li;
+                std::vector<int> nodes;
+                for (int b : bl)
+                    if (lv < (int)iblocks[b].lvl.size())
+                        nodes.insert(nodes.end(), iblocks[b].lvl[lv].begin(), iblocks[b].lvl[lv].end());
+                if (nodes.empty()) continue;
+                if (transpose) {   // y2[C_k] -= L(R_k in C_B, C_k)^T y2[R_k in C_B]
+                    const size_t o2 = B.tn.size();
+                    for (int j : nodes) {
+                        const NodeRT& nn = nd[j];
+                        if (nn.r == 0) continue;
+                        push_tn_chunks(B.tn, vtn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, d_rows + S.rows_ptr[j], 0,
+                                                 pl->y + nn.c0 * N, -1.0, 1.0));
+                        pl->bytes += sizeof(T) * (double)nn.r * nn.c;
+                    }
+                    emit(L_TN, o2, B.tn.size() - o2, 0);
+                }
+                std::vector<std::vector<Act>> acts;
+                std::vector<int> big;
+                const size_t o = B.trsv.size();
+                for (int j : nodes) {
+                    const NodeRT& nn = nd[j];
+                    pl->bytes += sizeof(T) * ((double)nn.c * (nn.c + 1) / 2);
+                    if (nn.c <= SOLVE_MAX)
+                        B.trsv.push_back(TrsvTask{inv_block(j, 0), nn.c, nn.c, N, pl->y + nn.c0 * N, N, transpose ? 1 : 0});
+                    else big.push_back(j);
+                }
+                emit(L_TRSV, o, B.trsv.size() - o, 0);
+                emit_hsolve(big, transpose, acts);
+                emit_acts(acts);
+                if (!transpose) {   // y2[R_k in C_B] -= L(R_k in C_B, C_k) y2[C_k]
+                    const size_t o3 = B.nn.size();
+                    for (int j : nodes) {
+                        const NodeRT& nn = nd[j];
+                        if (nn.r == 0) continue;
+                        push_nn_chunks(B.nn, vnn(arena + nn.off + nn.c, nn.ld, nn.c, nn.r, d_rows + S.rows_ptr[j], 0,
+                                                 pl->y + nn.c0 * N, true));
+                        pl->bytes += sizeof(T) * (double)nn.r * nn.c;
+                    }
+                    emit(L_NN, o3, B.nn.size() - o3, 0);
+                }
+            }
+            pl->y = keep;
+        };
+        auto ib_csr = [&](const IbCsr& c, const T* X, T* Y, double alpha, int mode) {
+            for (int r0 = 0; r0 < c.blk.nrows; r0 += 16) {
+                CsrTask t{c.blk, X, N, Y, N, N, r0, alpha};
+                t.rmap = c.rmap;
+                t.mode = mode;
+                B.csr.push_back(t);
+            }
+        };
+        auto ib_forward = [&](int l) {
+            if (!ib_on || ib_root[l].empty()) return;
+            const std::vector<int>& bl = ib_root[l];
+            size_t oc = B.copy.size();
+            for (int b : bl) {   // y2[C_B] = y[C_B]
+                const IBlock& Bk = iblocks[b];
+                const long long m = (Bk.c1 - Bk.c0) * N;
+                B.copy.push_back(CopyTask{pl->y + Bk.c0 * N, 1, 0, pl->y2 + Bk.c0 * N, 1, 0, (int)m, 1, 0});
+            }
+            emit(L_COPY, oc, B.copy.size() - oc, 0);
+            ib_solve(bl, l, true);
+            const size_t os = B.csr.size();
+            for (int b : bl) ib_csr(iblocks[b].fwd, pl->y2, pl->y, -1.0, 2);   // y[R_B] -= A(R_B, C_B) y2[C_B]
+            emit(L_CSR, os, B.csr.size() - os, 0);
+        };
+        auto ib_backward = [&](int l) {
+            if (!ib_on || ib_root[l].empty()) return;
+            const std::vector<int>& bl = ib_root[l];
+            size_t oc = B.copy.size();
+            for (int b : bl) {   // y2[C_B] = 0
+                const IBlock& Bk = iblocks[b];
+                B.copy.push_back(CopyTask{d_zero, 0, 0, pl->y2 + Bk.c0 * N, 1, 0, (int)((Bk.c1 - Bk.c0) * N), 1, 0});
+            }
+            emit(L_COPY, oc, B.copy.size() - oc, 0);
+            const size_t os = B.csr.size();
+            for (int b : bl) ib_csr(iblocks[b].bwd, pl->y, pl->y2, 1.0, 0);   // y2[C_B] = A(C_B, R_B) y[R_B]
+            emit(L_CSR, os, B.csr.size() - os, 0);
+            ib_solve(bl, l, false);
+            oc = B.copy.size();
+            for (int b : bl) {   // y[C_B] -= y2[C_B]
+                const IBlock& Bk = iblocks[b];
+                const long long m = (Bk.c1 - Bk.c0) * N;
+                B.copy.push_back(CopyTask{pl->y2 + Bk.c0 * N, 1, 0, pl->y + Bk.c0 * N, 1, 0, (int)m, 1, 1});
+            }
+            emit(L_COPY, oc, B.copy.size() - oc, 0);
+        };
         emit(L_PERM_IN, 0, 1, 0);
         std::vector<std::vector<T*>> ztmp(S.nlevels);
         // hierarchical diagonal blocks through the factors of their inverse: per level, the
@@ -2909,8 +3431,10 @@ struct EngineT final : EngineImpl {
             }
             emit(L_TN, o2, B.tn.size() - o2, 0);
             emit(L_NN, o3, B.nn.size() - o3, 0);
+            ib_forward(l);
         }
         for (int l = S.nlevels - 1; l >= 0; --l) {
+            ib_backward(l);
             size_t o2 = B.tn.size();
             size_t zi = 0;
             std::vector<NnTask> nnb;
@@ -2986,6 +3510,8 @@ struct EngineT final : EngineImpl {
         }
         pl->tn = pl->mem.upload(B.tn, stream);
         pl->nn = pl->mem.upload(B.nn, stream);
+        if (!B.copy.empty()) pl->copy = pl->mem.upload(B.copy, stream);
+        if (!B.csr.empty()) pl->csr = pl->mem.upload(B.csr, stream);
         for (auto& t : B.tn) pl->flops += 2.0 * t.nrow * std::min(ap_tn_cols(), t.K - t.t0) * N;
         for (auto& t : B.nn) pl->flops += 2.0 * std::min(NN_ROWS, t.nrow - t.row0) * t.K * N;
         pl->bytes += (4.0 * sizeof(T) * n + 16.0 * n) * N;
@@ -3035,6 +3561,12 @@ struct EngineT final : EngineImpl {
                     break;
                 case L_NN:
                     PROF(P, "ap_nn", s, 0, 0, k_nn<T><<<dim3(L.count, cdiv(N, 16)), NN_ROWS, 0, s>>>(A.nn + L.off));
+                    break;
+                case L_COPY:
+                    PROF(P, "ap_copy", s, 0, 0, k_copy<T><<<dim3(L.count, 32), 256, 0, s>>>(A.copy + L.off));
+                    break;
+                case L_CSR:
+                    PROF(P, "ap_csr", s, 0, 0, k_csr_mm<T><<<dim3(L.count, cdiv(N, 16)), 256, 0, s>>>(A.csr + L.off));
                     break;
                 case L_HSOLVE: {
                     const int cw = N == 1 ? 1 : std::max(1, std::min(pick_cw(L.flag), 8));
@@ -3099,6 +3631,7 @@ struct EngineT final : EngineImpl {
     const HTask* na_hs = nullptr;
 
     rsc_status load_noalloc(char* base, size_t cap, cudaStream_t s) {
+        if (ib_on) throw Error(RSC_ERR_INVALID_ARG, "the allocation-free apply does not take interior blocks");
         auto align = [](size_t x) { return (x + 255) / 256 * 256; };
         const long long n = S.n;
         long long tmp_total = 0;
@@ -3306,11 +3839,13 @@ struct EngineT final : EngineImpl {
                 }
             }
         }
-        if (LO && r > 0) {
-            if (!n.compressed) {
+        const int rfull = S.nrows(j);
+        if (LO && rfull > 0) {
+            if (!n.compressed) {   // interior blocks: the rows after C_B are not stored (NaN)
                 auto P = dl(arena + n.off, (size_t)n.ld * c);
                 for (int q = 0; q < c; ++q)
-                    for (int i = 0; i < r; ++i) LO[i + (size_t)q * r] = (double)P[c + i + (size_t)q * n.ld];
+                    for (int i = 0; i < rfull; ++i)
+                        LO[i + (size_t)q * rfull] = i < r ? (double)P[c + i + (size_t)q * n.ld] : std::nan("");
             } else {
                 std::fill(LO, LO + (size_t)r * c, 0.0);
                 if (n.rank) {

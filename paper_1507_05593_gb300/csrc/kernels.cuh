@@ -50,9 +50,14 @@ struct NnTask {              // Y[yrow_i, :] += alpha sum_l A[arow_i, l] Z[l, :]
 };
 struct TrsvTask { const void* L; int ld; int c; int N; void* X; int ldx; int transpose; };
 struct CsrBlock { const int32_t* rp; const int32_t* ci; const double* v; int nrows; int pad; };
-struct CsrTask { CsrBlock blk; const void* X; int ldx; void* Y; int ldy; int N; int row0; double alpha; };
+// Y(row i, column c) = alpha (A X)(i, c), or added (mode 1; mode 2 atomically).  With rmap the
+// output row of CSR row i is rmap[i]; with cmap column c goes to column cmap[c]; lower: only
+// entries whose output column index is >= the output row index (the lower triangle of a
+// column-major target written as rows of its transpose) are written.
+struct CsrTask { CsrBlock blk; const void* X; int ldx; void* Y; int ldy; int N; int row0; double alpha;
+                 const int32_t* rmap; const int32_t* cmap; int mode; int lower; };
 struct GaussTask { void* G; int m; int row0; uint32_t block_id; uint32_t word3; int ld; int col0; };
-struct CopyTask { const void* src; long long ssr, ssc; void* dst; long long dsr, dsc; int m, nc; };
+struct CopyTask { const void* src; long long ssr, ssc; void* dst; long long dsr, dsc; int m, nc; int sub; };  // sub: dst -= src
 // One action of a hierarchical (or blocked dense) diagonal solve, rows local to the block:
 //   HA_TRSV   X[o0:o0+no] <- L^{-1} X[..] or L^{-T} X[..]   (A1 = row-major L^{-1}, no <= SOLVE_MAX)
 //   HA_LR     X[o0:o0+no] -= A2 (A1^T X[i0:i0+ni])          (A1 ni x K, A2 no x K; low rank)
@@ -805,7 +810,14 @@ __global__ void k_csr_mm(const CsrTask* __restrict__ tasks) {
     T s = T(0);
     for (int q = tk.blk.rp[i]; q < tk.blk.rp[i + 1]; ++q)
         s = fma((T)tk.blk.v[q], X[(size_t)tk.blk.ci[q] * tk.ldx + c0 + c], s);
-    ((T*)tk.Y)[(size_t)i * tk.ldy + c0 + c] = (T)tk.alpha * s;
+    const long long orow = tk.rmap ? tk.rmap[i] : i;
+    const long long ocol = tk.cmap ? tk.cmap[c0 + c] : c0 + c;
+    if (tk.lower && ocol < orow) return;
+    T* y = (T*)tk.Y + orow * tk.ldy + ocol;
+    const T v = (T)tk.alpha * s;
+    if (tk.mode == 0) *y = v;
+    else if (tk.mode == 1) *y += v;
+    else atomicAdd(y, v);
 }
 
 // ------------------------------------------------------------------ dense triangular solves with many RHS
@@ -1119,14 +1131,16 @@ __global__ void k_gauss(const GaussTask* __restrict__ tasks, unsigned long long 
     G[(size_t)i * tk.ld + tk.col0 + 2 * cp + 1] = z1;
 }
 
-// dst[i*dsr + c*dsc] = src[i*ssr + c*ssc]; grid (tasks, 32).
+// dst[i*dsr + c*dsc] = src[i*ssr + c*ssc] (or -= with sub); grid (tasks, 32).
 template <class T>
 __global__ void k_copy(const CopyTask* __restrict__ tasks) {
     const CopyTask tk = tasks[blockIdx.x];
     const long long cnt = (long long)tk.m * tk.nc;
     for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.y * blockDim.x) {
         const long long i = e % tk.m, c = e / tk.m;
-        ((T*)tk.dst)[i * tk.dsr + c * tk.dsc] = ((const T*)tk.src)[i * tk.ssr + c * tk.ssc];
+        const T v = ((const T*)tk.src)[i * tk.ssr + c * tk.ssc];
+        if (tk.sub) ((T*)tk.dst)[i * tk.dsr + c * tk.dsc] -= v;
+        else ((T*)tk.dst)[i * tk.dsr + c * tk.dsc] = v;
     }
 }
 

@@ -31,6 +31,7 @@ def test_options_default_values():
     o = R.rsc_options_default()
     assert (o.tau_O, o.tau_D, o.leaf_size, o.sample_block, o.power_iters, o.dof_per_node) == (256, 256, 64, 16, 0, 1)
     assert (o.max_restarts, o.precision, o.diag_compress, o.seed) == (8, 0, 1, 0)
+    assert (o.amalgamate, o.interior_blocks) == (0, 0)
 
 
 def _bad(p, **changes):
@@ -41,7 +42,8 @@ def _bad(p, **changes):
     return loc
 
 
-@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "badordering", "dof", "range", "hugecoord"])
+@pytest.mark.parametrize("what", ["asym", "unsorted", "nodiag", "nan", "badordering", "dof", "range", "hugecoord",
+                                  "badinterior"])
 def test_analyze_rejects_bad_input(what):
     p = W.poisson7(4)
     rp, ci, v, xyz = p.row_ptr.copy(), p.col_idx.copy(), p.val.copy(), p.coords.copy()
@@ -69,6 +71,8 @@ def test_analyze_rejects_bad_input(what):
         ci[3] = 10_000
     elif what == "hugecoord":
         xyz[5, 0] = 1e12
+    elif what == "badinterior":
+        opts.interior_blocks = 2
     with pytest.raises(R.RscError) as e:
         R.rsc_analyze(n, rp, ci, v, xyz, opts)
     assert e.value.status == 1
