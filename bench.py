@@ -585,9 +585,10 @@ def main():
     d_x = torch.empty_like(d_b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def make(prec, power_iters=0):
+    def make(prec, power_iters=0, interior_blocks=0):
         t = time.perf_counter()
-        o = R.rsc_options_default(precision=prec, power_iters=power_iters, dof_per_node=p.dof_per_node)
+        o = R.rsc_options_default(precision=prec, power_iters=power_iters, dof_per_node=p.dof_per_node,
+                                  interior_blocks=interior_blocks)
         h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
         return h, time.perf_counter() - t
 
@@ -654,8 +655,8 @@ def main():
     res = np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
     # the other forms over the same number of timed steps (after one untimed step); the paper's
     # own rank rule over min(steps, 3)
-    def side_form(prec, power_iters=0, fixed_rank=False, nsteps=None):
-        hs, _ = make(prec, power_iters)
+    def side_form(prec, power_iters=0, fixed_rank=False, nsteps=None, interior_blocks=0):
+        hs, _ = make(prec, power_iters, interior_blocks)
         step(hs, fixed_rank)   # untimed (and the kernel-variant tuning of the BF16 / TF32 forms)
         runs = [step(hs, fixed_rank) for _ in range(nsteps or a.steps)]
         sts = runs[-1][3]
@@ -664,6 +665,7 @@ def main():
         return {"seconds": secs, "steps": len(runs), "factor_s": fsec, "solve_s": secs - fsec,
                 "iters": runs[-1][1], "relres": runs[-1][2], "factor_bytes": sts["factor_bytes"],
                 "restarts": sts["restarts"], "factor_tflops": sts["factor_flops"] / fsec / 1e12}
+    st_main_bytes = R.rsc_get_stats(h)["factor_bytes"]
     fp64 = side_form("fp64") if not a.no_fp64 and a.prec != "fp64" else None
     fp32 = side_form("fp32") if not a.no_fp64 and a.prec in ("bf16", "tf32") else None
     # the paper's own rank rule (Section 5.2) in the same form: RSC0 and RSC1 (one power iteration)
@@ -672,6 +674,12 @@ def main():
         fixed = {f"rsc{q}": side_form(a.prec, q, True, min(a.steps, 3)) for q in (0, 1)}
         for q, v in enumerate(fixed.values()):
             v.update({"alpha_O": 0.5, "alpha_D": 0.5, "p": 8, "power_iters": q})
+    # Section 5.1's time-memory trade: the same form with interior blocks (their off-diagonal
+    # factor blocks never stored), over min(steps, 3) steps
+    interior = None
+    if not a.no_fp64:
+        interior = side_form(a.prec, 0, False, min(a.steps, 3), 1)
+        interior["factor_bytes_saved"] = st_main_bytes - interior["factor_bytes"]
     # roofline of the dominant class, timed live over the K timed steps
     roof = None
     if dom and dom in kprof and kprof[dom]["ms"] > 0:
@@ -710,7 +718,7 @@ def main():
         "factor_tflops": st["factor_flops"] / st["factor_seconds"] / 1e12, "factor_gflop": st["factor_flops"] / 1e9,
         "factor_bytes": st["factor_bytes"], "analyze_s": t_an, "restarts": st["restarts"],
         "gpu_launches": st["gpu_launches"], "plain_fp64": fp64, "fp32_form": fp32,
-        "fixed_rank_form": fixed, "roofline": roof, "rooflines": rooflines,
+        "fixed_rank_form": fixed, "interior_blocks_form": interior, "roofline": roof, "rooflines": rooflines,
         "autotune": R.rsc_get_autotune(h),
         "kernel_profile_untimed": prof_all,
         "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "clocks": clk, "other_configs": others,

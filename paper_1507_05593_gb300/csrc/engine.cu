@@ -970,6 +970,7 @@ struct EngineT final : EngineImpl {
         CK(cudaFuncSetAttribute(k_tn_s<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_bytes<T>(32)));
         CK(cudaFuncSetAttribute(k_tn_s<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_bytes<T>(64)));
         CK(cudaFuncSetAttribute(k_rf_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RFD_SMEM_CAP));
+        CK(cudaFuncSetAttribute(k_trsv_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tt_smem_bytes<T>()));
         if (const char* e = std::getenv("RSC_PROFILE")) { prof.on = true; if (std::strcmp(e, "1") != 0) prof.only = e; }
         hs_attr<8>();
         hs_attr<4>();
@@ -1843,8 +1844,15 @@ struct EngineT final : EngineImpl {
             launch_kind("gauss", st.gauss, 1, [&](GaussTask* d, int n, int) { k_gauss<T><<<n, 256, 0, s>>>(d, seed); });
             launch_kind("copy", st.copy, 1, [&](CopyTask* d, int n, int) { k_copy<T><<<dim3(n, 32), 256, 0, s>>>(d); });
             launch_kind("csr", st.csr, yn_csr, [&](CsrTask* d, int n, int y) { k_csr_mm<T><<<dim3(n, y), 256, 0, s>>>(d); });
-            launch_kind("trsv", st.trsv, yn_tr,
-                        [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
+            int maxn_tr = 0;
+            for (auto& t : st.trsv) maxn_tr = std::max(maxn_tr, t.N);
+            if (maxn_tr >= 32)   // many right-hand sides: the tiled form
+                launch_kind("trsv", st.trsv, cdiv(maxn_tr, TT_COLS), [&](TrsvTask* d, int n, int y) {
+                    k_trsv_tile<T><<<dim3(n, y), 256, tt_smem_bytes<T>(), s>>>(d);
+                });
+            else
+                launch_kind("trsv", st.trsv, yn_tr,
+                            [&](TrsvTask* d, int n, int y) { k_trsv<T, TRSV_CW><<<dim3(n, y), 256, 0, s>>>(d); });
             int zs_tn = 1, yc_tn = 1, np_tn = 16;
             double fl_tn = 0;
             for (auto& t : st.tn) {
@@ -2004,7 +2012,7 @@ struct EngineT final : EngineImpl {
             T*& t = ib_tcache[std::make_tuple((const void*)W, s, (int)i, N)];
             if (!t) t = wsT((size_t)nb * N);
             Program sub;
-            add_copy(next(sub), d_zero, 0, 0, t, N, 1, nb, N);   // t = 0, then the listed rows
+            add_copy(next(sub), d_zero, 0, 0, t, 1, 0, nb * N, 1);   // t = 0 (contiguous), then the listed rows
             add_csr_map(sub.back(), in, X, ldx, t, N, N, 1.0, nullptr, 0, 0);
             prog_block_solve(sub, tm.b, t, N, false);
             prog_block_solve(sub, tm.b, t, N, true);
@@ -2019,6 +2027,8 @@ struct EngineT final : EngineImpl {
     static constexpr size_t IB_WS_CAP = (size_t)512 << 20;
     void ib_dense_level(int l) {
         if (!ib_on || ib_dense[l].empty()) return;
+        const std::string keep_tag = prof.tag;
+        prof.tag += "@ibd";
         const std::vector<IbDense>& v = ib_dense[l];
         size_t i = 0;
         while (i < v.size()) {
@@ -2035,7 +2045,7 @@ struct EngineT final : EngineImpl {
                     bytes += sizeof(T) * (size_t)nb * N;
                     progs.emplace_back();
                     Program& P = progs.back();
-                    add_copy(next(P), d_zero, 0, 0, t, N, 1, nb, N);
+                    add_copy(next(P), d_zero, 0, 0, t, 1, 0, nb * N, 1);
                     // columns p0 .. p0 + N - 1 of the identity over P: the window's rows ib_maxP ..
                     add_csr_map(P.back(), d.in, ib_win + (size_t)(ib_maxP - p0) * 64, 64, t, N, N, 1.0, nullptr, 0, 0);
                     prog_block_solve(P, d.b, t, N, false);
@@ -2045,6 +2055,7 @@ struct EngineT final : EngineImpl {
             }
             run(progs);
         }
+        prof.tag = keep_tag;
     }
 
     // ---------------------------------------------------------------- dense / hierarchical triangular solves (programs)

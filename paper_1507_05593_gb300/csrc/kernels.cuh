@@ -981,6 +981,92 @@ __global__ void __launch_bounds__(256) k_trsv(const TrsvTask* __restrict__ tasks
     }
 }
 
+// X (c x N, row-major) <- Linv X or Linv^T X, Linv the row-major inverse of a lower triangular
+// block (c <= SOLVE_MAX, entries above its diagonal ignored): one CTA per (task, 64 columns).
+// The CTA keeps its c x 64 slice of X in shared memory and runs 64 x 64 output tiles as a small
+// GEMM over the 64 x 64 tiles of Linv on the triangle's side, each thread a 4 x 4 register block;
+// Linv tiles are staged transposed (column kk of the tile contiguous) so both operands are read
+// as 16-byte vectors.  Output tiles go in the order that leaves their inputs untouched (last
+// tile first for Linv, first tile first for Linv^T), so X is updated in place.
+constexpr int TT_COLS = 64, TT_TILE = 64, TT_LPAD = TT_TILE + 4;
+template <class T>
+constexpr size_t tt_smem_bytes() { return sizeof(T) * ((size_t)SOLVE_MAX * TT_COLS + (size_t)TT_TILE * TT_LPAD); }
+template <class T>
+__global__ void __launch_bounds__(256) k_trsv_tile(const TrsvTask* __restrict__ tasks) {
+    extern __shared__ __align__(16) unsigned char tt_smem[];
+    T* Xs = (T*)tt_smem;                               // c x 64
+    T* Ls = Xs + (size_t)SOLVE_MAX * TT_COLS;          // [kk][ii], 64 x TT_LPAD
+    const TrsvTask tk = tasks[blockIdx.x];
+    const int c0 = blockIdx.y * TT_COLS;
+    const int nc = min(TT_COLS, tk.N - c0);
+    if (nc <= 0) return;
+    const int c = tk.c;
+    const bool tr = tk.transpose == 1;
+    const T* Li = (const T*)tk.L;
+    T* X = (T*)tk.X;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int e = tid; e < c * TT_COLS; e += blockDim.x) {
+        const int i = e >> 6, q = e & 63;
+        Xs[e] = q < nc ? X[(size_t)i * tk.ldx + c0 + q] : T(0);
+    }
+    const int nt = (c + TT_TILE - 1) / TT_TILE;
+    for (int it = 0; it < nt; ++it) {
+        const int I = tr ? it : nt - 1 - it;
+        const int i0 = I * TT_TILE;
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+        const int kb = tr ? I : 0, ke = tr ? nt - 1 : I;
+        for (int K = kb; K <= ke; ++K) {
+            const int k0 = K * TT_TILE;
+            __syncthreads();   // Ls free (and Xs written) before the next tile
+            for (int e = tid; e < TT_TILE * TT_TILE; e += blockDim.x) {
+                // element (ii, kk) of the operator tile: Linv(i, k) or Linv(k, i), 0 above the diagonal
+                int ii, kk;
+                T v = T(0);
+                if (!tr) {
+                    ii = e >> 6; kk = e & 63;    // reads along a row of Linv
+                    const int i = i0 + ii, k = k0 + kk;
+                    if (i < c && k <= i) v = Li[(size_t)i * c + k];
+                } else {
+                    kk = e >> 6; ii = e & 63;    // reads along a row of Linv (row k)
+                    const int i = i0 + ii, k = k0 + kk;
+                    if (k < c && i <= k) v = Li[(size_t)k * c + i];
+                }
+                Ls[kk * TT_LPAD + ii] = v;
+            }
+            __syncthreads();
+            const int kn = min(TT_TILE, c - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                T a[4], x[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] = Ls[kk * TT_LPAD + ty * 4 + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x[q] = Xs[(size_t)(k0 + kk) * TT_COLS + tx * 4 + q];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], x[q], acc[r][q]);
+            }
+        }
+        __syncthreads();   // every read of this tile's rows of X is done
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + ty * 4 + r;
+            if (i < c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Xs[(size_t)i * TT_COLS + tx * 4 + q] = acc[r][q];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < c * TT_COLS; e += blockDim.x) {
+        const int i = e >> 6, q = e & 63;
+        if (q < nc) X[(size_t)i * tk.ldx + c0 + q] = Xs[e];
+    }
+}
+
 // ------------------------------------------------------------------ persistent hierarchical solve
 // One CTA per (task, CW-column chunk) walks a diagonal block's whole action list
 // (Alg. 4 in order) with the right-hand side block (c x CW) staged in dynamic
@@ -1137,7 +1223,7 @@ __global__ void k_copy(const CopyTask* __restrict__ tasks) {
     const CopyTask tk = tasks[blockIdx.x];
     const long long cnt = (long long)tk.m * tk.nc;
     for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.y * blockDim.x) {
-        const long long i = e % tk.m, c = e / tk.m;
+        const long long i = tk.nc == 1 ? e : e % tk.m, c = tk.nc == 1 ? 0 : e / tk.m;
         const T v = ((const T*)tk.src)[i * tk.ssr + c * tk.ssc];
         if (tk.sub) ((T*)tk.dst)[i * tk.dsr + c * tk.dsc] -= v;
         else ((T*)tk.dst)[i * tk.dsr + c * tk.dsc] = v;

@@ -1,0 +1,38 @@
+"""Run-to-run spread of the factorization on one GPU.
+
+The extend-add and the scattered products accumulate with atomic adds, so the order of
+floating-point additions into a target may change from one run to the next; nothing else in
+the path depends on timing.  Two factorizations of the same matrix therefore agree to
+rounding: the same ranks (the adaptive stopping test of Alg. 3 sees norms that differ in the
+last bits only), blocks within a few units of rounding of the arithmetic's precision, and the
+same PCG iteration counts.
+"""
+import numpy as np
+import pytest
+
+import paper_1507_05593_gb300 as R
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-12), ("fp32", 1e-4), ("bf16", 1e-2)])
+def test_repeated_factorizations_agree(prec, bound):
+    p = W.diffusion_grf(16, 2.0, 4.0, 0)
+    o = R.rsc_options_default(precision=prec, leaf_size=16, tau_O=40, tau_D=32)
+    runs = []
+    for _ in range(3):
+        h = R.rsc_analyze(p.n, p.row_ptr, p.col_idx, p.val, p.coords, o)
+        R.rsc_factor(h, 0.01)
+        M = R.rsc_get_stats(h)["n_supernodes"]
+        ranks = [R.rsc_get_supernode_info(h, j)["rank"] for j in range(M)]
+        d_r = torch.tensor(np.random.default_rng(1).standard_normal(p.n), device="cuda")
+        d_z = torch.empty_like(d_r)
+        R.rsc_apply_preconditioner_device(h, d_r, d_z)
+        x, it, rr = R.rsc_solve(h, p.b, 1e-8, 500)
+        runs.append((ranks, d_z.cpu().numpy(), it))
+    for ranks, z, it in runs[1:]:
+        assert ranks == runs[0][0]
+        assert np.abs(z - runs[0][1]).max() <= bound * np.abs(runs[0][1]).max()
+        assert it == runs[0][2]
