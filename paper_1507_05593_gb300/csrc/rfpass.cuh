@@ -789,6 +789,36 @@ template <class T> inline size_t rfd_smem(int m, int c, int maxr) {
     return sizeof(T) * ((size_t)m * 16 + (size_t)c * 17 + (size_t)maxr * 17 + (size_t)c * 33);
 }
 
+// Sum over a warp of 16 per-lane values: at distance 16, 8, 4, 2 each lane keeps the half of its
+// values selected by that lane bit and adds its partner's copy of the same half; a last exchange
+// at distance 1 completes the sum.  Lane l returns the total of value rfd_fold16_col(l).
+__device__ __forceinline__ int rfd_fold16_col(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+template <class T>
+__device__ __forceinline__ T rfd_fold16(T (&a)[16], int lane) {
+    T b[8], c4[4], d2[2];
+    const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0, h2 = (lane & 2) != 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const T send = h16 ? a[i] : a[i + 8];
+        b[i] = (h16 ? a[i + 8] : a[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const T send = h8 ? b[i] : b[i + 4];
+        c4[i] = (h8 ? b[i + 4] : b[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const T send = h4 ? c4[i] : c4[i + 2];
+        d2[i] = (h4 ? c4[i + 2] : c4[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const T send = h2 ? d2[0] : d2[1];
+    const T e = (h2 ? d2[1] : d2[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+    return e + __shfl_xor_sync(0xffffffffu, e, 1);
+}
+
 template <class T>
 __global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restrict__ tasks, unsigned long long seed,
                                                   int* err) {
@@ -815,21 +845,23 @@ __global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restri
         __syncthreads();
         return t;
     };
-    // Y -= U (U^T Y) with the current rank
+    // Y -= U (U^T Y) with the current rank.  Z = U^T Y: a warp per column k of U, lanes along
+    // its rows (coalesced), 16 partial sums per lane folded across the warp in 16 shuffles
+    // (each step halves the sums a lane keeps); lane 2q' ends with the sum of column q(lane).
     auto project = [&](int rank) {
         if (rank == 0) return;
-        for (int k = tid; k < rank; k += nt) {
+        for (int k = warp; k < rank; k += (nt >> 5)) {
             T a[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) a[q] = T(0);
             const T* uk = tk.U + (size_t)k * c;
-            for (int j = 0; j < c; ++j) {
+            for (int j = lane; j < c; j += 32) {
                 const T uv = uk[j];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) a[q] = fma(uv, Y[j * 17 + q], a[q]);
             }
-#pragma unroll
-            for (int q = 0; q < 16; ++q) Z[k * 17 + q] = a[q];
+            const T v = rfd_fold16(a, lane);
+            if ((lane & 1) == 0) Z[k * 17 + rfd_fold16_col(lane)] = v;
         }
         __syncthreads();
         for (int j = tid; j < c; j += nt) {
