@@ -6,7 +6,7 @@ length 8 cells); compression tolerance 1e-2, 16-column Gaussian samples, PCG to
 ||r||/||b|| <= 1e-8.  One step = rsc_factor + rsc_solve_device (b resident on the
 device); its time is the sum of the two calls' device times (CUDA events on the
 library's stream).  The default form (BF16 Schur updates on tcgen05 tensor cores with
-FP32 accumulation, FP32 factor storage and sampling, FP64 diagonal Cholesky and PCG) is
+FP32 accumulation, FP32 factor storage, diagonal Cholesky and sampling, FP64 PCG) is
 timed for K steps; the FP32 form and the plain FP64 form are timed once beside it.  L2
 is flushed between steps (the factor storage is also larger than L2).
 
@@ -282,11 +282,11 @@ def other_configs(a):
 
 
 # ----------------------------------------------------------------------------- reference arm
-FORMS = {"bf16": "BF16 Schur updates on tcgen05 (FP32 accumulation), FP32 factor and sampling, FP64 diagonal "
-                 "Cholesky and PCG",
-         "tf32": "TF32 Schur updates on tcgen05 (FP32 accumulation), FP32 factor and sampling, FP64 diagonal "
-                 "Cholesky and PCG",
-         "fp32": "FP32 factor, Schur updates and sampling; FP64 diagonal Cholesky and PCG",
+FORMS = {"bf16": "BF16 Schur updates on tcgen05 (FP32 accumulation), FP32 factor, diagonal Cholesky and "
+                 "sampling, FP64 PCG",
+         "tf32": "TF32 Schur updates on tcgen05 (FP32 accumulation), FP32 factor, diagonal Cholesky and "
+                 "sampling, FP64 PCG",
+         "fp32": "FP32 factor, Schur updates, diagonal Cholesky and sampling; FP64 PCG",
          "fp64": "all FP64"}
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at 96^3, by kernel class, for the
@@ -309,9 +309,8 @@ def _peaks():
 
 
 # which compute roof bounds a kernel class: tensor-core classes against the tensor peak of their
-# operand type, the FP64 Cholesky tiles against FP64 SIMT, the rest against SIMT of the storage type
+# operand type, the rest (diagonal Cholesky tiles included) against SIMT of the storage type
 TENSOR_CLASSES = {"push_tc", "tn_tc", "nn_tc"}
-FP64_CLASSES = {"potrf"}
 
 
 def roofline_entry(name, k, prec, source):
@@ -327,7 +326,7 @@ def roofline_entry(name, k, prec, source):
     if name in TENSOR_CLASSES:
         cpk = pk["bf16"] * (1.1 / 2.25 if prec == "tf32" else 1.0)
         cunit, csrc = f"{'TF32' if prec == 'tf32' else 'BF16'} tensor", pk["src"]
-    elif name in FP64_CLASSES or prec == "fp64":
+    elif prec == "fp64":
         cpk, cunit, csrc = FP64_SIMT_TFLOPS, "FP64 SIMT", "of builder-measured (DFMA loop)"
     else:
         cpk, cunit, csrc = FP32_SIMT_TFLOPS, "FP32 SIMT", "of builder-measured (FFMA loop)"

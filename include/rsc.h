@@ -45,8 +45,8 @@ typedef enum {
 
 typedef enum {
     RSC_PREC_FP64 = 0,   /* every step in FP64 */
-    RSC_PREC_FP32 = 1,   /* Schur updates, sampling and the preconditioner apply in FP32
-                            (FP64 kept for diagonal Cholesky factorizations and PCG) */
+    RSC_PREC_FP32 = 1,   /* factor, Schur updates, diagonal Cholesky tiles, sampling and the
+                            preconditioner apply in FP32 (FP64 kept for PCG) */
     RSC_PREC_TF32 = 2,   /* as FP32, Schur-update GEMMs on tensor cores in TF32 */
     RSC_PREC_BF16 = 3    /* as FP32, Schur-update GEMMs on tensor cores in BF16 */
 } rsc_precision;

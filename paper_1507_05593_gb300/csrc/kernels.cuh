@@ -89,7 +89,17 @@ __global__ void k_assemble(const double* __restrict__ val, const long long* __re
     for (; e < cnt; e += stride) arena[dst[e]] = (T)val[src[e]];
 }
 
-// ------------------------------------------------------------------ diagonal tile Cholesky (FP64)
+// ------------------------------------------------------------------ diagonal tile Cholesky
+// The tiles are factored in the storage precision: FP64 in the FP64 form; FP32 where the factor
+// is stored in FP32 (on this part a warp's FP64 instruction holds its sub-partition about 64
+// cycles, so the pivots' dependent chains dominated the hierarchical leaves; FP32's tile error,
+// about 1e-7 relative, is far below the compression tolerances).
+template <class T> struct TileType { using type = T; };
+// 1 / sqrt(x) in FP32: the hardware estimate and one Newton step.
+__device__ __forceinline__ float rsqrt_f32(float x) {
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
 // 1 / sqrt(x) by Newton's method for f(y) = y^-2 - x (y <- y (3 - x y^2) / 2), two steps from
 // the single-precision estimate (about 22 correct bits -> 44 -> full double precision, within
 // a few ulp).  On this part a dependent FP64 operation takes about 64 cycles, the library's
@@ -106,38 +116,42 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
     return y;
 }
 
-// Cholesky of one nb x nb (nb <= 64) diagonal tile in FP64, lower triangle in place, in
-// shared memory (right-looking).  Thread 0 forms the pivot's square root and reciprocal
-// (rsqrt_newton); the column is scaled by multiplication, and the trailing update runs warps
-// over columns, lanes down the rows of each column's lower part (no index division).
+__device__ __forceinline__ double rsqrt_tile(double x) { return rsqrt_newton<2>(x); }
+__device__ __forceinline__ float rsqrt_tile(float x) { return rsqrt_f32(x); }
+
+// Cholesky of one nb x nb (nb <= 64) diagonal tile in the storage precision, lower triangle in
+// place, in shared memory (right-looking).  Thread 0 forms the pivot's square root and
+// reciprocal (rsqrt_tile); the column is scaled by multiplication, and the trailing update runs
+// warps over columns, lanes down the rows of each column's lower part (no index division).
 template <class T>
 __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict__ tasks, int* status) {
-    __shared__ double s[NB][NB + 1];
-    __shared__ double rpiv;
+    using TT = typename TileType<T>::type;
+    __shared__ TT s[NB][NB + 1];
+    __shared__ TT rpiv;
     const PotrfTask tk = tasks[blockIdx.x];
     T* a = (T*)tk.a;
     const int nb = tk.nb, ld = tk.ld;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = warp; j < nb; j += 8)
-        for (int i = j + lane; i < nb; i += 32) s[i][j] = (double)a[i + (size_t)j * ld];
+        for (int i = j + lane; i < nb; i += 32) s[i][j] = (TT)a[i + (size_t)j * ld];
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
         if (threadIdx.x == 0) {
-            double d = s[k][k];
-            if (!(d > 0.0)) {            // indefinite or NaN pivot: record, keep values finite
+            TT d = s[k][k];
+            if (!(d > TT(0))) {          // indefinite or NaN pivot: record, keep values finite
                 atomicCAS(status, 0, tk.node + 1);
-                d = 1.0;
+                d = TT(1);
             }
-            const double y = rsqrt_newton<sizeof(T) == 8 ? 2 : 1>(d);
+            const TT y = rsqrt_tile(d);
             s[k][k] = d * y;
             rpiv = y;
         }
         __syncthreads();
-        const double ri = rpiv;
+        const TT ri = rpiv;
         for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) s[i][k] *= ri;
         __syncthreads();
         for (int j = k + 1 + warp; j < nb; j += 8) {
-            const double ljk = s[j][k];
+            const TT ljk = s[j][k];
             for (int i = j + lane; i < nb; i += 32) s[i][j] = fma(-s[i][k], ljk, s[i][j]);
         }
         __syncthreads();
@@ -149,8 +163,8 @@ __global__ void __launch_bounds__(256) k_potrf_tile(const PotrfTask* __restrict_
 // ------------------------------------------------------------------ whole leaf block in one CTA
 // Cholesky of one sz x sz diagonal leaf (Alg. 6's leaf blocks, sz <= LEAF_FUSED_MAX) held in
 // shared memory, by 32-column panels:
-//  * the 32 x 32 diagonal tile in FP64 by four warps, one per SM sub-partition, so that the
-//    FP64 units of all four take part: per pivot every lane forms 1/sqrt by rsqrt_newton, holds
+//  * the 32 x 32 diagonal tile in the storage precision by four warps, one per SM sub-partition:
+//    per pivot every lane forms 1/sqrt by rsqrt_tile, holds
 //    l(i, k) of its row, and warp w updates the tile columns j = k + 1 + w (mod 4) with l(j, k)
 //    taken from lane j by a shuffle; a 128-thread barrier separates the pivots;
 //  * the rows below, X <- X L_D^{-T}, one thread per row by forward substitution (the tile
@@ -162,20 +176,20 @@ constexpr int LP = 32;   // panel width of the leaf factorization
 __host__ __device__ constexpr int leaf_ld(int sz) { return (sz + 4) / 4 * 4; }
 constexpr int LEAF_DT = LP + 1;          // column stride of the FP64 tile
 
-template <class T>
-__device__ __forceinline__ void leaf_tile_chol4(T* S, int L, int t0, int nb, double* D, T* dinv, int* status,
+template <class T, class TT>
+__device__ __forceinline__ void leaf_tile_chol4(T* S, int L, int t0, int nb, TT* D, T* dinv, int* status,
                                                 int node) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;   // w < 4
     for (int k = 0; k < nb; ++k) {
-        double piv = D[k * LEAF_DT + k];
-        if (!(piv > 0.0)) {          // indefinite or NaN pivot: record, keep values finite
+        TT piv = D[k * LEAF_DT + k];
+        if (!(piv > TT(0))) {        // indefinite or NaN pivot: record, keep values finite
             if (threadIdx.x == 0) atomicCAS(status, 0, node + 1);
-            piv = 1.0;
+            piv = TT(1);
         }
-        const double y = rsqrt_newton<sizeof(T) == 8 ? 2 : 1>(piv);
-        const double lik = (lane > k && lane < nb) ? D[k * LEAF_DT + lane] * y : 0.0;
+        const TT y = rsqrt_tile(piv);
+        const TT lik = (lane > k && lane < nb) ? D[k * LEAF_DT + lane] * y : TT(0);
         for (int j = k + 1 + w; j < nb; j += 4) {
-            const double ljk = __shfl_sync(0xffffffffu, lik, j);
+            const TT ljk = __shfl_sync(0xffffffffu, lik, j);
             if (lane >= j && lane < nb) D[j * LEAF_DT + lane] = fma(-lik, ljk, D[j * LEAF_DT + lane]);
         }
         if (w == 0) {
@@ -195,7 +209,8 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const PotrfTask* __restrict
     const int sz = tk.nb, ld = tk.ld, L = leaf_ld(sz);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     T* S = (T*)lf_smem;
-    double* D = (double*)(lf_smem + ((size_t)sizeof(T) * sz * L + 15) / 16 * 16);   // 32 x 33 FP64 tile
+    using TT = typename TileType<T>::type;
+    TT* D = (TT*)(lf_smem + ((size_t)sizeof(T) * sz * L + 15) / 16 * 16);   // 32 x 33 tile
     for (int j = warp; j < sz; j += 8)
         for (int i = j + lane; i < sz; i += 32) S[i + j * L] = a[i + (size_t)j * ld];
     __syncthreads();
@@ -203,10 +218,10 @@ __global__ void __launch_bounds__(256) k_leaf_factor(const PotrfTask* __restrict
         const int nb = min(LP, sz - t0);
         for (int e = tid; e < LP * LP; e += blockDim.x) {
             const int i = e & 31, j = e >> 5;
-            D[j * LEAF_DT + i] = (i < nb && j < nb && i >= j) ? (double)S[t0 + i + (size_t)(t0 + j) * L] : 0.0;
+            D[j * LEAF_DT + i] = (i < nb && j < nb && i >= j) ? (TT)S[t0 + i + (size_t)(t0 + j) * L] : TT(0);
         }
         __syncthreads();
-        if (warp < 4) leaf_tile_chol4<T>(S, L, t0, nb, D, dinv, status, tk.node);
+        if (warp < 4) leaf_tile_chol4<T, TT>(S, L, t0, nb, D, dinv, status, tk.node);
         __syncthreads();
         const int r0 = t0 + nb, m = sz - r0;             // rows below the tile
         if (m <= 0) break;
