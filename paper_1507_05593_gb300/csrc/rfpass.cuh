@@ -219,6 +219,10 @@ __device__ void rfp_apply_rsolve(const T* rf, int b, T (*Ys)[17], T (*Gs)[17], T
 // pivot are set to zero, so it leaves the block as a zero column.  Writes R (row-major
 // 16 x 16, upper b x b) and the reciprocal diagonal to out[0..271].  Returns true on
 // a non-finite pivot.
+// square root in the argument's own precision
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+
 template <class T>
 __device__ bool rfp_chol(T (*G)[17], int b, double coef, double delta, T* out) {
     const int j = threadIdx.x & 31;
@@ -234,22 +238,27 @@ __device__ bool rfp_chol(T (*G)[17], int b, double coef, double delta, T* out) {
         if (i == j) g0 = col[i];
     bool bad = false;
     T rdiag = T(0);
+    const T dlt = (T)delta;
+    // row k of R reaches the lanes through shared memory (double-buffered: one warp barrier per
+    // pivot); a shuffle per element was the slower form
+    __shared__ T rowb[2][16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-        if (k >= b) break;
-        const T d = __shfl_sync(0xffffffffu, col[k], k);
-        const T g0k = __shfl_sync(0xffffffffu, g0, k);
-        if (d != d) bad = true;
-        const bool keep = d > (T)delta * g0k;
-        const T r = keep ? sqrt(d) : T(0);
-        const T ri = keep ? T(1) / r : T(0);
-        const T rkj = j > k ? col[k] * ri : (j == k ? r : T(0));
-        col[k] = rkj;
-        if (j == k) rdiag = ri;
+        if (k < b) {
+            const T d = __shfl_sync(0xffffffffu, col[k], k);
+            const T g0k = __shfl_sync(0xffffffffu, g0, k);
+            if (d != d) bad = true;
+            const bool keep = d > dlt * g0k;
+            const T r = keep ? tsqrt(d) : T(0);
+            const T ri = keep ? T(1) / r : T(0);
+            const T rkj = j > k ? col[k] * ri : (j == k ? r : T(0));
+            col[k] = rkj;
+            if (j == k) rdiag = ri;
+            if (j < 16) rowb[k & 1][j] = rkj;
+            __syncwarp();
 #pragma unroll
-        for (int i = k + 1; i < 16; ++i) {
-            const T rki = __shfl_sync(0xffffffffu, rkj, i);
-            if (j >= i) col[i] = fma(-rki, rkj, col[i]);
+            for (int i = k + 1; i < 16; ++i)
+                if (j >= i) col[i] = fma(-rowb[k & 1][i], rkj, col[i]);
         }
     }
     if (j < 16) {
@@ -824,7 +833,7 @@ __global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restri
                                                   int* err) {
     extern __shared__ __align__(16) unsigned char rfd_smem_[];
     __shared__ T Gs[16][17], Rl[272], rd[16];
-    __shared__ double red[16];
+    __shared__ double red[17];
     __shared__ int flag_s;
     const RfDenseTask<T> tk = tasks[blockIdx.x];
     const int m = tk.m, c = tk.c, maxr = tk.maxr;
@@ -840,10 +849,13 @@ __global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restri
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) red[warp] = s;
         __syncthreads();
-        double t = 0.0;
-        for (int w = 0; w < (nt >> 5); ++w) t += red[w];
+        if (warp == 0) {   // the warps' sums, in a fixed order, by one warp
+            double t = lane < (nt >> 5) ? red[lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[16] = t;
+        }
         __syncthreads();
-        return t;
+        return red[16];
     };
     // Y -= U (U^T Y) with the current rank.  Z = U^T Y: a warp per column k of U, lanes along
     // its rows (coalesced), 16 partial sums per lane folded across the warp in 16 shuffles
@@ -919,6 +931,10 @@ __global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restri
         return flag_s != 0;
     };
 
+    // row ranges of the sample product: up to three when the columns leave threads idle (the
+    // partial sums of ranges 1, 2 need 2 c x 16 of the U tile's c x 33)
+    const int parts = c * 3 <= nt ? 3 : (c * 2 <= nt ? 2 : 1);
+    const int mpart = (m + parts - 1) / parts;
     int rank = 0;
     double y1 = 0.0;
     for (int t = 0; rank < maxr; ++t) {
@@ -931,19 +947,33 @@ __global__ void __launch_bounds__(512) k_rf_dense(const RfDenseTask<T>* __restri
             G[i * 16 + 2 * cp + 1] = z1;
         }
         __syncthreads();
-        for (int j = tid; j < c; j += nt) {
+        // Y = B^T G with the rows of B split in `parts` ranges over the threads; the partial sums
+        // of ranges 1, 2 go through the U tile's space (free until V = B U) and are added in order
+        for (int e = tid; e < c * parts; e += nt) {
+            const int j = e % c, pt = e / c;
+            const int i0 = pt * mpart, i1 = min(m, i0 + mpart);
             T a[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) a[q] = T(0);
-            for (int i = 0; i < m; ++i) {
+            for (int i = i0; i < i1; ++i) {
                 const T bv = tk.B[(size_t)i * c + j];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) a[q] = fma(bv, G[i * 16 + q], a[q]);
             }
+            T* dst = pt == 0 ? Y + (size_t)j * 17 : Ut + (size_t)(pt - 1) * c * 16 + (size_t)j * 16;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) Y[j * 17 + q] = a[q];
+            for (int q = 0; q < 16; ++q) dst[q] = a[q];
         }
         __syncthreads();
+        if (parts > 1) {
+            for (int e = tid; e < c * 16; e += nt) {
+                const int j = e >> 4, q = e & 15;
+                T v = Y[j * 17 + q] + Ut[(size_t)j * 16 + q];
+                if (parts > 2) v += Ut[(size_t)c * 16 + (size_t)j * 16 + q];
+                Y[j * 17 + q] = v;
+            }
+            __syncthreads();
+        }
         if (t == 0) y1 = sqrt(frob2());
         project(rank);
         project(rank);
