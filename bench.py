@@ -708,6 +708,7 @@ def main():
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "step_times_s": times,
         "dtype": {"bf16": "bf16", "tf32": "tf32", "fp32": "f32"}.get(a.prec, "f64"), "data": "synthetic",
         "config": {"workload": _workload_name(a.side, a.tol, a.workload)},
         "form": FORMS.get(a.prec, a.prec), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

@@ -30,7 +30,7 @@ namespace rsc {
 constexpr int RFP_ROWS = 64;             // rows per chunk
 constexpr int RFP_THREADS = 256;
 constexpr unsigned long long RFP_SPIN_LIMIT = 1ull << 22;   // default polls of a barrier wait (64 ns apart)
-constexpr int RFP_SMALL = 8;             // blocks of at most this many chunks: small-block mode
+constexpr int RFP_SMALL = 32;            // blocks of at most this many chunks: small-block mode
 
 template <class T>
 struct RfDev {
