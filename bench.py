@@ -253,8 +253,9 @@ def _compact(d, keys):
 def other_configs(a):
     """C1 (Poisson 32^3, all FP64), C3 (elasticity 40^3, TF32 Schur updates), C4 (256 systems x 8
     right-hand sides, BF16), C5 (differentiation 64^3, FP32 factor): value, iterations, the plain
-    FP64 GPU path beside and the oracle baseline, 3 timed steps each."""
-    base = ["--steps", "3", "--warmup", "1"]
+    FP64 GPU path beside and the oracle baseline, 3 timed steps each after 3 warm-up steps (a
+    handle's first factorizations still grow its workspaces)."""
+    base = ["--steps", "3", "--warmup", "3"]
     keys = ["value", "factor_s", "solve_s", "iters", "relres", "factor_bytes", "restarts", "factor_tflops",
             "cpu_baseline", "plain_fp64", "fp32_form", "roofline", "dtype", "config", "form", "e2e", "gpu_launches"]
     out = {}
@@ -267,7 +268,7 @@ def other_configs(a):
     bkeys = ["value", "factor_s", "solve_s", "iters_max", "iters_mean", "relres_max", "factor_bytes", "restarts",
              "config", "dtype", "cpu_baseline", "gpu_launches"]
     c4 = _compact(_sub_bench(["--workload", "batch"] + base), bkeys)
-    c4_64 = _sub_bench(["--workload", "batch", "--prec", "fp64", "--no-cpu-baseline", "--steps", "1", "--warmup", "1"])
+    c4_64 = _sub_bench(["--workload", "batch", "--prec", "fp64", "--no-cpu-baseline", "--steps", "1", "--warmup", "2"])
     if c4 and "failed" not in c4:
         c4["plain_fp64"] = _compact(c4_64, ["value", "factor_s", "solve_s", "iters_max", "factor_bytes"])
     out["C4_batch256x8_bf16"] = c4
@@ -467,7 +468,8 @@ def batch_workload(a):
             "factor_s": fs, "solve_s": ss, "iters_max": int(its.max()), "iters_mean": float(its.mean()),
             "relres_max": float(rr.max()), "analyze_s": t_an, "factor_bytes": st["factor_bytes"],
             "gpu_launches": st["gpu_launches"], "n_supernodes": st["n_supernodes"], "n_levels": st["n_levels"],
-            "restarts": st["restarts"], "cpu_baseline": cpu}
+            "restarts": st["restarts"], "cpu_baseline": cpu,
+            "step_factor_s": [r[0] for r in res], "step_solve_s": [r[1] for r in res]}
     print(json.dumps(line), flush=True)
 
 
