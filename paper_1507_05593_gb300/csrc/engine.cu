@@ -1658,9 +1658,15 @@ struct EngineT final : EngineImpl {
     static double now_ms() {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
     }
-    template <class X> void* upload_tmp(Scratch&, const std::vector<X>& v) {
+    // One region of the arena: fill(host staging, device address) writes the records (which may
+    // point into the region itself), then one copy is queued.  A wrap or a larger arena (after a
+    // stream synchronisation) happens only here, before the region is handed out, so records a
+    // later upload displaces were consumed by launches already queued -- provided every launch
+    // takes its records from a single upload (a launch whose records span two uploads could find
+    // the first one overwritten or freed by the second).
+    template <class F> char* upload_fill(size_t nbytes, F&& fill) {
         HostTimer ht_(this, "h_upload");
-        const size_t bytes = (sizeof(X) * std::max<size_t>(v.size(), 1) + 255) / 256 * 256;
+        const size_t bytes = (std::max<size_t>(nbytes, 1) + 255) / 256 * 256;
         if (arena_used + bytes > arena_cap) {
             sync_stream();
             if (bytes > arena_cap) {
@@ -1671,13 +1677,16 @@ struct EngineT final : EngineImpl {
                 CK(cudaMallocHost(&arena_host, arena_cap));
             }
         }
-        void* p = arena_base + arena_used;
-        if (!v.empty()) {
-            std::memcpy(arena_host + arena_used, v.data(), sizeof(X) * v.size());
-            CK(cudaMemcpyAsync(p, arena_host + arena_used, sizeof(X) * v.size(), cudaMemcpyHostToDevice, stream));
+        char* p = arena_base + arena_used;
+        if (nbytes) {
+            fill(arena_host + arena_used, p);
+            CK(cudaMemcpyAsync(p, arena_host + arena_used, nbytes, cudaMemcpyHostToDevice, stream));
         }
         arena_used += bytes;
         return p;
+    }
+    template <class X> void* upload_tmp(Scratch&, const std::vector<X>& v) {
+        return upload_fill(sizeof(X) * v.size(), [&](char* h, char*) { std::memcpy(h, v.data(), sizeof(X) * v.size()); });
     }
 
     // ---------------------------------------------------------------- stage programs
@@ -1836,11 +1845,7 @@ struct EngineT final : EngineImpl {
             for (auto& t : st.trsv) yn_tr = std::max(yn_tr, cdiv(t.N, TRSV_CW));
             const unsigned long long seed = o.seed;
             cudaStream_t s = stream;
-            if (!st.hs.empty()) {
-                HAct* dacts = (HAct*)upload_tmp(sTask, st.hacts);
-                for (auto& h : st.hs) h.acts = dacts + (intptr_t)h.acts;
-                run_hsolve(st.hs, s);
-            }
+            if (!st.hs.empty()) run_hsolve(st.hacts, st.hs, s);
             launch_kind("gauss", st.gauss, 1, [&](GaussTask* d, int n, int) { k_gauss<T><<<n, 256, 0, s>>>(d, seed); });
             launch_kind("copy", st.copy, 1, [&](CopyTask* d, int n, int) { k_copy<T><<<dim3(n, 32), 256, 0, s>>>(d); });
             launch_kind("csr", st.csr, yn_csr, [&](CsrTask* d, int n, int y) { k_csr_mm<T><<<dim3(n, y), 256, 0, s>>>(d); });
@@ -2120,26 +2125,42 @@ struct EngineT final : EngineImpl {
     // At most 4 columns per CTA: the hierarchical chain's solves have few tasks, and twice the
     // CTAs walking the action list beat the wider chunk (96^3: 14.2 -> 11.5 ms; 2 columns: 14.6)
     static constexpr int HS_CW_MAX = 4;
-    void run_hsolve(std::vector<HTask>& tasks, cudaStream_t s, int force_cw = 0) {
-        for (int cw : {8, 4, 2, 1}) {
-            std::vector<HTask> g;
-            int maxc = 0, ych = 1;
-            for (auto& t : tasks) {
-                const int w = force_cw ? force_cw : std::min(pick_cw(t.c), HS_CW_MAX);
-                if (w != cw) continue;
-                g.push_back(t);
-                maxc = std::max(maxc, t.c);
-                ych = std::max(ych, cdiv(t.N, cw));
-            }
-            if (g.empty()) continue;
-            HTask* d = (HTask*)upload_tmp(sTask, g);
-            const dim3 grid((unsigned)g.size(), (unsigned)ych);
-            const size_t sm = hs_smem(maxc, cw);
-            switch (cw) {
-                case 8: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 8><<<grid, HS_THREADS, sm, s>>>(d)); break;
-                case 4: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 4><<<grid, HS_THREADS, sm, s>>>(d)); break;
-                case 2: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 2><<<grid, HS_THREADS, sm, s>>>(d)); break;
-                default: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 1><<<grid, HS_THREADS, sm, s>>>(d)); break;
+    void run_hsolve(const std::vector<HAct>& acts, const std::vector<HTask>& tasks, cudaStream_t s) {
+        // tasks[i].acts holds an index into acts.  The actions and every width group's task list
+        // go up in one upload: a second upload could wrap the arena over the first one before the
+        // kernels that read both have run
+        const int widths[4] = {8, 4, 2, 1};
+        std::vector<HTask> grp[4];
+        int maxc[4] = {0, 0, 0, 0}, ych[4] = {1, 1, 1, 1};
+        for (const HTask& t : tasks) {
+            const int w = std::min(pick_cw(t.c), HS_CW_MAX);
+            const int g = w == 8 ? 0 : w == 4 ? 1 : w == 2 ? 2 : 3;
+            grp[g].push_back(t);
+            maxc[g] = std::max(maxc[g], t.c);
+            ych[g] = std::max(ych[g], cdiv(t.N, w));
+        }
+        auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+        size_t off[4], total = al(sizeof(HAct) * acts.size());
+        for (int g = 0; g < 4; ++g) { off[g] = total; total += al(sizeof(HTask) * grp[g].size()); }
+        char* d = upload_fill(total, [&](char* h, char* dd) {
+            if (!acts.empty()) std::memcpy(h, acts.data(), sizeof(HAct) * acts.size());
+            for (int g = 0; g < 4; ++g)
+                for (size_t i = 0; i < grp[g].size(); ++i) {
+                    HTask t = grp[g][i];
+                    t.acts = (const HAct*)dd + (intptr_t)t.acts;
+                    std::memcpy(h + off[g] + sizeof(HTask) * i, &t, sizeof(HTask));
+                }
+        });
+        for (int g = 0; g < 4; ++g) {
+            if (grp[g].empty()) continue;
+            const HTask* dt = (const HTask*)(d + off[g]);
+            const dim3 grid((unsigned)grp[g].size(), (unsigned)ych[g]);
+            const size_t sm = hs_smem(maxc[g], widths[g]);
+            switch (widths[g]) {
+                case 8: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 8><<<grid, HS_THREADS, sm, s>>>(dt)); break;
+                case 4: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 4><<<grid, HS_THREADS, sm, s>>>(dt)); break;
+                case 2: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 2><<<grid, HS_THREADS, sm, s>>>(dt)); break;
+                default: PROF(prof, "hsolve", s, 0, 0, k_hsolve<T, 1><<<grid, HS_THREADS, sm, s>>>(dt)); break;
             }
             launches++;
             LAUNCH_CHECK();
