@@ -36,3 +36,31 @@ def test_repeated_factorizations_agree(prec, bound):
         assert ranks == runs[0][0]
         assert np.abs(z - runs[0][1]).max() <= bound * np.abs(runs[0][1]).max()
         assert it == runs[0][2]
+
+
+def test_batch_of_256_systems_repeats_exactly_in_fp64():
+    """The 256-system batch (5.8M unknowns, the batching configuration's systems) factored four
+    times on one handle in FP64: the same rank on every supernode and no restart each time.
+    With the cooperative pass's small-block mode this failed about one factorization in four
+    (wrong samples at this scale; 64 systems repeated exactly), so it needs the full batch."""
+    import scipy.sparse as sp
+    sides = np.random.Generator(np.random.Philox(0)).integers(12, 41, 256)
+    ps = [W.diffusion_lognormal(int(sd), 1.0, seed=i) for i, sd in enumerate(sides)]
+    A = sp.block_diag([p.scipy() for p in ps]).tocsr()
+    A.sort_indices()
+    coords, off = [], 0
+    for p in ps:
+        c = p.coords.copy()
+        c[:, 0] += off
+        off = int(c[:, 0].max()) + 4
+        coords.append(c)
+    h = R.rsc_analyze(A.shape[0], A.indptr, A.indices, A.data, np.vstack(coords), R.rsc_options_default())
+    M = R.rsc_get_stats(h)["n_supernodes"]
+    ref = None
+    for _ in range(4):
+        R.rsc_factor(h, 0.01)
+        assert R.rsc_get_stats(h)["restarts"] == 0
+        ranks = [R.rsc_get_supernode_info(h, j)["rank"] for j in range(M)]
+        if ref is None:
+            ref = ranks
+        assert ranks == ref
