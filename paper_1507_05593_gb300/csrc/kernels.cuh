@@ -105,7 +105,7 @@ __device__ __forceinline__ float rsqrt_f32(float x) {
 // a few ulp).  On this part a dependent FP64 operation takes about 64 cycles, the library's
 // FP64 square root about 690 and division about 440, so the pivot's square root and
 // reciprocal come from these six operations.  Outside the float range the library is used.
-// STEPS = 1 leaves about 44 correct bits: enough where the factor is stored in FP32.
+// (The FP64 form uses two steps; the FP32-storage forms factor their tiles in FP32.)
 template <int STEPS = 2>
 __device__ __forceinline__ double rsqrt_newton(double x) {
     if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
